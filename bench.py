@@ -1,0 +1,338 @@
+"""Benchmark: contact pairs per second of the local-crop contact detector.
+
+Workload (default): batched uneven scenes -- 8192 environments, each with
+Poisson(8) objects clipped to [1, 25] drawn from a 64-shape procedural library
+(unions of 2-5 boxes / ellipsoids, 300-2000 triangles, 2048 surface samples per
+shape), uniform rotations, positions uniform in [-1, 1]^3.  One step is the
+whole path on the device: AABB broadphase -> crop gather -> encoder -> head ->
+epilogue, issued as one ``locc_step`` call (no host synchronisation inside).
+Inputs are synthetic and resident in HBM before timing; L2 is flushed (a
+256 MiB write) between timed steps, and each step is timed with CUDA events on
+the launching stream.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision bf16|fp32|fp8]
+    python bench.py --impl reference ...   # the CPU oracle on the same workload
+
+Under torchrun every rank runs its own scene (weak scaling, no collective on
+the data path); the timing is the max over ranks.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+N_ENV = 8192
+N_SHAPES = 64
+LIB_SEED = 4
+RADIUS = 0.25
+MAX_PAIRS = 400_000
+FLOP_ENC = 2 * 128 * (3 * 64 + 64 * 128 + 128 * 256)       # per pair
+FLOP_HEAD = 2 * (512 * 256 + 256 * 256 + 256 * 8)          # per pair
+WORKLOAD = "uneven_scenes_8192env_poisson8_64shapes"
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0,
+                "bf16_tflops_sustained": 1400.0, "sm_max_mhz": 2032.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def make_inputs(rank: int, n_sets: int):
+    lib = synth.make_library(N_SHAPES, LIB_SEED)
+    scenes = [synth.uneven_scene(N_ENV, N_SHAPES, seed=LIB_SEED + 1000 * rank + i)
+              for i in range(n_sets)]
+    return lib, scenes
+
+
+def run_reference(args, rank: int, world: int) -> None:
+    """The oracle (plain CPU code) on the same workload, rank 0 only."""
+    if rank != 0:
+        return
+    import oracle
+    lib, scenes = make_inputs(0, 1)
+    poses, osh, env = scenes[0]
+    pairs = oracle.broadphase(lib.aabb, poses, osh, env)
+    params = oracle.flatten_params(synth.xavier_weights(1))
+    cores = os.cpu_count() or 1
+    sample = int(args.ref_sample)
+    rng = np.random.default_rng(0)
+    times = []
+    for i in range(args.warmup + args.steps):
+        sel = np.sort(rng.choice(len(pairs), min(sample, len(pairs)), replace=False))
+        t0 = time.perf_counter()
+        oracle.crop_forward(lib.points, lib.aabb, poses, osh, pairs[sel], RADIUS, params,
+                            n_threads=cores)
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append(dt)
+    value = sample * len(times) / sum(times)
+    line = {
+        "impl": "reference", "metric": "contact pairs/sec", "value": value, "unit": "pairs/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * float(np.mean(times)), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n_env": N_ENV, "n_shapes": N_SHAPES,
+                   "pairs_per_step": int(len(pairs)), "crop_radius": RADIUS},
+        "cpu_baseline": {"value": value, "unit": "pairs/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{sample} random broadphase pairs of one scene per step "
+                                   "(crop selection + float64 network forward)"},
+        "e2e": {"value": value, "unit": "pairs/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(lib, scene, seconds: float = 12.0):
+    """Oracle (b) on a bounded sample of the workload (host cores)."""
+    import oracle
+    poses, osh, env = scene
+    pairs = oracle.broadphase(lib.aabb, poses, osh, env)
+    params = oracle.flatten_params(synth.xavier_weights(1))
+    cores = os.cpu_count() or 1
+    rng = np.random.default_rng(1)
+    n, dt = 512, 0.0
+    while True:
+        sel = np.sort(rng.choice(len(pairs), min(n, len(pairs)), replace=False))
+        t0 = time.perf_counter()
+        oracle.crop_forward(lib.points, lib.aabb, poses, osh, pairs[sel], RADIUS, params,
+                            n_threads=cores)
+        dt = time.perf_counter() - t0
+        if dt > seconds / 4 or n >= len(pairs):
+            break
+        n = min(len(pairs), int(n * max(2.0, seconds / 4 / max(dt, 1e-3))))
+    return {"value": len(sel) / dt, "unit": "pairs/s", "cores": cores, "kind": "oracle",
+            "sample": f"{len(sel)} random broadphase pairs of one scene (crop selection + "
+                      f"float64 network forward), {dt:.1f} s"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "fp8"])
+    ap.add_argument("--ref-sample", type=int, default=4096)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--sets", type=int, default=3, help="distinct scenes cycled over steps")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+    import torch.distributed as dist
+    from paper_2304_09439_b300 import Detector
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    lib, scenes = make_inputs(rank, args.sets)
+    layers = synth.xavier_weights(1)
+    det = Detector(lib.points, lib.aabb, layers, RADIUS, args.precision)
+    det.reserve(MAX_PAIRS, N_ENV)
+    dsc = []
+    for poses, osh, env in scenes:
+        dsc.append((torch.from_numpy(poses).to(dev), torch.from_numpy(osh).to(dev),
+                    torch.from_numpy(env).to(dev)))
+    pairs_buf = torch.empty((MAX_PAIRS, 2), dtype=torch.int32, device=dev)
+    n_buf = torch.zeros(1, dtype=torch.int32, device=dev)
+    out_buf = torch.empty((MAX_PAIRS, 8), dtype=torch.float32, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    # pairs per scene (counted once, outside timing)
+    n_pairs = []
+    for p, s, e in dsc:
+        det.step(p, s, e, MAX_PAIRS, pairs_buf, n_buf, out_buf)
+        n_pairs.append(int(n_buf.item()))
+    det.status()
+    if max(n_pairs) > MAX_PAIRS:
+        raise RuntimeError("pair buffer too small")
+
+    det.profile(True)
+    for i in range(args.warmup):
+        p, s, e = dsc[i % len(dsc)]
+        flush.zero_()
+        det.step(p, s, e, MAX_PAIRS, pairs_buf, n_buf, out_buf)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    stage = np.zeros(4)
+    total_pairs = 0
+    with ClockSampler(local) as clk:
+        t_wall = time.perf_counter()
+        for i in range(args.steps):
+            p, s, e = dsc[i % len(dsc)]
+            flush.zero_()
+            ev0[i].record(stream)
+            det.step(p, s, e, MAX_PAIRS, pairs_buf, n_buf, out_buf)
+            ev1[i].record(stream)
+            ev1[i].synchronize()
+            stage += det.stage_times()
+            total_pairs += n_pairs[i % len(dsc)]
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter() - t_wall
+    det.status()
+    ms = sum(a.elapsed_time(b) for a, b in zip(ev0, ev1))
+    det.profile(False)
+
+    # end to end through the host-buffer C call: H2D inputs, step, D2H outputs
+    host_scenes = scenes
+    det.step_host(*host_scenes[0], MAX_PAIRS)
+    e2e_t, e2e_pairs, h2d, d2h = 0.0, 0, 0, 0
+    for i in range(args.steps):
+        poses, osh, env = host_scenes[i % len(host_scenes)]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        pr, out, n = det.step_host(poses, osh, env, MAX_PAIRS)
+        e2e_t += time.perf_counter() - t0
+        e2e_pairs += n
+        h2d += poses.nbytes + osh.nbytes + env.nbytes
+        d2h += 4 + pr.nbytes + out.nbytes
+
+    stats = torch.tensor([ms, float(total_pairs), e2e_t, float(e2e_pairs)], dtype=torch.float64,
+                         device=dev)
+    if world > 1:
+        mx = stats.clone()
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        sm = stats.clone()
+        dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+        ms_max, pairs_all, e2e_max, e2e_pairs_all = mx[0].item(), sm[1].item(), mx[2].item(), sm[3].item()
+    else:
+        ms_max, pairs_all, e2e_max, e2e_pairs_all = ms, float(total_pairs), e2e_t, float(e2e_pairs)
+
+    if rank == 0:
+        peaks, src = _peaks()
+        per_step_pairs = total_pairs / args.steps
+        enc_ms = stage[2] / args.steps
+        if args.precision == "fp32":
+            # CUDA-core float32: 148 SMs x 128 FMA lanes x 2 FLOP x max SM clock
+            peak = 148 * 128 * 2 * peaks.get("sm_max_mhz", 2032.0) * 1e6 / 1e12
+            bound, peak_src = "alu", "derived: 148 SM x 128 FP32 lanes x 2 x sm_max_mhz"
+        else:
+            peak = peaks["bf16_tflops_sustained"] * (2.0 if args.precision == "fp8" else 1.0)
+            bound, peak_src = "tensor", f"{src} bf16_tflops_sustained" + \
+                (" x 2 (fp8/bf16 nominal ratio)" if args.precision == "fp8" else "")
+        achieved = FLOP_ENC * per_step_pairs / (enc_ms * 1e-3) / 1e12
+        cpu = None
+        if not args.no_cpu_baseline and world == 1:
+            cpu = cpu_baseline(lib, scenes[0])
+        line = {
+            "metric": "contact pairs/sec", "value": pairs_all / (ms_max * 1e-3),
+            "unit": "pairs/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": args.precision if args.precision != "fp8" else "e4m3",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n_env": N_ENV, "n_shapes": N_SHAPES,
+                       "pairs_per_step": per_step_pairs, "crop_radius": RADIUS,
+                       "points_per_shape": 2048, "crop_points": 64, "precision": args.precision,
+                       "l2": "flushed between steps (256 MiB write)",
+                       "parallelism": f"replicas{world}"},
+            "stage_ms": {"broadphase": stage[0] / args.steps, "crop": stage[1] / args.steps,
+                         "encoder": enc_ms, "head": stage[3] / args.steps},
+            "roofline": {"kernel": "encoder", "bound": bound, "achieved": achieved,
+                         "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                         "traffic": None, "peak_source": peak_src,
+                         "algorithmic": f"{FLOP_ENC} FLOP per pair x pairs per launch"},
+            "e2e": {"value": e2e_pairs_all / e2e_max, "unit": "pairs/s",
+                    "h2d_bytes_per_step": h2d // args.steps, "d2h_bytes_per_step": d2h // args.steps},
+            "gpu_launches": 6 * args.steps,
+            "clocks": clk.summary(),
+            "cpu_baseline": cpu,
+            "wall_s_timed": t_wall,
+        }
+        print(json.dumps(line), flush=True)
+    det.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

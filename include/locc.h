@@ -1,0 +1,208 @@
+/*
+ * locc.h -- C ABI of the B300 (sm_103a) local-crop contact detector.
+ *
+ * Method: "Local object crop collision network for efficient simulation of
+ * non-convex objects in GPU-based simulators" (Son & Kim, RSS 2023).  Given two
+ * posed objects, the detector looks only at the local crops of the two shapes
+ * where they may touch (Sec. III, collision predictor: cells of each object's
+ * pose-transformed grid that lie in the intersection region of the two boxes;
+ * appendix: "intersection region of two AABB"), encodes each crop with a
+ * point-wise MLP and pooling (Sec. III, shape encoder; appendix: point-wise
+ * MLP, ReLU everywhere) and predicts the contact with an MLP head.
+ *
+ * This library computes, for every candidate pair:
+ *   1. pose composition:   R_rel = R_A^T R_B, t_rel = R_A^T (t_B - t_A);
+ *   2. crop centre:        centre of (A's body box) n (B's box seen in A's
+ *                          frame), in A's body frame;
+ *   3. crop gather:        per object, the <= 64 surface points nearest to the
+ *                          centre inside a ball of radius r (ties to the lower
+ *                          point index), in the canonical crop frame (A's axes,
+ *                          origin at the centre), zero padded;
+ *   4. encoder:            3 -> 64 -> 128 -> 256 (ReLU) per point, max-pool over
+ *                          the valid points of each object;
+ *   5. head:               [f_A, f_B] 512 -> 256 -> 256 (ReLU) -> 8;
+ *   6. epilogue:           out = {logit, contact point (world), unit normal
+ *                          (world, from A towards B), penetration depth}.
+ * plus an AABB broadphase that turns environments of objects into pairs (the
+ * broad phase that rules out far-apart pairs, Sec. II footnote 1).
+ *
+ * Conventions
+ *   - Every array argument of locc_detect / locc_crop / locc_network /
+ *     locc_broadphase is a DEVICE pointer owned by the caller (for example the
+ *     data pointer of a CUDA tensor).  locc_detect_host takes HOST pointers.
+ *   - A pose is 7 float32: unit quaternion (w, x, y, z) then translation;
+ *     p_world = R(q) p_body + t.  Quaternions are used as given (not
+ *     renormalised).
+ *   - Calls are asynchronous and ordered on `stream` (a cudaStream_t; NULL is
+ *     the legacy default stream).  Nothing blocks except locc_status,
+ *     locc_detect_host and locc_create / locc_destroy.
+ *   - A pair whose object index or shape id is out of range gets an all-NaN
+ *     output row and raises a device error flag; locc_status reports it.  No
+ *     kernel traps.
+ *   - Return codes: 0 on success, otherwise one of LOCC_ERR_*; the message of
+ *     the last failing call on this host thread is locc_last_error().
+ *   - A handle is not thread-safe: one host thread (or external locking) per
+ *     handle.  Its scratch buffers are reused by every call, so calls on
+ *     different streams of one handle must not overlap in time.
+ */
+#ifndef LOCC_H_
+#define LOCC_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LOCC_OK 0
+#define LOCC_ERR_INVALID_ARG (-1)  /* bad argument (NULL, size, range) */
+#define LOCC_ERR_OOM (-2)          /* device or host allocation failed */
+#define LOCC_ERR_CUDA (-3)         /* a CUDA runtime call failed */
+#define LOCC_ERR_TIMEOUT (-4)      /* a bounded device wait ran out */
+#define LOCC_ERR_BAD_WEIGHTS (-5)  /* weights blob malformed */
+#define LOCC_ERR_BAD_INDEX (-6)    /* a kernel met an out-of-range index */
+
+#define LOCC_CROP_POINTS 64        /* points kept per object */
+#define LOCC_OUT_DIM 8             /* logit, point xyz, normal xyz, depth */
+#define LOCC_N_PARAMS 240776       /* parameters of the crop network */
+
+typedef struct locc_handle locc_handle;
+
+/* Shape library: surface samples and box of every shape, in body frames.
+ *   points: host float32 [n_shapes][n_points][3]
+ *   aabb:   host float32 [n_shapes][6] = (lo.x, lo.y, lo.z, hi.x, hi.y, hi.z)
+ * 1 <= n_points <= 65536.  locc_create copies both; the caller keeps
+ * ownership of its arrays. */
+typedef struct {
+  int32_t n_shapes;
+  int32_t n_points;
+  const float *points;
+  const float *aabb;
+} locc_shape_library;
+
+/* Arithmetic of the encoder and head matrix products.  Pose composition and
+ * crop selection are float32 in every mode.
+ *   LOCC_FP32: float32 CUDA-core products (the plain path);
+ *   LOCC_BF16: bf16 operands on the tensor cores, float32 accumulation;
+ *   LOCC_FP8:  e4m3 operands with per-channel weight scales and per-row
+ *              activation scales on the tensor cores, float32 accumulation. */
+typedef enum { LOCC_FP32 = 0, LOCC_BF16 = 1, LOCC_FP8 = 2 } locc_precision;
+
+/* Create a detector on the current CUDA device.
+ *   lib:          shape library (host memory, copied).
+ *   weights_blob: host bytes of a "LOCCW001" parameter blob: 8-byte magic,
+ *                 uint32 version (1), uint32 n_layers (6), 6 x (uint32 in,
+ *                 uint32 out) = (3,64) (64,128) (128,256) (512,256) (256,256)
+ *                 (256,8), then for each layer float32 W[out][in] followed by
+ *                 float32 b[out], little endian.  Copied.
+ *   crop_radius:  radius r of the crop ball, > 0 (body-frame units).
+ *   prec:         arithmetic of the network products (see above).
+ *   out:          receives the handle; *out is NULL on failure.
+ * Errors: INVALID_ARG, BAD_WEIGHTS, OOM, CUDA. */
+int locc_create(const locc_shape_library *lib, const void *weights_blob,
+                size_t blob_bytes, float crop_radius, locc_precision prec,
+                locc_handle **out);
+
+/* Switch the arithmetic used by later calls (weights are kept for all modes). */
+int locc_set_precision(locc_handle *h, locc_precision prec);
+
+/* Contact detection for n_pairs pairs (all device pointers, steps 1-6).
+ *   poses:     float32 [n_obj][7]
+ *   obj_shape: int32 [n_obj], shape id of each object
+ *   pairs:     int32 [n_pairs][2], object indices (A, B)
+ *   out:       float32 [n_pairs][8] = {logit, px, py, pz, nx, ny, nz, depth};
+ *              collision <=> logit > 0.
+ * n_pairs == 0 is a no-op.  Scratch grows on demand (stream-ordered
+ * allocation); call locc_reserve first to keep this call allocation-free. */
+int locc_detect(locc_handle *h, const float *poses, const int32_t *obj_shape,
+                int32_t n_obj, const int32_t *pairs, int32_t n_pairs,
+                float *out, void *stream);
+
+/* Same as locc_detect with HOST arrays: copies inputs to the device, runs,
+ * copies out back, and waits for the stream.  Uses pinned staging owned by
+ * the handle. */
+int locc_detect_host(locc_handle *h, const float *poses,
+                     const int32_t *obj_shape, int32_t n_obj,
+                     const int32_t *pairs, int32_t n_pairs, float *out,
+                     void *stream);
+
+/* Steps 1-3 only (device pointers).  Outputs (idx_out / centre_out may be NULL):
+ *   xyz_out:    float32 [n_pairs][2][64][4]: canonical x, y, z and 1.0 for a
+ *               selected point, all zeros for padding; object A then B, nearest
+ *               point first;
+ *   idx_out:    int32 [n_pairs][2][64] library point index, -1 for padding;
+ *   cnt_out:    int32 [n_pairs][2] number of selected points;
+ *   centre_out: float32 [n_pairs][4] crop centre in A's body frame (w = 0). */
+int locc_crop(locc_handle *h, const float *poses, const int32_t *obj_shape,
+              int32_t n_obj, const int32_t *pairs, int32_t n_pairs,
+              float *xyz_out, int32_t *idx_out, int32_t *cnt_out,
+              float *centre_out, void *stream);
+
+/* Steps 4-5 only, on crops in locc_crop's layout (device pointers):
+ *   xyz: float32 [n_pairs][2][64][4] (w = 1 marks a valid point);
+ *   y_out: float32 [n_pairs][8] raw head outputs in the crop frame;
+ *   feat_out (may be NULL): float32 [n_pairs][512] pooled [f_A, f_B]. */
+int locc_network(locc_handle *h, const float *xyz, int32_t n_pairs,
+                 float *y_out, float *feat_out, void *stream);
+
+/* AABB broadphase (device pointers): objects of environment e are
+ * env_offsets[e] .. env_offsets[e+1]-1.  Writes every pair (i, j), i < j, of
+ * one environment whose world boxes (the axis-aligned box of each object's
+ * posed body box) overlap into pairs_out (int32 [max_pairs][2]), in order of
+ * environment then i then j, and the total count into *n_pairs_out (device
+ * int32).  If the total exceeds max_pairs, only the first max_pairs are
+ * written and *n_pairs_out holds the full count. */
+int locc_broadphase(locc_handle *h, const float *poses, const int32_t *obj_shape,
+                    const int32_t *env_offsets, int32_t n_env, int32_t *pairs_out,
+                    int32_t *n_pairs_out, int32_t max_pairs, void *stream);
+
+/* One simulator step on the device (all device pointers): locc_broadphase of
+ * the environments, then contact detection (as locc_detect) of every candidate
+ * pair, with out: float32 [max_pairs][8]; rows at and beyond *n_pairs_out are
+ * left untouched, and only the first max_pairs pairs are detected.  The pair
+ * count stays on the device and launch shapes depend only on max_pairs and
+ * n_env, so after locc_reserve(h, max_pairs, n_env) the call allocates nothing,
+ * never synchronises the host and can be captured in a CUDA graph. */
+int locc_step(locc_handle *h, const float *poses, const int32_t *obj_shape,
+              int32_t n_obj, const int32_t *env_offsets, int32_t n_env,
+              int32_t *pairs_out, int32_t *n_pairs_out, int32_t max_pairs,
+              float *out, void *stream);
+
+/* locc_step with HOST arrays: copies poses [n_obj][7], obj_shape [n_obj] and
+ * env_offsets [n_env+1] to the device, runs the step, waits, and copies back
+ * the pair count (*n_pairs_out, host), the first min(count, max_pairs) pairs
+ * (pairs_out, host int32 [max_pairs][2]) and their outputs (out, host float32
+ * [max_pairs][8]). */
+int locc_step_host(locc_handle *h, const float *poses, const int32_t *obj_shape,
+                   int32_t n_obj, const int32_t *env_offsets, int32_t n_env,
+                   int32_t *pairs_out, int32_t *n_pairs_out, int32_t max_pairs,
+                   float *out, void *stream);
+
+/* Pre-allocate scratch for up to max_pairs pairs and max_envs environments
+ * per call (blocking).  Later calls within these sizes allocate nothing. */
+int locc_reserve(locc_handle *h, int32_t max_pairs, int32_t max_envs);
+
+/* Stage timing: with enable != 0, later locc_step calls record CUDA events
+ * on their stream around each stage.  locc_stage_times waits for the last
+ * step's final event and writes up to n durations in milliseconds:
+ * [0] broadphase, [1] crop gather, [2] encoder, [3] head + epilogue.
+ * Returns the number written (>= 0) or an error code. */
+int locc_profile(locc_handle *h, int enable);
+int locc_stage_times(locc_handle *h, float *ms_out, int n);
+
+/* Wait for `stream`, then report and clear the device error flag:
+ * 0 or LOCC_ERR_BAD_INDEX. */
+int locc_status(locc_handle *h, void *stream);
+
+/* Release all device and host memory of the handle (blocking). */
+void locc_destroy(locc_handle *h);
+
+/* Message of the last failing call on this host thread ("" if none). */
+const char *locc_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LOCC_H_ */

@@ -74,6 +74,8 @@ def _load():
         lib.ora_contact_batch.restype = I
         lib.ora_inside.argtypes = [P, I, P, P, I, P, P, I, P]
         lib.ora_inside.restype = I
+        lib.orb_broadphase.argtypes = [P, I, P, P, P, I, P, ctypes.c_longlong]
+        lib.orb_broadphase.restype = ctypes.c_longlong
         assert lib.orb_n_params() == N_PARAMS
         _lib = lib
         return lib
@@ -179,6 +181,25 @@ def loss_grad(params: np.ndarray, xyz: np.ndarray, cnt: np.ndarray,
     L = lib.orb_loss_grad(_ptr(params), _ptr(xyz), _ptr(cnt), _ptr(tgt),
                           cnt.shape[0], kmax, _ptr(hp), _ptr(g))
     return float(L), g
+
+
+def broadphase(aabb, poses, obj_shape, env_offsets) -> np.ndarray:
+    """Oracle broad phase: int32 [n_pairs, 2] overlapping pairs per environment,
+    ordered by environment, then i, then j."""
+    lib = _load()
+    aabb = _c(aabb, np.float32)
+    poses = _c(poses, np.float32)
+    obj_shape = _c(obj_shape, np.int32)
+    env_offsets = _c(env_offsets, np.int32)
+    n_env = env_offsets.shape[0] - 1
+    n = lib.orb_broadphase(_ptr(aabb), aabb.shape[0], _ptr(poses), _ptr(obj_shape),
+                           _ptr(env_offsets), n_env, None, 0)
+    if n < 0:
+        raise ValueError("bad shape id")
+    out = np.empty((max(n, 1), 2), np.int32)
+    lib.orb_broadphase(_ptr(aabb), aabb.shape[0], _ptr(poses), _ptr(obj_shape),
+                       _ptr(env_offsets), n_env, _ptr(out), n)
+    return out[:n]
 
 
 def _pack_meshes(meshes):

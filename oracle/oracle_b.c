@@ -571,3 +571,56 @@ double orb_loss_grad(const double *params, const float *xyz, const int32_t *cnt,
   }
   return total / n_pairs;
 }
+
+/* ------------------------------------------------------------- broadphase */
+
+/* Broad phase (Sec. II, footnote 1: far-apart objects are ruled out before
+ * the narrow phase): the world axis-aligned box of each object's posed body
+ * box (centre R c + t, half extents |R| h, float32 in the fixed order of
+ * orb_dot3), and every pair (i, j), i < j, of one environment whose boxes
+ * overlap on all axes (|c_i - c_j| <= h_i + h_j).  Pairs are listed by
+ * environment, then i, then j.  Writes at most max_pairs pairs; returns the
+ * full count (or -1 on a bad shape id). */
+static void orb_world_box(const float *pose, const float *aabb, float c[3], float h[3]) {
+  float R[3][3];
+  orb_rotation(pose, R);
+  float cl[3], hl[3];
+  for (int j = 0; j < 3; ++j) {
+    cl[j] = (aabb[j] + aabb[3 + j]) * 0.5f;
+    hl[j] = (aabb[3 + j] - aabb[j]) * 0.5f;
+  }
+  for (int i = 0; i < 3; ++i) {
+    c[i] = orb_dot3(R[i][0], R[i][1], R[i][2], cl[0], cl[1], cl[2]) + pose[4 + i];
+    h[i] = orb_dot3(fabsf(R[i][0]), fabsf(R[i][1]), fabsf(R[i][2]), hl[0], hl[1], hl[2]);
+  }
+}
+
+long long orb_broadphase(const float *aabb, int n_shapes, const float *poses,
+                         const int32_t *obj_shape, const int32_t *env_offsets, int n_env,
+                         int32_t *pairs_out, long long max_pairs) {
+  long long n = 0;
+  for (int e = 0; e < n_env; ++e) {
+    int o0 = env_offsets[e], o1 = env_offsets[e + 1];
+    for (int i = o0; i < o1; ++i) {
+      if (obj_shape[i] < 0 || obj_shape[i] >= n_shapes) return -1;
+      float ci[3], hi[3];
+      orb_world_box(poses + 7 * (size_t)i, aabb + 6 * (size_t)obj_shape[i], ci, hi);
+      for (int j = i + 1; j < o1; ++j) {
+        if (obj_shape[j] < 0 || obj_shape[j] >= n_shapes) return -1;
+        float cj[3], hj[3];
+        orb_world_box(poses + 7 * (size_t)j, aabb + 6 * (size_t)obj_shape[j], cj, hj);
+        int ov = 1;
+        for (int a = 0; a < 3; ++a)
+          if (!(fabsf(ci[a] - cj[a]) <= hi[a] + hj[a])) ov = 0;
+        if (ov) {
+          if (n < max_pairs) {
+            pairs_out[2 * n] = i;
+            pairs_out[2 * n + 1] = j;
+          }
+          ++n;
+        }
+      }
+    }
+  }
+  return n;
+}

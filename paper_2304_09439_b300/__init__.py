@@ -1,0 +1,213 @@
+"""B300-native local-crop contact detection (LOCC, Son & Kim, RSS 2023).
+
+The compute path lives in the sm_103a library ``liblocc.so`` behind the C ABI
+of ``include/locc.h``; this package is its thin Python binding.  PyTorch is
+used only for device memory and streams.
+
+    det = Detector(points, aabb, weights, radius=0.25, precision="bf16")
+    out = det.detect(poses, obj_shape, pairs)   # [P, 8] on the device
+"""
+
+from __future__ import annotations
+
+import ctypes
+from typing import Optional
+
+from . import abi, weights
+from .abi import LoccError, LOCC_FP32, LOCC_BF16, LOCC_FP8, PRECISIONS
+
+KMAX = 64
+OUT_DIM = 8
+
+__all__ = ["Detector", "LoccError", "LOCC_FP32", "LOCC_BF16", "LOCC_FP8", "weights",
+           "abi", "KMAX", "OUT_DIM"]
+
+
+def _prec(p) -> int:
+    if isinstance(p, str):
+        return PRECISIONS[p.lower()]
+    return int(p)
+
+
+def _need(t, dtype, name, device=None):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if device is not None and t.device.index != device:
+        raise ValueError(f"{name} is on cuda:{t.device.index}, detector on cuda:{device}")
+
+
+class Detector:
+    """Owns one ``locc_handle`` on the current CUDA device."""
+
+    def __init__(self, points, aabb, layers, radius: float = 0.25, precision="fp32"):
+        import torch
+        self._lib = abi.load()
+        self.device = torch.cuda.current_device()
+        blob = layers if isinstance(layers, (bytes, bytearray)) else weights.pack(layers)
+        self._h = abi.create(points, aabb, bytes(blob), radius, _prec(precision))
+        self.radius = float(radius)
+        self.precision = _prec(precision)
+
+    # -- lifetime ---------------------------------------------------------
+    def close(self) -> None:
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.locc_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -- configuration ----------------------------------------------------
+    def set_precision(self, precision) -> None:
+        abi.check(self._lib.locc_set_precision(self._h, _prec(precision)))
+        self.precision = _prec(precision)
+
+    def reserve(self, max_pairs: int, max_envs: int = 0) -> None:
+        abi.check(self._lib.locc_reserve(self._h, int(max_pairs), int(max_envs)))
+
+    def profile(self, enable: bool = True) -> None:
+        abi.check(self._lib.locc_profile(self._h, int(bool(enable))))
+
+    def stage_times(self):
+        """Durations (ms) of the last step's stages: broadphase, crop, encoder,
+        head."""
+        import numpy as np
+        ms = np.zeros(4, np.float32)
+        n = self._lib.locc_stage_times(self._h, abi.ptr(ms), 4)
+        if n < 0:
+            abi.check(n)
+        return ms[:n]
+
+    def status(self, stream=None) -> None:
+        """Wait for the stream; raise if a kernel flagged a bad index."""
+        abi.check(self._lib.locc_status(self._h, abi.stream_ptr(stream)))
+
+    # -- the path -----------------------------------------------------------
+    def detect(self, poses, obj_shape, pairs, out=None, stream=None):
+        import torch
+        _need(poses, torch.float32, "poses", self.device)
+        _need(obj_shape, torch.int32, "obj_shape", self.device)
+        _need(pairs, torch.int32, "pairs", self.device)
+        P = pairs.shape[0]
+        if out is None:
+            out = torch.empty((P, OUT_DIM), dtype=torch.float32, device=pairs.device)
+        _need(out, torch.float32, "out", self.device)
+        abi.check(self._lib.locc_detect(self._h, abi.ptr(poses), abi.ptr(obj_shape),
+                                        poses.shape[0], abi.ptr(pairs), P, abi.ptr(out),
+                                        abi.stream_ptr(stream)))
+        return out
+
+    def detect_host(self, poses, obj_shape, pairs, out=None, stream=None):
+        """Host (numpy) arrays in and out; copies and waits inside the call."""
+        import numpy as np
+        poses = np.ascontiguousarray(poses, np.float32)
+        obj_shape = np.ascontiguousarray(obj_shape, np.int32)
+        pairs = np.ascontiguousarray(pairs, np.int32)
+        P = pairs.shape[0]
+        if out is None:
+            out = np.empty((P, OUT_DIM), np.float32)
+        abi.check(self._lib.locc_detect_host(self._h, abi.ptr(poses), abi.ptr(obj_shape),
+                                             poses.shape[0], abi.ptr(pairs), P, abi.ptr(out),
+                                             abi.stream_ptr(stream)))
+        return out
+
+    def crop(self, poses, obj_shape, pairs, with_idx=True, stream=None):
+        import torch
+        _need(poses, torch.float32, "poses", self.device)
+        _need(obj_shape, torch.int32, "obj_shape", self.device)
+        _need(pairs, torch.int32, "pairs", self.device)
+        P = pairs.shape[0]
+        dev = pairs.device
+        xyz = torch.empty((P, 2, KMAX, 4), dtype=torch.float32, device=dev)
+        idx = torch.empty((P, 2, KMAX), dtype=torch.int32, device=dev) if with_idx else None
+        cnt = torch.empty((P, 2), dtype=torch.int32, device=dev)
+        centre = torch.empty((P, 4), dtype=torch.float32, device=dev)
+        abi.check(self._lib.locc_crop(self._h, abi.ptr(poses), abi.ptr(obj_shape),
+                                      poses.shape[0], abi.ptr(pairs), P, abi.ptr(xyz),
+                                      abi.ptr(idx), abi.ptr(cnt), abi.ptr(centre),
+                                      abi.stream_ptr(stream)))
+        return dict(xyz=xyz, idx=idx, cnt=cnt, centre=centre)
+
+    def network(self, xyz, with_feat=False, stream=None):
+        import torch
+        _need(xyz, torch.float32, "xyz", self.device)
+        P = xyz.shape[0]
+        y = torch.empty((P, OUT_DIM), dtype=torch.float32, device=xyz.device)
+        f = torch.empty((P, 512), dtype=torch.float32, device=xyz.device) if with_feat else None
+        abi.check(self._lib.locc_network(self._h, abi.ptr(xyz), P, abi.ptr(y), abi.ptr(f),
+                                         abi.stream_ptr(stream)))
+        return (y, f) if with_feat else y
+
+    def broadphase(self, poses, obj_shape, env_offsets, max_pairs: int, pairs_out=None,
+                   n_pairs_out=None, stream=None):
+        import torch
+        _need(poses, torch.float32, "poses", self.device)
+        _need(obj_shape, torch.int32, "obj_shape", self.device)
+        _need(env_offsets, torch.int32, "env_offsets", self.device)
+        dev = poses.device
+        if pairs_out is None:
+            pairs_out = torch.empty((max(int(max_pairs), 1), 2), dtype=torch.int32, device=dev)
+        if n_pairs_out is None:
+            n_pairs_out = torch.zeros(1, dtype=torch.int32, device=dev)
+        abi.check(self._lib.locc_broadphase(self._h, abi.ptr(poses), abi.ptr(obj_shape),
+                                            abi.ptr(env_offsets), env_offsets.shape[0] - 1,
+                                            abi.ptr(pairs_out), abi.ptr(n_pairs_out),
+                                            int(max_pairs), abi.stream_ptr(stream)))
+        return pairs_out, n_pairs_out
+
+    def step(self, poses, obj_shape, env_offsets, max_pairs: int, pairs_out=None,
+             n_pairs_out=None, out=None, stream=None):
+        """Broadphase + detection on the device; returns (pairs, n_pairs, out)
+        with the count left on the device."""
+        import torch
+        _need(poses, torch.float32, "poses", self.device)
+        _need(obj_shape, torch.int32, "obj_shape", self.device)
+        _need(env_offsets, torch.int32, "env_offsets", self.device)
+        dev = poses.device
+        M = int(max_pairs)
+        if pairs_out is None:
+            pairs_out = torch.empty((max(M, 1), 2), dtype=torch.int32, device=dev)
+        if n_pairs_out is None:
+            n_pairs_out = torch.zeros(1, dtype=torch.int32, device=dev)
+        if out is None:
+            out = torch.empty((max(M, 1), OUT_DIM), dtype=torch.float32, device=dev)
+        abi.check(self._lib.locc_step(self._h, abi.ptr(poses), abi.ptr(obj_shape),
+                                      poses.shape[0], abi.ptr(env_offsets),
+                                      env_offsets.shape[0] - 1, abi.ptr(pairs_out),
+                                      abi.ptr(n_pairs_out), M, abi.ptr(out),
+                                      abi.stream_ptr(stream)))
+        return pairs_out, n_pairs_out, out
+
+    def step_host(self, poses, obj_shape, env_offsets, max_pairs: int, pairs_out=None,
+                  out=None, stream=None):
+        """Host arrays in and out; returns (pairs [n,2], out [n,8]) as numpy."""
+        import numpy as np
+        poses = np.ascontiguousarray(poses, np.float32)
+        obj_shape = np.ascontiguousarray(obj_shape, np.int32)
+        env_offsets = np.ascontiguousarray(env_offsets, np.int32)
+        M = int(max_pairs)
+        if pairs_out is None:
+            pairs_out = np.empty((max(M, 1), 2), np.int32)
+        if out is None:
+            out = np.empty((max(M, 1), OUT_DIM), np.float32)
+        n = np.zeros(1, np.int32)
+        abi.check(self._lib.locc_step_host(self._h, abi.ptr(poses), abi.ptr(obj_shape),
+                                           poses.shape[0], abi.ptr(env_offsets),
+                                           env_offsets.shape[0] - 1, abi.ptr(pairs_out),
+                                           abi.ptr(n), M, abi.ptr(out), abi.stream_ptr(stream)))
+        m = min(int(n[0]), M)
+        return pairs_out[:m], out[:m], int(n[0])

@@ -1,0 +1,117 @@
+"""ctypes binding of the C ABI in ``include/locc.h`` (argument marshalling only).
+
+Every step of the contact path runs in ``liblocc.so``; this module converts
+PyTorch tensors to device pointers and return codes to exceptions.  There is no
+other implementation behind it: if the library cannot be loaded, importing the
+package still works but every call raises ``LoccError``.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from typing import Optional
+
+from . import build as _build
+
+LOCC_FP32, LOCC_BF16, LOCC_FP8 = 0, 1, 2
+PRECISIONS = {"fp32": LOCC_FP32, "bf16": LOCC_BF16, "fp8": LOCC_FP8}
+ERRORS = {-1: "INVALID_ARG", -2: "OOM", -3: "CUDA", -4: "TIMEOUT",
+          -5: "BAD_WEIGHTS", -6: "BAD_INDEX"}
+
+# every symbol include/locc.h declares
+EXPORTS = ["locc_create", "locc_set_precision", "locc_detect", "locc_detect_host",
+           "locc_crop", "locc_network", "locc_broadphase", "locc_step", "locc_step_host",
+           "locc_reserve", "locc_profile", "locc_stage_times", "locc_status", "locc_destroy",
+           "locc_last_error"]
+
+
+class LoccError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"locc error {code} ({ERRORS.get(code, '?')}): {msg}")
+        self.code = code
+
+
+class _ShapeLibrary(ctypes.Structure):
+    _fields_ = [("n_shapes", ctypes.c_int32), ("n_points", ctypes.c_int32),
+                ("points", ctypes.c_void_p), ("aabb", ctypes.c_void_p)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load(build_if_needed: bool = True) -> ctypes.CDLL:
+    """Load liblocc.so (building it with nvcc first if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.SO_PATH
+        if build_if_needed and not _build.up_to_date():
+            _build.build()
+        if not os.path.exists(path):
+            raise LoccError(-3, f"{path} is missing; build it with "
+                                "`python -m paper_2304_09439_b300.build`")
+        lib = ctypes.CDLL(path)
+        P, I, F = ctypes.c_void_p, ctypes.c_int32, ctypes.c_float
+        lib.locc_create.argtypes = [ctypes.POINTER(_ShapeLibrary), P, ctypes.c_size_t, F,
+                                    ctypes.c_int, ctypes.POINTER(P)]
+        lib.locc_set_precision.argtypes = [P, ctypes.c_int]
+        lib.locc_detect.argtypes = [P, P, P, I, P, I, P, P]
+        lib.locc_detect_host.argtypes = [P, P, P, I, P, I, P, P]
+        lib.locc_crop.argtypes = [P, P, P, I, P, I, P, P, P, P, P]
+        lib.locc_network.argtypes = [P, P, I, P, P, P]
+        lib.locc_broadphase.argtypes = [P, P, P, P, I, P, P, I, P]
+        lib.locc_step.argtypes = [P, P, P, I, P, I, P, P, I, P, P]
+        lib.locc_step_host.argtypes = [P, P, P, I, P, I, P, P, I, P, P]
+        lib.locc_reserve.argtypes = [P, I, I]
+        lib.locc_profile.argtypes = [P, ctypes.c_int]
+        lib.locc_stage_times.argtypes = [P, P, ctypes.c_int]
+        lib.locc_status.argtypes = [P, P]
+        lib.locc_destroy.argtypes = [P]
+        lib.locc_destroy.restype = None
+        lib.locc_last_error.restype = ctypes.c_char_p
+        for name in EXPORTS:
+            if name not in ("locc_destroy", "locc_last_error"):
+                getattr(lib, name).restype = ctypes.c_int
+        _lib = lib
+        return lib
+
+
+def check(code: int) -> None:
+    if code != 0:
+        msg = load().locc_last_error().decode(errors="replace")
+        raise LoccError(code, msg)
+
+
+def ptr(t) -> Optional[int]:
+    """Device (or host) address of a tensor / numpy array, None for None."""
+    if t is None:
+        return None
+    if hasattr(t, "data_ptr"):
+        return t.data_ptr() or None
+    return t.ctypes.data or None
+
+
+def stream_ptr(stream) -> Optional[int]:
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    return getattr(stream, "cuda_stream", stream) or None
+
+
+def create(points, aabb, blob: bytes, radius: float, precision: int):
+    import numpy as np
+    lib = load()
+    points = np.ascontiguousarray(points, np.float32)
+    aabb = np.ascontiguousarray(aabb, np.float32)
+    if points.ndim != 3 or points.shape[2] != 3 or aabb.shape != (points.shape[0], 6):
+        raise ValueError("points must be [S, n_points, 3] and aabb [S, 6]")
+    sl = _ShapeLibrary(points.shape[0], points.shape[1], points.ctypes.data, aabb.ctypes.data)
+    h = ctypes.c_void_p()
+    buf = ctypes.create_string_buffer(blob, len(blob))
+    check(lib.locc_create(ctypes.byref(sl), ctypes.cast(buf, ctypes.c_void_p), len(blob),
+                          float(radius), int(precision), ctypes.byref(h)))
+    return h

@@ -1,0 +1,476 @@
+// Host side of the C ABI declared in include/locc.h: handle, shape library and
+// parameter upload, scratch management and the stream-ordered call sequence of
+// the contact path.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <numeric>
+#include <vector>
+
+#include "common.cuh"
+#include "handle.cuh"
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+int fail(int code, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+  return code;
+}
+
+#define CUDA_TRY(expr)                                                              \
+  do {                                                                              \
+    cudaError_t e_ = (expr);                                                        \
+    if (e_ != cudaSuccess)                                                          \
+      return fail(LOCC_ERR_CUDA, "%s failed: %s", #expr, cudaGetErrorString(e_)); \
+  } while (0)
+
+uint32_t spread10(uint32_t v) {
+  v &= 0x3ffu;
+  v = (v | (v << 16)) & 0x030000ffu;
+  v = (v | (v << 8)) & 0x0300f00fu;
+  v = (v | (v << 4)) & 0x030c30c3u;
+  v = (v | (v << 2)) & 0x09249249u;
+  return v;
+}
+
+template <typename T>
+cudaError_t upload(T** dptr, const std::vector<T>& host) {
+  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(dptr), host.size() * sizeof(T));
+  if (e != cudaSuccess) return e;
+  return cudaMemcpy(*dptr, host.data(), host.size() * sizeof(T), cudaMemcpyHostToDevice);
+}
+
+}  // namespace
+
+namespace locc {
+
+void set_error(const char* msg) { snprintf(g_err, sizeof(g_err), "%s", msg); }
+
+int ensure_capacity(locc_handle* h, int n_pairs, cudaStream_t stream) {
+  if (n_pairs <= h->cap_pairs) return LOCC_OK;
+  CUDA_TRY(cudaStreamSynchronize(stream));
+  free_scratch(h);
+  const size_t P = (size_t)std::max(n_pairs, 1024);
+  if (cudaMalloc(&h->d_xyz, P * ROWS * sizeof(float4)) != cudaSuccess ||
+      cudaMalloc(&h->d_cnt, P * 2 * sizeof(int32_t)) != cudaSuccess ||
+      cudaMalloc(&h->d_centre, P * sizeof(float4)) != cudaSuccess ||
+      cudaMalloc(&h->d_feat, P * 512 * sizeof(float)) != cudaSuccess) {
+    cudaGetLastError();
+    free_scratch(h);
+    return fail(LOCC_ERR_OOM, "cannot allocate scratch for %d pairs", n_pairs);
+  }
+  h->cap_pairs = (int)P;
+  return LOCC_OK;
+}
+
+void free_scratch(locc_handle* h) {
+  cudaFree(h->d_xyz);
+  cudaFree(h->d_cnt);
+  cudaFree(h->d_centre);
+  cudaFree(h->d_feat);
+  h->d_xyz = nullptr, h->d_cnt = nullptr, h->d_centre = nullptr, h->d_feat = nullptr;
+  h->cap_pairs = 0;
+}
+
+int ensure_env_capacity(locc_handle* h, int n_env, cudaStream_t stream) {
+  if (n_env <= h->cap_env) return LOCC_OK;
+  CUDA_TRY(cudaStreamSynchronize(stream));
+  cudaFree(h->d_env_counts);
+  h->d_env_counts = nullptr;
+  h->cap_env = 0;
+  if (cudaMalloc(&h->d_env_counts, (size_t)n_env * sizeof(int32_t)) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(LOCC_ERR_OOM, "cannot allocate broadphase scratch for %d environments", n_env);
+  }
+  h->cap_env = n_env;
+  return LOCC_OK;
+}
+
+int ensure_stage(locc_handle* h, size_t need, cudaStream_t s) {
+  if (need <= h->stage_bytes) return LOCC_OK;
+  CUDA_TRY(cudaStreamSynchronize(s));
+  cudaFreeHost(h->h_stage);
+  cudaFree(h->d_stage);
+  h->h_stage = nullptr, h->d_stage = nullptr, h->stage_bytes = 0;
+  if (cudaMallocHost(&h->h_stage, need) != cudaSuccess || cudaMalloc(&h->d_stage, need) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(LOCC_ERR_OOM, "cannot allocate %zu staging bytes", need);
+  }
+  h->stage_bytes = need;
+  return LOCC_OK;
+}
+
+DevLibrary dev_library(const locc_handle* h) {
+  DevLibrary L;
+  L.points = h->d_points;
+  L.blocks = h->d_blocks;
+  L.aabb = h->d_aabb;
+  L.n_shapes = h->n_shapes;
+  L.n_points = h->n_points;
+  L.n_pad = h->n_pad;
+  L.n_blocks = h->n_blocks;
+  return L;
+}
+
+// Network on the crops in h->d_xyz (or `xyz`): feat -> y / out.
+int run_network(locc_handle* h, const float4* xyz, int n_pairs, const int* n_dev,
+                const PairInputs* in, const float4* centre, float* out, float* y_raw,
+                float* feat_out, cudaStream_t stream, cudaEvent_t mid) {
+  float* feat = feat_out ? feat_out : h->d_feat;
+  switch (h->prec) {
+    case LOCC_FP32:
+      CUDA_TRY(launch_encoder_fp32(xyz, n_pairs, n_dev, h->fp32, feat, h->n_sm, stream));
+      if (mid) CUDA_TRY(cudaEventRecord(mid, stream));
+      CUDA_TRY(launch_head_fp32(feat, n_pairs, n_dev, h->fp32, in, centre, out, y_raw, h->n_sm,
+                                stream));
+      return LOCC_OK;
+    default:
+      return run_network_tc(h, xyz, n_pairs, n_dev, in, centre, out, y_raw, feat_out, stream, mid);
+  }
+}
+
+}  // namespace locc
+
+using namespace locc;
+
+extern "C" {
+
+const char* locc_last_error(void) { return g_err; }
+
+int locc_create(const locc_shape_library* lib, const void* blob, size_t blob_bytes,
+                float crop_radius, locc_precision prec, locc_handle** out) {
+  if (!out) return fail(LOCC_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!lib || !lib->points || !lib->aabb) return fail(LOCC_ERR_INVALID_ARG, "library is NULL");
+  if (lib->n_shapes < 1 || lib->n_points < 1 || lib->n_points > 65536)
+    return fail(LOCC_ERR_INVALID_ARG, "need n_shapes >= 1 and 1 <= n_points <= 65536");
+  if (!(crop_radius > 0.0f) || !std::isfinite(crop_radius))
+    return fail(LOCC_ERR_INVALID_ARG, "crop_radius must be finite and > 0");
+  if (prec != LOCC_FP32 && prec != LOCC_BF16 && prec != LOCC_FP8)
+    return fail(LOCC_ERR_INVALID_ARG, "unknown precision %d", (int)prec);
+  std::vector<float> params;
+  {
+    int st = parse_weights(blob, blob_bytes, &params);
+    if (st) return st;
+  }
+  locc_handle* h = new (std::nothrow) locc_handle();
+  if (!h) return fail(LOCC_ERR_OOM, "host allocation failed");
+  cudaGetDevice(&h->device);
+  if (cudaDeviceGetAttribute(&h->n_sm, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess ||
+      h->n_sm <= 0) {
+    cudaGetLastError();
+    delete h;
+    return fail(LOCC_ERR_CUDA, "no usable CUDA device");
+  }
+  h->n_shapes = lib->n_shapes;
+  h->n_points = lib->n_points;
+  h->n_pad = (lib->n_points + BLOCK_PTS - 1) / BLOCK_PTS * BLOCK_PTS;
+  h->n_blocks = h->n_pad / BLOCK_PTS;
+  h->radius = crop_radius;
+  h->prec = prec;
+
+  // shape library: Morton-ordered blocks of 32 samples with block boxes
+  const size_t S = (size_t)h->n_shapes, NP = (size_t)h->n_points, NPAD = (size_t)h->n_pad;
+  std::vector<float4> pts(S * NPAD), blocks(S * h->n_blocks * 2), aabb(S * 2);
+  const float nanv = std::nanf("");
+  std::vector<uint32_t> code(NP);
+  std::vector<int> order(NP);
+  for (size_t s = 0; s < S; ++s) {
+    const float* P = lib->points + s * NP * 3;
+    const float* B = lib->aabb + s * 6;
+    aabb[2 * s] = make_float4(B[0], B[1], B[2], 0.f);
+    aabb[2 * s + 1] = make_float4(B[3], B[4], B[5], 0.f);
+    for (size_t i = 0; i < NP; ++i) {
+      uint32_t c = 0;
+      for (int a = 0; a < 3; ++a) {
+        const float ext = B[3 + a] - B[a];
+        float u = ext > 0 ? (P[3 * i + a] - B[a]) / ext : 0.f;
+        u = std::min(std::max(u, 0.f), 1.f);
+        c |= spread10((uint32_t)(u * 1023.0f)) << a;
+      }
+      code[i] = c;
+    }
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return code[x] < code[y]; });
+    for (size_t k = 0; k < NPAD; ++k) {
+      float4 v;
+      if (k < NP) {
+        const int i = order[k];
+        uint32_t bits = (uint32_t)i;
+        float w;
+        std::memcpy(&w, &bits, 4);
+        v = make_float4(P[3 * i], P[3 * i + 1], P[3 * i + 2], w);
+      } else {
+        v = make_float4(nanv, nanv, nanv, 0.f);
+      }
+      pts[s * NPAD + k] = v;
+    }
+    for (int b = 0; b < h->n_blocks; ++b) {
+      float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+      for (int k = b * BLOCK_PTS; k < (b + 1) * BLOCK_PTS && k < (int)NP; ++k) {
+        const float4 v = pts[s * NPAD + k];
+        const float c3[3] = {v.x, v.y, v.z};
+        for (int a = 0; a < 3; ++a) lo[a] = std::min(lo[a], c3[a]), hi[a] = std::max(hi[a], c3[a]);
+      }
+      blocks[(s * h->n_blocks + b) * 2] = make_float4(lo[0], lo[1], lo[2], 0.f);
+      blocks[(s * h->n_blocks + b) * 2 + 1] = make_float4(hi[0], hi[1], hi[2], 0.f);
+    }
+  }
+  int st = LOCC_OK;
+  if (upload(&h->d_points, pts) != cudaSuccess || upload(&h->d_blocks, blocks) != cudaSuccess ||
+      upload(&h->d_aabb, aabb) != cudaSuccess) {
+    st = fail(LOCC_ERR_OOM, "cannot upload the shape library: %s",
+              cudaGetErrorString(cudaGetLastError()));
+  }
+  if (st == LOCC_OK) st = upload_params(h, params);
+  if (st == LOCC_OK && cudaMalloc(&h->d_err, sizeof(int)) != cudaSuccess)
+    st = fail(LOCC_ERR_OOM, "cannot allocate the error flag");
+  if (st == LOCC_OK && cudaMemset(h->d_err, 0, sizeof(int)) != cudaSuccess)
+    st = fail(LOCC_ERR_CUDA, "cudaMemset failed");
+  if (st != LOCC_OK) {
+    locc_destroy(h);
+    return st;
+  }
+  *out = h;
+  return LOCC_OK;
+}
+
+int locc_set_precision(locc_handle* h, locc_precision prec) {
+  if (!h) return fail(LOCC_ERR_INVALID_ARG, "handle is NULL");
+  if (prec != LOCC_FP32 && prec != LOCC_BF16 && prec != LOCC_FP8)
+    return fail(LOCC_ERR_INVALID_ARG, "unknown precision %d", (int)prec);
+  h->prec = prec;
+  return LOCC_OK;
+}
+
+int locc_reserve(locc_handle* h, int32_t max_pairs, int32_t max_envs) {
+  if (!h || max_pairs < 0 || max_envs < 0) return fail(LOCC_ERR_INVALID_ARG, "bad handle or size");
+  int st = ensure_capacity(h, max_pairs, nullptr);
+  if (st) return st;
+  return ensure_env_capacity(h, max_envs, nullptr);
+}
+
+int locc_step(locc_handle* h, const float* poses, const int32_t* obj_shape, int32_t n_obj,
+              const int32_t* env_offsets, int32_t n_env, int32_t* pairs_out, int32_t* n_pairs_out,
+              int32_t max_pairs, float* out, void* stream) {
+  if (!h) return fail(LOCC_ERR_INVALID_ARG, "handle is NULL");
+  if (n_env < 0 || max_pairs < 0 || n_obj < 0) return fail(LOCC_ERR_INVALID_ARG, "negative size");
+  if (!n_pairs_out) return fail(LOCC_ERR_INVALID_ARG, "n_pairs_out is NULL");
+  if (n_env > 0 && (!poses || !obj_shape || !env_offsets))
+    return fail(LOCC_ERR_INVALID_ARG, "NULL array");
+  if (max_pairs > 0 && (!pairs_out || !out)) return fail(LOCC_ERR_INVALID_ARG, "NULL output");
+  cudaStream_t s = (cudaStream_t)stream;
+  int st = ensure_capacity(h, max_pairs, s);
+  if (st) return st;
+  const bool prof = h->profiling;
+  if (prof) CUDA_TRY(cudaEventRecord(h->ev[0], s));
+  st = broadphase_run(h, poses, obj_shape, env_offsets, n_env, pairs_out, n_pairs_out, max_pairs, s);
+  if (st) return st == LOCC_ERR_CUDA ? fail(st, "broadphase launch failed") : st;
+  if (prof) CUDA_TRY(cudaEventRecord(h->ev[1], s));
+  if (max_pairs > 0 && n_env > 0) {
+    PairInputs in{poses, obj_shape, pairs_out, n_obj, max_pairs};
+    CUDA_TRY(launch_crop(dev_library(h), in, n_pairs_out, h->radius, h->d_xyz, nullptr, h->d_cnt,
+                         h->d_centre, h->d_err, h->n_sm, s));
+    if (prof) CUDA_TRY(cudaEventRecord(h->ev[2], s));
+    st = run_network(h, h->d_xyz, max_pairs, n_pairs_out, &in, h->d_centre, out, nullptr, nullptr,
+                     s, prof ? h->ev[3] : nullptr);
+    if (st) return st;
+  } else if (prof) {
+    CUDA_TRY(cudaEventRecord(h->ev[2], s));
+    CUDA_TRY(cudaEventRecord(h->ev[3], s));
+  }
+  if (prof) CUDA_TRY(cudaEventRecord(h->ev[4], s));
+  return LOCC_OK;
+}
+
+int locc_profile(locc_handle* h, int enable) {
+  if (!h) return fail(LOCC_ERR_INVALID_ARG, "handle is NULL");
+  if (enable && !h->ev[0]) {
+    for (int i = 0; i < 5; ++i) CUDA_TRY(cudaEventCreate(&h->ev[i]));
+  }
+  h->profiling = enable != 0;
+  h->prof_valid = false;
+  return LOCC_OK;
+}
+
+int locc_stage_times(locc_handle* h, float* ms_out, int n) {
+  if (!h || !ms_out || n < 0) return fail(LOCC_ERR_INVALID_ARG, "bad argument");
+  if (!h->profiling || !h->ev[0]) return fail(LOCC_ERR_INVALID_ARG, "profiling is off");
+  CUDA_TRY(cudaEventSynchronize(h->ev[4]));
+  int k = 0;
+  for (; k < n && k < 4; ++k) CUDA_TRY(cudaEventElapsedTime(&ms_out[k], h->ev[k], h->ev[k + 1]));
+  return k;
+}
+
+int locc_step_host(locc_handle* h, const float* poses, const int32_t* obj_shape, int32_t n_obj,
+                   const int32_t* env_offsets, int32_t n_env, int32_t* pairs_out,
+                   int32_t* n_pairs_out, int32_t max_pairs, float* out, void* stream) {
+  if (!h) return fail(LOCC_ERR_INVALID_ARG, "handle is NULL");
+  if (n_env < 0 || max_pairs < 0 || n_obj < 0) return fail(LOCC_ERR_INVALID_ARG, "negative size");
+  if (!n_pairs_out || (n_env > 0 && (!poses || !obj_shape || !env_offsets)) ||
+      (max_pairs > 0 && (!pairs_out || !out)))
+    return fail(LOCC_ERR_INVALID_ARG, "NULL array");
+  cudaStream_t s = (cudaStream_t)stream;
+  auto al = [](size_t x) { return (x + 255) / 256 * 256; };
+  const size_t b_poses = (size_t)n_obj * 28, b_shape = (size_t)n_obj * 4;
+  const size_t b_env = (size_t)(n_env + 1) * 4;
+  const size_t b_pairs = (size_t)max_pairs * 8, b_out = (size_t)max_pairs * 32;
+  const size_t o_shape = al(b_poses), o_env = o_shape + al(b_shape), in_bytes = o_env + al(b_env);
+  const size_t o_cnt = in_bytes, o_pairs = o_cnt + 256, o_out = o_pairs + al(b_pairs);
+  const size_t need = o_out + al(b_out);
+  int st = ensure_stage(h, need, s);
+  if (st) return st;
+  char* hs = static_cast<char*>(h->h_stage);
+  char* ds = static_cast<char*>(h->d_stage);
+  std::memcpy(hs, poses, b_poses);
+  std::memcpy(hs + o_shape, obj_shape, b_shape);
+  std::memcpy(hs + o_env, env_offsets, b_env);
+  CUDA_TRY(cudaMemcpyAsync(ds, hs, in_bytes, cudaMemcpyHostToDevice, s));
+  st = locc_step(h, reinterpret_cast<float*>(ds), reinterpret_cast<int32_t*>(ds + o_shape), n_obj,
+                 reinterpret_cast<int32_t*>(ds + o_env), n_env,
+                 reinterpret_cast<int32_t*>(ds + o_pairs), reinterpret_cast<int32_t*>(ds + o_cnt),
+                 max_pairs, reinterpret_cast<float*>(ds + o_out), stream);
+  if (st) return st;
+  CUDA_TRY(cudaMemcpyAsync(hs + o_cnt, ds + o_cnt, 4, cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  int32_t n = 0;
+  std::memcpy(&n, hs + o_cnt, 4);
+  *n_pairs_out = n;
+  const int32_t m = std::min(n, max_pairs);
+  if (m > 0) {
+    CUDA_TRY(cudaMemcpyAsync(hs + o_pairs, ds + o_pairs, (size_t)m * 8, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaMemcpyAsync(hs + o_out, ds + o_out, (size_t)m * 32, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    std::memcpy(pairs_out, hs + o_pairs, (size_t)m * 8);
+    std::memcpy(out, hs + o_out, (size_t)m * 32);
+  }
+  return LOCC_OK;
+}
+
+int locc_crop(locc_handle* h, const float* poses, const int32_t* obj_shape, int32_t n_obj,
+              const int32_t* pairs, int32_t n_pairs, float* xyz_out, int32_t* idx_out,
+              int32_t* cnt_out, float* centre_out, void* stream) {
+  if (!h) return fail(LOCC_ERR_INVALID_ARG, "handle is NULL");
+  if (n_pairs < 0 || n_obj < 0) return fail(LOCC_ERR_INVALID_ARG, "negative size");
+  if (n_pairs == 0) return LOCC_OK;
+  if (!poses || !obj_shape || !pairs || !xyz_out || !cnt_out)
+    return fail(LOCC_ERR_INVALID_ARG, "NULL array");
+  PairInputs in{poses, obj_shape, pairs, n_obj, n_pairs};
+  CUDA_TRY(launch_crop(dev_library(h), in, nullptr, h->radius, reinterpret_cast<float4*>(xyz_out),
+                       idx_out, cnt_out, reinterpret_cast<float4*>(centre_out), h->d_err, h->n_sm,
+                       (cudaStream_t)stream));
+  return LOCC_OK;
+}
+
+int locc_network(locc_handle* h, const float* xyz, int32_t n_pairs, float* y_out,
+                 float* feat_out, void* stream) {
+  if (!h) return fail(LOCC_ERR_INVALID_ARG, "handle is NULL");
+  if (n_pairs < 0) return fail(LOCC_ERR_INVALID_ARG, "negative size");
+  if (n_pairs == 0) return LOCC_OK;
+  if (!xyz || !y_out) return fail(LOCC_ERR_INVALID_ARG, "NULL array");
+  cudaStream_t s = (cudaStream_t)stream;
+  int st = ensure_capacity(h, n_pairs, s);
+  if (st) return st;
+  return run_network(h, reinterpret_cast<const float4*>(xyz), n_pairs, nullptr, nullptr, nullptr,
+                     nullptr, y_out, feat_out, s, nullptr);
+}
+
+int locc_detect(locc_handle* h, const float* poses, const int32_t* obj_shape, int32_t n_obj,
+                const int32_t* pairs, int32_t n_pairs, float* out, void* stream) {
+  if (!h) return fail(LOCC_ERR_INVALID_ARG, "handle is NULL");
+  if (n_pairs < 0 || n_obj < 0) return fail(LOCC_ERR_INVALID_ARG, "negative size");
+  if (n_pairs == 0) return LOCC_OK;
+  if (!poses || !obj_shape || !pairs || !out) return fail(LOCC_ERR_INVALID_ARG, "NULL array");
+  cudaStream_t s = (cudaStream_t)stream;
+  int st = ensure_capacity(h, n_pairs, s);
+  if (st) return st;
+  PairInputs in{poses, obj_shape, pairs, n_obj, n_pairs};
+  CUDA_TRY(launch_crop(dev_library(h), in, nullptr, h->radius, h->d_xyz, nullptr, h->d_cnt,
+                       h->d_centre, h->d_err, h->n_sm, s));
+  return run_network(h, h->d_xyz, n_pairs, nullptr, &in, h->d_centre, out, nullptr, nullptr, s,
+                     nullptr);
+}
+
+int locc_detect_host(locc_handle* h, const float* poses, const int32_t* obj_shape, int32_t n_obj,
+                     const int32_t* pairs, int32_t n_pairs, float* out, void* stream) {
+  if (!h) return fail(LOCC_ERR_INVALID_ARG, "handle is NULL");
+  if (n_pairs < 0 || n_obj < 0) return fail(LOCC_ERR_INVALID_ARG, "negative size");
+  if (n_pairs == 0) return LOCC_OK;
+  if (!poses || !obj_shape || !pairs || !out) return fail(LOCC_ERR_INVALID_ARG, "NULL array");
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t b_poses = (size_t)n_obj * 7 * 4, b_shape = (size_t)n_obj * 4;
+  const size_t b_pairs = (size_t)n_pairs * 8, b_out = (size_t)n_pairs * 8 * 4;
+  auto al = [](size_t x) { return (x + 255) / 256 * 256; };
+  const size_t in_bytes = al(b_poses) + al(b_shape) + al(b_pairs);
+  const size_t need = in_bytes + al(b_out);
+  int st0 = ensure_stage(h, need, s);
+  if (st0) return st0;
+  char* hs = static_cast<char*>(h->h_stage);
+  char* ds = static_cast<char*>(h->d_stage);
+  std::memcpy(hs, poses, b_poses);
+  std::memcpy(hs + al(b_poses), obj_shape, b_shape);
+  std::memcpy(hs + al(b_poses) + al(b_shape), pairs, b_pairs);
+  CUDA_TRY(cudaMemcpyAsync(ds, hs, in_bytes, cudaMemcpyHostToDevice, s));
+  int st = locc_detect(h, reinterpret_cast<float*>(ds), reinterpret_cast<int32_t*>(ds + al(b_poses)),
+                       n_obj, reinterpret_cast<int32_t*>(ds + al(b_poses) + al(b_shape)), n_pairs,
+                       reinterpret_cast<float*>(ds + in_bytes), stream);
+  if (st) return st;
+  CUDA_TRY(cudaMemcpyAsync(hs + in_bytes, ds + in_bytes, b_out, cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  std::memcpy(out, hs + in_bytes, b_out);
+  return LOCC_OK;
+}
+
+int locc_broadphase(locc_handle* h, const float* poses, const int32_t* obj_shape,
+                    const int32_t* env_offsets, int32_t n_env, int32_t* pairs_out,
+                    int32_t* n_pairs_out, int32_t max_pairs, void* stream) {
+  if (!h) return fail(LOCC_ERR_INVALID_ARG, "handle is NULL");
+  if (n_env < 0 || max_pairs < 0) return fail(LOCC_ERR_INVALID_ARG, "negative size");
+  if (!n_pairs_out) return fail(LOCC_ERR_INVALID_ARG, "n_pairs_out is NULL");
+  if (n_env > 0 && (!poses || !obj_shape || !env_offsets || (max_pairs > 0 && !pairs_out)))
+    return fail(LOCC_ERR_INVALID_ARG, "NULL array");
+  const int st = broadphase_run(h, poses, obj_shape, env_offsets, n_env, pairs_out, n_pairs_out,
+                                max_pairs, (cudaStream_t)stream);
+  if (st == LOCC_ERR_CUDA) return fail(st, "broadphase launch failed");
+  return st;
+}
+
+int locc_status(locc_handle* h, void* stream) {
+  if (!h) return fail(LOCC_ERR_INVALID_ARG, "handle is NULL");
+  CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+  int flag = 0;
+  CUDA_TRY(cudaMemcpy(&flag, h->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (flag) {
+    CUDA_TRY(cudaMemset(h->d_err, 0, sizeof(int)));
+    if (flag & 2) return fail(LOCC_ERR_TIMEOUT, "a bounded device wait ran out");
+    return fail(LOCC_ERR_BAD_INDEX, "a pair or shape index was out of range");
+  }
+  return LOCC_OK;
+}
+
+void locc_destroy(locc_handle* h) {
+  if (!h) return;
+  cudaDeviceSynchronize();
+  free_scratch(h);
+  free_params(h);
+  cudaFree(h->d_points);
+  cudaFree(h->d_blocks);
+  cudaFree(h->d_aabb);
+  cudaFree(h->d_err);
+  cudaFree(h->d_env_counts);
+  cudaFree(h->d_stage);
+  cudaFreeHost(h->h_stage);
+  for (int i = 0; i < 5; ++i)
+    if (h->ev[i]) cudaEventDestroy(h->ev[i]);
+  delete h;
+}
+
+}  // extern "C"

@@ -1,0 +1,135 @@
+// Shared definitions of the sm_103a contact-detection library.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/locc.h"
+
+namespace locc {
+
+constexpr int KMAX = LOCC_CROP_POINTS;   // points per object crop
+constexpr int ROWS = 2 * KMAX;           // crop rows per pair (A then B)
+constexpr int FEAT = 256;                // pooled feature per object
+constexpr int OUTD = LOCC_OUT_DIM;
+constexpr int BLOCK_PTS = 32;            // library points per culling block
+
+// Layer dimensions (in, out): encoder 3-64-128-256, head 512-256-256-8.
+constexpr int L_IN[6] = {3, 64, 128, 512, 256, 256};
+constexpr int L_OUT[6] = {64, 128, 256, 256, 256, 8};
+
+// Device copy of the shape library.
+//   points: [S][n_pad] float4 (x, y, z, bits = (orig_index)), blocks of 32
+//           points in Morton order, tail padded with NaN points;
+//   blocks: [S][n_blocks][2] float4 (lo, hi) bounding box of each block;
+//   aabb:   [S][2] float4 (lo, hi) body box of each shape.
+struct DevLibrary {
+  const float4* points;
+  const float4* blocks;
+  const float4* aabb;
+  int n_shapes;
+  int n_points;
+  int n_pad;
+  int n_blocks;
+};
+
+// Pair-level inputs shared by every kernel of the path.
+struct PairInputs {
+  const float* poses;       // [n_obj][7]
+  const int32_t* obj_shape; // [n_obj]
+  const int32_t* pairs;     // [n_pairs][2]
+  int n_obj;
+  int n_pairs;
+};
+
+// Float32 parameters for the CUDA-core kernels: per layer W^T [in][out]
+// followed by b [out].
+struct Fp32Params {
+  const float* wt[6];
+  const float* b[6];
+};
+
+__device__ __forceinline__ float fmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float fadd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float fsub(float a, float b) { return __fsub_rn(a, b); }
+
+// (a0 b0 + a1 b1) + a2 b2, every operation rounded separately (no FMA).
+__device__ __forceinline__ float dot3_rn(float a0, float a1, float a2, float b0,
+                                         float b1, float b2) {
+  float s = fmul(a0, b0);
+  s = fadd(s, fmul(a1, b1));
+  return fadd(s, fmul(a2, b2));
+}
+
+// Rotation of the unit quaternion (w, x, y, z), row-major R[9], body -> world.
+__device__ __forceinline__ void quat_to_rot(const float* q, float* R) {
+  const float w = q[0], x = q[1], y = q[2], z = q[3];
+  const float xx = fmul(x, x), yy = fmul(y, y), zz = fmul(z, z);
+  const float xy = fmul(x, y), xz = fmul(x, z), yz = fmul(y, z);
+  const float wx = fmul(w, x), wy = fmul(w, y), wz = fmul(w, z);
+  R[0] = fsub(1.0f, fmul(2.0f, fadd(yy, zz)));
+  R[1] = fmul(2.0f, fsub(xy, wz));
+  R[2] = fmul(2.0f, fadd(xz, wy));
+  R[3] = fmul(2.0f, fadd(xy, wz));
+  R[4] = fsub(1.0f, fmul(2.0f, fadd(xx, zz)));
+  R[5] = fmul(2.0f, fsub(yz, wx));
+  R[6] = fmul(2.0f, fsub(xz, wy));
+  R[7] = fmul(2.0f, fadd(yz, wx));
+  R[8] = fsub(1.0f, fmul(2.0f, fadd(xx, yy)));
+}
+
+// Validated indices of pair p; returns false (and raises the error flag) if
+// an object index or shape id is out of range.
+__device__ __forceinline__ bool load_pair(const PairInputs& in, int n_shapes,
+                                          int p, int* a, int* b, int* sa,
+                                          int* sb, int* err) {
+  const int ia = in.pairs[2 * p], ib = in.pairs[2 * p + 1];
+  bool ok = ia >= 0 && ib >= 0 && ia < in.n_obj && ib < in.n_obj;
+  int s0 = -1, s1 = -1;
+  if (ok) {
+    s0 = in.obj_shape[ia];
+    s1 = in.obj_shape[ib];
+    ok = s0 >= 0 && s1 >= 0 && s0 < n_shapes && s1 < n_shapes;
+  }
+  if (!ok && err) atomicOr(err, 1);
+  *a = ia, *b = ib, *sa = s0, *sb = s1;
+  return ok;
+}
+
+// Epilogue (shared with the tensor-core head): raw crop-frame outputs y[8] ->
+// world frame.  Point: R_A (y[1:4] + c) + t_A; normal: R_A n / max(|n|, 1e-12).
+__device__ __forceinline__ void epilogue_world(const float* y, const float* poseA, float4 c, float* o) {
+  float R[9];
+  quat_to_rot(poseA, R);
+  const float px = y[1] + c.x, py = y[2] + c.y, pz = y[3] + c.z;
+  float nx = y[4], ny = y[5], nz = y[6];
+  const float nn = fmaxf(sqrtf(nx * nx + ny * ny + nz * nz), 1e-12f);
+  nx /= nn, ny /= nn, nz /= nn;
+  o[0] = y[0];
+  o[1] = R[0] * px + R[1] * py + R[2] * pz + poseA[4];
+  o[2] = R[3] * px + R[4] * py + R[5] * pz + poseA[5];
+  o[3] = R[6] * px + R[7] * py + R[8] * pz + poseA[6];
+  o[4] = R[0] * nx + R[1] * ny + R[2] * nz;
+  o[5] = R[3] * nx + R[4] * ny + R[5] * nz;
+  o[6] = R[6] * nx + R[7] * ny + R[8] * nz;
+  o[7] = y[7];
+}
+
+}  // namespace locc
+
+// Launchers (defined in the .cu files), all asynchronous on `stream`.
+namespace locc {
+// n_dev (nullable): device count of pairs actually present (<= n_pairs), read
+// by the kernels so that a fixed launch serves a count produced on the device.
+cudaError_t launch_crop(const DevLibrary& lib, const PairInputs& in, const int* n_dev,
+                        float r, float4* xyz, int32_t* idx, int32_t* cnt, float4* centre,
+                        int* err, int n_sm, cudaStream_t stream);
+cudaError_t launch_encoder_fp32(const float4* xyz, int n_pairs, const int* n_dev,
+                                const Fp32Params& prm, float* feat, int n_sm,
+                                cudaStream_t stream);
+cudaError_t launch_head_fp32(const float* feat, int n_pairs, const int* n_dev,
+                             const Fp32Params& prm, const PairInputs* in,
+                             const float4* centre, float* out, float* y_raw, int n_sm,
+                             cudaStream_t stream);
+}  // namespace locc

@@ -1,0 +1,274 @@
+// Crop gather: pose composition, crop centre and nearest-first selection of
+// each object's surface points inside the crop ball (steps 1-3 of the path).
+//
+// Paper: Sec. III (collision predictor: "create the OBB of shape embeddings of
+// two objects by using their poses ... select the features in colliding
+// cells"), appendix ("identify the intersection region of two AABB").  The
+// crop centre is the centre of A's body box intersected with B's posed box
+// seen as an axis-aligned box of A's frame; each object keeps at most 64 of
+// its surface samples inside the ball of radius r about that centre, nearest
+// first, ties to the lower sample index, expressed in the canonical crop frame
+// (A's body axes, origin at the centre).
+//
+// Design (one CTA of two warps per pair, warp 0 = object A, warp 1 = B):
+//   * every float32 operation of the selection uses an explicit round-to-
+//     nearest intrinsic in a fixed order, so index sets are reproducible bit
+//     for bit on any IEEE-754 machine that performs the same operations;
+//   * the library keeps each shape's samples in Morton-ordered blocks of 32
+//     with a bounding box per block; a warp first tests the ball against the
+//     block boxes (conservatively) and streams only the blocks that may hold
+//     in-ball points, one coalesced 512-byte float4 load per block;
+//   * in-ball points become 64-bit keys (d^2 bits, sample index, slot) and are
+//     appended to a per-warp shared-memory list by ballot + popc compaction;
+//     when the list is about to overflow it is bitonic-sorted in registers
+//     and cut to its 64 smallest keys, whose largest then bounds new arrivals
+//     (an exact streaming top-64);
+//   * the final list is sorted and its first min(64, n) keys are written out.
+#include <algorithm>
+
+#include "common.cuh"
+
+namespace locc {
+namespace {
+
+constexpr int CAND_CAP = 256;
+constexpr unsigned FULL = 0xffffffffu;
+
+// Bitonic sort (ascending) of N = 32 * R keys held R per lane, element
+// e = lane * R + r.
+template <int R>
+__device__ __forceinline__ void warp_bitonic(unsigned long long (&v)[R], int lane) {
+  constexpr int N = 32 * R;
+#pragma unroll
+  for (int k = 2; k <= N; k <<= 1) {
+#pragma unroll
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      if (j >= R) {
+        const int lj = j / R;
+        const bool lower = (lane & lj) == 0;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          const unsigned long long w = __shfl_xor_sync(FULL, v[r], lj);
+          const bool asc = ((lane * R + r) & k) == 0;
+          const unsigned long long lo = v[r] < w ? v[r] : w;
+          const unsigned long long hi = v[r] < w ? w : v[r];
+          v[r] = (lower == asc) ? lo : hi;
+        }
+      } else {
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          if ((r & j) == 0) {
+            const int r2 = r | j;
+            const bool asc = ((lane * R + r) & k) == 0;
+            const unsigned long long a = v[r], b = v[r2];
+            const bool sw = asc ? (a > b) : (a < b);
+            v[r] = sw ? b : a;
+            v[r2] = sw ? a : b;
+          }
+        }
+      }
+    }
+  }
+}
+
+// Sort the first n keys of buf (n <= 32 R) in place; slots n.. become ~0.
+template <int R>
+__device__ __forceinline__ void sort_list(unsigned long long* buf, int n, int lane) {
+  unsigned long long v[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int e = lane * R + r;
+    v[r] = e < n ? buf[e] : ~0ull;
+  }
+  warp_bitonic<R>(v, lane);
+  __syncwarp();
+#pragma unroll
+  for (int r = 0; r < R; ++r) buf[lane * R + r] = v[r];
+  __syncwarp();
+}
+
+__device__ __forceinline__ void sort_any(unsigned long long* buf, int n, int lane) {
+  if (n <= 64) sort_list<2>(buf, n, lane);
+  else if (n <= 128) sort_list<4>(buf, n, lane);
+  else sort_list<8>(buf, n, lane);
+}
+
+struct Frame {
+  float rrel[9];
+  float c[3];   // crop centre, A frame
+  float cb[3];  // crop centre, B frame
+};
+
+__device__ __forceinline__ void pair_frame(const float* pa, const float* pb,
+                                           float4 alo, float4 ahi, float4 blo,
+                                           float4 bhi, Frame& f) {
+  float RA[9], RB[9];
+  quat_to_rot(pa, RA);
+  quat_to_rot(pb, RB);
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+      f.rrel[3 * i + j] = dot3_rn(RA[i], RA[3 + i], RA[6 + i], RB[j], RB[3 + j], RB[6 + j]);
+  const float dt0 = fsub(pb[4], pa[4]), dt1 = fsub(pb[5], pa[5]), dt2 = fsub(pb[6], pa[6]);
+  float trel[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) trel[i] = dot3_rn(RA[i], RA[3 + i], RA[6 + i], dt0, dt1, dt2);
+  const float bl[3] = {blo.x, blo.y, blo.z}, bh[3] = {bhi.x, bhi.y, bhi.z};
+  const float al[3] = {alo.x, alo.y, alo.z}, ah[3] = {ahi.x, ahi.y, ahi.z};
+  float cbx[3], hbx[3];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    cbx[j] = fmul(fadd(bl[j], bh[j]), 0.5f);
+    hbx[j] = fmul(fsub(bh[j], bl[j]), 0.5f);
+  }
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const float* r = f.rrel + 3 * i;
+    const float c = fadd(dot3_rn(r[0], r[1], r[2], cbx[0], cbx[1], cbx[2]), trel[i]);
+    const float h = dot3_rn(fabsf(r[0]), fabsf(r[1]), fabsf(r[2]), hbx[0], hbx[1], hbx[2]);
+    const float lo = fsub(c, h), hi = fadd(c, h);
+    const float a = fmaxf(al[i], lo);
+    const float b = fminf(ah[i], hi);
+    f.c[i] = fmul(fadd(a, b), 0.5f);
+  }
+  const float e0 = fsub(f.c[0], trel[0]), e1 = fsub(f.c[1], trel[1]), e2 = fsub(f.c[2], trel[2]);
+#pragma unroll
+  for (int j = 0; j < 3; ++j)
+    f.cb[j] = dot3_rn(f.rrel[j], f.rrel[3 + j], f.rrel[6 + j], e0, e1, e2);
+}
+
+__device__ __forceinline__ float box_dist2(float4 lo, float4 hi, float cx, float cy, float cz) {
+  const float dx = fmaxf(fmaxf(lo.x - cx, cx - hi.x), 0.0f);
+  const float dy = fmaxf(fmaxf(lo.y - cy, cy - hi.y), 0.0f);
+  const float dz = fmaxf(fmaxf(lo.z - cz, cz - hi.z), 0.0f);
+  return dx * dx + dy * dy + dz * dz;
+}
+
+__device__ __forceinline__ void crop_pair(const DevLibrary& lib, const PairInputs& in, int p, int warp,
+                                          int lane, float r, float4* __restrict__ xyz_out,
+                                          int32_t* __restrict__ idx_out,
+                                          int32_t* __restrict__ cnt_out,
+                                          float4* __restrict__ centre_out, int* __restrict__ err,
+                                          unsigned long long* buf) {
+  int a, b, sa, sb;
+  const bool ok = load_pair(in, lib.n_shapes, p, &a, &b, &sa, &sb, (warp == 0 && lane == 0) ? err : nullptr);
+  float4* xo = xyz_out + ((size_t)p * 2 + warp) * KMAX;
+  int32_t* io = idx_out ? idx_out + ((size_t)p * 2 + warp) * KMAX : nullptr;
+  if (!ok) {
+    const float nan = __int_as_float(0x7fc00000);
+    xo[lane] = xo[lane + 32] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (io) io[lane] = io[lane + 32] = -1;
+    if (lane == 0) cnt_out[2 * p + warp] = 0;
+    if (warp == 0 && lane == 0 && centre_out) centre_out[p] = make_float4(nan, nan, nan, nan);
+    return;
+  }
+  Frame f;
+  pair_frame(in.poses + 7 * (size_t)a, in.poses + 7 * (size_t)b, lib.aabb[2 * sa],
+             lib.aabb[2 * sa + 1], lib.aabb[2 * sb], lib.aabb[2 * sb + 1], f);
+  if (warp == 0 && lane == 0 && centre_out) centre_out[p] = make_float4(f.c[0], f.c[1], f.c[2], 0.f);
+
+  const int shape = warp == 0 ? sa : sb;
+  const float cx = warp == 0 ? f.c[0] : f.cb[0];
+  const float cy = warp == 0 ? f.c[1] : f.cb[1];
+  const float cz = warp == 0 ? f.c[2] : f.cb[2];
+  const float r2 = fmul(r, r);
+  const float r2_cull = r2 * 1.001f + 1e-30f;  // conservative block test
+  const float4* pts = lib.points + (size_t)shape * lib.n_pad;
+  const float4* blk = lib.blocks + (size_t)shape * lib.n_blocks * 2;
+  unsigned long long bound = ~0ull;  // keys >= bound cannot reach the top 64
+  int n = 0;
+
+  for (int bg = 0; bg < lib.n_blocks; bg += 32) {
+    const int bi = bg + lane;
+    bool hit = false;
+    if (bi < lib.n_blocks) hit = box_dist2(blk[2 * bi], blk[2 * bi + 1], cx, cy, cz) <= r2_cull;
+    unsigned mask = __ballot_sync(FULL, hit);
+    while (mask) {
+      const int bb = bg + __ffs(mask) - 1;
+      mask &= mask - 1;
+      const int pos = bb * BLOCK_PTS + lane;
+      const float4 q = pts[pos];
+      const float d0 = fsub(q.x, cx), d1 = fsub(q.y, cy), d2 = fsub(q.z, cz);
+      float s = fmul(d0, d0);
+      s = fadd(s, fmul(d1, d1));
+      s = fadd(s, fmul(d2, d2));
+      const unsigned long long key =
+          ((unsigned long long)__float_as_uint(s) << 32) |
+          ((unsigned long long)(__float_as_uint(q.w) & 0xffffu) << 16) | (unsigned)pos;
+      const bool take = (s <= r2) && key < bound;
+      const unsigned tm = __ballot_sync(FULL, take);
+      if (tm == 0) continue;
+      if (n + __popc(tm) > CAND_CAP) {
+        sort_list<8>(buf, n, lane);
+        n = KMAX;
+        bound = buf[KMAX - 1];
+      }
+      const bool take2 = take && key < bound;
+      const unsigned tm2 = __ballot_sync(FULL, take2);
+      if (take2) buf[n + __popc(tm2 & ((1u << lane) - 1u))] = key;
+      n += __popc(tm2);
+      __syncwarp();
+    }
+  }
+  sort_any(buf, n, lane);
+  const int cnt = n < KMAX ? n : KMAX;
+  const float* R = f.rrel;
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int s = lane + 32 * h;
+    float4 o = make_float4(0.f, 0.f, 0.f, 0.f);
+    int oi = -1;
+    if (s < cnt) {
+      const unsigned long long key = buf[s];
+      const int pos = (int)(key & 0xffffu);
+      oi = (int)((key >> 16) & 0xffffu);
+      const float4 q = pts[pos];
+      const float d0 = fsub(q.x, cx), d1 = fsub(q.y, cy), d2 = fsub(q.z, cz);
+      if (warp == 0) {
+        o = make_float4(d0, d1, d2, 1.0f);
+      } else {
+        o = make_float4(dot3_rn(R[0], R[1], R[2], d0, d1, d2),
+                        dot3_rn(R[3], R[4], R[5], d0, d1, d2),
+                        dot3_rn(R[6], R[7], R[8], d0, d1, d2), 1.0f);
+      }
+    }
+    xo[s] = o;
+    if (io) io[s] = oi;
+  }
+  if (lane == 0) cnt_out[2 * p + warp] = cnt;
+  __syncwarp();
+}
+
+__global__ void __launch_bounds__(64) crop_kernel(DevLibrary lib, PairInputs in, const int* n_dev,
+                                                  float r, float4* __restrict__ xyz_out,
+                                                  int32_t* __restrict__ idx_out,
+                                                  int32_t* __restrict__ cnt_out,
+                                                  float4* __restrict__ centre_out,
+                                                  int* __restrict__ err) {
+  __shared__ unsigned long long cand[2][CAND_CAP];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int n_pairs = n_dev ? min(*n_dev, in.n_pairs) : in.n_pairs;
+  for (int p = blockIdx.x; p < n_pairs; p += gridDim.x) {
+    crop_pair(lib, in, p, warp, lane, r, xyz_out, idx_out, cnt_out, centre_out, err, cand[warp]);
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_crop(const DevLibrary& lib, const PairInputs& in, const int* n_dev, float r,
+                        float4* xyz, int32_t* idx, int32_t* cnt, float4* centre, int* err,
+                        int n_sm, cudaStream_t stream) {
+  if (in.n_pairs <= 0) return cudaSuccess;
+  // one wave of resident CTAs; each strides over the pairs
+  static int per_sm = 0;
+  if (per_sm == 0) {
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, crop_kernel, 64, 0);
+    if (e != cudaSuccess || per_sm < 1) per_sm = 1;
+  }
+  const int grid = std::min(in.n_pairs, n_sm * per_sm);
+  crop_kernel<<<grid, 64, 0, stream>>>(lib, in, n_dev, r, xyz, idx, cnt, centre, err);
+  return cudaGetLastError();
+}
+
+}  // namespace locc

@@ -1,0 +1,59 @@
+"""The "LOCCW001" parameter blob read by ``locc_create``.
+
+Layout (little endian): 8-byte magic ``LOCCW001``, uint32 version (1), uint32
+number of layers (6), six (uint32 in, uint32 out) pairs, then for every layer
+float32 W[out][in] followed by float32 b[out].
+"""
+
+from __future__ import annotations
+
+import struct
+from typing import List, Sequence, Tuple
+
+import numpy as np
+
+MAGIC = b"LOCCW001"
+LAYER_DIMS: List[Tuple[int, int]] = [(3, 64), (64, 128), (128, 256),
+                                     (512, 256), (256, 256), (256, 8)]
+N_PARAMS = sum(i * o + o for i, o in LAYER_DIMS)
+
+
+def pack(layers: Sequence[Tuple[np.ndarray, np.ndarray]]) -> bytes:
+    """[(W [out,in], b [out]) x 6] -> blob bytes."""
+    if len(layers) != len(LAYER_DIMS):
+        raise ValueError("expected 6 layers")
+    head = MAGIC + struct.pack("<II", 1, len(LAYER_DIMS))
+    body = []
+    for (w, b), (fi, fo) in zip(layers, LAYER_DIMS):
+        w = np.asarray(w, np.float32)
+        b = np.asarray(b, np.float32)
+        if w.shape != (fo, fi) or b.shape != (fo,):
+            raise ValueError(f"layer {fi}->{fo}: got W{w.shape} b{b.shape}")
+        head += struct.pack("<II", fi, fo)
+        body += [w.astype("<f4").tobytes(), b.astype("<f4").tobytes()]
+    return head + b"".join(body)
+
+
+def unpack(blob: bytes):
+    """Blob bytes -> [(W [out,in], b [out]) x 6] float32."""
+    if blob[:8] != MAGIC:
+        raise ValueError("bad magic")
+    version, n = struct.unpack_from("<II", blob, 8)
+    if version != 1 or n != 6:
+        raise ValueError("unsupported blob")
+    off = 16 + 8 * n
+    out = []
+    for fi, fo in LAYER_DIMS:
+        w = np.frombuffer(blob, "<f4", fi * fo, off).reshape(fo, fi).copy()
+        off += 4 * fi * fo
+        b = np.frombuffer(blob, "<f4", fo, off).copy()
+        off += 4 * fo
+        out.append((w, b))
+    return out
+
+
+def flat(layers) -> np.ndarray:
+    """Concatenate W1 b1 ... W6 b6 as float32."""
+    return np.concatenate([np.concatenate([np.asarray(w, np.float32).ravel(),
+                                           np.asarray(b, np.float32)])
+                           for w, b in layers])
