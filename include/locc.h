@@ -195,6 +195,28 @@ int locc_stage_times(locc_handle *h, float *ms_out, int n);
  * 0 or LOCC_ERR_BAD_INDEX. */
 int locc_status(locc_handle *h, void *stream);
 
+/* Allocation-free detection, for callers that may not allocate device memory
+ * while they run: a simulator whose own pool allocator owns all of HBM after
+ * start-up, or a latency-critical loop where cudaMalloc / cudaFree (which can
+ * synchronise the device) are not allowed.  The paper has no counterpart; this
+ * is a deployment variant of locc_detect.
+ *   Same arguments and outputs as locc_detect (device pointers), computed with
+ *   the float32 network whatever the handle's precision.  n_pairs must be
+ *   <= LOCC_NOALLOC_MAX_PAIRS, else LOCC_ERR_INVALID_ARG with a message.
+ *   Scratch: one library-owned __device__ array of about 4 MiB, resident on
+ *   every device that loads the library until the process exits.  The call
+ *   allocates nothing (no cudaMalloc / cudaFree, no allocating library call).
+ *   The first call on a device looks up that array's device address
+ *   (cudaGetSymbolAddress), so make it before any stream capture.
+ *   All calls share the array: calls whose kernels may overlap on the GPU
+ *   (other streams, handles or host threads) race and must be ordered by the
+ *   caller.  The current device must be the handle's device. */
+#define LOCC_NOALLOC_MAX_PAIRS 1024
+int locc_detect_noalloc(locc_handle *h, const float *poses,
+                        const int32_t *obj_shape, int32_t n_obj,
+                        const int32_t *pairs, int32_t n_pairs, float *out,
+                        void *stream);
+
 /* Release all device and host memory of the handle (blocking). */
 void locc_destroy(locc_handle *h);
 

@@ -24,7 +24,8 @@ ERRORS = {-1: "INVALID_ARG", -2: "OOM", -3: "CUDA", -4: "TIMEOUT",
 EXPORTS = ["locc_create", "locc_set_precision", "locc_detect", "locc_detect_host",
            "locc_crop", "locc_network", "locc_broadphase", "locc_step", "locc_step_host",
            "locc_reserve", "locc_profile", "locc_stage_times", "locc_status", "locc_destroy",
-           "locc_last_error"]
+           "locc_last_error", "locc_detect_noalloc"]
+NOALLOC_MAX_PAIRS = 1024
 
 
 class LoccError(RuntimeError):
@@ -61,6 +62,7 @@ def load(build_if_needed: bool = True) -> ctypes.CDLL:
         lib.locc_set_precision.argtypes = [P, ctypes.c_int]
         lib.locc_detect.argtypes = [P, P, P, I, P, I, P, P]
         lib.locc_detect_host.argtypes = [P, P, P, I, P, I, P, P]
+        lib.locc_detect_noalloc.argtypes = [P, P, P, I, P, I, P, P]
         lib.locc_crop.argtypes = [P, P, P, I, P, I, P, P, P, P, P]
         lib.locc_network.argtypes = [P, P, I, P, P, P]
         lib.locc_broadphase.argtypes = [P, P, P, P, I, P, P, I, P]
