@@ -21,6 +21,8 @@ struct locc_handle {
   // parameters (device): tensor-core operand images and scales
   void* d_wtc = nullptr;
   size_t wtc_bytes = 0;
+  const unsigned char* wtc_enc = nullptr;   // encoder image (W1 hi/lo, W2, W3, biases)
+  const unsigned char* wtc_head = nullptr;  // head image (Wh3, biases, Wh1 / Wh2 K-chunks)
   // per-call scratch (device), capacity cap_pairs
   int cap_pairs = 0;
   float4* d_xyz = nullptr;
