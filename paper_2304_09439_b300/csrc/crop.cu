@@ -34,53 +34,65 @@ namespace {
 constexpr int CAND_CAP = 256;
 constexpr unsigned FULL = 0xffffffffu;
 
-// Bitonic sort (ascending) of N = 32 * R keys held R per lane, element
-// e = lane * R + r.
+// One compare-exchange stage between lanes (partner lane ^ lj) for all R
+// registers; element e = lane * R + r sorts ascending where (e & k) == 0.
 template <int R>
-__device__ __forceinline__ void warp_bitonic(unsigned long long (&v)[R], int lane) {
-  constexpr int N = 32 * R;
+__device__ __forceinline__ void lane_stage(unsigned long long (&v)[R], int lane, int lj, int k) {
+  const bool lower = (lane & lj) == 0;
 #pragma unroll
-  for (int k = 2; k <= N; k <<= 1) {
+  for (int r = 0; r < R; ++r) {
+    const unsigned long long w = __shfl_xor_sync(FULL, v[r], lj);
+    const bool asc = ((lane * R + r) & k) == 0;
+    const unsigned long long lo = v[r] < w ? v[r] : w;
+    const unsigned long long hi = v[r] < w ? w : v[r];
+    v[r] = (lower == asc) ? lo : hi;
+  }
+}
+
+// One compare-exchange stage inside a lane between registers r and r | J.
+template <int R, int J>
+__device__ __forceinline__ void reg_stage(unsigned long long (&v)[R], int lane, int k) {
 #pragma unroll
-    for (int j = k >> 1; j > 0; j >>= 1) {
-      if (j >= R) {
-        const int lj = j / R;
-        const bool lower = (lane & lj) == 0;
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-          const unsigned long long w = __shfl_xor_sync(FULL, v[r], lj);
-          const bool asc = ((lane * R + r) & k) == 0;
-          const unsigned long long lo = v[r] < w ? v[r] : w;
-          const unsigned long long hi = v[r] < w ? w : v[r];
-          v[r] = (lower == asc) ? lo : hi;
-        }
-      } else {
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-          if ((r & j) == 0) {
-            const int r2 = r | j;
-            const bool asc = ((lane * R + r) & k) == 0;
-            const unsigned long long a = v[r], b = v[r2];
-            const bool sw = asc ? (a > b) : (a < b);
-            v[r] = sw ? b : a;
-            v[r2] = sw ? a : b;
-          }
-        }
-      }
+  for (int r = 0; r < R; ++r) {
+    if ((r & J) == 0) {
+      const int r2 = r | J;
+      const bool asc = ((lane * R + r) & k) == 0;
+      const unsigned long long a = v[r], b = v[r2];
+      const bool sw = asc ? (a > b) : (a < b);
+      v[r] = sw ? b : a;
+      v[r2] = sw ? a : b;
     }
   }
 }
 
-// Sort the first n keys of buf (n <= 32 R) in place; slots n.. become ~0.
+// Sort the first n keys of buf ascending in place (n <= 32 R; slots n.. become
+// ~0): bitonic network over N = 32 R keys, R per lane (element
+// e = lane * R + r).  Stage loops stay rolled and the function is not inlined,
+// so each size exists once in the binary (instruction-cache footprint).
 template <int R>
-__device__ __forceinline__ void sort_list(unsigned long long* buf, int n, int lane) {
+__device__ __noinline__ void sort_list(unsigned long long* buf, int n, int lane) {
+  constexpr int N = 32 * R;
   unsigned long long v[R];
 #pragma unroll
   for (int r = 0; r < R; ++r) {
     const int e = lane * R + r;
     v[r] = e < n ? buf[e] : ~0ull;
   }
-  warp_bitonic<R>(v, lane);
+#pragma unroll 1
+  for (int k = 2; k <= N; k <<= 1) {
+#pragma unroll 1
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      if (j >= R) {
+        lane_stage<R>(v, lane, j / R, k);
+      } else if (j == 4) {
+        if constexpr (R > 4) reg_stage<R, 4>(v, lane, k);
+      } else if (j == 2) {
+        if constexpr (R > 2) reg_stage<R, 2>(v, lane, k);
+      } else {
+        reg_stage<R, 1>(v, lane, k);
+      }
+    }
+  }
   __syncwarp();
 #pragma unroll
   for (int r = 0; r < R; ++r) buf[lane * R + r] = v[r];
@@ -240,7 +252,7 @@ __device__ __forceinline__ void crop_pair(const DevLibrary& lib, const PairInput
   __syncwarp();
 }
 
-__global__ void __launch_bounds__(64) crop_kernel(DevLibrary lib, PairInputs in, const int* n_dev,
+__global__ void __launch_bounds__(64, 16) crop_kernel(DevLibrary lib, PairInputs in, const int* n_dev,
                                                   float r, float4* __restrict__ xyz_out,
                                                   int32_t* __restrict__ idx_out,
                                                   int32_t* __restrict__ cnt_out,

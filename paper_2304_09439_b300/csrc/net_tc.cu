@@ -46,21 +46,53 @@ constexpr int E_W2 = E_W1 + 64 * 16 * 2;      // [128 x 64] 16 KB
 constexpr int E_W3 = E_W2 + 128 * 64 * 2;     // [256 x 128] 64 KB
 constexpr int E_BIAS = E_W3 + 256 * 128 * 2;  // b1 64, b2 128, b3 256 (f32)
 constexpr int E_IMG_BYTES = E_BIAS + (64 + 128 + 256) * 4;
-constexpr int E_X = (E_IMG_BYTES + 127) / 128 * 128;  // [128 x 16]  4 KB
-constexpr int E_H1 = E_X + 128 * 16 * 2;              // [128 x 64] 16 KB
-constexpr int E_H2 = E_H1 + 128 * 64 * 2;             // [128 x 128] 32 KB
-constexpr int E_CTRL = E_H2 + 128 * 128 * 2;          // mbar, tmem base, counts
-constexpr int E_SMEM = E_CTRL + 64;
 static_assert(E_IMG_BYTES % 16 == 0, "image must be a whole number of 16-byte chunks");
+// two pair slots, each: raw crop rows (f32), X tile, H1 tile, H2 tile
+constexpr int E_SLOT0 = (E_IMG_BYTES + 1023) / 1024 * 1024;
+constexpr int S_STG = 0;                        // [128] float4   2 KB
+constexpr int S_X = S_STG + ROWS * 16;          // [128 x 16]     4 KB
+constexpr int S_H1 = S_X + 128 * 16 * 2;        // [128 x 64]    16 KB
+constexpr int S_H2 = S_H1 + 128 * 64 * 2;       // [128 x 128]   32 KB
+constexpr int SLOT_BYTES = S_H2 + 128 * 128 * 2;
+constexpr int E_CTRL = E_SLOT0 + 2 * SLOT_BYTES;
+// control block: 16 mbarriers (8 B each), tmem slot, abort flag, counts
+constexpr int C_BAR = 0, C_TMEM = 128, C_ABORT = 132, C_CNT = 136;  // C_CNT: [2 slots][4 warps]
+constexpr int E_SMEM = E_CTRL + 256;
+static_assert(E_SMEM <= 227 * 1024, "encoder shared memory");
+constexpr int E_THREADS = 288;  // warps 0-3: slot-0 epilogue, 4-7: slot-1 epilogue, 8: MMA + TMA
+constexpr int SLOT_COLS = 256;  // TMEM columns per slot: D1 [0,64) D2 [64,192) D3 [0,256)
 
-// TMEM columns: D1 [0, 64), D2 [64, 192), D3 halves [256, 384), [384, 512)
-constexpr uint32_t T_D1 = 0, T_D2 = 64, T_D3 = 256;
+// barrier indices (per slot s: index + s)
+constexpr int B_FULLX = 0, B_XRDY = 2, B_H1RDY = 4, B_H2RDY = 6, B_D1 = 8, B_D2 = 10, B_D3 = 12,
+              B_W = 14, B_DRAIN = 15;
 
 __device__ __forceinline__ uint4 ld_global_v4(const void* p) {
   return __ldg(reinterpret_cast<const uint4*>(p));
 }
 
-__global__ void __launch_bounds__(128, 1)
+// Epilogue of layers 1 and 2: TMEM row -> relu(x + b) -> bf16 row of the next
+// A operand (K = NCOL).
+template <int NCOL>
+__device__ __forceinline__ void enc_epi_rows(uint32_t taddr, const float* b, unsigned char* dst,
+                                             int row) {
+  float v[32];
+#pragma unroll
+  for (int h = 0; h < NCOL / 32; ++h) {
+    tmem_ld32(taddr + 32 * h, v);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      uint4 w;
+      const int j = 8 * c, o = 32 * h + j;
+      w.x = pack_relu_bf16(v[j + 0] + b[o + 0], v[j + 1] + b[o + 1]);
+      w.y = pack_relu_bf16(v[j + 2] + b[o + 2], v[j + 3] + b[o + 3]);
+      w.z = pack_relu_bf16(v[j + 4] + b[o + 4], v[j + 5] + b[o + 5]);
+      w.w = pack_relu_bf16(v[j + 6] + b[o + 6], v[j + 7] + b[o + 7]);
+      *reinterpret_cast<uint4*>(dst + kmajor_off(row, o, NCOL)) = w;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(E_THREADS, 1)
     encoder_tc_kernel(const float4* __restrict__ xyz, int n_pairs, const int* n_dev,
                       const unsigned char* __restrict__ img, float* __restrict__ feat,
                       int* __restrict__ err) {
@@ -68,141 +100,170 @@ __global__ void __launch_bounds__(128, 1)
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int n = n_dev ? min(*n_dev, n_pairs) : n_pairs;
   if ((int)blockIdx.x >= n) return;
+  const int my_pairs = (n - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
 
-  // resident weights and biases
-  for (int i = tid; i < E_IMG_BYTES / 16; i += 128)
-    reinterpret_cast<uint4*>(smem)[i] = ld_global_v4(img + 16 * (size_t)i);
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + E_CTRL);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + E_CTRL + 8);
-  int* s_cnt = reinterpret_cast<int*>(smem + E_CTRL + 16);
-  const uint32_t bar = smem_u32(mbar);
+  unsigned char* ctrl = smem + E_CTRL;
+  const uint32_t bar0 = smem_u32(ctrl + C_BAR);
+  auto BAR = [&](int i) { return bar0 + 8u * (uint32_t)i; };
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(ctrl + C_TMEM);
+  volatile int* abort = reinterpret_cast<volatile int*>(ctrl + C_ABORT);
+  int* s_cnt = reinterpret_cast<int*>(ctrl + C_CNT);
+
   if (tid == 0) {
-    mbar_init(bar, 1);
+    for (int s = 0; s < 2; ++s) {
+      mbar_init(BAR(B_FULLX + s), 1);
+      mbar_init(BAR(B_XRDY + s), 128);
+      mbar_init(BAR(B_H1RDY + s), 128);
+      mbar_init(BAR(B_H2RDY + s), 128);
+      mbar_init(BAR(B_D1 + s), 1);
+      mbar_init(BAR(B_D2 + s), 1);
+      mbar_init(BAR(B_D3 + s), 1);
+    }
+    mbar_init(BAR(B_W), 1);
+    mbar_init(BAR(B_DRAIN), 1);
+    *abort = 0;
     fence_mbar_init();
   }
   if (warp == 0) {
     tmem_alloc(smem_u32(tmem_slot), 512);
     tmem_relinquish();
   }
-  fence_async_smem();
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tbase = *tmem_slot;
-  const uint32_t lane_off = (uint32_t)(32 * warp) << 16;
   const float* b1 = reinterpret_cast<const float*>(smem + E_BIAS);
   const float* b2 = b1 + 64;
   const float* b3 = b2 + 128;
-  const uint32_t sW1 = smem_u32(smem + E_W1), sW2 = smem_u32(smem + E_W2);
-  const uint32_t sW3 = smem_u32(smem + E_W3), sX = smem_u32(smem + E_X);
-  const uint32_t sH1 = smem_u32(smem + E_H1), sH2 = smem_u32(smem + E_H2);
-  uint32_t phase = 0;
-  bool ok = true;
 
-  for (int p = blockIdx.x; p < n && ok; p += gridDim.x) {
-    // ---- stage the crop rows (row = tid) as bf16 hi/lo, K = 16
-    {
-      const float4 q = xyz[(size_t)p * ROWS + tid];
-      const bool valid = q.w > 0.5f;
-      const unsigned m = __ballot_sync(0xffffffffu, valid);
-      if (lane == 0) s_cnt[warp] = __popc(m);
-      const __nv_bfloat16 xh = __float2bfloat16_rn(q.x), yh = __float2bfloat16_rn(q.y),
-                          zh = __float2bfloat16_rn(q.z);
-      const float xl = q.x - __bfloat162float(xh), yl = q.y - __bfloat162float(yh),
-                  zl = q.z - __bfloat162float(zh);
-      uint4 c0, c1;
-      c0.x = pack_bf16(__bfloat162float(xh), __bfloat162float(yh));
-      c0.y = pack_bf16(__bfloat162float(zh), xl);
-      c0.z = pack_bf16(yl, zl);
-      c0.w = pack_bf16(__bfloat162float(xh), __bfloat162float(yh));
-      c1.x = pack_bf16(__bfloat162float(zh), 0.f);
-      c1.y = c1.z = c1.w = 0u;
-      *reinterpret_cast<uint4*>(smem + E_X + kmajor_off(tid, 0, 16)) = c0;
-      *reinterpret_cast<uint4*>(smem + E_X + kmajor_off(tid, 8, 16)) = c1;
-    }
-    fence_async_smem();
-    tc_fence_before();
-    __syncthreads();
-    const int cntA = s_cnt[0] + s_cnt[1], cntB = s_cnt[2] + s_cnt[3];
-    // ---- layer 1: D1[128 x 64] = X[128 x 16] . W1img^T
-    if (tid == 0) {
+  if (warp == 8) {
+    // ------------------------------------------------ MMA issuer + TMA producer
+    if (lane == 0) {
+      const uint32_t sW1 = smem_u32(smem + E_W1), sW2 = smem_u32(smem + E_W2);
+      const uint32_t sW3 = smem_u32(smem + E_W3);
+      // resident weights, in 4 bulk copies
+      mbar_expect_tx(BAR(B_W), E_IMG_BYTES);
+      for (int off = 0; off < E_IMG_BYTES; off += 32768) {
+        const int bytes = min(32768, E_IMG_BYTES - off);
+        bulk_g2s(smem_u32(smem + off), img + off, bytes, BAR(B_W));
+      }
+      int issued[2] = {0, 0};
+      auto load_pair = [&](int i) {
+        const int s = i & 1;
+        const int p = blockIdx.x + i * gridDim.x;
+        mbar_expect_tx(BAR(B_FULLX + s), ROWS * 16);
+        bulk_g2s(smem_u32(smem + E_SLOT0 + s * SLOT_BYTES + S_STG), xyz + (size_t)p * ROWS, ROWS * 16,
+                 BAR(B_FULLX + s));
+        ++issued[s];
+      };
+      load_pair(0);
+      if (my_pairs > 1) load_pair(1);
+      bool ok = mbar_wait_or_abort(BAR(B_W), 0, abort, WAIT_CYCLES);
       tc_fence_after();
-      mma_bf16(tbase + T_D1, sdesc(sX, 128, 256), sdesc(sW1, 128, 256), idesc_bf16(128, 64), 0);
-      mma_commit(bar);
-    }
-    ok = mbar_wait(bar, phase, WAIT_CYCLES);
-    phase ^= 1;
-    if (!__syncthreads_and(ok)) { ok = false; break; }
-    tc_fence_after();
-    {
-      float v[32];
+      const uint32_t id64 = idesc_bf16(128, 64), id128 = idesc_bf16(128, 128);
+      for (int r = 0; ok && 2 * r < my_pairs; ++r) {
+        const uint32_t ph = r & 1;
+        // layer 1 of both slots
+        for (int s = 0; s < 2 && ok; ++s) {
+          const int i = 2 * r + s;
+          if (i >= my_pairs) break;
+          if (!(ok = mbar_wait_or_abort(BAR(B_XRDY + s), ph, abort, WAIT_CYCLES))) break;
+          tc_fence_after();
+          if (i + 2 < my_pairs) load_pair(i + 2);  // staging buffer of slot s is free again
+          const uint32_t sX = smem_u32(smem + E_SLOT0 + s * SLOT_BYTES + S_X);
+          mma_bf16(tbase + s * SLOT_COLS, sdesc(sX, 128, 256), sdesc(sW1, 128, 256), id64, 0);
+          mma_commit(BAR(B_D1 + s));
+        }
+        // layer 2
+        for (int s = 0; s < 2 && ok; ++s) {
+          if (2 * r + s >= my_pairs) break;
+          if (!(ok = mbar_wait_or_abort(BAR(B_H1RDY + s), ph, abort, WAIT_CYCLES))) break;
+          tc_fence_after();
+          const uint32_t sH1 = smem_u32(smem + E_SLOT0 + s * SLOT_BYTES + S_H1);
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        tmem_ld32(tbase + lane_off + T_D1 + 32 * h, v);
+          for (int kk = 0; kk < 4; ++kk)
+            mma_bf16(tbase + s * SLOT_COLS + 64, sdesc(sH1 + 256 * kk, 128, 1024),
+                     sdesc(sW2 + 256 * kk, 128, 1024), id128, kk > 0);
+          mma_commit(BAR(B_D2 + s));
+        }
+        // layer 3, transposed: D3^T[128 ch x 128 pts] per half
+        for (int s = 0; s < 2 && ok; ++s) {
+          if (2 * r + s >= my_pairs) break;
+          if (!(ok = mbar_wait_or_abort(BAR(B_H2RDY + s), ph, abort, WAIT_CYCLES))) break;
+          tc_fence_after();
+          const uint32_t sH2 = smem_u32(smem + E_SLOT0 + s * SLOT_BYTES + S_H2);
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-          uint4 w;
-          const int j = 8 * c;
-          w.x = pack_bf16(fmaxf(v[j + 0] + b1[32 * h + j + 0], 0.f), fmaxf(v[j + 1] + b1[32 * h + j + 1], 0.f));
-          w.y = pack_bf16(fmaxf(v[j + 2] + b1[32 * h + j + 2], 0.f), fmaxf(v[j + 3] + b1[32 * h + j + 3], 0.f));
-          w.z = pack_bf16(fmaxf(v[j + 4] + b1[32 * h + j + 4], 0.f), fmaxf(v[j + 5] + b1[32 * h + j + 5], 0.f));
-          w.w = pack_bf16(fmaxf(v[j + 6] + b1[32 * h + j + 6], 0.f), fmaxf(v[j + 7] + b1[32 * h + j + 7], 0.f));
-          *reinterpret_cast<uint4*>(smem + E_H1 + kmajor_off(tid, 32 * h + j, 64)) = w;
+          for (int half = 0; half < 2; ++half)
+#pragma unroll
+            for (int kk = 0; kk < 8; ++kk)
+              mma_bf16(tbase + s * SLOT_COLS + 128 * half,
+                       sdesc(sW3 + half * 32768 + 256 * kk, 128, 2048),
+                       sdesc(sH2 + 256 * kk, 128, 2048), id128, kk > 0);
+          mma_commit(BAR(B_D3 + s));
         }
       }
-    }
-    fence_async_smem();
-    tc_fence_before();
-    __syncthreads();
-    // ---- layer 2: D2[128 x 128] = H1[128 x 64] . W2img^T
-    if (tid == 0) {
-      tc_fence_after();
-#pragma unroll
-      for (int kk = 0; kk < 4; ++kk)
-        mma_bf16(tbase + T_D2, sdesc(sH1 + 256 * kk, 128, 1024), sdesc(sW2 + 256 * kk, 128, 1024),
-                 idesc_bf16(128, 128), kk > 0);
-      mma_commit(bar);
-    }
-    ok = mbar_wait(bar, phase, WAIT_CYCLES);
-    phase ^= 1;
-    if (!__syncthreads_and(ok)) { ok = false; break; }
-    tc_fence_after();
-    {
-      float v[32];
-#pragma unroll
-      for (int h = 0; h < 4; ++h) {
-        tmem_ld32(tbase + lane_off + T_D2 + 32 * h, v);
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-          uint4 w;
-          const int j = 8 * c, o = 32 * h + j;
-          w.x = pack_bf16(fmaxf(v[j + 0] + b2[o + 0], 0.f), fmaxf(v[j + 1] + b2[o + 1], 0.f));
-          w.y = pack_bf16(fmaxf(v[j + 2] + b2[o + 2], 0.f), fmaxf(v[j + 3] + b2[o + 3], 0.f));
-          w.z = pack_bf16(fmaxf(v[j + 4] + b2[o + 4], 0.f), fmaxf(v[j + 5] + b2[o + 5], 0.f));
-          w.w = pack_bf16(fmaxf(v[j + 6] + b2[o + 6], 0.f), fmaxf(v[j + 7] + b2[o + 7], 0.f));
-          *reinterpret_cast<uint4*>(smem + E_H2 + kmajor_off(tid, o, 128)) = w;
-        }
+      if (*abort) {
+        // drain: wait (bounded) for every MMA and bulk copy this thread issued
+        mma_commit(BAR(B_DRAIN));
+        mbar_wait(BAR(B_DRAIN), 0, WAIT_CYCLES);
+        for (int s = 0; s < 2; ++s)
+          if (issued[s] > 0) mbar_wait(BAR(B_FULLX + s), (issued[s] - 1) & 1, WAIT_CYCLES);
       }
     }
-    fence_async_smem();
-    tc_fence_before();
-    __syncthreads();
-    // ---- layer 3 (transposed): D3^T[128 ch x 128 pts] = W3img[half] . H2^T
-    if (tid == 0) {
+    __syncwarp();
+  } else {
+    // ------------------------------------------------ epilogue warpgroup of slot s
+    const int s = warp >> 2, row = tid & 127, wq = warp & 3;
+    unsigned char* slot = smem + E_SLOT0 + s * SLOT_BYTES;
+    const uint32_t lane_off = (uint32_t)(32 * wq) << 16;
+    const uint32_t tslot = tbase + s * SLOT_COLS + lane_off;
+    int* cnt_s = s_cnt + 4 * s;
+    bool ok = mbar_wait_or_abort(BAR(B_W), 0, abort, WAIT_CYCLES);
+    for (int j = 0; ok; ++j) {
+      const int i = 2 * j + s;
+      if (i >= my_pairs) break;
+      const int p = blockIdx.x + i * gridDim.x;
+      const uint32_t ph = j & 1;
+      // crop rows -> bf16 hi/lo X tile
+      if (!(ok = mbar_wait_or_abort(BAR(B_FULLX + s), ph, abort, WAIT_CYCLES))) break;
+      {
+        const float4 q = reinterpret_cast<const float4*>(slot + S_STG)[row];
+        const unsigned m = __ballot_sync(0xffffffffu, q.w > 0.5f);
+        if (lane == 0) cnt_s[wq] = __popc(m);
+        const __nv_bfloat16 xh = __float2bfloat16_rn(q.x), yh = __float2bfloat16_rn(q.y),
+                            zh = __float2bfloat16_rn(q.z);
+        const float fx = __bfloat162float(xh), fy = __bfloat162float(yh), fz = __bfloat162float(zh);
+        uint4 c0, c1;
+        c0.x = pack_bf16(fx, fy);
+        c0.y = pack_bf16(fz, q.x - fx);
+        c0.z = pack_bf16(q.y - fy, q.z - fz);
+        c0.w = pack_bf16(fx, fy);
+        c1.x = pack_bf16(fz, 0.f);
+        c1.y = c1.z = c1.w = 0u;
+        *reinterpret_cast<uint4*>(slot + S_X + kmajor_off(row, 0, 16)) = c0;
+        *reinterpret_cast<uint4*>(slot + S_X + kmajor_off(row, 8, 16)) = c1;
+      }
+      fence_async_smem();
+      tc_fence_before();
+      mbar_arrive(BAR(B_XRDY + s));
+      // layer 1 epilogue
+      if (!(ok = mbar_wait_or_abort(BAR(B_D1 + s), ph, abort, WAIT_CYCLES))) break;
       tc_fence_after();
-#pragma unroll
-      for (int half = 0; half < 2; ++half)
-#pragma unroll
-        for (int kk = 0; kk < 8; ++kk)
-          mma_bf16(tbase + T_D3 + 128 * half, sdesc(sW3 + half * 32768 + 256 * kk, 128, 2048),
-                   sdesc(sH2 + 256 * kk, 128, 2048), idesc_bf16(128, 128), kk > 0);
-      mma_commit(bar);
-    }
-    ok = mbar_wait(bar, phase, WAIT_CYCLES);
-    phase ^= 1;
-    if (!__syncthreads_and(ok)) { ok = false; break; }
-    tc_fence_after();
-    {
+      enc_epi_rows<64>(tslot + 0, b1, slot + S_H1, row);
+      fence_async_smem();
+      tc_fence_before();
+      mbar_arrive(BAR(B_H1RDY + s));
+      // layer 2 epilogue
+      if (!(ok = mbar_wait_or_abort(BAR(B_D2 + s), ph, abort, WAIT_CYCLES))) break;
+      tc_fence_after();
+      enc_epi_rows<128>(tslot + 64, b2, slot + S_H2, row);
+      fence_async_smem();
+      tc_fence_before();
+      mbar_arrive(BAR(B_H2RDY + s));
+      // layer 3 epilogue: masked max over the valid points of each object
+      if (!(ok = mbar_wait_or_abort(BAR(B_D3 + s), ph, abort, WAIT_CYCLES))) break;
+      tc_fence_after();
+      const int cntA = cnt_s[0] + cnt_s[1], cntB = cnt_s[2] + cnt_s[3];
       float v[32];
 #pragma unroll
       for (int half = 0; half < 2; ++half) {
@@ -210,28 +271,31 @@ __global__ void __launch_bounds__(128, 1)
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           const int cnt = q < 2 ? cntA : cntB;
-          const int c0 = 32 * (q & 1);  // first point slot of this chunk within its object
+          const int c0 = 32 * (q & 1);
           if (c0 < cnt) {
-            tmem_ld32(tbase + lane_off + T_D3 + 128 * half + 32 * q, v);
+            tmem_ld32(tslot + 128 * half + 32 * q, v);
             float m = -INFINITY;
+            if (c0 + 32 <= cnt) {
 #pragma unroll
-            for (int j = 0; j < 32; ++j) m = fmaxf(m, (c0 + j < cnt) ? v[j] : -INFINITY);
+              for (int jj = 0; jj < 32; ++jj) m = fmaxf(m, v[jj]);
+            } else {
+#pragma unroll
+              for (int jj = 0; jj < 32; ++jj) m = fmaxf(m, (c0 + jj < cnt) ? v[jj] : -INFINITY);
+            }
             if (q < 2) mA = fmaxf(mA, m);
             else mB = fmaxf(mB, m);
           }
         }
-        const int ch = 128 * half + tid;
+        const int ch = 128 * half + row;
         const float bias = b3[ch];
         feat[(size_t)p * 512 + ch] = cntA > 0 ? fmaxf(mA + bias, 0.f) : 0.f;
         feat[(size_t)p * 512 + 256 + ch] = cntB > 0 ? fmaxf(mB + bias, 0.f) : 0.f;
       }
+      tc_fence_before();
     }
-    tc_fence_before();
-    __syncthreads();
   }
-  if (!ok && tid == 0) atomicOr(err, 2);
-  tc_fence_before();
   __syncthreads();
+  if (tid == 0 && *abort) atomicOr(err, 2);
   if (warp == 0) {
     tc_fence_after();
     tmem_dealloc(tbase, 512);
@@ -534,7 +598,7 @@ int run_network_tc(locc_handle* h, const float4* xyz, int n_pairs, const int* n_
   }
   float* feat = feat_out ? feat_out : h->d_feat;
   const int grid_e = std::min(n_pairs, h->n_sm);
-  encoder_tc_kernel<<<grid_e, 128, E_SMEM, stream>>>(xyz, n_pairs, n_dev, h->wtc_enc, feat,
+  encoder_tc_kernel<<<grid_e, E_THREADS, E_SMEM, stream>>>(xyz, n_pairs, n_dev, h->wtc_enc, feat,
                                                      h->d_err);
   if (cudaGetLastError() != cudaSuccess) {
     set_error("encoder_tc_kernel launch failed");
