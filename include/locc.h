@@ -217,6 +217,50 @@ int locc_detect_noalloc(locc_handle *h, const float *poses,
                         const int32_t *pairs, int32_t n_pairs, float *out,
                         void *stream);
 
+/* ---------------------------------------------------------------- training
+ * The crop network is trained on the GPU with this library's own forward and
+ * backward kernels (float32): binary cross-entropy on the collision logit plus
+ * alpha * mean(f^2) on the pooled embedding (Sec. III-A loss, alpha = 0.5),
+ * regression terms on the contact point, normal and depth (collisions only for
+ * point and normal; Huber loss on depth), Adam with bias correction (Sec. IV-A
+ * and the hyper-parameter table: lr 1e-3, beta1 0.9, beta2 0.999, eps 1e-8). */
+typedef struct locc_trainer locc_trainer;
+typedef struct {
+  float lr, beta1, beta2, eps;       /* Adam */
+  float w_pt, w_n, w_d, huber_beta;  /* regression weights, Huber width */
+  float alpha;                       /* embedding regulariser */
+} locc_train_config;
+
+/* Trainer for the handle's network; parameters start from the handle's
+ * current weights.  max_batch: largest n_pairs of a step.  Blocking. */
+int locc_trainer_create(locc_handle *h, int32_t max_batch,
+                        const locc_train_config *cfg, locc_trainer **out);
+
+/* One step on n_pairs (1..max_batch) pairs, device pointers:
+ *   poses / obj_shape / pairs: as locc_detect;
+ *   targets: float32 [n_pairs][8] world-frame {label (0/1), contact point xyz,
+ *            normal xyz (A towards B), depth (> 0 overlap, < 0 gap)};
+ *   rot:     float32 [n_pairs][9] row-major rotation of each pair's canonical
+ *            crop frame (rotation augmentation, Sec. III-A), or NULL;
+ *   loss_out: device float32 [1] mean loss of the batch, or NULL;
+ *   update:  nonzero -> Adam step; zero -> gradients only.
+ * Asynchronous on `stream`. */
+int locc_train_step(locc_trainer *t, const float *poses, const int32_t *obj_shape,
+                    int32_t n_obj, const int32_t *pairs, int32_t n_pairs,
+                    const float *targets, const float *rot, float *loss_out,
+                    int32_t update, void *stream);
+
+/* Copy the last step's gradient / the current parameters (device float32
+ * [LOCC_N_PARAMS], per layer W[out][in] then b[out]), or set the parameters. */
+int locc_trainer_grad(locc_trainer *t, float *grad_out, void *stream);
+int locc_trainer_params(locc_trainer *t, float *params_out, void *stream);
+int locc_trainer_set_params(locc_trainer *t, const float *params, void *stream);
+
+/* Install the trainer's parameters as the handle's inference weights (all
+ * precisions); blocking. */
+int locc_trainer_commit(locc_trainer *t);
+void locc_trainer_destroy(locc_trainer *t);
+
 /* Release all device and host memory of the handle (blocking). */
 void locc_destroy(locc_handle *h);
 

@@ -19,7 +19,7 @@ from .abi import LoccError, LOCC_FP32, LOCC_BF16, LOCC_FP8, PRECISIONS
 KMAX = 64
 OUT_DIM = 8
 
-__all__ = ["Detector", "LoccError", "LOCC_FP32", "LOCC_BF16", "LOCC_FP8", "weights",
+__all__ = ["Detector", "Trainer", "LoccError", "LOCC_FP32", "LOCC_BF16", "LOCC_FP8", "weights",
            "abi", "KMAX", "OUT_DIM"]
 
 
@@ -211,3 +211,68 @@ class Detector:
                                            abi.ptr(n), M, abi.ptr(out), abi.stream_ptr(stream)))
         m = min(int(n[0]), M)
         return pairs_out[:m], out[:m], int(n[0])
+
+
+class Trainer:
+    """Owns one ``locc_trainer`` (GPU training of a Detector's network)."""
+
+    def __init__(self, det: "Detector", max_batch: int, lr=1e-3, beta1=0.9, beta2=0.999,
+                 eps=1e-8, w_pt=1.0, w_n=1.0, w_d=1.0, huber_beta=0.01, alpha=0.5):
+        self._lib = abi.load()
+        self.det = det
+        self.max_batch = int(max_batch)
+        cfg = abi.TrainConfig(lr, beta1, beta2, eps, w_pt, w_n, w_d, huber_beta, alpha)
+        self._t = ctypes.c_void_p()
+        abi.check(self._lib.locc_trainer_create(det._h, self.max_batch, ctypes.byref(cfg),
+                                                ctypes.byref(self._t)))
+
+    def close(self) -> None:
+        if getattr(self, "_t", None) is not None and self._t.value:
+            self._lib.locc_trainer_destroy(self._t)
+            self._t = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, poses, obj_shape, pairs, targets, rot=None, update=True, loss_out=None,
+             stream=None):
+        """One step; returns the device scalar holding the batch's mean loss."""
+        import torch
+        dev = self.det.device
+        _need(poses, torch.float32, "poses", dev)
+        _need(obj_shape, torch.int32, "obj_shape", dev)
+        _need(pairs, torch.int32, "pairs", dev)
+        _need(targets, torch.float32, "targets", dev)
+        if rot is not None:
+            _need(rot, torch.float32, "rot", dev)
+        if loss_out is None:
+            loss_out = torch.zeros(1, dtype=torch.float32, device=pairs.device)
+        abi.check(self._lib.locc_train_step(self._t, abi.ptr(poses), abi.ptr(obj_shape),
+                                            poses.shape[0], abi.ptr(pairs), pairs.shape[0],
+                                            abi.ptr(targets), abi.ptr(rot), abi.ptr(loss_out),
+                                            int(bool(update)), abi.stream_ptr(stream)))
+        return loss_out
+
+    def grad(self, stream=None):
+        import torch
+        g = torch.empty(weights.N_PARAMS, dtype=torch.float32, device=f"cuda:{self.det.device}")
+        abi.check(self._lib.locc_trainer_grad(self._t, abi.ptr(g), abi.stream_ptr(stream)))
+        return g
+
+    def params(self, stream=None):
+        import torch
+        p = torch.empty(weights.N_PARAMS, dtype=torch.float32, device=f"cuda:{self.det.device}")
+        abi.check(self._lib.locc_trainer_params(self._t, abi.ptr(p), abi.stream_ptr(stream)))
+        return p
+
+    def set_params(self, p, stream=None) -> None:
+        import torch
+        _need(p, torch.float32, "params", self.det.device)
+        abi.check(self._lib.locc_trainer_set_params(self._t, abi.ptr(p), abi.stream_ptr(stream)))
+
+    def commit(self) -> None:
+        """Install the trained parameters as the detector's inference weights."""
+        abi.check(self._lib.locc_trainer_commit(self._t))

@@ -24,7 +24,9 @@ ERRORS = {-1: "INVALID_ARG", -2: "OOM", -3: "CUDA", -4: "TIMEOUT",
 EXPORTS = ["locc_create", "locc_set_precision", "locc_detect", "locc_detect_host",
            "locc_crop", "locc_network", "locc_broadphase", "locc_step", "locc_step_host",
            "locc_reserve", "locc_profile", "locc_stage_times", "locc_status", "locc_destroy",
-           "locc_last_error", "locc_detect_noalloc"]
+           "locc_last_error", "locc_detect_noalloc", "locc_trainer_create", "locc_train_step",
+           "locc_trainer_grad", "locc_trainer_params", "locc_trainer_set_params",
+           "locc_trainer_commit", "locc_trainer_destroy"]
 NOALLOC_MAX_PAIRS = 1024
 
 
@@ -32,6 +34,11 @@ class LoccError(RuntimeError):
     def __init__(self, code: int, msg: str):
         super().__init__(f"locc error {code} ({ERRORS.get(code, '?')}): {msg}")
         self.code = code
+
+
+class TrainConfig(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_float) for n in
+                ("lr", "beta1", "beta2", "eps", "w_pt", "w_n", "w_d", "huber_beta", "alpha")]
 
 
 class _ShapeLibrary(ctypes.Structure):
@@ -72,11 +79,19 @@ def load(build_if_needed: bool = True) -> ctypes.CDLL:
         lib.locc_profile.argtypes = [P, ctypes.c_int]
         lib.locc_stage_times.argtypes = [P, P, ctypes.c_int]
         lib.locc_status.argtypes = [P, P]
+        lib.locc_trainer_create.argtypes = [P, I, ctypes.POINTER(TrainConfig), ctypes.POINTER(P)]
+        lib.locc_train_step.argtypes = [P, P, P, I, P, I, P, P, P, I, P]
+        lib.locc_trainer_grad.argtypes = [P, P, P]
+        lib.locc_trainer_params.argtypes = [P, P, P]
+        lib.locc_trainer_set_params.argtypes = [P, P, P]
+        lib.locc_trainer_commit.argtypes = [P]
+        lib.locc_trainer_destroy.argtypes = [P]
+        lib.locc_trainer_destroy.restype = None
         lib.locc_destroy.argtypes = [P]
         lib.locc_destroy.restype = None
         lib.locc_last_error.restype = ctypes.c_char_p
         for name in EXPORTS:
-            if name not in ("locc_destroy", "locc_last_error"):
+            if name not in ("locc_destroy", "locc_last_error", "locc_trainer_destroy"):
                 getattr(lib, name).restype = ctypes.c_int
         _lib = lib
         return lib

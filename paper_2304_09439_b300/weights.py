@@ -57,3 +57,18 @@ def flat(layers) -> np.ndarray:
     return np.concatenate([np.concatenate([np.asarray(w, np.float32).ravel(),
                                            np.asarray(b, np.float32)])
                            for w, b in layers])
+
+
+def from_flat(flat) -> list:
+    """Flat W1 b1 ... W6 b6 -> [(W [out,in], b [out]) x 6] float32."""
+    flat = np.asarray(flat, np.float32).ravel()
+    if flat.size != N_PARAMS:
+        raise ValueError("wrong parameter count")
+    out, o = [], 0
+    for fi, fo in LAYER_DIMS:
+        w = flat[o:o + fi * fo].reshape(fo, fi).copy()
+        o += fi * fo
+        b = flat[o:o + fo].copy()
+        o += fo
+        out.append((w, b))
+    return out
