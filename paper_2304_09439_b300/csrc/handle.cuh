@@ -23,6 +23,9 @@ struct locc_handle {
   size_t wtc_bytes = 0;
   const unsigned char* wtc_enc = nullptr;   // encoder image (W1 hi/lo, W2, W3, biases)
   const unsigned char* wtc_head = nullptr;  // head image (Wh3, biases, Wh1 / Wh2 K-chunks)
+  void* d_wf8 = nullptr;                    // e4m3 images with per-channel scales
+  const unsigned char* wf8_enc = nullptr;
+  const unsigned char* wf8_head = nullptr;
   // per-call scratch (device), capacity cap_pairs
   int cap_pairs = 0;
   float4* d_xyz = nullptr;
@@ -62,6 +65,10 @@ DevLibrary dev_library(const locc_handle* h);
 int run_network(locc_handle* h, const float4* xyz, int n_pairs, const int* n_dev,
                 const PairInputs* in, const float4* centre, float* out, float* y_raw,
                 float* feat_out, cudaStream_t stream, cudaEvent_t mid);
+int upload_fp8_params(locc_handle* h, const std::vector<float>& params);
+int run_network_fp8(locc_handle* h, const float4* xyz, int n_pairs, const int* n_dev,
+                    const PairInputs* in, const float4* centre, float* out, float* y_raw,
+                    float* feat_out, cudaStream_t stream, cudaEvent_t mid);
 int run_network_tc(locc_handle* h, const float4* xyz, int n_pairs, const int* n_dev,
                    const PairInputs* in, const float4* centre, float* out, float* y_raw,
                    float* feat_out, cudaStream_t stream, cudaEvent_t mid);

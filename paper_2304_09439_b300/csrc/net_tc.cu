@@ -263,6 +263,8 @@ __global__ void __launch_bounds__(E_THREADS, 1)
       // layer 3 epilogue: masked max over the valid points of each object
       if (!(ok = mbar_wait_or_abort(BAR(B_D3 + s), ph, abort, WAIT_CYCLES))) break;
       tc_fence_after();
+      // crop counts (and row scales) written by other threads of this warpgroup
+      asm volatile("bar.sync %0, 128;" ::"r"(1 + s) : "memory");
       const int cntA = cnt_s[0] + cnt_s[1], cntB = cnt_s[2] + cnt_s[3];
       float v[32];
 #pragma unroll
@@ -581,10 +583,8 @@ int upload_tc_params(locc_handle* h, const std::vector<float>& params) {
 int run_network_tc(locc_handle* h, const float4* xyz, int n_pairs, const int* n_dev,
                    const PairInputs* in, const float4* centre, float* out, float* y_raw,
                    float* feat_out, cudaStream_t stream, cudaEvent_t mid) {
-  if (h->prec != LOCC_BF16) {
-    set_error("FP8 tensor-core path not available in this build");
-    return LOCC_ERR_INVALID_ARG;
-  }
+  if (h->prec == LOCC_FP8)
+    return run_network_fp8(h, xyz, n_pairs, n_dev, in, centre, out, y_raw, feat_out, stream, mid);
   static bool attr = false;
   if (!attr) {
     if (cudaFuncSetAttribute(encoder_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -84,14 +84,17 @@ int upload_params(locc_handle* h, const std::vector<float>& params) {
     h->fp32.wt[l] = h->d_w32 + offw[l];
     h->fp32.b[l] = h->d_w32 + offb[l];
   }
-  return upload_tc_params(h, params);
+  const int st = upload_tc_params(h, params);
+  if (st) return st;
+  return upload_fp8_params(h, params);
 }
 
 void free_params(locc_handle* h) {
   cudaFree(h->d_w32);
   cudaFree(h->d_wtc);
   cudaFree(h->d_feat_tc);
-  h->d_w32 = nullptr, h->d_wtc = nullptr, h->d_feat_tc = nullptr;
+  cudaFree(h->d_wf8);
+  h->d_w32 = nullptr, h->d_wtc = nullptr, h->d_feat_tc = nullptr, h->d_wf8 = nullptr;
 }
 
 }  // namespace locc
