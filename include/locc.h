@@ -183,13 +183,34 @@ int locc_step_host(locc_handle *h, const float *poses, const int32_t *obj_shape,
  * per call (blocking).  Later calls within these sizes allocate nothing. */
 int locc_reserve(locc_handle *h, int32_t max_pairs, int32_t max_envs);
 
-/* Stage timing: with enable != 0, later locc_step calls record CUDA events
- * on their stream around each stage.  locc_stage_times waits for the last
- * step's final event and writes up to n durations in milliseconds:
- * [0] broadphase, [1] crop gather, [2] encoder, [3] head + epilogue.
- * Returns the number written (>= 0) or an error code. */
+/* Stage timing: with enable != 0, later locc_step / locc_detect calls record
+ * CUDA events on their streams around each stage.  locc_stage_times waits for
+ * the last call's final event and writes up to n durations in milliseconds:
+ * [0] broadphase, [1] crop gather, [2] encoder, [3] head + epilogue (each
+ * summed over the pipeline chunks; chunks of different stages overlap), [4]
+ * the whole call.  Returns the number written (>= 0) or an error code. */
 int locc_profile(locc_handle *h, int enable);
 int locc_stage_times(locc_handle *h, float *ms_out, int n);
+
+/* Pipelining of locc_detect / locc_step: the pairs are cut into n_chunks
+ * (1..16) parts; the crop gather of part i + 1 runs on the caller's stream
+ * while the network of part i runs on a stream owned by the handle (forked
+ * from and joined back into the caller's stream, so the call stays
+ * capturable).  crop_ctas_per_sm caps the resident crop CTAs per SM (0 = no
+ * cap) so they fit beside a network CTA.  Defaults: 1 chunk, no cap.  Results
+ * do not depend on these settings. */
+int locc_set_pipeline(locc_handle *h, int32_t n_chunks, int32_t crop_ctas_per_sm);
+
+/* Autotuner: times locc_step (reps repetitions after one warm-up) for each
+ * pipelining setting in {1, 2, 4, 8} chunks x {no cap, 8, 6, 4} crop CTAs per
+ * SM on the given step inputs (as locc_step), keeps the fastest and writes it
+ * to best_out[2] = {n_chunks, crop_ctas_per_sm} and its mean step time in ms
+ * to *best_ms_out (either may be NULL).  Blocking. */
+int locc_autotune(locc_handle *h, const float *poses, const int32_t *obj_shape,
+                  int32_t n_obj, const int32_t *env_offsets, int32_t n_env,
+                  int32_t *pairs_out, int32_t *n_pairs_out, int32_t max_pairs,
+                  float *out, int32_t reps, int32_t *best_out, float *best_ms_out,
+                  void *stream);
 
 /* Wait for `stream`, then report and clear the device error flag:
  * 0 or LOCC_ERR_BAD_INDEX. */

@@ -82,12 +82,38 @@ class Detector:
     def profile(self, enable: bool = True) -> None:
         abi.check(self._lib.locc_profile(self._h, int(bool(enable))))
 
-    def stage_times(self):
-        """Durations (ms) of the last step's stages: broadphase, crop, encoder,
-        head."""
+    def set_pipeline(self, n_chunks: int, crop_ctas_per_sm: int = 0) -> None:
+        abi.check(self._lib.locc_set_pipeline(self._h, int(n_chunks), int(crop_ctas_per_sm)))
+
+    def autotune(self, poses, obj_shape, env_offsets, max_pairs: int, reps: int = 3,
+                 pairs_out=None, n_pairs_out=None, out=None, stream=None):
+        """Pick the fastest pipelining setting for these step inputs; returns
+        ((n_chunks, crop_ctas_per_sm), ms per step)."""
         import numpy as np
-        ms = np.zeros(4, np.float32)
-        n = self._lib.locc_stage_times(self._h, abi.ptr(ms), 4)
+        import torch
+        dev = poses.device
+        M = int(max_pairs)
+        if pairs_out is None:
+            pairs_out = torch.empty((max(M, 1), 2), dtype=torch.int32, device=dev)
+        if n_pairs_out is None:
+            n_pairs_out = torch.zeros(1, dtype=torch.int32, device=dev)
+        if out is None:
+            out = torch.empty((max(M, 1), OUT_DIM), dtype=torch.float32, device=dev)
+        best = np.zeros(2, np.int32)
+        ms = np.zeros(1, np.float32)
+        abi.check(self._lib.locc_autotune(self._h, abi.ptr(poses), abi.ptr(obj_shape),
+                                          poses.shape[0], abi.ptr(env_offsets),
+                                          env_offsets.shape[0] - 1, abi.ptr(pairs_out),
+                                          abi.ptr(n_pairs_out), M, abi.ptr(out), int(reps),
+                                          abi.ptr(best), abi.ptr(ms), abi.stream_ptr(stream)))
+        return (int(best[0]), int(best[1])), float(ms[0])
+
+    def stage_times(self):
+        """Durations (ms) of the last call's stages: broadphase, crop, encoder,
+        head (each summed over pipeline chunks), whole call."""
+        import numpy as np
+        ms = np.zeros(5, np.float32)
+        n = self._lib.locc_stage_times(self._h, abi.ptr(ms), 5)
         if n < 0:
             abi.check(n)
         return ms[:n]

@@ -26,7 +26,7 @@ EXPORTS = ["locc_create", "locc_set_precision", "locc_detect", "locc_detect_host
            "locc_reserve", "locc_profile", "locc_stage_times", "locc_status", "locc_destroy",
            "locc_last_error", "locc_detect_noalloc", "locc_trainer_create", "locc_train_step",
            "locc_trainer_grad", "locc_trainer_params", "locc_trainer_set_params",
-           "locc_trainer_commit", "locc_trainer_destroy"]
+           "locc_trainer_commit", "locc_trainer_destroy", "locc_set_pipeline", "locc_autotune"]
 NOALLOC_MAX_PAIRS = 1024
 
 
@@ -76,6 +76,8 @@ def load(build_if_needed: bool = True) -> ctypes.CDLL:
         lib.locc_step.argtypes = [P, P, P, I, P, I, P, P, I, P, P]
         lib.locc_step_host.argtypes = [P, P, P, I, P, I, P, P, I, P, P]
         lib.locc_reserve.argtypes = [P, I, I]
+        lib.locc_set_pipeline.argtypes = [P, I, I]
+        lib.locc_autotune.argtypes = [P, P, P, I, P, I, P, P, I, P, I, P, P, P]
         lib.locc_profile.argtypes = [P, ctypes.c_int]
         lib.locc_stage_times.argtypes = [P, P, ctypes.c_int]
         lib.locc_status.argtypes = [P, P]

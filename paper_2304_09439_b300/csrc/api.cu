@@ -121,20 +121,79 @@ DevLibrary dev_library(const locc_handle* h) {
 }
 
 // Network on the crops in h->d_xyz (or `xyz`): feat -> y / out.
-int run_network(locc_handle* h, const float4* xyz, int n_pairs, const int* n_dev,
-                const PairInputs* in, const float4* centre, float* out, float* y_raw,
-                float* feat_out, cudaStream_t stream, cudaEvent_t mid) {
+int run_network(locc_handle* h, const float4* xyz, const PairRange& rg, const PairInputs* in,
+                const float4* centre, float* out, float* y_raw, float* feat_out,
+                cudaStream_t stream, cudaEvent_t mid) {
   float* feat = feat_out ? feat_out : h->d_feat;
   switch (h->prec) {
     case LOCC_FP32:
-      CUDA_TRY(launch_encoder_fp32(xyz, n_pairs, n_dev, h->fp32, feat, h->n_sm, stream));
+      CUDA_TRY(launch_encoder_fp32(xyz, rg, h->fp32, feat, h->n_sm, stream));
       if (mid) CUDA_TRY(cudaEventRecord(mid, stream));
-      CUDA_TRY(launch_head_fp32(feat, n_pairs, n_dev, h->fp32, in, centre, out, y_raw, h->n_sm,
-                                stream));
+      CUDA_TRY(launch_head_fp32(feat, rg, h->fp32, in, centre, out, y_raw, h->n_sm, stream));
       return LOCC_OK;
     default:
-      return run_network_tc(h, xyz, n_pairs, n_dev, in, centre, out, y_raw, feat_out, stream, mid);
+      return run_network_tc(h, xyz, rg, in, centre, out, y_raw, feat_out, stream, mid);
   }
+}
+
+int ensure_pipeline(locc_handle* h) {
+  if (h->aux) return LOCC_OK;
+  CUDA_TRY(cudaStreamCreateWithFlags(&h->aux, cudaStreamNonBlocking));
+  CUDA_TRY(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+  CUDA_TRY(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
+  for (int i = 0; i < LOCC_MAX_CHUNKS; ++i)
+    CUDA_TRY(cudaEventCreateWithFlags(&h->ev_crop[i], cudaEventDisableTiming));
+  return LOCC_OK;
+}
+
+// Crop gather and network for the pairs [0, n) (n = min(*n_dev, n_cap), or
+// n_cap).  With h->n_chunks > 1 the range is cut into chunks: the crop of
+// chunk i runs on `s`, the network of chunk i on h->aux after that crop, so
+// the crop of chunk i + 1 overlaps the network of chunk i; the two streams
+// fork from and join back into `s` (capturable in a CUDA graph).
+int run_path(locc_handle* h, const PairInputs& in, int n_cap, const int* n_dev, float* out,
+             cudaStream_t s) {
+  int C = std::max(1, std::min(h->n_chunks, LOCC_MAX_CHUNKS));
+  if (n_cap < 4096) C = 1;
+  const bool prof = h->profiling;
+  const DevLibrary lib = dev_library(h);
+  h->prof_chunks = C;
+  if (C == 1) {
+    const PairRange rg = whole_range(n_cap, n_dev);
+    if (prof) CUDA_TRY(cudaEventRecord(h->ev_c0[0], s));
+    CUDA_TRY(launch_crop(lib, in, rg, h->radius, h->d_xyz, nullptr, h->d_cnt, h->d_centre, h->d_err,
+                         h->n_sm, h->crop_cap, s));
+    if (prof) {
+      CUDA_TRY(cudaEventRecord(h->ev_c1[0], s));
+      CUDA_TRY(cudaEventRecord(h->ev_e0[0], s));
+    }
+    const int st = run_network(h, h->d_xyz, rg, &in, h->d_centre, out, nullptr, nullptr, s,
+                               prof ? h->ev_e1[0] : nullptr);
+    if (st) return st;
+    if (prof) CUDA_TRY(cudaEventRecord(h->ev_h1[0], s));
+    return LOCC_OK;
+  }
+  int st = ensure_pipeline(h);
+  if (st) return st;
+  CUDA_TRY(cudaEventRecord(h->ev_fork, s));
+  CUDA_TRY(cudaStreamWaitEvent(h->aux, h->ev_fork, 0));
+  for (int i = 0; i < C; ++i) {
+    const PairRange rg{n_cap, n_dev, i, C};
+    if (prof) CUDA_TRY(cudaEventRecord(h->ev_c0[i], s));
+    CUDA_TRY(launch_crop(lib, in, rg, h->radius, h->d_xyz, nullptr, h->d_cnt, h->d_centre, h->d_err,
+                         h->n_sm, h->crop_cap, s));
+    if (prof) CUDA_TRY(cudaEventRecord(h->ev_c1[i], s));
+    CUDA_TRY(cudaEventRecord(h->ev_crop[i], s));
+    CUDA_TRY(cudaStreamWaitEvent(h->aux, h->ev_crop[i], 0));
+    if (prof) CUDA_TRY(cudaEventRecord(h->ev_e0[i], h->aux));
+    st = run_network(h, h->d_xyz, rg, &in, h->d_centre, out, nullptr, nullptr, h->aux,
+                     prof ? h->ev_e1[i] : nullptr);
+    if (st) return st;
+    if (prof) CUDA_TRY(cudaEventRecord(h->ev_h1[i], h->aux));
+  }
+  CUDA_TRY(cudaEventRecord(h->ev_join, h->aux));
+  CUDA_TRY(cudaStreamWaitEvent(s, h->ev_join, 0));
+  return LOCC_OK;
 }
 
 }  // namespace locc
@@ -271,43 +330,117 @@ int locc_step(locc_handle* h, const float* poses, const int32_t* obj_shape, int3
   int st = ensure_capacity(h, max_pairs, s);
   if (st) return st;
   const bool prof = h->profiling;
-  if (prof) CUDA_TRY(cudaEventRecord(h->ev[0], s));
+  h->prof_chunks = 0;
+  if (prof) CUDA_TRY(cudaEventRecord(h->ev_bp0, s));
   st = broadphase_run(h, poses, obj_shape, env_offsets, n_env, pairs_out, n_pairs_out, max_pairs, s);
   if (st) return st == LOCC_ERR_CUDA ? fail(st, "broadphase launch failed") : st;
-  if (prof) CUDA_TRY(cudaEventRecord(h->ev[1], s));
+  if (prof) CUDA_TRY(cudaEventRecord(h->ev_bp1, s));
   if (max_pairs > 0 && n_env > 0) {
     PairInputs in{poses, obj_shape, pairs_out, n_obj, max_pairs};
-    CUDA_TRY(launch_crop(dev_library(h), in, n_pairs_out, h->radius, h->d_xyz, nullptr, h->d_cnt,
-                         h->d_centre, h->d_err, h->n_sm, s));
-    if (prof) CUDA_TRY(cudaEventRecord(h->ev[2], s));
-    st = run_network(h, h->d_xyz, max_pairs, n_pairs_out, &in, h->d_centre, out, nullptr, nullptr,
-                     s, prof ? h->ev[3] : nullptr);
+    st = run_path(h, in, max_pairs, n_pairs_out, out, s);
     if (st) return st;
-  } else if (prof) {
-    CUDA_TRY(cudaEventRecord(h->ev[2], s));
-    CUDA_TRY(cudaEventRecord(h->ev[3], s));
   }
-  if (prof) CUDA_TRY(cudaEventRecord(h->ev[4], s));
+  if (prof) CUDA_TRY(cudaEventRecord(h->ev_end, s));
   return LOCC_OK;
 }
 
 int locc_profile(locc_handle* h, int enable) {
   if (!h) return fail(LOCC_ERR_INVALID_ARG, "handle is NULL");
-  if (enable && !h->ev[0]) {
-    for (int i = 0; i < 5; ++i) CUDA_TRY(cudaEventCreate(&h->ev[i]));
+  if (enable && !h->ev_bp0) {
+    CUDA_TRY(cudaEventCreate(&h->ev_bp0));
+    CUDA_TRY(cudaEventCreate(&h->ev_bp1));
+    CUDA_TRY(cudaEventCreate(&h->ev_end));
+    for (int i = 0; i < LOCC_MAX_CHUNKS; ++i) {
+      CUDA_TRY(cudaEventCreate(&h->ev_c0[i]));
+      CUDA_TRY(cudaEventCreate(&h->ev_c1[i]));
+      CUDA_TRY(cudaEventCreate(&h->ev_e0[i]));
+      CUDA_TRY(cudaEventCreate(&h->ev_e1[i]));
+      CUDA_TRY(cudaEventCreate(&h->ev_h1[i]));
+    }
   }
   h->profiling = enable != 0;
-  h->prof_valid = false;
+  h->prof_chunks = 0;
   return LOCC_OK;
 }
 
 int locc_stage_times(locc_handle* h, float* ms_out, int n) {
   if (!h || !ms_out || n < 0) return fail(LOCC_ERR_INVALID_ARG, "bad argument");
-  if (!h->profiling || !h->ev[0]) return fail(LOCC_ERR_INVALID_ARG, "profiling is off");
-  CUDA_TRY(cudaEventSynchronize(h->ev[4]));
+  if (!h->profiling || !h->ev_bp0) return fail(LOCC_ERR_INVALID_ARG, "profiling is off");
+  CUDA_TRY(cudaEventSynchronize(h->ev_end));
+  float t[5] = {0.f, 0.f, 0.f, 0.f, 0.f}, x = 0.f;
+  CUDA_TRY(cudaEventElapsedTime(&t[0], h->ev_bp0, h->ev_bp1));
+  for (int i = 0; i < h->prof_chunks; ++i) {
+    CUDA_TRY(cudaEventElapsedTime(&x, h->ev_c0[i], h->ev_c1[i]));
+    t[1] += x;
+    CUDA_TRY(cudaEventElapsedTime(&x, h->ev_e0[i], h->ev_e1[i]));
+    t[2] += x;
+    CUDA_TRY(cudaEventElapsedTime(&x, h->ev_e1[i], h->ev_h1[i]));
+    t[3] += x;
+  }
+  CUDA_TRY(cudaEventElapsedTime(&t[4], h->ev_bp0, h->ev_end));
   int k = 0;
-  for (; k < n && k < 4; ++k) CUDA_TRY(cudaEventElapsedTime(&ms_out[k], h->ev[k], h->ev[k + 1]));
+  for (; k < n && k < 5; ++k) ms_out[k] = t[k];
   return k;
+}
+
+int locc_set_pipeline(locc_handle* h, int32_t n_chunks, int32_t crop_ctas_per_sm) {
+  if (!h) return fail(LOCC_ERR_INVALID_ARG, "handle is NULL");
+  if (n_chunks < 1 || n_chunks > LOCC_MAX_CHUNKS || crop_ctas_per_sm < 0)
+    return fail(LOCC_ERR_INVALID_ARG, "n_chunks must be 1..%d, crop_ctas_per_sm >= 0",
+                LOCC_MAX_CHUNKS);
+  h->n_chunks = n_chunks;
+  h->crop_cap = crop_ctas_per_sm;
+  return LOCC_OK;
+}
+
+int locc_autotune(locc_handle* h, const float* poses, const int32_t* obj_shape, int32_t n_obj,
+                  const int32_t* env_offsets, int32_t n_env, int32_t* pairs_out,
+                  int32_t* n_pairs_out, int32_t max_pairs, float* out, int32_t reps,
+                  int32_t* best_out, float* best_ms_out, void* stream) {
+  if (!h || reps < 1) return fail(LOCC_ERR_INVALID_ARG, "bad argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  static const int kChunks[] = {1, 2, 4, 8};
+  static const int kCaps[] = {0, 8, 6, 4};
+  cudaEvent_t e0, e1;
+  CUDA_TRY(cudaEventCreate(&e0));
+  CUDA_TRY(cudaEventCreate(&e1));
+  const bool prof = h->profiling;
+  h->profiling = false;
+  float best = 1e30f;
+  int bc = h->n_chunks, bp = h->crop_cap, st = LOCC_OK;
+  for (int c : kChunks) {
+    for (int cap : kCaps) {
+      if (c == 1 && cap != 0) continue;
+      h->n_chunks = c;
+      h->crop_cap = cap;
+      st = locc_step(h, poses, obj_shape, n_obj, env_offsets, n_env, pairs_out, n_pairs_out,
+                     max_pairs, out, stream);  // warm-up
+      if (st) break;
+      float tot = 0.f;
+      for (int r = 0; r < reps && st == LOCC_OK; ++r) {
+        cudaEventRecord(e0, s);
+        st = locc_step(h, poses, obj_shape, n_obj, env_offsets, n_env, pairs_out, n_pairs_out,
+                       max_pairs, out, stream);
+        cudaEventRecord(e1, s);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        tot += ms;
+      }
+      if (st) break;
+      if (tot / reps < best) best = tot / reps, bc = c, bp = cap;
+    }
+    if (st) break;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  h->profiling = prof;
+  h->n_chunks = bc;
+  h->crop_cap = bp;
+  if (st) return st;
+  if (best_out) best_out[0] = bc, best_out[1] = bp;
+  if (best_ms_out) *best_ms_out = best;
+  return LOCC_OK;
 }
 
 int locc_step_host(locc_handle* h, const float* poses, const int32_t* obj_shape, int32_t n_obj,
@@ -364,8 +497,9 @@ int locc_crop(locc_handle* h, const float* poses, const int32_t* obj_shape, int3
   if (!poses || !obj_shape || !pairs || !xyz_out || !cnt_out)
     return fail(LOCC_ERR_INVALID_ARG, "NULL array");
   PairInputs in{poses, obj_shape, pairs, n_obj, n_pairs};
-  CUDA_TRY(launch_crop(dev_library(h), in, nullptr, h->radius, reinterpret_cast<float4*>(xyz_out),
-                       idx_out, cnt_out, reinterpret_cast<float4*>(centre_out), h->d_err, h->n_sm,
+  CUDA_TRY(launch_crop(dev_library(h), in, whole_range(n_pairs, nullptr), h->radius,
+                       reinterpret_cast<float4*>(xyz_out), idx_out, cnt_out,
+                       reinterpret_cast<float4*>(centre_out), h->d_err, h->n_sm, 0,
                        (cudaStream_t)stream));
   return LOCC_OK;
 }
@@ -379,8 +513,8 @@ int locc_network(locc_handle* h, const float* xyz, int32_t n_pairs, float* y_out
   cudaStream_t s = (cudaStream_t)stream;
   int st = ensure_capacity(h, n_pairs, s);
   if (st) return st;
-  return run_network(h, reinterpret_cast<const float4*>(xyz), n_pairs, nullptr, nullptr, nullptr,
-                     nullptr, y_out, feat_out, s, nullptr);
+  return run_network(h, reinterpret_cast<const float4*>(xyz), whole_range(n_pairs, nullptr),
+                     nullptr, nullptr, nullptr, y_out, feat_out, s, nullptr);
 }
 
 int locc_detect(locc_handle* h, const float* poses, const int32_t* obj_shape, int32_t n_obj,
@@ -393,10 +527,16 @@ int locc_detect(locc_handle* h, const float* poses, const int32_t* obj_shape, in
   int st = ensure_capacity(h, n_pairs, s);
   if (st) return st;
   PairInputs in{poses, obj_shape, pairs, n_obj, n_pairs};
-  CUDA_TRY(launch_crop(dev_library(h), in, nullptr, h->radius, h->d_xyz, nullptr, h->d_cnt,
-                       h->d_centre, h->d_err, h->n_sm, s));
-  return run_network(h, h->d_xyz, n_pairs, nullptr, &in, h->d_centre, out, nullptr, nullptr, s,
-                     nullptr);
+  const bool prof = h->profiling;
+  h->prof_chunks = 0;
+  if (prof) {
+    CUDA_TRY(cudaEventRecord(h->ev_bp0, s));
+    CUDA_TRY(cudaEventRecord(h->ev_bp1, s));
+  }
+  st = run_path(h, in, n_pairs, nullptr, out, s);
+  if (st) return st;
+  if (prof) CUDA_TRY(cudaEventRecord(h->ev_end, s));
+  return LOCC_OK;
 }
 
 int locc_detect_host(locc_handle* h, const float* poses, const int32_t* obj_shape, int32_t n_obj,
@@ -468,8 +608,15 @@ void locc_destroy(locc_handle* h) {
   cudaFree(h->d_env_counts);
   cudaFree(h->d_stage);
   cudaFreeHost(h->h_stage);
-  for (int i = 0; i < 5; ++i)
-    if (h->ev[i]) cudaEventDestroy(h->ev[i]);
+  cudaEvent_t evs[] = {h->ev_fork, h->ev_join, h->ev_bp0, h->ev_bp1, h->ev_end};
+  for (cudaEvent_t e : evs)
+    if (e) cudaEventDestroy(e);
+  for (int i = 0; i < LOCC_MAX_CHUNKS; ++i) {
+    cudaEvent_t ce[] = {h->ev_crop[i], h->ev_c0[i], h->ev_c1[i], h->ev_e0[i], h->ev_e1[i], h->ev_h1[i]};
+    for (cudaEvent_t e : ce)
+      if (e) cudaEventDestroy(e);
+  }
+  if (h->aux) cudaStreamDestroy(h->aux);
   delete h;
 }
 

@@ -43,6 +43,29 @@ struct PairInputs {
   int n_pairs;
 };
 
+// The pairs a launch works on: chunk `chunk` of `n_chunks` equal parts of
+// [0, n), where n = min(*n_dev, n_cap) when the count lives on the device
+// (n_dev != NULL) and n_cap otherwise.  Chunks let the crop gather of one part
+// run on one stream while the network runs on the previous part on another.
+struct PairRange {
+  int n_cap;
+  const int* n_dev;
+  int chunk;
+  int n_chunks;
+};
+
+__host__ __device__ inline PairRange whole_range(int n, const int* n_dev) {
+  return PairRange{n, n_dev, 0, 1};
+}
+
+__device__ __forceinline__ void range_bounds(const PairRange& r, int* lo, int* hi) {
+  int n = r.n_cap;
+  if (r.n_dev) n = min(*r.n_dev, r.n_cap);
+  if (n < 0) n = 0;
+  *lo = (int)(((long long)n * r.chunk) / r.n_chunks);
+  *hi = (int)(((long long)n * (r.chunk + 1)) / r.n_chunks);
+}
+
 // Float32 parameters for the CUDA-core kernels: per layer W^T [in][out]
 // followed by b [out].
 struct Fp32Params {
@@ -122,13 +145,14 @@ __device__ __forceinline__ void epilogue_world(const float* y, const float* pose
 namespace locc {
 // n_dev (nullable): device count of pairs actually present (<= n_pairs), read
 // by the kernels so that a fixed launch serves a count produced on the device.
-cudaError_t launch_crop(const DevLibrary& lib, const PairInputs& in, const int* n_dev,
+// grid_cap (crop): at most this many resident CTAs per SM (0 = occupancy limit).
+cudaError_t launch_crop(const DevLibrary& lib, const PairInputs& in, const PairRange& rg,
                         float r, float4* xyz, int32_t* idx, int32_t* cnt, float4* centre,
-                        int* err, int n_sm, cudaStream_t stream);
-cudaError_t launch_encoder_fp32(const float4* xyz, int n_pairs, const int* n_dev,
+                        int* err, int n_sm, int grid_cap, cudaStream_t stream);
+cudaError_t launch_encoder_fp32(const float4* xyz, const PairRange& rg,
                                 const Fp32Params& prm, float* feat, int n_sm,
                                 cudaStream_t stream);
-cudaError_t launch_head_fp32(const float* feat, int n_pairs, const int* n_dev,
+cudaError_t launch_head_fp32(const float* feat, const PairRange& rg,
                              const Fp32Params& prm, const PairInputs* in,
                              const float4* centre, float* out, float* y_raw, int n_sm,
                              cudaStream_t stream);

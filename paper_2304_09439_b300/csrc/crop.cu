@@ -32,6 +32,7 @@ namespace locc {
 namespace {
 
 constexpr int CAND_CAP = 256;
+constexpr int NBINS = 64;  // d^2 histogram bins of the exact top-64 selection
 constexpr unsigned FULL = 0xffffffffu;
 
 // One compare-exchange stage between lanes (partner lane ^ lj) for all R
@@ -162,7 +163,7 @@ __device__ __forceinline__ void crop_pair(const DevLibrary& lib, const PairInput
                                           int32_t* __restrict__ idx_out,
                                           int32_t* __restrict__ cnt_out,
                                           float4* __restrict__ centre_out, int* __restrict__ err,
-                                          unsigned long long* buf) {
+                                          unsigned long long* buf, int* hist) {
   int a, b, sa, sb;
   const bool ok = load_pair(in, lib.n_shapes, p, &a, &b, &sa, &sb, (warp == 0 && lane == 0) ? err : nullptr);
   float4* xo = xyz_out + ((size_t)p * 2 + warp) * KMAX;
@@ -190,7 +191,49 @@ __device__ __forceinline__ void crop_pair(const DevLibrary& lib, const PairInput
   const float4* blk = lib.blocks + (size_t)shape * lib.n_blocks * 2;
   unsigned long long bound = ~0ull;  // keys >= bound cannot reach the top 64
   int n = 0;
-
+  // Pass 1: histogram of d^2 over NBINS equal bins of [0, r^2].  The bin is a
+  // non-decreasing function of d^2, so every key of a lower bin is smaller
+  // than every key of a higher bin, and the first bin b* at which the
+  // cumulative count reaches 64 bounds the 64 smallest keys: pass 2 keeps
+  // only keys of bins <= b* (about 64 + n / NBINS of them).
+  const float inv_w = (float)NBINS / r2;
+  hist[lane] = 0;
+  hist[lane + 32] = 0;
+  __syncwarp();
+  int n_in = 0;
+  for (int bg = 0; bg < lib.n_blocks; bg += 32) {
+    const int bi = bg + lane;
+    bool hit = false;
+    if (bi < lib.n_blocks) hit = box_dist2(blk[2 * bi], blk[2 * bi + 1], cx, cy, cz) <= r2_cull;
+    unsigned mask = __ballot_sync(FULL, hit);
+    while (mask) {
+      const int bb = bg + __ffs(mask) - 1;
+      mask &= mask - 1;
+      const float4 q = pts[bb * BLOCK_PTS + lane];
+      const float d0 = fsub(q.x, cx), d1 = fsub(q.y, cy), d2 = fsub(q.z, cz);
+      float s = fmul(d0, d0);
+      s = fadd(s, fmul(d1, d1));
+      s = fadd(s, fmul(d2, d2));
+      const bool in = s <= r2;
+      if (in) atomicAdd(&hist[min(NBINS - 1, (int)(s * inv_w))], 1);
+      n_in += __popc(__ballot_sync(FULL, in));
+    }
+  }
+  __syncwarp();
+  int bstar = NBINS - 1;
+  if (n_in > KMAX) {
+    const int h0 = hist[2 * lane], h1 = hist[2 * lane + 1];
+    int c = h0 + h1;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(FULL, c, o);
+      if (lane >= o) c += t;
+    }
+    const int first_half = (c - h1) >= KMAX ? 0 : 1;  // does bin 2*lane already reach 64?
+    const int L = __ffs(__ballot_sync(FULL, c >= KMAX)) - 1;
+    bstar = 2 * L + __shfl_sync(FULL, first_half, L);
+  }
+  // Pass 2: collect the keys of bins <= b* (streaming top-64 if they overflow)
   for (int bg = 0; bg < lib.n_blocks; bg += 32) {
     const int bi = bg + lane;
     bool hit = false;
@@ -208,7 +251,9 @@ __device__ __forceinline__ void crop_pair(const DevLibrary& lib, const PairInput
       const unsigned long long key =
           ((unsigned long long)__float_as_uint(s) << 32) |
           ((unsigned long long)(__float_as_uint(q.w) & 0xffffu) << 16) | (unsigned)pos;
-      const bool take = (s <= r2) && key < bound;
+      const bool in = s <= r2;
+      const int bin = in ? min(NBINS - 1, (int)(s * inv_w)) : NBINS;
+      const bool take = in && bin <= bstar && key < bound;
       const unsigned tm = __ballot_sync(FULL, take);
       if (tm == 0) continue;
       if (n + __popc(tm) > CAND_CAP) {
@@ -252,34 +297,39 @@ __device__ __forceinline__ void crop_pair(const DevLibrary& lib, const PairInput
   __syncwarp();
 }
 
-__global__ void __launch_bounds__(64, 16) crop_kernel(DevLibrary lib, PairInputs in, const int* n_dev,
-                                                  float r, float4* __restrict__ xyz_out,
-                                                  int32_t* __restrict__ idx_out,
-                                                  int32_t* __restrict__ cnt_out,
-                                                  float4* __restrict__ centre_out,
-                                                  int* __restrict__ err) {
+__global__ void __launch_bounds__(64, 16) crop_kernel(DevLibrary lib, PairInputs in, PairRange rg,
+                                                      float r, float4* __restrict__ xyz_out,
+                                                      int32_t* __restrict__ idx_out,
+                                                      int32_t* __restrict__ cnt_out,
+                                                      float4* __restrict__ centre_out,
+                                                      int* __restrict__ err) {
   __shared__ unsigned long long cand[2][CAND_CAP];
+  __shared__ int hist[2][NBINS];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int n_pairs = n_dev ? min(*n_dev, in.n_pairs) : in.n_pairs;
-  for (int p = blockIdx.x; p < n_pairs; p += gridDim.x) {
-    crop_pair(lib, in, p, warp, lane, r, xyz_out, idx_out, cnt_out, centre_out, err, cand[warp]);
+  int lo, hi;
+  range_bounds(rg, &lo, &hi);
+  for (int p = lo + blockIdx.x; p < hi; p += gridDim.x) {
+    crop_pair(lib, in, p, warp, lane, r, xyz_out, idx_out, cnt_out, centre_out, err, cand[warp],
+              hist[warp]);
   }
 }
 
 }  // namespace
 
-cudaError_t launch_crop(const DevLibrary& lib, const PairInputs& in, const int* n_dev, float r,
+cudaError_t launch_crop(const DevLibrary& lib, const PairInputs& in, const PairRange& rg, float r,
                         float4* xyz, int32_t* idx, int32_t* cnt, float4* centre, int* err,
-                        int n_sm, cudaStream_t stream) {
+                        int n_sm, int grid_cap, cudaStream_t stream) {
   if (in.n_pairs <= 0) return cudaSuccess;
-  // one wave of resident CTAs; each strides over the pairs
+  // one wave of resident CTAs (at most grid_cap per SM); each strides over its pairs
   static int per_sm = 0;
   if (per_sm == 0) {
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, crop_kernel, 64, 0);
     if (e != cudaSuccess || per_sm < 1) per_sm = 1;
   }
-  const int grid = std::min(in.n_pairs, n_sm * per_sm);
-  crop_kernel<<<grid, 64, 0, stream>>>(lib, in, n_dev, r, xyz, idx, cnt, centre, err);
+  const int cap = grid_cap > 0 ? std::min(grid_cap, per_sm) : per_sm;
+  const int span = (in.n_pairs + rg.n_chunks - 1) / rg.n_chunks + 1;
+  const int grid = std::max(1, std::min(span, n_sm * cap));
+  crop_kernel<<<grid, 64, 0, stream>>>(lib, in, rg, r, xyz, idx, cnt, centre, err);
   return cudaGetLastError();
 }
 

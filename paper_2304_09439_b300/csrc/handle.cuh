@@ -5,6 +5,8 @@
 
 #include "common.cuh"
 
+constexpr int LOCC_MAX_CHUNKS = 16;
+
 struct locc_handle {
   int device = 0;
   int n_sm = 1;
@@ -42,10 +44,21 @@ struct locc_handle {
   void* h_stage = nullptr;
   void* d_stage = nullptr;
   size_t stage_bytes = 0;
-  // stage timing (locc_profile)
+  // pipelining: the crop gather of chunk i + 1 (caller's stream) overlaps the
+  // network of chunk i (aux stream); crop_cap limits the crop CTAs per SM so
+  // that they fit beside a network CTA
+  int n_chunks = 1;
+  int crop_cap = 0;
+  cudaStream_t aux = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  cudaEvent_t ev_crop[LOCC_MAX_CHUNKS] = {};
+  // stage timing (locc_profile): per chunk, crop start / end on the crop
+  // stream, encoder start / end and head end on the network stream
   bool profiling = false;
-  bool prof_valid = false;
-  cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  cudaEvent_t ev_bp0 = nullptr, ev_bp1 = nullptr, ev_end = nullptr;
+  cudaEvent_t ev_c0[LOCC_MAX_CHUNKS] = {}, ev_c1[LOCC_MAX_CHUNKS] = {};
+  cudaEvent_t ev_e0[LOCC_MAX_CHUNKS] = {}, ev_e1[LOCC_MAX_CHUNKS] = {}, ev_h1[LOCC_MAX_CHUNKS] = {};
+  int prof_chunks = 0;
 };
 
 namespace locc {
@@ -61,15 +74,16 @@ int broadphase_run(locc_handle* h, const float* poses, const int32_t* obj_shape,
                    const int32_t* env_offsets, int n_env, int32_t* pairs_out,
                    int32_t* n_pairs_out, int max_pairs, cudaStream_t stream);
 DevLibrary dev_library(const locc_handle* h);
-// mid (nullable): event recorded between the encoder and the head.
-int run_network(locc_handle* h, const float4* xyz, int n_pairs, const int* n_dev,
-                const PairInputs* in, const float4* centre, float* out, float* y_raw,
-                float* feat_out, cudaStream_t stream, cudaEvent_t mid);
+// Encoder then head for the pairs of `rg`; mid (nullable): event recorded
+// between the encoder and the head.
+int run_network(locc_handle* h, const float4* xyz, const PairRange& rg, const PairInputs* in,
+                const float4* centre, float* out, float* y_raw, float* feat_out,
+                cudaStream_t stream, cudaEvent_t mid);
 int upload_fp8_params(locc_handle* h, const std::vector<float>& params);
-int run_network_fp8(locc_handle* h, const float4* xyz, int n_pairs, const int* n_dev,
-                    const PairInputs* in, const float4* centre, float* out, float* y_raw,
-                    float* feat_out, cudaStream_t stream, cudaEvent_t mid);
-int run_network_tc(locc_handle* h, const float4* xyz, int n_pairs, const int* n_dev,
-                   const PairInputs* in, const float4* centre, float* out, float* y_raw,
-                   float* feat_out, cudaStream_t stream, cudaEvent_t mid);
+int run_network_fp8(locc_handle* h, const float4* xyz, const PairRange& rg, const PairInputs* in,
+                    const float4* centre, float* out, float* y_raw, float* feat_out,
+                    cudaStream_t stream, cudaEvent_t mid);
+int run_network_tc(locc_handle* h, const float4* xyz, const PairRange& rg, const PairInputs* in,
+                   const float4* centre, float* out, float* y_raw, float* feat_out,
+                   cudaStream_t stream, cudaEvent_t mid);
 }  // namespace locc

@@ -131,12 +131,12 @@ __device__ __forceinline__ void encode_pair(const float4* __restrict__ xyz, int 
 }
 
 __global__ void __launch_bounds__(ENC_THREADS, 2) encoder_fp32_kernel(const float4* __restrict__ xyz,
-                                                                      int n_pairs, const int* n_dev,
-                                                                      Fp32Params prm,
+                                                                      PairRange rg, Fp32Params prm,
                                                                       float* __restrict__ feat) {
   extern __shared__ __align__(16) unsigned char smem[];
-  const int n = n_dev ? min(*n_dev, n_pairs) : n_pairs;
-  for (int p = blockIdx.x; p < n; p += gridDim.x) {
+  int lo, hi;
+  range_bounds(rg, &lo, &hi);
+  for (int p = lo + blockIdx.x; p < hi; p += gridDim.x) {
     encode_pair(xyz, p, prm, feat, smem);
     __syncthreads();
   }
@@ -186,16 +186,16 @@ __device__ __forceinline__ void head_tile(const float* __restrict__ feat, int n_
                                           const float4* __restrict__ centre, float* __restrict__ out,
                                           float* __restrict__ y_raw, float* hsm);
 
-__global__ void __launch_bounds__(256) head_fp32_kernel(const float* __restrict__ feat, int n_pairs,
-                                                        const int* n_dev, Fp32Params prm,
-                                                        PairInputs in, int have_in,
+__global__ void __launch_bounds__(256) head_fp32_kernel(const float* __restrict__ feat, PairRange rg,
+                                                        Fp32Params prm, PairInputs in, int have_in,
                                                         const float4* __restrict__ centre,
                                                         float* __restrict__ out,
                                                         float* __restrict__ y_raw) {
   extern __shared__ __align__(16) float hsm[];
-  const int n = n_dev ? min(*n_dev, n_pairs) : n_pairs;
-  for (int q0 = blockIdx.x * HEAD_PAIRS; q0 < n; q0 += gridDim.x * HEAD_PAIRS) {
-    head_tile(feat, n, q0, prm, in, have_in, centre, out, y_raw, hsm);
+  int lo, hi;
+  range_bounds(rg, &lo, &hi);
+  for (int q0 = lo + blockIdx.x * HEAD_PAIRS; q0 < hi; q0 += gridDim.x * HEAD_PAIRS) {
+    head_tile(feat, hi, q0, prm, in, have_in, centre, out, y_raw, hsm);
     __syncthreads();
   }
 }
@@ -255,10 +255,10 @@ __device__ __forceinline__ void head_tile(const float* __restrict__ feat, int n_
 
 }  // namespace
 
-cudaError_t launch_encoder_fp32(const float4* xyz, int n_pairs, const int* n_dev,
-                                const Fp32Params& prm, float* feat, int n_sm,
-                                cudaStream_t stream) {
-  if (n_pairs <= 0) return cudaSuccess;
+cudaError_t launch_encoder_fp32(const float4* xyz, const PairRange& rg, const Fp32Params& prm,
+                                float* feat, int n_sm, cudaStream_t stream) {
+  const int n_pairs = (rg.n_cap + rg.n_chunks - 1) / rg.n_chunks + 1;
+  if (rg.n_cap <= 0) return cudaSuccess;
   static bool attr = false;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(encoder_fp32_kernel,
@@ -267,14 +267,15 @@ cudaError_t launch_encoder_fp32(const float4* xyz, int n_pairs, const int* n_dev
     attr = true;
   }
   const int grid = std::min(n_pairs, 2 * n_sm);
-  encoder_fp32_kernel<<<grid, ENC_THREADS, ENC_SMEM, stream>>>(xyz, n_pairs, n_dev, prm, feat);
+  encoder_fp32_kernel<<<grid, ENC_THREADS, ENC_SMEM, stream>>>(xyz, rg, prm, feat);
   return cudaGetLastError();
 }
 
-cudaError_t launch_head_fp32(const float* feat, int n_pairs, const int* n_dev,
-                             const Fp32Params& prm, const PairInputs* in, const float4* centre,
-                             float* out, float* y_raw, int n_sm, cudaStream_t stream) {
-  if (n_pairs <= 0) return cudaSuccess;
+cudaError_t launch_head_fp32(const float* feat, const PairRange& rg, const Fp32Params& prm,
+                             const PairInputs* in, const float4* centre, float* out, float* y_raw,
+                             int n_sm, cudaStream_t stream) {
+  const int n_pairs = (rg.n_cap + rg.n_chunks - 1) / rg.n_chunks + 1;
+  if (rg.n_cap <= 0) return cudaSuccess;
   static bool attr = false;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(head_fp32_kernel,
@@ -285,8 +286,8 @@ cudaError_t launch_head_fp32(const float* feat, int n_pairs, const int* n_dev,
   PairInputs pin{};
   if (in) pin = *in;
   const int grid = std::min((n_pairs + HEAD_PAIRS - 1) / HEAD_PAIRS, n_sm);
-  head_fp32_kernel<<<grid, 256, HEAD_SMEM, stream>>>(feat, n_pairs, n_dev, prm, pin,
-                                                     in != nullptr, centre, out, y_raw);
+  head_fp32_kernel<<<grid, 256, HEAD_SMEM, stream>>>(feat, rg, prm, pin, in != nullptr, centre,
+                                                     out, y_raw);
   return cudaGetLastError();
 }
 

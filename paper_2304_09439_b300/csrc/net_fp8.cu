@@ -1,19 +1,23 @@
 // FP8 (e4m3) crop network on tcgen05 (LOCC_FP8).
 //
-// Same network and kernel structure as the BF16 path (net_tc.cu); the matrix
-// products of encoder layers 2-3 and of all head layers use tcgen05.mma
-// kind::f8f6f4 with e4m3 operands and float32 accumulation in TMEM:
-//   * weights: one scale per output channel, s_w[c] = max_k |W[c][k]| / 448,
-//     quantised once on the GPU (quant_e4m3_kernel);
-//   * activations: one scale per row (crop point, or pair in the head),
-//     s_a[r] = max_k a[r][k] / 448, chosen by the epilogue that produces the
-//     row (ReLU outputs are >= 0);
-//   * the accumulator is dequantised in the epilogue: z = D s_a[r] s_w[c] + b.
-// Layer 1 (K = 3) keeps the bf16 hi/lo split of the BF16 path.  In the
-// transposed layer 3 each thread owns a channel, so the per-point scales s_h2
-// of the columns come from shared memory and the channel scale is applied
-// after the max (a positive factor commutes with max).
+// Same network and kernel structure as the BF16 path (net_tc.cu); encoder
+// layers 2-3 and all head layers use tcgen05.mma kind::f8f6f4 (e4m3 operands,
+// float32 accumulation in TMEM).  Layer 1 (K = 3) keeps the bf16 hi/lo split.
+//
+// Scales.  Crop coordinates lie in the crop ball (|x| <= r), so every
+// activation channel has a bound that follows from the weights alone:
+//   B1_c = r |W1_c|_2 + b1_c,  B_{l+1,c} = sum_k |W_{l+1}[c][k]| B_{l,k} + b_{l+1,c}
+// (ReLU outputs lie in [0, B]).  Channel k of a layer's output is stored as
+// e4m3 of a / s_k with the static scale s_k = 1.1 B_k / 448, and s_k is folded
+// into the next layer's weights: W'[c][k] = W[c][k] s_k, quantised with one
+// scale per output channel, w_c = max_k |W'[c][k]| / 448.  The accumulator D of
+// channel c then equals sum_k a_k W[c][k] / w_c, so each epilogue is one FMA
+// and one saturating cvt:  next = cvt_relu(D alpha_c + beta_c) with
+// alpha_c = w_c / s_c, beta_c = b_c / s_c.  e4m3 is a floating-point format
+// (2^14.8 of range), so a loose bound costs little precision.  The
+// coefficients are computed on the host in float64 at create time.
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <vector>
 
@@ -26,54 +30,39 @@ namespace {
 using namespace tc;
 
 constexpr long long WAIT_CYCLES = 2000000000LL;  // ~1 s at 2 GHz
-constexpr float E4M3_MAX = 448.f;
 
 __device__ __forceinline__ uint4 ldg_v4(const void* p) {
   return __ldg(reinterpret_cast<const uint4*>(p));
 }
 
 // ------------------------------------------------------ weight quantisation
-// Row r of W [rows][K] (float32, row-major) -> e4m3 bytes in K-chunks of
-// chunkK columns, each chunk a K-major no-swizzle tile [rows][chunkK] stored
-// one after the other; scales[r] = max |W[r][:]| / 448 (1 for an all-zero row).
-__global__ void quant_e4m3_kernel(const float* __restrict__ W, int rows, int K, int chunkK,
-                                  unsigned char* __restrict__ img, float* __restrict__ scales) {
-  __shared__ float red[128];
-  const int r = blockIdx.x, t = threadIdx.x;
-  float m = 0.f;
-  for (int k = t; k < K; k += 128) m = fmaxf(m, fabsf(W[(size_t)r * K + k]));
-  red[t] = m;
-  __syncthreads();
-  for (int s = 64; s > 0; s >>= 1) {
-    if (t < s) red[t] = fmaxf(red[t], red[t + s]);
-    __syncthreads();
-  }
-  const float amax = red[0];
-  const float sc = amax > 0.f ? amax / E4M3_MAX : 1.f;
-  const float inv = amax > 0.f ? E4M3_MAX / amax : 0.f;
-  for (int k = t; k < K; k += 128) {
-    const uint32_t q = pack_e4m3x4(W[(size_t)r * K + k] * inv, 0.f, 0.f, 0.f);
+// Row r of W [rows][K] (float32, row-major) times inv[r] -> e4m3 bytes in
+// K-chunks of chunkK columns, each chunk a K-major no-swizzle tile
+// [rows][chunkK] stored one after the other.
+__global__ void quant_e4m3_kernel(const float* __restrict__ W, const float* __restrict__ inv,
+                                  int rows, int K, int chunkK, unsigned char* __restrict__ img) {
+  const int r = blockIdx.x;
+  const float s = inv[r];
+  for (int k = threadIdx.x; k < K; k += blockDim.x) {
+    const uint32_t q = pack_e4m3x4(W[(size_t)r * K + k] * s, 0.f, 0.f, 0.f);
     const int c = k / chunkK, kk = k % chunkK;
     img[(size_t)c * rows * chunkK + kmajor_off8(r, kk, chunkK)] = (unsigned char)(q & 0xffu);
   }
-  if (t == 0) scales[r] = sc;
 }
 
 // ------------------------------------------------------------- encoder
 constexpr int F_W1 = 0;                        // [64 x 16] bf16 (hi/lo)   2 KB
 constexpr int F_W2 = F_W1 + 64 * 16 * 2;       // [128 x 64] e4m3          8 KB
 constexpr int F_W3 = F_W2 + 128 * 64;          // [256 x 128] e4m3        32 KB
-constexpr int F_SC = F_W3 + 256 * 128;         // sw2 128, sw3 256 (f32)
-constexpr int F_BIAS = F_SC + (128 + 256) * 4; // b1 64, b2 128, b3 256 (f32)
-constexpr int F_IMG_BYTES = F_BIAS + (64 + 128 + 256) * 4;
+constexpr int F_EP = F_W3 + 256 * 128;         // a1 c1 [64], a2 c2 [128], w3 b3 [256] (f32)
+constexpr int F_IMG_BYTES = F_EP + (2 * 64 + 2 * 128 + 2 * 256) * 4;
 static_assert(F_IMG_BYTES % 16 == 0, "encoder fp8 image must be 16-byte chunks");
 constexpr int F_SLOT0 = (F_IMG_BYTES + 1023) / 1024 * 1024;
 constexpr int FS_STG = 0;                   // [128] float4        2 KB
 constexpr int FS_X = FS_STG + ROWS * 16;    // [128 x 16] bf16     4 KB
 constexpr int FS_H1 = FS_X + 128 * 16 * 2;  // [128 x 64] e4m3     8 KB
 constexpr int FS_H2 = FS_H1 + 128 * 64;     // [128 x 128] e4m3   16 KB
-constexpr int FS_SH2 = FS_H2 + 128 * 128;   // s_h2 [128] f32
-constexpr int F_SLOT_BYTES = FS_SH2 + 128 * 4;
+constexpr int F_SLOT_BYTES = FS_H2 + 128 * 128;
 constexpr int F_CTRL = F_SLOT0 + 2 * F_SLOT_BYTES;
 constexpr int C_BAR = 0, C_TMEM = 128, C_ABORT = 132, C_CNT = 136;
 constexpr int F_SMEM = F_CTRL + 256;
@@ -83,13 +72,34 @@ constexpr int SLOT_COLS = 256;
 constexpr int B_FULLX = 0, B_XRDY = 2, B_H1RDY = 4, B_H2RDY = 6, B_D1 = 8, B_D2 = 10, B_D3 = 12,
               B_W = 14, B_DRAIN = 15;
 
+// relu(D alpha + beta) for 32 TMEM columns -> 32 e4m3 bytes at row `row`,
+// columns [k0, k0 + 32) of a K-wide tile.
+template <int K>
+__device__ __forceinline__ void epi_e4m3_32(const float (&v)[32], const float* alpha,
+                                            const float* beta, unsigned char* dst, int row, int k0) {
+#pragma unroll
+  for (int c = 0; c < 2; ++c) {
+    float t[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) t[j] = fmaf(v[16 * c + j], alpha[16 * c + j], beta[16 * c + j]);
+    uint4 w;
+    w.x = pack_e4m3x4_relu(t[0], t[1], t[2], t[3]);
+    w.y = pack_e4m3x4_relu(t[4], t[5], t[6], t[7]);
+    w.z = pack_e4m3x4_relu(t[8], t[9], t[10], t[11]);
+    w.w = pack_e4m3x4_relu(t[12], t[13], t[14], t[15]);
+    *reinterpret_cast<uint4*>(dst + kmajor_off8(row, k0 + 16 * c, K)) = w;
+  }
+}
+
 __global__ void __launch_bounds__(F_THREADS, 1)
-    encoder_fp8_kernel(const float4* __restrict__ xyz, int n_pairs, const int* n_dev,
+    encoder_fp8_kernel(const float4* __restrict__ xyz, PairRange rg,
                        const unsigned char* __restrict__ img, float* __restrict__ feat,
                        int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char smem[];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int n = n_dev ? min(*n_dev, n_pairs) : n_pairs;
+  int lo, hi;
+  range_bounds(rg, &lo, &hi);
+  const int n = hi - lo;
   if ((int)blockIdx.x >= n) return;
   const int my_pairs = (n - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
 
@@ -123,11 +133,12 @@ __global__ void __launch_bounds__(F_THREADS, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tbase = *tmem_slot;
-  const float* sw2 = reinterpret_cast<const float*>(smem + F_SC);
-  const float* sw3 = sw2 + 128;
-  const float* b1 = reinterpret_cast<const float*>(smem + F_BIAS);
-  const float* b2 = b1 + 64;
-  const float* b3 = b2 + 128;
+  const float* a1 = reinterpret_cast<const float*>(smem + F_EP);
+  const float* c1 = a1 + 64;
+  const float* a2 = c1 + 64;
+  const float* c2 = a2 + 128;
+  const float* w3 = c2 + 128;
+  const float* b3 = w3 + 256;
 
   if (warp == 8) {
     if (lane == 0) {
@@ -139,7 +150,7 @@ __global__ void __launch_bounds__(F_THREADS, 1)
       int issued[2] = {0, 0};
       auto load_pair = [&](int i) {
         const int s = i & 1;
-        const int p = blockIdx.x + i * gridDim.x;
+        const int p = lo + blockIdx.x + i * gridDim.x;
         mbar_expect_tx(BAR(B_FULLX + s), ROWS * 16);
         bulk_g2s(smem_u32(smem + F_SLOT0 + s * F_SLOT_BYTES + FS_STG), xyz + (size_t)p * ROWS,
                  ROWS * 16, BAR(B_FULLX + s));
@@ -199,14 +210,13 @@ __global__ void __launch_bounds__(F_THREADS, 1)
   } else {
     const int s = warp >> 2, row = tid & 127, wq = warp & 3;
     unsigned char* slot = smem + F_SLOT0 + s * F_SLOT_BYTES;
-    float* s_h2 = reinterpret_cast<float*>(slot + FS_SH2);
     const uint32_t tslot = tbase + s * SLOT_COLS + ((uint32_t)(32 * wq) << 16);
     int* cnt_s = s_cnt + 4 * s;
     bool ok = mbar_wait_or_abort(BAR(B_W), 0, abort, WAIT_CYCLES);
     for (int j = 0; ok; ++j) {
       const int i = 2 * j + s;
       if (i >= my_pairs) break;
-      const int p = blockIdx.x + i * gridDim.x;
+      const int p = lo + blockIdx.x + i * gridDim.x;
       const uint32_t ph = j & 1;
       if (!(ok = mbar_wait_or_abort(BAR(B_FULLX + s), ph, abort, WAIT_CYCLES))) break;
       {
@@ -216,95 +226,51 @@ __global__ void __launch_bounds__(F_THREADS, 1)
         const float fx = __bfloat162float(__float2bfloat16_rn(q.x));
         const float fy = __bfloat162float(__float2bfloat16_rn(q.y));
         const float fz = __bfloat162float(__float2bfloat16_rn(q.z));
-        uint4 c0, c1;
+        uint4 c0, cc1;
         c0.x = pack_bf16(fx, fy);
         c0.y = pack_bf16(fz, q.x - fx);
         c0.z = pack_bf16(q.y - fy, q.z - fz);
         c0.w = pack_bf16(fx, fy);
-        c1.x = pack_bf16(fz, 0.f);
-        c1.y = c1.z = c1.w = 0u;
+        cc1.x = pack_bf16(fz, 0.f);
+        cc1.y = cc1.z = cc1.w = 0u;
         *reinterpret_cast<uint4*>(slot + FS_X + kmajor_off(row, 0, 16)) = c0;
-        *reinterpret_cast<uint4*>(slot + FS_X + kmajor_off(row, 8, 16)) = c1;
+        *reinterpret_cast<uint4*>(slot + FS_X + kmajor_off(row, 8, 16)) = cc1;
       }
       fence_async_smem();
       tc_fence_before();
       mbar_arrive(BAR(B_XRDY + s));
-      // ---- layer 1 epilogue: relu(D1 + b1), per-row e4m3 scale
+      // ---- layer 1 epilogue -> e4m3 H1 (static per-channel scale)
       if (!(ok = mbar_wait_or_abort(BAR(B_D1 + s), ph, abort, WAIT_CYCLES))) break;
       tc_fence_after();
-      float sa;  // this row's H1 scale
       {
-        float v0[32], v1[32];
-        tmem_ld32(tslot + 0, v0);
-        tmem_ld32(tslot + 32, v1);
-        float amax = 0.f;
+        float v[32];
 #pragma unroll
-        for (int jj = 0; jj < 32; ++jj) {
-          v0[jj] = fmaxf(v0[jj] + b1[jj], 0.f);
-          v1[jj] = fmaxf(v1[jj] + b1[32 + jj], 0.f);
-          amax = fmaxf(amax, fmaxf(v0[jj], v1[jj]));
-        }
-        sa = amax > 0.f ? amax / E4M3_MAX : 1.f;
-        const float inv = amax > 0.f ? E4M3_MAX / amax : 0.f;
-#pragma unroll
-        for (int c = 0; c < 2; ++c) {
-          uint4 w;
-          w.x = pack_e4m3x4(v0[16 * c + 0] * inv, v0[16 * c + 1] * inv, v0[16 * c + 2] * inv, v0[16 * c + 3] * inv);
-          w.y = pack_e4m3x4(v0[16 * c + 4] * inv, v0[16 * c + 5] * inv, v0[16 * c + 6] * inv, v0[16 * c + 7] * inv);
-          w.z = pack_e4m3x4(v0[16 * c + 8] * inv, v0[16 * c + 9] * inv, v0[16 * c + 10] * inv, v0[16 * c + 11] * inv);
-          w.w = pack_e4m3x4(v0[16 * c + 12] * inv, v0[16 * c + 13] * inv, v0[16 * c + 14] * inv, v0[16 * c + 15] * inv);
-          *reinterpret_cast<uint4*>(slot + FS_H1 + kmajor_off8(row, 16 * c, 64)) = w;
-          w.x = pack_e4m3x4(v1[16 * c + 0] * inv, v1[16 * c + 1] * inv, v1[16 * c + 2] * inv, v1[16 * c + 3] * inv);
-          w.y = pack_e4m3x4(v1[16 * c + 4] * inv, v1[16 * c + 5] * inv, v1[16 * c + 6] * inv, v1[16 * c + 7] * inv);
-          w.z = pack_e4m3x4(v1[16 * c + 8] * inv, v1[16 * c + 9] * inv, v1[16 * c + 10] * inv, v1[16 * c + 11] * inv);
-          w.w = pack_e4m3x4(v1[16 * c + 12] * inv, v1[16 * c + 13] * inv, v1[16 * c + 14] * inv, v1[16 * c + 15] * inv);
-          *reinterpret_cast<uint4*>(slot + FS_H1 + kmajor_off8(row, 32 + 16 * c, 64)) = w;
+        for (int h = 0; h < 2; ++h) {
+          tmem_ld32(tslot + 32 * h, v);
+          epi_e4m3_32<64>(v, a1 + 32 * h, c1 + 32 * h, slot + FS_H1, row, 32 * h);
         }
       }
       fence_async_smem();
       tc_fence_before();
       mbar_arrive(BAR(B_H1RDY + s));
-      // ---- layer 2 epilogue: z = D2 sa sw2 + b2, relu; two passes over TMEM
+      // ---- layer 2 epilogue -> e4m3 H2
       if (!(ok = mbar_wait_or_abort(BAR(B_D2 + s), ph, abort, WAIT_CYCLES))) break;
       tc_fence_after();
       {
         float v[32];
-        float amax = 0.f;
-#pragma unroll 1
+#pragma unroll
         for (int h = 0; h < 4; ++h) {
           tmem_ld32(tslot + 64 + 32 * h, v);
-#pragma unroll
-          for (int jj = 0; jj < 32; ++jj)
-            amax = fmaxf(amax, fmaf(v[jj], sa * sw2[32 * h + jj], b2[32 * h + jj]));
+          epi_e4m3_32<128>(v, a2 + 32 * h, c2 + 32 * h, slot + FS_H2, row, 32 * h);
         }
-        const float sh = amax > 0.f ? amax / E4M3_MAX : 1.f;
-        const float inv = amax > 0.f ? E4M3_MAX / amax : 0.f;
-#pragma unroll 1
-        for (int h = 0; h < 4; ++h) {
-          tmem_ld32(tslot + 64 + 32 * h, v);
-#pragma unroll
-          for (int jj = 0; jj < 32; ++jj)
-            v[jj] = fmaxf(fmaf(v[jj], sa * sw2[32 * h + jj], b2[32 * h + jj]), 0.f) * inv;
-#pragma unroll
-          for (int c = 0; c < 2; ++c) {
-            uint4 w;
-            w.x = pack_e4m3x4(v[16 * c + 0], v[16 * c + 1], v[16 * c + 2], v[16 * c + 3]);
-            w.y = pack_e4m3x4(v[16 * c + 4], v[16 * c + 5], v[16 * c + 6], v[16 * c + 7]);
-            w.z = pack_e4m3x4(v[16 * c + 8], v[16 * c + 9], v[16 * c + 10], v[16 * c + 11]);
-            w.w = pack_e4m3x4(v[16 * c + 12], v[16 * c + 13], v[16 * c + 14], v[16 * c + 15]);
-            *reinterpret_cast<uint4*>(slot + FS_H2 + kmajor_off8(row, 32 * h + 16 * c, 128)) = w;
-          }
-        }
-        s_h2[row] = sh;
       }
       fence_async_smem();
       tc_fence_before();
       mbar_arrive(BAR(B_H2RDY + s));
-      // ---- layer 3 epilogue: max over valid points of D3^T s_h2[pt], then * sw3 + b3
+      // ---- layer 3 epilogue: max over valid points, then * w3 + b3, relu
       if (!(ok = mbar_wait_or_abort(BAR(B_D3 + s), ph, abort, WAIT_CYCLES))) break;
       tc_fence_after();
-      // crop counts (and row scales) written by other threads of this warpgroup
-      asm volatile("bar.sync %0, 128;" ::"r"(1 + s) : "memory");
+      asm volatile("bar.sync %0, 128;" ::"r"(1 + s) : "memory");  // counts of other warps
       const int cntA = cnt_s[0] + cnt_s[1], cntB = cnt_s[2] + cnt_s[3];
       float v[32];
 #pragma unroll
@@ -313,19 +279,23 @@ __global__ void __launch_bounds__(F_THREADS, 1)
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           const int cnt = q < 2 ? cntA : cntB;
-          const int c0 = 32 * (q & 1);
-          if (c0 < cnt) {
+          const int q0 = 32 * (q & 1);
+          if (q0 < cnt) {
             tmem_ld32(tslot + 128 * half + 32 * q, v);
             float m = -INFINITY;
+            if (q0 + 32 <= cnt) {
 #pragma unroll
-            for (int jj = 0; jj < 32; ++jj)
-              m = fmaxf(m, (c0 + jj < cnt) ? v[jj] * s_h2[32 * q + jj] : -INFINITY);
+              for (int jj = 0; jj < 32; ++jj) m = fmaxf(m, v[jj]);
+            } else {
+#pragma unroll
+              for (int jj = 0; jj < 32; ++jj) m = fmaxf(m, (q0 + jj < cnt) ? v[jj] : -INFINITY);
+            }
             if (q < 2) mA = fmaxf(mA, m);
             else mB = fmaxf(mB, m);
           }
         }
         const int ch = 128 * half + row;
-        const float sc = sw3[ch], bias = b3[ch];
+        const float sc = w3[ch], bias = b3[ch];
         feat[(size_t)p * 512 + ch] = cntA > 0 ? fmaxf(fmaf(mA, sc, bias), 0.f) : 0.f;
         feat[(size_t)p * 512 + 256 + ch] = cntB > 0 ? fmaxf(fmaf(mB, sc, bias), 0.f) : 0.f;
       }
@@ -342,18 +312,17 @@ __global__ void __launch_bounds__(F_THREADS, 1)
 
 // ----------------------------------------------------------------- head
 constexpr int HT = 128;
-constexpr int G_W3 = 0;                          // Wh3 [16 x 256] e4m3 (rows 8.. zero) 4 KB
-constexpr int G_SC = G_W3 + 16 * 256;            // swh1 256, swh2 256, swh3 16 (f32)
-constexpr int G_BIAS = G_SC + (256 + 256 + 16) * 4;  // hb1 256, hb2 256, hb3 16
-constexpr int G_RES_BYTES = G_BIAS + (256 + 256 + 16) * 4;
+constexpr int G_W3 = 0;                  // Wh3' [16 x 256] e4m3 (rows 8.. zero) 4 KB
+constexpr int G_EP = G_W3 + 16 * 256;    // f_inv [256], a4 c4 [256], a5 c5 [256], w6 hb3 [16]
+constexpr int G_RES_BYTES = G_EP + (5 * 256 + 2 * 16) * 4;
 static_assert(G_RES_BYTES % 128 == 0, "fp8 head resident image");
-constexpr int G_CHUNK = 256 * 128;               // one B chunk [256 x 128] e4m3, 32 KB
-constexpr int G_IMG_W1 = G_RES_BYTES;            // 4 chunks
-constexpr int G_IMG_W2 = G_IMG_W1 + 4 * G_CHUNK; // 2 chunks
+constexpr int G_CHUNK = 256 * 128;       // one B chunk [256 x 128] e4m3, 32 KB
+constexpr int G_IMG_W1 = G_RES_BYTES;    // 4 chunks
+constexpr int G_IMG_W2 = G_IMG_W1 + 4 * G_CHUNK;  // 2 chunks
 constexpr int G_IMG_BYTES = G_IMG_W2 + 2 * G_CHUNK;
-constexpr int G_A = G_RES_BYTES;                 // A chunk [128 x 128] e4m3, 16 KB
-constexpr int G_B = G_A + 128 * 128;             // B chunk 32 KB
-constexpr int G_G = G_B + G_CHUNK;               // G [128 x 256] e4m3, 32 KB
+constexpr int G_A = G_RES_BYTES;         // A chunk [128 x 128] e4m3, 16 KB
+constexpr int G_B = G_A + 128 * 128;     // B chunk 32 KB
+constexpr int G_G = G_B + G_CHUNK;       // G [128 x 256] e4m3, 32 KB
 constexpr int G_CTRL = G_G + 128 * 256;
 constexpr int G_SMEM = G_CTRL + 64;
 
@@ -362,47 +331,26 @@ __device__ __forceinline__ void copy_chunk(unsigned char* dst, const unsigned ch
     reinterpret_cast<uint4*>(dst)[i] = ldg_v4(src + 16 * (size_t)i);
 }
 
-// Head epilogue of a 256-wide layer in e4m3: z = relu(D sa sw + b), per-row
-// scale; writes G (K = 256) and returns the row scale.
-__device__ __forceinline__ float head_epi_fp8(uint32_t taddr, float sa, const float* sw,
-                                              const float* b, unsigned char* G, int row) {
+__device__ __forceinline__ void head_epi_fp8(uint32_t taddr, const float* alpha, const float* beta,
+                                             unsigned char* G, int row) {
   float v[32];
-  float amax = 0.f;
-#pragma unroll 1
+#pragma unroll 2
   for (int h = 0; h < 8; ++h) {
     tmem_ld32(taddr + 32 * h, v);
-#pragma unroll
-    for (int jj = 0; jj < 32; ++jj) amax = fmaxf(amax, fmaf(v[jj], sa * sw[32 * h + jj], b[32 * h + jj]));
+    epi_e4m3_32<256>(v, alpha + 32 * h, beta + 32 * h, G, row, 32 * h);
   }
-  const float inv = amax > 0.f ? E4M3_MAX / amax : 0.f;
-#pragma unroll 1
-  for (int h = 0; h < 8; ++h) {
-    tmem_ld32(taddr + 32 * h, v);
-#pragma unroll
-    for (int jj = 0; jj < 32; ++jj)
-      v[jj] = fmaxf(fmaf(v[jj], sa * sw[32 * h + jj], b[32 * h + jj]), 0.f) * inv;
-#pragma unroll
-    for (int c = 0; c < 2; ++c) {
-      uint4 w;
-      w.x = pack_e4m3x4(v[16 * c + 0], v[16 * c + 1], v[16 * c + 2], v[16 * c + 3]);
-      w.y = pack_e4m3x4(v[16 * c + 4], v[16 * c + 5], v[16 * c + 6], v[16 * c + 7]);
-      w.z = pack_e4m3x4(v[16 * c + 8], v[16 * c + 9], v[16 * c + 10], v[16 * c + 11]);
-      w.w = pack_e4m3x4(v[16 * c + 12], v[16 * c + 13], v[16 * c + 14], v[16 * c + 15]);
-      *reinterpret_cast<uint4*>(G + kmajor_off8(row, 32 * h + 16 * c, 256)) = w;
-    }
-  }
-  return amax > 0.f ? amax / E4M3_MAX : 1.f;
 }
 
 __global__ void __launch_bounds__(128, 1)
-    head_fp8_kernel(const float* __restrict__ feat, int n_pairs, const int* n_dev,
+    head_fp8_kernel(const float* __restrict__ feat, PairRange rg,
                     const unsigned char* __restrict__ img, PairInputs in, int have_in,
                     const float4* __restrict__ centre, float* __restrict__ out,
                     float* __restrict__ y_raw, int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char smem[];
   const int tid = threadIdx.x, warp = tid >> 5;
-  const int n = n_dev ? min(*n_dev, n_pairs) : n_pairs;
-  const int n_tiles = (n + HT - 1) / HT;
+  int lo, n;
+  range_bounds(rg, &lo, &n);  // this launch's pairs: [lo, n)
+  const int n_tiles = (n - lo + HT - 1) / HT;
   if ((int)blockIdx.x >= n_tiles) return;
   for (int i = tid; i < G_RES_BYTES / 16; i += 128)
     reinterpret_cast<uint4*>(smem)[i] = ldg_v4(img + 16 * (size_t)i);
@@ -423,12 +371,13 @@ __global__ void __launch_bounds__(128, 1)
   tc_fence_after();
   const uint32_t tbase = *tmem_slot;
   const uint32_t lane_off = (uint32_t)(32 * warp) << 16;
-  const float* swh1 = reinterpret_cast<const float*>(smem + G_SC);
-  const float* swh2 = swh1 + 256;
-  const float* swh3 = swh2 + 256;
-  const float* hb1 = reinterpret_cast<const float*>(smem + G_BIAS);
-  const float* hb2 = hb1 + 256;
-  const float* hb3 = hb2 + 256;
+  const float* finv = reinterpret_cast<const float*>(smem + G_EP);
+  const float* a4 = finv + 256;
+  const float* c4 = a4 + 256;
+  const float* a5 = c4 + 256;
+  const float* c5 = a5 + 256;
+  const float* w6 = c5 + 256;
+  const float* hb3 = w6 + 16;
   unsigned char* A = smem + G_A;
   unsigned char* B = smem + G_B;
   unsigned char* G = smem + G_G;
@@ -438,36 +387,33 @@ __global__ void __launch_bounds__(128, 1)
   bool ok = true;
 
   for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
-    const int pr = tile * HT + tid;
+    const int pr = lo + tile * HT + tid;
     const bool row_ok = pr < n;
     const float* src = feat + (size_t)pr * 512;
-    // per-pair scale of the pooled features
-    float amax = 0.f;
-    if (row_ok) {
-      for (int k = 0; k < 512; k += 4) {
-        const float4 f = __ldg(reinterpret_cast<const float4*>(src + k));
-        amax = fmaxf(amax, fmaxf(fmaxf(f.x, f.y), fmaxf(f.z, f.w)));
-      }
-    }
-    const float sf = amax > 0.f ? amax / E4M3_MAX : 1.f;
-    const float inv = amax > 0.f ? E4M3_MAX / amax : 0.f;
 #pragma unroll 1
     for (int kc = 0; kc < 4; ++kc) {
+      const float* fi = finv + (128 * kc) % 256;
 #pragma unroll
       for (int c = 0; c < 8; ++c) {
-        float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f), a1 = a0, a2 = a0, a3 = a0;
+        float t[16];
         if (row_ok) {
-          const float* sp = src + 128 * kc + 16 * c;
-          a0 = __ldg(reinterpret_cast<const float4*>(sp));
-          a1 = __ldg(reinterpret_cast<const float4*>(sp + 4));
-          a2 = __ldg(reinterpret_cast<const float4*>(sp + 8));
-          a3 = __ldg(reinterpret_cast<const float4*>(sp + 12));
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const float4 f = __ldg(reinterpret_cast<const float4*>(src + 128 * kc + 16 * c + 4 * q));
+            t[4 * q + 0] = f.x * fi[16 * c + 4 * q + 0];
+            t[4 * q + 1] = f.y * fi[16 * c + 4 * q + 1];
+            t[4 * q + 2] = f.z * fi[16 * c + 4 * q + 2];
+            t[4 * q + 3] = f.w * fi[16 * c + 4 * q + 3];
+          }
+        } else {
+#pragma unroll
+          for (int q = 0; q < 16; ++q) t[q] = 0.f;
         }
         uint4 w;
-        w.x = pack_e4m3x4(a0.x * inv, a0.y * inv, a0.z * inv, a0.w * inv);
-        w.y = pack_e4m3x4(a1.x * inv, a1.y * inv, a1.z * inv, a1.w * inv);
-        w.z = pack_e4m3x4(a2.x * inv, a2.y * inv, a2.z * inv, a2.w * inv);
-        w.w = pack_e4m3x4(a3.x * inv, a3.y * inv, a3.z * inv, a3.w * inv);
+        w.x = pack_e4m3x4(t[0], t[1], t[2], t[3]);
+        w.y = pack_e4m3x4(t[4], t[5], t[6], t[7]);
+        w.z = pack_e4m3x4(t[8], t[9], t[10], t[11]);
+        w.w = pack_e4m3x4(t[12], t[13], t[14], t[15]);
         *reinterpret_cast<uint4*>(A + kmajor_off8(tid, 16 * c, 128)) = w;
       }
       copy_chunk(B, img + G_IMG_W1 + (size_t)kc * G_CHUNK, G_CHUNK);
@@ -488,7 +434,7 @@ __global__ void __launch_bounds__(128, 1)
       tc_fence_after();
     }
     if (!ok) break;
-    const float sg1 = head_epi_fp8(tbase + lane_off + 0, sf, swh1, hb1, G, tid);
+    head_epi_fp8(tbase + lane_off + 0, a4, c4, G, tid);
 #pragma unroll 1
     for (int kc = 0; kc < 2; ++kc) {
       copy_chunk(B, img + G_IMG_W2 + (size_t)kc * G_CHUNK, G_CHUNK);
@@ -509,7 +455,7 @@ __global__ void __launch_bounds__(128, 1)
       tc_fence_after();
     }
     if (!ok) break;
-    const float sg2 = head_epi_fp8(tbase + lane_off + 256, sg1, swh2, hb2, G, tid);
+    head_epi_fp8(tbase + lane_off + 256, a5, c5, G, tid);
     fence_async_smem();
     tc_fence_before();
     __syncthreads();
@@ -531,7 +477,7 @@ __global__ void __launch_bounds__(128, 1)
       if (row_ok) {
         float y[8];
 #pragma unroll
-        for (int o = 0; o < 8; ++o) y[o] = fmaf(v[o], sg2 * swh3[o], hb3[o]);
+        for (int o = 0; o < 8; ++o) y[o] = fmaf(v[o], w6[o], hb3[o]);
         if (y_raw) {
 #pragma unroll
           for (int o = 0; o < 8; ++o) y_raw[(size_t)pr * 8 + o] = y[o];
@@ -576,6 +522,44 @@ float bf16_value_h(uint16_t b) {
   return f;
 }
 
+// Scales of one folded layer: for W [out][in] with input channel scales
+// s_in[in], returns the folded weights W' = W s_in (float32 [out][in]), the
+// per-output-channel weight scales w = max|W'| / 448 and their inverses, and
+// the output bound B_out[c] = max(0, sum_k |W[c][k]| B_in[k] + b[c]).
+struct Folded {
+  std::vector<float> Wf, inv;
+  std::vector<double> w, bound;
+};
+
+Folded fold(const float* W, const float* b, int out, int in, const std::vector<double>& s_in,
+            const std::vector<double>& B_in) {
+  Folded f;
+  f.Wf.resize((size_t)out * in);
+  f.inv.resize(out);
+  f.w.resize(out);
+  f.bound.resize(out);
+  for (int c = 0; c < out; ++c) {
+    double amax = 0.0, acc = b[c];
+    for (int k = 0; k < in; ++k) {
+      const double wf = (double)W[(size_t)c * in + k] * s_in[k % s_in.size()];
+      f.Wf[(size_t)c * in + k] = (float)wf;
+      amax = std::max(amax, std::fabs(wf));
+      acc += std::fabs((double)W[(size_t)c * in + k]) * B_in[k % B_in.size()];
+    }
+    f.w[c] = amax > 0 ? amax / 448.0 : 1.0;
+    f.inv[c] = (float)(1.0 / f.w[c]);
+    f.bound[c] = std::max(0.0, acc);
+  }
+  return f;
+}
+
+// activation scale of a channel with bound B: 1.1 B / 448 (1 for B == 0)
+std::vector<double> act_scale(const std::vector<double>& B) {
+  std::vector<double> s(B.size());
+  for (size_t i = 0; i < B.size(); ++i) s[i] = B[i] > 0 ? 1.1 * B[i] / 448.0 : 1.0;
+  return s;
+}
+
 }  // namespace
 
 int upload_fp8_params(locc_handle* h, const std::vector<float>& params) {
@@ -586,6 +570,25 @@ int upload_fp8_params(locc_handle* h, const std::vector<float>& params) {
     offb[l] = o;
     o += L_OUT[l];
   }
+  const float* P = params.data();
+  // layer-1 output bound from the crop ball |x| <= r
+  std::vector<double> B1(64);
+  for (int c = 0; c < 64; ++c) {
+    const float* w = P + off[0] + 3 * c;
+    const double nrm = std::sqrt((double)w[0] * w[0] + (double)w[1] * w[1] + (double)w[2] * w[2]);
+    B1[c] = std::max(0.0, (double)h->radius * nrm + P[offb[0] + c]);
+  }
+  const std::vector<double> s1 = act_scale(B1);
+  const Folded L2 = fold(P + off[1], P + offb[1], 128, 64, s1, B1);
+  const std::vector<double> s2 = act_scale(L2.bound);
+  const Folded L3 = fold(P + off[2], P + offb[2], 256, 128, s2, L2.bound);
+  const std::vector<double> s3 = act_scale(L3.bound);
+  const Folded H1 = fold(P + off[3], P + offb[3], 256, 512, s3, L3.bound);
+  const std::vector<double> s4 = act_scale(H1.bound);
+  const Folded H2 = fold(P + off[4], P + offb[4], 256, 256, s4, H1.bound);
+  const std::vector<double> s5 = act_scale(H2.bound);
+  const Folded H3 = fold(P + off[5], P + offb[5], 8, 256, s5, H2.bound);
+
   const size_t enc_bytes = (F_IMG_BYTES + 255) / 256 * 256;
   const size_t total = enc_bytes + G_IMG_BYTES;
   std::vector<unsigned char> img(total, 0);
@@ -594,40 +597,66 @@ int upload_fp8_params(locc_handle* h, const std::vector<float>& params) {
     for (int k = 0; k < 16; ++k) {
       float val = 0.f;
       if (k < 9) {
-        const float w = params[off[0] + (size_t)c * 3 + (k % 3)];
+        const float w = P[off[0] + (size_t)c * 3 + (k % 3)];
         const float hi = bf16_value_h(bf16_bits_h(w));
         val = k < 6 ? hi : w - hi;
       }
       const uint16_t b = bf16_bits_h(val);
       std::memcpy(e + F_W1 + kmajor_off(c, k, 16), &b, 2);
     }
-  std::memcpy(e + F_BIAS, &params[offb[0]], 64 * 4);
-  std::memcpy(e + F_BIAS + 64 * 4, &params[offb[1]], 128 * 4);
-  std::memcpy(e + F_BIAS + 192 * 4, &params[offb[2]], 256 * 4);
+  float* ep = reinterpret_cast<float*>(e + F_EP);
+  for (int c = 0; c < 64; ++c) {
+    ep[c] = (float)(1.0 / s1[c]);                     // a1
+    ep[64 + c] = (float)(P[offb[0] + c] / s1[c]);     // c1
+  }
+  for (int c = 0; c < 128; ++c) {
+    ep[128 + c] = (float)(L2.w[c] / s2[c]);           // a2
+    ep[256 + c] = (float)(P[offb[1] + c] / s2[c]);    // c2
+  }
+  for (int c = 0; c < 256; ++c) {
+    ep[384 + c] = (float)L3.w[c];                     // w3
+    ep[640 + c] = P[offb[2] + c];                     // b3
+  }
   unsigned char* hd = img.data() + enc_bytes;
-  std::memcpy(hd + G_BIAS, &params[offb[3]], 256 * 4);
-  std::memcpy(hd + G_BIAS + 256 * 4, &params[offb[4]], 256 * 4);
-  std::memcpy(hd + G_BIAS + 512 * 4, &params[offb[5]], 8 * 4);
-  float* d_params = nullptr;
+  float* hp = reinterpret_cast<float*>(hd + G_EP);
+  for (int c = 0; c < 256; ++c) {
+    hp[c] = (float)(1.0 / s3[c]);                     // feature inverse scale
+    hp[256 + c] = (float)(H1.w[c] / s4[c]);           // a4
+    hp[512 + c] = (float)(P[offb[3] + c] / s4[c]);    // c4
+    hp[768 + c] = (float)(H2.w[c] / s5[c]);           // a5
+    hp[1024 + c] = (float)(P[offb[4] + c] / s5[c]);   // c5
+  }
+  for (int c = 0; c < 8; ++c) {
+    hp[1280 + c] = (float)H3.w[c];                    // w6
+    hp[1296 + c] = P[offb[5] + c];                    // hb3
+  }
+  // folded weights and their inverse scales, quantised on the GPU
+  std::vector<float> fw;
+  auto put = [&](const Folded& f) {
+    const size_t at = fw.size();
+    fw.insert(fw.end(), f.Wf.begin(), f.Wf.end());
+    fw.insert(fw.end(), f.inv.begin(), f.inv.end());
+    return at;
+  };
+  const size_t o2 = put(L2), o3 = put(L3), o4 = put(H1), o5 = put(H2), o6 = put(H3);
+  float* d_fw = nullptr;
   bool ok = cudaMalloc(&h->d_wf8, total) == cudaSuccess &&
             cudaMemcpy(h->d_wf8, img.data(), total, cudaMemcpyHostToDevice) == cudaSuccess &&
-            cudaMalloc(&d_params, params.size() * 4) == cudaSuccess &&
-            cudaMemcpy(d_params, params.data(), params.size() * 4, cudaMemcpyHostToDevice) == cudaSuccess;
+            cudaMalloc(&d_fw, fw.size() * 4) == cudaSuccess &&
+            cudaMemcpy(d_fw, fw.data(), fw.size() * 4, cudaMemcpyHostToDevice) == cudaSuccess;
   if (ok) {
     unsigned char* de = static_cast<unsigned char*>(h->d_wf8);
     unsigned char* dh = de + enc_bytes;
-    float* esc = reinterpret_cast<float*>(de + F_SC);
-    float* hsc = reinterpret_cast<float*>(dh + G_SC);
-    quant_e4m3_kernel<<<128, 128>>>(d_params + off[1], 128, 64, 64, de + F_W2, esc);
-    quant_e4m3_kernel<<<256, 128>>>(d_params + off[2], 256, 128, 128, de + F_W3, esc + 128);
-    quant_e4m3_kernel<<<256, 128>>>(d_params + off[3], 256, 512, 128, dh + G_IMG_W1, hsc);
-    quant_e4m3_kernel<<<256, 128>>>(d_params + off[4], 256, 256, 128, dh + G_IMG_W2, hsc + 256);
-    quant_e4m3_kernel<<<8, 128>>>(d_params + off[5], 8, 256, 256, dh + G_W3, hsc + 512);
+    quant_e4m3_kernel<<<128, 128>>>(d_fw + o2, d_fw + o2 + 128 * 64, 128, 64, 64, de + F_W2);
+    quant_e4m3_kernel<<<256, 128>>>(d_fw + o3, d_fw + o3 + 256 * 128, 256, 128, 128, de + F_W3);
+    quant_e4m3_kernel<<<256, 128>>>(d_fw + o4, d_fw + o4 + 256 * 512, 256, 512, 128, dh + G_IMG_W1);
+    quant_e4m3_kernel<<<256, 128>>>(d_fw + o5, d_fw + o5 + 256 * 256, 256, 256, 128, dh + G_IMG_W2);
+    quant_e4m3_kernel<<<8, 128>>>(d_fw + o6, d_fw + o6 + 8 * 256, 8, 256, 256, dh + G_W3);
     ok = cudaGetLastError() == cudaSuccess && cudaDeviceSynchronize() == cudaSuccess;
     h->wf8_enc = de;
     h->wf8_head = dh;
   }
-  cudaFree(d_params);
+  cudaFree(d_fw);
   if (!ok) {
     cudaGetLastError();
     set_error("cannot build the e4m3 parameter images");
@@ -636,9 +665,10 @@ int upload_fp8_params(locc_handle* h, const std::vector<float>& params) {
   return LOCC_OK;
 }
 
-int run_network_fp8(locc_handle* h, const float4* xyz, int n_pairs, const int* n_dev,
-                    const PairInputs* in, const float4* centre, float* out, float* y_raw,
-                    float* feat_out, cudaStream_t stream, cudaEvent_t mid) {
+int run_network_fp8(locc_handle* h, const float4* xyz, const PairRange& rg, const PairInputs* in,
+                    const float4* centre, float* out, float* y_raw, float* feat_out,
+                    cudaStream_t stream, cudaEvent_t mid) {
+  const int n_pairs = (rg.n_cap + rg.n_chunks - 1) / rg.n_chunks + 1;  // pairs of one chunk, at most
   static bool attr = false;
   if (!attr) {
     if (cudaFuncSetAttribute(encoder_fp8_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -652,7 +682,7 @@ int run_network_fp8(locc_handle* h, const float4* xyz, int n_pairs, const int* n
   }
   float* feat = feat_out ? feat_out : h->d_feat;
   encoder_fp8_kernel<<<std::min(n_pairs, h->n_sm), F_THREADS, F_SMEM, stream>>>(
-      xyz, n_pairs, n_dev, h->wf8_enc, feat, h->d_err);
+      xyz, rg, h->wf8_enc, feat, h->d_err);
   if (cudaGetLastError() != cudaSuccess) {
     set_error("encoder_fp8_kernel launch failed");
     return LOCC_ERR_CUDA;
@@ -661,7 +691,7 @@ int run_network_fp8(locc_handle* h, const float4* xyz, int n_pairs, const int* n
   PairInputs pin{};
   if (in) pin = *in;
   head_fp8_kernel<<<std::min((n_pairs + HT - 1) / HT, h->n_sm), 128, G_SMEM, stream>>>(
-      feat, n_pairs, n_dev, h->wf8_head, pin, in != nullptr, centre, out, y_raw, h->d_err);
+      feat, rg, h->wf8_head, pin, in != nullptr, centre, out, y_raw, h->d_err);
   if (cudaGetLastError() != cudaSuccess) {
     set_error("head_fp8_kernel launch failed");
     return LOCC_ERR_CUDA;

@@ -93,12 +93,14 @@ __device__ __forceinline__ void enc_epi_rows(uint32_t taddr, const float* b, uns
 }
 
 __global__ void __launch_bounds__(E_THREADS, 1)
-    encoder_tc_kernel(const float4* __restrict__ xyz, int n_pairs, const int* n_dev,
+    encoder_tc_kernel(const float4* __restrict__ xyz, PairRange rg,
                       const unsigned char* __restrict__ img, float* __restrict__ feat,
                       int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char smem[];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int n = n_dev ? min(*n_dev, n_pairs) : n_pairs;
+  int lo, hi;
+  range_bounds(rg, &lo, &hi);
+  const int n = hi - lo;
   if ((int)blockIdx.x >= n) return;
   const int my_pairs = (n - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
 
@@ -150,7 +152,7 @@ __global__ void __launch_bounds__(E_THREADS, 1)
       int issued[2] = {0, 0};
       auto load_pair = [&](int i) {
         const int s = i & 1;
-        const int p = blockIdx.x + i * gridDim.x;
+        const int p = lo + blockIdx.x + i * gridDim.x;
         mbar_expect_tx(BAR(B_FULLX + s), ROWS * 16);
         bulk_g2s(smem_u32(smem + E_SLOT0 + s * SLOT_BYTES + S_STG), xyz + (size_t)p * ROWS, ROWS * 16,
                  BAR(B_FULLX + s));
@@ -222,7 +224,7 @@ __global__ void __launch_bounds__(E_THREADS, 1)
     for (int j = 0; ok; ++j) {
       const int i = 2 * j + s;
       if (i >= my_pairs) break;
-      const int p = blockIdx.x + i * gridDim.x;
+      const int p = lo + blockIdx.x + i * gridDim.x;
       const uint32_t ph = j & 1;
       // crop rows -> bf16 hi/lo X tile
       if (!(ok = mbar_wait_or_abort(BAR(B_FULLX + s), ph, abort, WAIT_CYCLES))) break;
@@ -347,14 +349,15 @@ __device__ __forceinline__ void head_epi_256(uint32_t taddr, const float* b, uns
 }
 
 __global__ void __launch_bounds__(128, 1)
-    head_tc_kernel(const float* __restrict__ feat, int n_pairs, const int* n_dev,
+    head_tc_kernel(const float* __restrict__ feat, PairRange rg,
                    const unsigned char* __restrict__ img, PairInputs in, int have_in,
                    const float4* __restrict__ centre, float* __restrict__ out,
                    float* __restrict__ y_raw, int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char smem[];
   const int tid = threadIdx.x, warp = tid >> 5;
-  const int n = n_dev ? min(*n_dev, n_pairs) : n_pairs;
-  const int n_tiles = (n + HT - 1) / HT;
+  int lo, n;
+  range_bounds(rg, &lo, &n);  // this launch's pairs: [lo, n)
+  const int n_tiles = (n - lo + HT - 1) / HT;
   if ((int)blockIdx.x >= n_tiles) return;
   for (int i = tid; i < H_RES_BYTES / 16; i += 128)
     reinterpret_cast<uint4*>(smem)[i] = ld_global_v4(img + 16 * (size_t)i);
@@ -386,7 +389,7 @@ __global__ void __launch_bounds__(128, 1)
   bool ok = true;
 
   for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
-    const int q0 = tile * HT;
+    const int q0 = lo + tile * HT;
     const int pr = q0 + tid;  // this thread's pair (row)
     const bool row_ok = pr < n;
     // ---- layer 1: D1[128 x 256] = F[128 x 512] . Wh1^T, K in chunks of 64
@@ -580,11 +583,12 @@ int upload_tc_params(locc_handle* h, const std::vector<float>& params) {
   return LOCC_OK;
 }
 
-int run_network_tc(locc_handle* h, const float4* xyz, int n_pairs, const int* n_dev,
-                   const PairInputs* in, const float4* centre, float* out, float* y_raw,
-                   float* feat_out, cudaStream_t stream, cudaEvent_t mid) {
+int run_network_tc(locc_handle* h, const float4* xyz, const PairRange& rg, const PairInputs* in,
+                   const float4* centre, float* out, float* y_raw, float* feat_out,
+                   cudaStream_t stream, cudaEvent_t mid) {
   if (h->prec == LOCC_FP8)
-    return run_network_fp8(h, xyz, n_pairs, n_dev, in, centre, out, y_raw, feat_out, stream, mid);
+    return run_network_fp8(h, xyz, rg, in, centre, out, y_raw, feat_out, stream, mid);
+  const int n_pairs = (rg.n_cap + rg.n_chunks - 1) / rg.n_chunks + 1;  // pairs of one chunk, at most
   static bool attr = false;
   if (!attr) {
     if (cudaFuncSetAttribute(encoder_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -598,8 +602,7 @@ int run_network_tc(locc_handle* h, const float4* xyz, int n_pairs, const int* n_
   }
   float* feat = feat_out ? feat_out : h->d_feat;
   const int grid_e = std::min(n_pairs, h->n_sm);
-  encoder_tc_kernel<<<grid_e, E_THREADS, E_SMEM, stream>>>(xyz, n_pairs, n_dev, h->wtc_enc, feat,
-                                                     h->d_err);
+  encoder_tc_kernel<<<grid_e, E_THREADS, E_SMEM, stream>>>(xyz, rg, h->wtc_enc, feat, h->d_err);
   if (cudaGetLastError() != cudaSuccess) {
     set_error("encoder_tc_kernel launch failed");
     return LOCC_ERR_CUDA;
@@ -608,8 +611,8 @@ int run_network_tc(locc_handle* h, const float4* xyz, int n_pairs, const int* n_
   PairInputs pin{};
   if (in) pin = *in;
   const int grid_h = std::min((n_pairs + HT - 1) / HT, h->n_sm);
-  head_tc_kernel<<<grid_h, 128, H_SMEM, stream>>>(feat, n_pairs, n_dev, h->wtc_head, pin,
-                                                  in != nullptr, centre, out, y_raw, h->d_err);
+  head_tc_kernel<<<grid_h, 128, H_SMEM, stream>>>(feat, rg, h->wtc_head, pin, in != nullptr,
+                                                  centre, out, y_raw, h->d_err);
   if (cudaGetLastError() != cudaSuccess) {
     set_error("head_tc_kernel launch failed");
     return LOCC_ERR_CUDA;

@@ -97,11 +97,12 @@ extern "C" int locc_detect_noalloc(locc_handle* h, const float* poses, const int
   int32_t* cnt = reinterpret_cast<int32_t*>(base + kXyzBytes + kFeatBytes + kCentreBytes);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   PairInputs in{poses, obj_shape, pairs, n_obj, n_pairs};
-  cudaError_t e = launch_crop(dev_library(h), in, nullptr, h->radius, xyz, nullptr, cnt, centre,
-                              h->d_err, h->n_sm, s);
-  if (e == cudaSuccess) e = launch_encoder_fp32(xyz, n_pairs, nullptr, h->fp32, feat, h->n_sm, s);
+  const PairRange rg = whole_range(n_pairs, nullptr);
+  cudaError_t e = launch_crop(dev_library(h), in, rg, h->radius, xyz, nullptr, cnt, centre,
+                              h->d_err, h->n_sm, 0, s);
+  if (e == cudaSuccess) e = launch_encoder_fp32(xyz, rg, h->fp32, feat, h->n_sm, s);
   if (e == cudaSuccess)
-    e = launch_head_fp32(feat, n_pairs, nullptr, h->fp32, &in, centre, out, nullptr, h->n_sm, s);
+    e = launch_head_fp32(feat, rg, h->fp32, &in, centre, out, nullptr, h->n_sm, s);
   if (e != cudaSuccess) {
     set_error(cudaGetErrorString(e));
     return LOCC_ERR_CUDA;

@@ -248,3 +248,62 @@ def test_step_matches_broadphase_then_detect(scene64):
         ref = oracle.crop_forward(lib.points, lib.aabb, poses, osh, pairs[sample], R, params,
                                   n_threads=8)
         assert_close_rel(ref_dev[sample], ref["out"], what="step outputs")
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16", "fp8"])
+def test_pipelined_step_is_bit_identical(scene64, prec):
+    lib, poses, osh, env, pairs, layers = scene64
+    dev = _dev()
+    with _detector(lib, layers, prec) as det:
+        det.reserve(400_000, len(env) - 1)
+        tp, ts, te = _t(poses, dev), _t(osh, dev), _t(env, dev)
+        _, n, ref = det.step(tp, ts, te, 400_000)
+        n = int(n.item())
+        ref = ref[:n].cpu().numpy()
+        for chunks, cap in ((2, 0), (4, 6), (8, 4), (3, 8)):
+            det.set_pipeline(chunks, cap)
+            _, n2, out = det.step(tp, ts, te, 400_000)
+            assert int(n2.item()) == n
+            np.testing.assert_array_equal(out[:n].cpu().numpy(), ref)
+            d = det.detect(tp, ts, _t(pairs, dev)).cpu().numpy()
+            np.testing.assert_array_equal(d, ref)
+        best, ms = det.autotune(tp, ts, te, 400_000, reps=1)
+        assert best[0] in (1, 2, 4, 8) and ms > 0
+        _, _, out = det.step(tp, ts, te, 400_000)
+        np.testing.assert_array_equal(out[:n].cpu().numpy(), ref)
+        det.status()
+
+
+def test_step_replays_as_cuda_graph(scene64):
+    lib, poses, osh, env, pairs, layers = scene64
+    dev = _dev()
+    with _detector(lib, layers, "bf16") as det:
+        det.reserve(400_000, len(env) - 1)
+        det.set_pipeline(4, 6)
+        tp, ts, te = _t(poses, dev), _t(osh, dev), _t(env, dev)
+        pr = torch.empty((400_000, 2), dtype=torch.int32, device=dev)
+        n = torch.zeros(1, dtype=torch.int32, device=dev)
+        out = torch.empty((400_000, 8), dtype=torch.float32, device=dev)
+        s = torch.cuda.Stream()
+        with torch.cuda.stream(s):
+            det.step(tp, ts, te, 400_000, pr, n, out)  # warm-up outside capture
+            ref = out[:len(pairs)].clone()
+            g = torch.cuda.CUDAGraph()
+            out.zero_()
+            with torch.cuda.graph(g, stream=s):
+                det.step(tp, ts, te, 400_000, pr, n, out)
+        torch.cuda.synchronize()
+        out.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        assert int(n.item()) == len(pairs)
+        assert torch.equal(out[:len(pairs)], ref)
+        # new poses in the same buffers: the replay follows them
+        p2 = synth.random_poses(len(poses), np.random.default_rng(11), -1, 1)
+        tp.copy_(_t(p2, dev))
+        g.replay()
+        torch.cuda.synchronize()
+        ref2 = oracle.broadphase(lib.aabb, p2, osh, env)
+        assert int(n.item()) == len(ref2)
+        np.testing.assert_array_equal(pr[:len(ref2)].cpu().numpy(), ref2)
+        det.status()
