@@ -47,24 +47,29 @@ constexpr int E_W3 = E_W2 + 128 * 64 * 2;     // [256 x 128] 64 KB
 constexpr int E_BIAS = E_W3 + 256 * 128 * 2;  // b1 64, b2 128, b3 256 (f32)
 constexpr int E_IMG_BYTES = E_BIAS + (64 + 128 + 256) * 4;
 static_assert(E_IMG_BYTES % 16 == 0, "image must be a whole number of 16-byte chunks");
-// two pair slots, each: raw crop rows (f32), X tile, H1 tile, H2 tile
+// NSLOT pair slots.  Each slot: raw crop rows (f32, 2 KB) and one 32 KB
+// operand region that holds, in turn, the X tile (4 KB), H1 (16 KB) and H2
+// (32 KB): each is dead once the MMA that reads it has completed, which the
+// epilogue that writes the next one has already waited for.
+constexpr int NSLOT = 4;
 constexpr int E_SLOT0 = (E_IMG_BYTES + 1023) / 1024 * 1024;
-constexpr int S_STG = 0;                        // [128] float4   2 KB
-constexpr int S_X = S_STG + ROWS * 16;          // [128 x 16]     4 KB
-constexpr int S_H1 = S_X + 128 * 16 * 2;        // [128 x 64]    16 KB
-constexpr int S_H2 = S_H1 + 128 * 64 * 2;       // [128 x 128]   32 KB
-constexpr int SLOT_BYTES = S_H2 + 128 * 128 * 2;
-constexpr int E_CTRL = E_SLOT0 + 2 * SLOT_BYTES;
-// control block: 16 mbarriers (8 B each), tmem slot, abort flag, counts
-constexpr int C_BAR = 0, C_TMEM = 128, C_ABORT = 132, C_CNT = 136;  // C_CNT: [2 slots][4 warps]
-constexpr int E_SMEM = E_CTRL + 256;
+constexpr int S_STG = 0;                  // [128] float4                    2 KB
+constexpr int S_OPD = S_STG + ROWS * 16;  // X [128x16] / H1 [128x64] / H2 [128x128] bf16
+constexpr int SLOT_BYTES = S_OPD + 128 * 128 * 2;
+constexpr int E_CTRL = E_SLOT0 + NSLOT * SLOT_BYTES;
+// control block: mbarriers (8 B each), tmem slot, abort flag, counts [slot][4 warps]
+constexpr int NBAR = 9 * NSLOT + 2;
+constexpr int C_BAR = 0, C_TMEM = 8 * NBAR, C_ABORT = C_TMEM + 4, C_CNT = C_ABORT + 4;
+constexpr int E_SMEM = E_CTRL + C_CNT + 16 * NSLOT;
 static_assert(E_SMEM <= 227 * 1024, "encoder shared memory");
-constexpr int E_THREADS = 288;  // warps 0-3: slot-0 epilogue, 4-7: slot-1 epilogue, 8: MMA + TMA
-constexpr int SLOT_COLS = 256;  // TMEM columns per slot: D1 [0,64) D2 [64,192) D3 [0,256)
+constexpr int E_THREADS = 32 * (4 * NSLOT + 1);  // 4 epilogue warps per slot + the MMA/TMA warp
+constexpr int MMA_WARP = 4 * NSLOT;
+constexpr int SLOT_COLS = 512 / NSLOT;  // TMEM columns per slot: D1 [0,64), D2 / D3a / D3b [0,128)
 
 // barrier indices (per slot s: index + s)
-constexpr int B_FULLX = 0, B_XRDY = 2, B_H1RDY = 4, B_H2RDY = 6, B_D1 = 8, B_D2 = 10, B_D3 = 12,
-              B_W = 14, B_DRAIN = 15;
+constexpr int B_FULLX = 0, B_XRDY = NSLOT, B_H1RDY = 2 * NSLOT, B_H2RDY = 3 * NSLOT,
+              B_E3A = 4 * NSLOT, B_D1 = 5 * NSLOT, B_D2 = 6 * NSLOT, B_D3A = 7 * NSLOT,
+              B_D3B = 8 * NSLOT, B_W = 9 * NSLOT, B_DRAIN = 9 * NSLOT + 1;
 
 __device__ __forceinline__ uint4 ld_global_v4(const void* p) {
   return __ldg(reinterpret_cast<const uint4*>(p));
@@ -92,6 +97,33 @@ __device__ __forceinline__ void enc_epi_rows(uint32_t taddr, const float* b, uns
   }
 }
 
+// Masked max over the valid points of each object of one layer-3 half
+// (thread = channel): TMEM columns [0, 64) are A's points, [64, 128) B's.
+__device__ __forceinline__ void enc_pool(uint32_t taddr, int cntA, int cntB, float* mA, float* mB) {
+  float v[32];
+  float a = -INFINITY, b = -INFINITY;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int cnt = q < 2 ? cntA : cntB;
+    const int c0 = 32 * (q & 1);  // first point slot of this chunk within its object
+    if (c0 < cnt) {
+      tmem_ld32(taddr + 32 * q, v);
+      float m = -INFINITY;
+      if (c0 + 32 <= cnt) {
+#pragma unroll
+        for (int jj = 0; jj < 32; ++jj) m = fmaxf(m, v[jj]);
+      } else {
+#pragma unroll
+        for (int jj = 0; jj < 32; ++jj) m = fmaxf(m, (c0 + jj < cnt) ? v[jj] : -INFINITY);
+      }
+      if (q < 2) a = fmaxf(a, m);
+      else b = fmaxf(b, m);
+    }
+  }
+  *mA = a;
+  *mB = b;
+}
+
 __global__ void __launch_bounds__(E_THREADS, 1)
     encoder_tc_kernel(const float4* __restrict__ xyz, PairRange rg,
                       const unsigned char* __restrict__ img, float* __restrict__ feat,
@@ -112,14 +144,16 @@ __global__ void __launch_bounds__(E_THREADS, 1)
   int* s_cnt = reinterpret_cast<int*>(ctrl + C_CNT);
 
   if (tid == 0) {
-    for (int s = 0; s < 2; ++s) {
+    for (int s = 0; s < NSLOT; ++s) {
       mbar_init(BAR(B_FULLX + s), 1);
       mbar_init(BAR(B_XRDY + s), 128);
       mbar_init(BAR(B_H1RDY + s), 128);
       mbar_init(BAR(B_H2RDY + s), 128);
+      mbar_init(BAR(B_E3A + s), 128);
       mbar_init(BAR(B_D1 + s), 1);
       mbar_init(BAR(B_D2 + s), 1);
-      mbar_init(BAR(B_D3 + s), 1);
+      mbar_init(BAR(B_D3A + s), 1);
+      mbar_init(BAR(B_D3B + s), 1);
     }
     mbar_init(BAR(B_W), 1);
     mbar_init(BAR(B_DRAIN), 1);
@@ -138,77 +172,82 @@ __global__ void __launch_bounds__(E_THREADS, 1)
   const float* b2 = b1 + 64;
   const float* b3 = b2 + 128;
 
-  if (warp == 8) {
+  if (warp == MMA_WARP) {
     // ------------------------------------------------ MMA issuer + TMA producer
     if (lane == 0) {
       const uint32_t sW1 = smem_u32(smem + E_W1), sW2 = smem_u32(smem + E_W2);
       const uint32_t sW3 = smem_u32(smem + E_W3);
-      // resident weights, in 4 bulk copies
+      // resident weights, in bulk copies of at most 32 KB
       mbar_expect_tx(BAR(B_W), E_IMG_BYTES);
       for (int off = 0; off < E_IMG_BYTES; off += 32768) {
         const int bytes = min(32768, E_IMG_BYTES - off);
         bulk_g2s(smem_u32(smem + off), img + off, bytes, BAR(B_W));
       }
-      int issued[2] = {0, 0};
+      int issued[NSLOT] = {};
       auto load_pair = [&](int i) {
-        const int s = i & 1;
+        const int s = i % NSLOT;
         const int p = lo + blockIdx.x + i * gridDim.x;
         mbar_expect_tx(BAR(B_FULLX + s), ROWS * 16);
-        bulk_g2s(smem_u32(smem + E_SLOT0 + s * SLOT_BYTES + S_STG), xyz + (size_t)p * ROWS, ROWS * 16,
-                 BAR(B_FULLX + s));
+        bulk_g2s(smem_u32(smem + E_SLOT0 + s * SLOT_BYTES + S_STG), xyz + (size_t)p * ROWS,
+                 ROWS * 16, BAR(B_FULLX + s));
         ++issued[s];
       };
-      load_pair(0);
-      if (my_pairs > 1) load_pair(1);
+      for (int i = 0; i < NSLOT && i < my_pairs; ++i) load_pair(i);
       bool ok = mbar_wait_or_abort(BAR(B_W), 0, abort, WAIT_CYCLES);
       tc_fence_after();
       const uint32_t id64 = idesc_bf16(128, 64), id128 = idesc_bf16(128, 128);
-      for (int r = 0; ok && 2 * r < my_pairs; ++r) {
+      for (int r = 0; ok && NSLOT * r < my_pairs; ++r) {
         const uint32_t ph = r & 1;
-        // layer 1 of both slots
-        for (int s = 0; s < 2 && ok; ++s) {
-          const int i = 2 * r + s;
-          if (i >= my_pairs) break;
+        const int ns = min(NSLOT, my_pairs - NSLOT * r);  // slots in use this round
+        // layer 1: D1[128 x 64] = X[128 x 16] . W1img^T
+        for (int s = 0; s < ns && ok; ++s) {
           if (!(ok = mbar_wait_or_abort(BAR(B_XRDY + s), ph, abort, WAIT_CYCLES))) break;
           tc_fence_after();
-          if (i + 2 < my_pairs) load_pair(i + 2);  // staging buffer of slot s is free again
-          const uint32_t sX = smem_u32(smem + E_SLOT0 + s * SLOT_BYTES + S_X);
+          const int i = NSLOT * r + s;
+          if (i + NSLOT < my_pairs) load_pair(i + NSLOT);  // staging rows of slot s are free
+          const uint32_t sX = smem_u32(smem + E_SLOT0 + s * SLOT_BYTES + S_OPD);
           mma_bf16(tbase + s * SLOT_COLS, sdesc(sX, 128, 256), sdesc(sW1, 128, 256), id64, 0);
           mma_commit(BAR(B_D1 + s));
         }
-        // layer 2
-        for (int s = 0; s < 2 && ok; ++s) {
-          if (2 * r + s >= my_pairs) break;
+        // layer 2: D2[128 x 128] = H1[128 x 64] . W2img^T
+        for (int s = 0; s < ns && ok; ++s) {
           if (!(ok = mbar_wait_or_abort(BAR(B_H1RDY + s), ph, abort, WAIT_CYCLES))) break;
           tc_fence_after();
-          const uint32_t sH1 = smem_u32(smem + E_SLOT0 + s * SLOT_BYTES + S_H1);
+          const uint32_t sH = smem_u32(smem + E_SLOT0 + s * SLOT_BYTES + S_OPD);
 #pragma unroll
           for (int kk = 0; kk < 4; ++kk)
-            mma_bf16(tbase + s * SLOT_COLS + 64, sdesc(sH1 + 256 * kk, 128, 1024),
+            mma_bf16(tbase + s * SLOT_COLS, sdesc(sH + 256 * kk, 128, 1024),
                      sdesc(sW2 + 256 * kk, 128, 1024), id128, kk > 0);
           mma_commit(BAR(B_D2 + s));
         }
-        // layer 3, transposed: D3^T[128 ch x 128 pts] per half
-        for (int s = 0; s < 2 && ok; ++s) {
-          if (2 * r + s >= my_pairs) break;
+        // layer 3, half 0 (channels 0..127), transposed: D3^T = W3img[0:128] . H2^T
+        for (int s = 0; s < ns && ok; ++s) {
           if (!(ok = mbar_wait_or_abort(BAR(B_H2RDY + s), ph, abort, WAIT_CYCLES))) break;
           tc_fence_after();
-          const uint32_t sH2 = smem_u32(smem + E_SLOT0 + s * SLOT_BYTES + S_H2);
+          const uint32_t sH = smem_u32(smem + E_SLOT0 + s * SLOT_BYTES + S_OPD);
 #pragma unroll
-          for (int half = 0; half < 2; ++half)
+          for (int kk = 0; kk < 8; ++kk)
+            mma_bf16(tbase + s * SLOT_COLS, sdesc(sW3 + 256 * kk, 128, 2048),
+                     sdesc(sH + 256 * kk, 128, 2048), id128, kk > 0);
+          mma_commit(BAR(B_D3A + s));
+        }
+        // layer 3, half 1 (channels 128..255), once half 0 has been pooled
+        for (int s = 0; s < ns && ok; ++s) {
+          if (!(ok = mbar_wait_or_abort(BAR(B_E3A + s), ph, abort, WAIT_CYCLES))) break;
+          tc_fence_after();
+          const uint32_t sH = smem_u32(smem + E_SLOT0 + s * SLOT_BYTES + S_OPD);
 #pragma unroll
-            for (int kk = 0; kk < 8; ++kk)
-              mma_bf16(tbase + s * SLOT_COLS + 128 * half,
-                       sdesc(sW3 + half * 32768 + 256 * kk, 128, 2048),
-                       sdesc(sH2 + 256 * kk, 128, 2048), id128, kk > 0);
-          mma_commit(BAR(B_D3 + s));
+          for (int kk = 0; kk < 8; ++kk)
+            mma_bf16(tbase + s * SLOT_COLS, sdesc(sW3 + 32768 + 256 * kk, 128, 2048),
+                     sdesc(sH + 256 * kk, 128, 2048), id128, kk > 0);
+          mma_commit(BAR(B_D3B + s));
         }
       }
       if (*abort) {
         // drain: wait (bounded) for every MMA and bulk copy this thread issued
         mma_commit(BAR(B_DRAIN));
         mbar_wait(BAR(B_DRAIN), 0, WAIT_CYCLES);
-        for (int s = 0; s < 2; ++s)
+        for (int s = 0; s < NSLOT; ++s)
           if (issued[s] > 0) mbar_wait(BAR(B_FULLX + s), (issued[s] - 1) & 1, WAIT_CYCLES);
       }
     }
@@ -217,12 +256,12 @@ __global__ void __launch_bounds__(E_THREADS, 1)
     // ------------------------------------------------ epilogue warpgroup of slot s
     const int s = warp >> 2, row = tid & 127, wq = warp & 3;
     unsigned char* slot = smem + E_SLOT0 + s * SLOT_BYTES;
-    const uint32_t lane_off = (uint32_t)(32 * wq) << 16;
-    const uint32_t tslot = tbase + s * SLOT_COLS + lane_off;
+    unsigned char* opd = slot + S_OPD;
+    const uint32_t tslot = tbase + s * SLOT_COLS + ((uint32_t)(32 * wq) << 16);
     int* cnt_s = s_cnt + 4 * s;
     bool ok = mbar_wait_or_abort(BAR(B_W), 0, abort, WAIT_CYCLES);
     for (int j = 0; ok; ++j) {
-      const int i = 2 * j + s;
+      const int i = NSLOT * j + s;
       if (i >= my_pairs) break;
       const int p = lo + blockIdx.x + i * gridDim.x;
       const uint32_t ph = j & 1;
@@ -242,58 +281,48 @@ __global__ void __launch_bounds__(E_THREADS, 1)
         c0.w = pack_bf16(fx, fy);
         c1.x = pack_bf16(fz, 0.f);
         c1.y = c1.z = c1.w = 0u;
-        *reinterpret_cast<uint4*>(slot + S_X + kmajor_off(row, 0, 16)) = c0;
-        *reinterpret_cast<uint4*>(slot + S_X + kmajor_off(row, 8, 16)) = c1;
+        *reinterpret_cast<uint4*>(opd + kmajor_off(row, 0, 16)) = c0;
+        *reinterpret_cast<uint4*>(opd + kmajor_off(row, 8, 16)) = c1;
       }
       fence_async_smem();
       tc_fence_before();
       mbar_arrive(BAR(B_XRDY + s));
-      // layer 1 epilogue
+      // layer 1 epilogue -> H1 (over X: MMA1 has completed)
       if (!(ok = mbar_wait_or_abort(BAR(B_D1 + s), ph, abort, WAIT_CYCLES))) break;
       tc_fence_after();
-      enc_epi_rows<64>(tslot + 0, b1, slot + S_H1, row);
+      enc_epi_rows<64>(tslot, b1, opd, row);
       fence_async_smem();
       tc_fence_before();
       mbar_arrive(BAR(B_H1RDY + s));
-      // layer 2 epilogue
+      // layer 2 epilogue -> H2 (over H1: MMA2 has completed)
       if (!(ok = mbar_wait_or_abort(BAR(B_D2 + s), ph, abort, WAIT_CYCLES))) break;
       tc_fence_after();
-      enc_epi_rows<128>(tslot + 64, b2, slot + S_H2, row);
+      enc_epi_rows<128>(tslot, b2, opd, row);
       fence_async_smem();
       tc_fence_before();
       mbar_arrive(BAR(B_H2RDY + s));
-      // layer 3 epilogue: masked max over the valid points of each object
-      if (!(ok = mbar_wait_or_abort(BAR(B_D3 + s), ph, abort, WAIT_CYCLES))) break;
+      // layer 3 epilogues: masked max over the valid points of each object
+      if (!(ok = mbar_wait_or_abort(BAR(B_D3A + s), ph, abort, WAIT_CYCLES))) break;
       tc_fence_after();
-      // crop counts (and row scales) written by other threads of this warpgroup
+      // crop counts written by other threads of this warpgroup
       asm volatile("bar.sync %0, 128;" ::"r"(1 + s) : "memory");
       const int cntA = cnt_s[0] + cnt_s[1], cntB = cnt_s[2] + cnt_s[3];
-      float v[32];
-#pragma unroll
-      for (int half = 0; half < 2; ++half) {
-        float mA = -INFINITY, mB = -INFINITY;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const int cnt = q < 2 ? cntA : cntB;
-          const int c0 = 32 * (q & 1);
-          if (c0 < cnt) {
-            tmem_ld32(tslot + 128 * half + 32 * q, v);
-            float m = -INFINITY;
-            if (c0 + 32 <= cnt) {
-#pragma unroll
-              for (int jj = 0; jj < 32; ++jj) m = fmaxf(m, v[jj]);
-            } else {
-#pragma unroll
-              for (int jj = 0; jj < 32; ++jj) m = fmaxf(m, (c0 + jj < cnt) ? v[jj] : -INFINITY);
-            }
-            if (q < 2) mA = fmaxf(mA, m);
-            else mB = fmaxf(mB, m);
-          }
-        }
-        const int ch = 128 * half + row;
-        const float bias = b3[ch];
-        feat[(size_t)p * 512 + ch] = cntA > 0 ? fmaxf(mA + bias, 0.f) : 0.f;
-        feat[(size_t)p * 512 + 256 + ch] = cntB > 0 ? fmaxf(mB + bias, 0.f) : 0.f;
+      float mA, mB;
+      enc_pool(tslot, cntA, cntB, &mA, &mB);
+      tc_fence_before();
+      mbar_arrive(BAR(B_E3A + s));
+      {
+        const float bias = b3[row];
+        feat[(size_t)p * 512 + row] = cntA > 0 ? fmaxf(mA + bias, 0.f) : 0.f;
+        feat[(size_t)p * 512 + 256 + row] = cntB > 0 ? fmaxf(mB + bias, 0.f) : 0.f;
+      }
+      if (!(ok = mbar_wait_or_abort(BAR(B_D3B + s), ph, abort, WAIT_CYCLES))) break;
+      tc_fence_after();
+      enc_pool(tslot, cntA, cntB, &mA, &mB);
+      {
+        const float bias = b3[128 + row];
+        feat[(size_t)p * 512 + 128 + row] = cntA > 0 ? fmaxf(mA + bias, 0.f) : 0.f;
+        feat[(size_t)p * 512 + 384 + row] = cntB > 0 ? fmaxf(mB + bias, 0.f) : 0.f;
       }
       tc_fence_before();
     }
