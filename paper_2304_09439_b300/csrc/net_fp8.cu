@@ -57,20 +57,24 @@ constexpr int F_W3 = F_W2 + 128 * 64;          // [256 x 128] e4m3        32 KB
 constexpr int F_EP = F_W3 + 256 * 128;         // a1 c1 [64], a2 c2 [128], w3 b3 [256] (f32)
 constexpr int F_IMG_BYTES = F_EP + (2 * 64 + 2 * 128 + 2 * 256) * 4;
 static_assert(F_IMG_BYTES % 16 == 0, "encoder fp8 image must be 16-byte chunks");
+// NSLOT pair slots; each: raw crop rows (2 KB) and a 16 KB operand region
+// holding in turn X (bf16, 4 KB), H1 (e4m3, 8 KB) and H2 (e4m3, 16 KB).
+constexpr int NSLOT = 4;
 constexpr int F_SLOT0 = (F_IMG_BYTES + 1023) / 1024 * 1024;
-constexpr int FS_STG = 0;                   // [128] float4        2 KB
-constexpr int FS_X = FS_STG + ROWS * 16;    // [128 x 16] bf16     4 KB
-constexpr int FS_H1 = FS_X + 128 * 16 * 2;  // [128 x 64] e4m3     8 KB
-constexpr int FS_H2 = FS_H1 + 128 * 64;     // [128 x 128] e4m3   16 KB
-constexpr int F_SLOT_BYTES = FS_H2 + 128 * 128;
-constexpr int F_CTRL = F_SLOT0 + 2 * F_SLOT_BYTES;
-constexpr int C_BAR = 0, C_TMEM = 128, C_ABORT = 132, C_CNT = 136;
-constexpr int F_SMEM = F_CTRL + 256;
+constexpr int FS_STG = 0;
+constexpr int FS_OPD = FS_STG + ROWS * 16;
+constexpr int F_SLOT_BYTES = FS_OPD + 128 * 128;
+constexpr int F_CTRL = F_SLOT0 + NSLOT * F_SLOT_BYTES;
+constexpr int NBAR = 9 * NSLOT + 2;
+constexpr int C_BAR = 0, C_TMEM = 8 * NBAR, C_ABORT = C_TMEM + 4, C_CNT = C_ABORT + 4;
+constexpr int F_SMEM = F_CTRL + C_CNT + 16 * NSLOT;
 static_assert(F_SMEM <= 227 * 1024, "fp8 encoder shared memory");
-constexpr int F_THREADS = 288;
-constexpr int SLOT_COLS = 256;
-constexpr int B_FULLX = 0, B_XRDY = 2, B_H1RDY = 4, B_H2RDY = 6, B_D1 = 8, B_D2 = 10, B_D3 = 12,
-              B_W = 14, B_DRAIN = 15;
+constexpr int F_THREADS = 32 * (4 * NSLOT + 1);
+constexpr int MMA_WARP = 4 * NSLOT;
+constexpr int SLOT_COLS = 512 / NSLOT;
+constexpr int B_FULLX = 0, B_XRDY = NSLOT, B_H1RDY = 2 * NSLOT, B_H2RDY = 3 * NSLOT,
+              B_E3A = 4 * NSLOT, B_D1 = 5 * NSLOT, B_D2 = 6 * NSLOT, B_D3A = 7 * NSLOT,
+              B_D3B = 8 * NSLOT, B_W = 9 * NSLOT, B_DRAIN = 9 * NSLOT + 1;
 
 // relu(D alpha + beta) for 32 TMEM columns -> 32 e4m3 bytes at row `row`,
 // columns [k0, k0 + 32) of a K-wide tile.
@@ -89,6 +93,33 @@ __device__ __forceinline__ void epi_e4m3_32(const float (&v)[32], const float* a
     w.w = pack_e4m3x4_relu(t[12], t[13], t[14], t[15]);
     *reinterpret_cast<uint4*>(dst + kmajor_off8(row, k0 + 16 * c, K)) = w;
   }
+}
+
+// Masked max over the valid points of each object (thread = channel);
+// columns [0, 64) are A's points, [64, 128) B's.
+__device__ __forceinline__ void pool8(uint32_t taddr, int cntA, int cntB, float* mA, float* mB) {
+  float v[32];
+  float a = -INFINITY, b = -INFINITY;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int cnt = q < 2 ? cntA : cntB;
+    const int q0 = 32 * (q & 1);
+    if (q0 < cnt) {
+      tmem_ld32(taddr + 32 * q, v);
+      float m = -INFINITY;
+      if (q0 + 32 <= cnt) {
+#pragma unroll
+        for (int jj = 0; jj < 32; ++jj) m = fmaxf(m, v[jj]);
+      } else {
+#pragma unroll
+        for (int jj = 0; jj < 32; ++jj) m = fmaxf(m, (q0 + jj < cnt) ? v[jj] : -INFINITY);
+      }
+      if (q < 2) a = fmaxf(a, m);
+      else b = fmaxf(b, m);
+    }
+  }
+  *mA = a;
+  *mB = b;
 }
 
 __global__ void __launch_bounds__(F_THREADS, 1)
@@ -111,14 +142,16 @@ __global__ void __launch_bounds__(F_THREADS, 1)
   int* s_cnt = reinterpret_cast<int*>(ctrl + C_CNT);
 
   if (tid == 0) {
-    for (int s = 0; s < 2; ++s) {
+    for (int s = 0; s < NSLOT; ++s) {
       mbar_init(BAR(B_FULLX + s), 1);
       mbar_init(BAR(B_XRDY + s), 128);
       mbar_init(BAR(B_H1RDY + s), 128);
       mbar_init(BAR(B_H2RDY + s), 128);
+      mbar_init(BAR(B_E3A + s), 128);
       mbar_init(BAR(B_D1 + s), 1);
       mbar_init(BAR(B_D2 + s), 1);
-      mbar_init(BAR(B_D3 + s), 1);
+      mbar_init(BAR(B_D3A + s), 1);
+      mbar_init(BAR(B_D3B + s), 1);
     }
     mbar_init(BAR(B_W), 1);
     mbar_init(BAR(B_DRAIN), 1);
@@ -140,69 +173,73 @@ __global__ void __launch_bounds__(F_THREADS, 1)
   const float* w3 = c2 + 128;
   const float* b3 = w3 + 256;
 
-  if (warp == 8) {
+  if (warp == MMA_WARP) {
     if (lane == 0) {
       const uint32_t sW1 = smem_u32(smem + F_W1), sW2 = smem_u32(smem + F_W2);
       const uint32_t sW3 = smem_u32(smem + F_W3);
       mbar_expect_tx(BAR(B_W), F_IMG_BYTES);
       for (int off = 0; off < F_IMG_BYTES; off += 32768)
         bulk_g2s(smem_u32(smem + off), img + off, min(32768, F_IMG_BYTES - off), BAR(B_W));
-      int issued[2] = {0, 0};
+      int issued[NSLOT] = {};
       auto load_pair = [&](int i) {
-        const int s = i & 1;
+        const int s = i % NSLOT;
         const int p = lo + blockIdx.x + i * gridDim.x;
         mbar_expect_tx(BAR(B_FULLX + s), ROWS * 16);
         bulk_g2s(smem_u32(smem + F_SLOT0 + s * F_SLOT_BYTES + FS_STG), xyz + (size_t)p * ROWS,
                  ROWS * 16, BAR(B_FULLX + s));
         ++issued[s];
       };
-      load_pair(0);
-      if (my_pairs > 1) load_pair(1);
+      for (int i = 0; i < NSLOT && i < my_pairs; ++i) load_pair(i);
       bool ok = mbar_wait_or_abort(BAR(B_W), 0, abort, WAIT_CYCLES);
       tc_fence_after();
       const uint32_t id64 = idesc_bf16(128, 64), id128 = idesc_e4m3(128, 128);
-      for (int r = 0; ok && 2 * r < my_pairs; ++r) {
+      for (int r = 0; ok && NSLOT * r < my_pairs; ++r) {
         const uint32_t ph = r & 1;
-        for (int s = 0; s < 2 && ok; ++s) {
-          const int i = 2 * r + s;
-          if (i >= my_pairs) break;
+        const int ns = min(NSLOT, my_pairs - NSLOT * r);
+        for (int s = 0; s < ns && ok; ++s) {
           if (!(ok = mbar_wait_or_abort(BAR(B_XRDY + s), ph, abort, WAIT_CYCLES))) break;
           tc_fence_after();
-          if (i + 2 < my_pairs) load_pair(i + 2);
-          const uint32_t sX = smem_u32(smem + F_SLOT0 + s * F_SLOT_BYTES + FS_X);
+          const int i = NSLOT * r + s;
+          if (i + NSLOT < my_pairs) load_pair(i + NSLOT);
+          const uint32_t sX = smem_u32(smem + F_SLOT0 + s * F_SLOT_BYTES + FS_OPD);
           mma_bf16(tbase + s * SLOT_COLS, sdesc(sX, 128, 256), sdesc(sW1, 128, 256), id64, 0);
           mma_commit(BAR(B_D1 + s));
         }
-        for (int s = 0; s < 2 && ok; ++s) {
-          if (2 * r + s >= my_pairs) break;
+        for (int s = 0; s < ns && ok; ++s) {
           if (!(ok = mbar_wait_or_abort(BAR(B_H1RDY + s), ph, abort, WAIT_CYCLES))) break;
           tc_fence_after();
-          const uint32_t sH1 = smem_u32(smem + F_SLOT0 + s * F_SLOT_BYTES + FS_H1);
+          const uint32_t sH = smem_u32(smem + F_SLOT0 + s * F_SLOT_BYTES + FS_OPD);
 #pragma unroll
           for (int kk = 0; kk < 2; ++kk)
-            mma_e4m3(tbase + s * SLOT_COLS + 64, sdesc(sH1 + 256 * kk, 128, 512),
+            mma_e4m3(tbase + s * SLOT_COLS, sdesc(sH + 256 * kk, 128, 512),
                      sdesc(sW2 + 256 * kk, 128, 512), id128, kk > 0);
           mma_commit(BAR(B_D2 + s));
         }
-        for (int s = 0; s < 2 && ok; ++s) {
-          if (2 * r + s >= my_pairs) break;
+        for (int s = 0; s < ns && ok; ++s) {
           if (!(ok = mbar_wait_or_abort(BAR(B_H2RDY + s), ph, abort, WAIT_CYCLES))) break;
           tc_fence_after();
-          const uint32_t sH2 = smem_u32(smem + F_SLOT0 + s * F_SLOT_BYTES + FS_H2);
+          const uint32_t sH = smem_u32(smem + F_SLOT0 + s * F_SLOT_BYTES + FS_OPD);
 #pragma unroll
-          for (int half = 0; half < 2; ++half)
+          for (int kk = 0; kk < 4; ++kk)
+            mma_e4m3(tbase + s * SLOT_COLS, sdesc(sW3 + 256 * kk, 128, 1024),
+                     sdesc(sH + 256 * kk, 128, 1024), id128, kk > 0);
+          mma_commit(BAR(B_D3A + s));
+        }
+        for (int s = 0; s < ns && ok; ++s) {
+          if (!(ok = mbar_wait_or_abort(BAR(B_E3A + s), ph, abort, WAIT_CYCLES))) break;
+          tc_fence_after();
+          const uint32_t sH = smem_u32(smem + F_SLOT0 + s * F_SLOT_BYTES + FS_OPD);
 #pragma unroll
-            for (int kk = 0; kk < 4; ++kk)
-              mma_e4m3(tbase + s * SLOT_COLS + 128 * half,
-                       sdesc(sW3 + half * 16384 + 256 * kk, 128, 1024),
-                       sdesc(sH2 + 256 * kk, 128, 1024), id128, kk > 0);
-          mma_commit(BAR(B_D3 + s));
+          for (int kk = 0; kk < 4; ++kk)
+            mma_e4m3(tbase + s * SLOT_COLS, sdesc(sW3 + 16384 + 256 * kk, 128, 1024),
+                     sdesc(sH + 256 * kk, 128, 1024), id128, kk > 0);
+          mma_commit(BAR(B_D3B + s));
         }
       }
       if (*abort) {
         mma_commit(BAR(B_DRAIN));
         mbar_wait(BAR(B_DRAIN), 0, WAIT_CYCLES);
-        for (int s = 0; s < 2; ++s)
+        for (int s = 0; s < NSLOT; ++s)
           if (issued[s] > 0) mbar_wait(BAR(B_FULLX + s), (issued[s] - 1) & 1, WAIT_CYCLES);
       }
     }
@@ -210,11 +247,12 @@ __global__ void __launch_bounds__(F_THREADS, 1)
   } else {
     const int s = warp >> 2, row = tid & 127, wq = warp & 3;
     unsigned char* slot = smem + F_SLOT0 + s * F_SLOT_BYTES;
+    unsigned char* opd = slot + FS_OPD;
     const uint32_t tslot = tbase + s * SLOT_COLS + ((uint32_t)(32 * wq) << 16);
     int* cnt_s = s_cnt + 4 * s;
     bool ok = mbar_wait_or_abort(BAR(B_W), 0, abort, WAIT_CYCLES);
     for (int j = 0; ok; ++j) {
-      const int i = 2 * j + s;
+      const int i = NSLOT * j + s;
       if (i >= my_pairs) break;
       const int p = lo + blockIdx.x + i * gridDim.x;
       const uint32_t ph = j & 1;
@@ -233,13 +271,13 @@ __global__ void __launch_bounds__(F_THREADS, 1)
         c0.w = pack_bf16(fx, fy);
         cc1.x = pack_bf16(fz, 0.f);
         cc1.y = cc1.z = cc1.w = 0u;
-        *reinterpret_cast<uint4*>(slot + FS_X + kmajor_off(row, 0, 16)) = c0;
-        *reinterpret_cast<uint4*>(slot + FS_X + kmajor_off(row, 8, 16)) = cc1;
+        *reinterpret_cast<uint4*>(opd + kmajor_off(row, 0, 16)) = c0;
+        *reinterpret_cast<uint4*>(opd + kmajor_off(row, 8, 16)) = cc1;
       }
       fence_async_smem();
       tc_fence_before();
       mbar_arrive(BAR(B_XRDY + s));
-      // ---- layer 1 epilogue -> e4m3 H1 (static per-channel scale)
+      // layer 1 epilogue -> e4m3 H1 (static per-channel scale), over X
       if (!(ok = mbar_wait_or_abort(BAR(B_D1 + s), ph, abort, WAIT_CYCLES))) break;
       tc_fence_after();
       {
@@ -247,57 +285,47 @@ __global__ void __launch_bounds__(F_THREADS, 1)
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
           tmem_ld32(tslot + 32 * h, v);
-          epi_e4m3_32<64>(v, a1 + 32 * h, c1 + 32 * h, slot + FS_H1, row, 32 * h);
+          epi_e4m3_32<64>(v, a1 + 32 * h, c1 + 32 * h, opd, row, 32 * h);
         }
       }
       fence_async_smem();
       tc_fence_before();
       mbar_arrive(BAR(B_H1RDY + s));
-      // ---- layer 2 epilogue -> e4m3 H2
+      // layer 2 epilogue -> e4m3 H2, over H1
       if (!(ok = mbar_wait_or_abort(BAR(B_D2 + s), ph, abort, WAIT_CYCLES))) break;
       tc_fence_after();
       {
         float v[32];
 #pragma unroll
         for (int h = 0; h < 4; ++h) {
-          tmem_ld32(tslot + 64 + 32 * h, v);
-          epi_e4m3_32<128>(v, a2 + 32 * h, c2 + 32 * h, slot + FS_H2, row, 32 * h);
+          tmem_ld32(tslot + 32 * h, v);
+          epi_e4m3_32<128>(v, a2 + 32 * h, c2 + 32 * h, opd, row, 32 * h);
         }
       }
       fence_async_smem();
       tc_fence_before();
       mbar_arrive(BAR(B_H2RDY + s));
-      // ---- layer 3 epilogue: max over valid points, then * w3 + b3, relu
-      if (!(ok = mbar_wait_or_abort(BAR(B_D3 + s), ph, abort, WAIT_CYCLES))) break;
+      // layer 3 epilogues: max over valid points, then * w3 + b3, relu
+      if (!(ok = mbar_wait_or_abort(BAR(B_D3A + s), ph, abort, WAIT_CYCLES))) break;
       tc_fence_after();
       asm volatile("bar.sync %0, 128;" ::"r"(1 + s) : "memory");  // counts of other warps
       const int cntA = cnt_s[0] + cnt_s[1], cntB = cnt_s[2] + cnt_s[3];
-      float v[32];
-#pragma unroll
-      for (int half = 0; half < 2; ++half) {
-        float mA = -INFINITY, mB = -INFINITY;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const int cnt = q < 2 ? cntA : cntB;
-          const int q0 = 32 * (q & 1);
-          if (q0 < cnt) {
-            tmem_ld32(tslot + 128 * half + 32 * q, v);
-            float m = -INFINITY;
-            if (q0 + 32 <= cnt) {
-#pragma unroll
-              for (int jj = 0; jj < 32; ++jj) m = fmaxf(m, v[jj]);
-            } else {
-#pragma unroll
-              for (int jj = 0; jj < 32; ++jj) m = fmaxf(m, (q0 + jj < cnt) ? v[jj] : -INFINITY);
-            }
-            if (q < 2) mA = fmaxf(mA, m);
-            else mB = fmaxf(mB, m);
-          }
-        }
-        const int ch = 128 * half + row;
-        const float sc = w3[ch], bias = b3[ch];
-        feat[(size_t)p * 512 + ch] = cntA > 0 ? fmaxf(fmaf(mA, sc, bias), 0.f) : 0.f;
-        feat[(size_t)p * 512 + 256 + ch] = cntB > 0 ? fmaxf(fmaf(mB, sc, bias), 0.f) : 0.f;
+      float mA, mB;
+      pool8(tslot, cntA, cntB, &mA, &mB);
+      tc_fence_before();
+      mbar_arrive(BAR(B_E3A + s));
+      {
+        const float sc = w3[row], bias = b3[row];
+        feat[(size_t)p * 512 + row] = cntA > 0 ? fmaxf(fmaf(mA, sc, bias), 0.f) : 0.f;
+        feat[(size_t)p * 512 + 256 + row] = cntB > 0 ? fmaxf(fmaf(mB, sc, bias), 0.f) : 0.f;
+      }
+      if (!(ok = mbar_wait_or_abort(BAR(B_D3B + s), ph, abort, WAIT_CYCLES))) break;
+      tc_fence_after();
+      pool8(tslot, cntA, cntB, &mA, &mB);
+      {
+        const float sc = w3[128 + row], bias = b3[128 + row];
+        feat[(size_t)p * 512 + 128 + row] = cntA > 0 ? fmaxf(fmaf(mA, sc, bias), 0.f) : 0.f;
+        feat[(size_t)p * 512 + 384 + row] = cntB > 0 ? fmaxf(fmaf(mB, sc, bias), 0.f) : 0.f;
       }
       tc_fence_before();
     }
