@@ -156,6 +156,110 @@ def run_reference(args, rank: int, world: int) -> None:
     print(json.dumps(line), flush=True)
 
 
+def _pinned_like(a):
+    import torch
+    t = torch.empty(a.shape, dtype=torch.from_numpy(a[:0]).dtype, pin_memory=True).numpy()
+    t[...] = a
+    return t
+
+
+def serving_pool(n_tmpl: int, seed: int):
+    """Client batches of the serving workload: environments log-uniform in
+    [64, 16384], pairs log-uniform in [1e2, 1e6] (page-locked host arrays)."""
+    rng = np.random.default_rng(seed)
+    sizes = np.exp(rng.uniform(np.log(1e2), np.log(1e6), n_tmpl)).astype(int)
+    envs = np.exp(rng.uniform(np.log(64), np.log(16384), n_tmpl)).astype(int)
+    pool = []
+    for i, (e, n) in enumerate(zip(envs, sizes)):
+        p, s, q = synth.client_batch(N_SHAPES, int(e), int(n), seed + 1 + i)
+        pool.append((_pinned_like(p), _pinned_like(s), _pinned_like(q),
+                     _pinned_like(np.zeros((int(n), 8), np.float32))))
+    return pool
+
+
+def serving_run(srv, pool, rate: float, seconds: float, seed: int):
+    """Poisson arrivals at `rate` requests/s for `seconds`; each arrival
+    submits a random batch of the pool.  Returns achieved pairs/s over the
+    arrival window, latency percentiles of completed requests and counts.
+    Results land in per-batch output arrays that concurrent requests of the
+    same batch share (their contents are not checked here; the serving tests
+    check results)."""
+    import queue as _q
+    from paper_2304_09439_b300 import LoccError
+    rng = np.random.default_rng(seed)
+    srv.stats(reset=True)
+    ids = _q.Queue()
+    lat, offered = [], [0, 0]
+    done_pairs = [0]
+
+    def waiter():
+        while True:
+            item = ids.get()
+            if item is None:
+                return
+            rid, n = item
+            info = srv.wait(rid)
+            lat.append(info["done_us"])
+            done_pairs[0] += n
+
+    th = threading.Thread(target=waiter, daemon=True)
+    th.start()
+    rejected = 0
+    t0 = time.perf_counter()
+    t_next = t0
+    while True:
+        t_next += rng.exponential(1.0 / rate)
+        if t_next - t0 > seconds:
+            break
+        d = t_next - time.perf_counter()
+        if d > 0:
+            time.sleep(d)
+        p, s, q, o = pool[int(rng.integers(len(pool)))]
+        offered[0] += 1
+        offered[1] += len(q)
+        try:
+            ids.put((srv.submit(p, s, q, out=o), len(q)))
+        except LoccError as e:
+            if e.code != -7:
+                raise
+            rejected += 1
+    t_end = time.perf_counter()
+    st_window = srv.stats()
+    ids.put(None)
+    th.join()
+    st = srv.stats()
+    window = t_end - t0
+    return {"offered_req_per_s": offered[0] / window, "offered_pairs_per_s": offered[1] / window,
+            "achieved_pairs_per_s": st_window["pairs_completed"] / window,
+            "completed": st["completed"], "rejected": rejected,
+            "latency_p50_ms": st["latency_p50_us"] / 1e3,
+            "latency_p99_ms": st["latency_p99_us"] / 1e3,
+            "latency_max_ms": st["latency_max_us"] / 1e3,
+            "mean_pairs_per_launch": st["mean_pairs_per_launch"],
+            "max_active": st["max_active_seen"], "arena_peak_bytes": st["arena_peak"],
+            "window_s": window}
+
+
+def serving_leg(det, seconds: float, rate: float, max_queued: int, seed: int = 6):
+    """Serving workload: an overloaded run at `rate` requests/s, then a run at
+    half of the capacity measured there."""
+    from paper_2304_09439_b300 import Server
+    pool = serving_pool(48, seed)
+    mean_pairs = float(np.mean([len(x[2]) for x in pool]))
+    with Server(det, arena_bytes=8 << 30, max_batch_pairs=131072, max_active=256,
+                max_queued_pairs=max_queued) as srv:
+        # warm-up: one pass over a few batches
+        for p, s, q, o in pool[:4]:
+            srv.wait(srv.submit(p, s, q, out=o))
+        over = serving_run(srv, pool, rate, seconds, seed + 1)
+        cap = over["achieved_pairs_per_s"]
+        half = serving_run(srv, pool, 0.5 * cap / mean_pairs, seconds, seed + 2)
+    return {"workload": "clients: envs log-U[64,16384], pairs log-U[1e2,1e6], Poisson arrivals",
+            "pool_batches": len(pool), "mean_pairs_per_request": mean_pairs,
+            "max_batch_pairs": 131072, "max_queued_pairs": max_queued,
+            "arena_bytes": 8 << 30, "overload": over, "half_capacity": half}
+
+
 def cpu_baseline(lib, scene, seconds: float = 12.0):
     """Oracle (b) on a bounded sample of the workload (host cores)."""
     import oracle
@@ -192,6 +296,11 @@ def main():
     ap.add_argument("--pipeline", default="auto",
                     help="'auto' (autotune) or 'CHUNKS,CROP_CTAS_PER_SM'")
     ap.add_argument("--sets", type=int, default=3, help="distinct scenes cycled over steps")
+    ap.add_argument("--serve-seconds", type=float, default=8.0,
+                    help="length of each serving run (0 = no serving leg)")
+    ap.add_argument("--serve-rate", type=float, default=2000.0, help="offered requests/s")
+    ap.add_argument("--serve-max-queued", type=int, default=8_000_000,
+                    help="queued pairs beyond which requests are refused")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -340,6 +449,10 @@ def main():
         cpu = None
         if not args.no_cpu_baseline and world == 1:
             cpu = cpu_baseline(lib, scenes[0])
+        serving = None
+        if args.serve_seconds > 0:
+            serving = serving_leg(det, args.serve_seconds, args.serve_rate,
+                                  args.serve_max_queued)
         line = {
             "metric": "contact pairs/sec", "value": pairs_all / (ms_max * 1e-3),
             "unit": "pairs/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -366,6 +479,7 @@ def main():
             "gpu_launches": launches_per_step * args.steps,
             "clocks": clk.summary(),
             "cpu_baseline": cpu,
+            "serving": serving,
             "wall_s_timed": t_wall,
         }
         print(json.dumps(line), flush=True)

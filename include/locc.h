@@ -62,6 +62,7 @@ extern "C" {
 #define LOCC_ERR_TIMEOUT (-4)      /* a bounded device wait ran out */
 #define LOCC_ERR_BAD_WEIGHTS (-5)  /* weights blob malformed */
 #define LOCC_ERR_BAD_INDEX (-6)    /* a kernel met an out-of-range index */
+#define LOCC_ERR_BUSY (-7)         /* server queue full: request rejected */
 
 #define LOCC_CROP_POINTS 64        /* points kept per object */
 #define LOCC_OUT_DIM 8             /* logit, point xyz, normal xyz, depth */
@@ -280,7 +281,104 @@ int locc_trainer_set_params(locc_trainer *t, const float *params, void *stream);
 /* Install the trainer's parameters as the handle's inference weights (all
  * precisions); blocking. */
 int locc_trainer_commit(locc_trainer *t);
+
+/* Learning rate of the following steps (learning-rate schedules); host-side,
+ * takes effect at the next locc_train_step.  lr >= 0 and finite, else
+ * LOCC_ERR_INVALID_ARG. */
+int locc_trainer_set_lr(locc_trainer *t, float lr);
 void locc_trainer_destroy(locc_trainer *t);
+
+/* ---------------------------------------------------------------- serving
+ * A request server on one handle: simulator clients submit contact-query
+ * batches of any size (their own objects, poses and pair lists) from any host
+ * thread, and a scheduler thread owned by the server runs them with continuous
+ * batching.  The paper runs the detector for thousands of simulated
+ * environments in parallel on one GPU (Sec. I; Sec. IV, Claim 3); the server
+ * is the deployment form of locc_detect for many simulators sharing a GPU,
+ * which the paper does not describe.
+ *   - Admission by device memory: a request's inputs are copied into a device
+ *     arena of arena_bytes (a budget of HBM) when a block large enough is
+ *     free; queued requests are admitted in arrival order as blocks free up.
+ *   - Continuous batching: every launch packs the pending pairs of all
+ *     admitted requests, up to max_batch_pairs: each request first gets an
+ *     equal share, the room left goes in admission order.  A large request
+ *     spans several launches; requests that arrive meanwhile join the next
+ *     launch.  Host->device copies of newly admitted requests, the launches
+ *     and the device->host copies of results run on three streams and overlap.
+ *   - A pair's result does not depend on which launch or batch mates it got:
+ *     every output row is computed from that pair's inputs alone, with the
+ *     same arithmetic as locc_detect at the handle's precision.
+ * While a server exists it owns the handle: make no other call on the handle
+ * until locc_server_destroy returns. */
+typedef struct locc_server locc_server;
+typedef struct {
+  int64_t arena_bytes;      /* device bytes for admitted requests' inputs;
+                               0 -> half of the device's free memory */
+  int32_t max_batch_pairs;  /* pairs per launch, >= 1 (0 -> 131072) */
+  int32_t max_active;       /* admitted requests at once, 1..1024 (0 -> 256) */
+  int64_t max_queued_pairs; /* pairs waiting for admission beyond which
+                               locc_server_submit rejects (an empty queue
+                               always accepts); 0 -> no limit */
+} locc_server_config;
+
+/* A request: HOST arrays, read until the request completes; `out` is written
+ * when it completes.  Page-locked (pinned) memory lets the copies overlap.
+ *   poses [n_obj][7], obj_shape [n_obj], pairs [n_pairs][2] (object indices
+ *   of this request, 0 <= index < n_obj), out float32 [n_pairs][8] as
+ *   locc_detect. */
+typedef struct {
+  const float *poses;
+  const int32_t *obj_shape;
+  int32_t n_obj;
+  const int32_t *pairs;
+  int32_t n_pairs;
+  float *out;
+} locc_request;
+
+/* Timeline of one completed request, microseconds since its submission. */
+typedef struct {
+  double admit_us;     /* admitted (inputs placed in the arena) */
+  double done_us;      /* last result row copied to `out` */
+  int32_t launches;    /* launches that carried some of its pairs */
+  int32_t status;      /* 0, or the error code of a failed launch */
+} locc_request_info;
+
+typedef struct {
+  int64_t submitted, rejected, completed, failed;
+  int64_t queued, active;          /* now: waiting for admission / admitted */
+  int64_t pairs_completed, launches;
+  int64_t arena_bytes, arena_used, arena_peak;
+  double latency_p50_us, latency_p99_us, latency_max_us;  /* completed requests */
+  double mean_pairs_per_launch;
+  int32_t max_active_seen;         /* most requests admitted at once */
+} locc_server_counters;
+
+/* Start a server on h (reserves the handle's scratch for max_batch_pairs).
+ * cfg may be NULL (all defaults).  Errors: INVALID_ARG, OOM, CUDA. */
+int locc_server_create(locc_handle *h, const locc_server_config *cfg,
+                       locc_server **out);
+
+/* Queue a request; thread-safe, never blocks on the GPU.  *id_out receives
+ * its id.  n_pairs == 0 completes at once.  Checks every pair index and shape
+ * id on the host: INVALID_ARG for a bad one.  OOM when the request's inputs
+ * could never fit in the arena; BUSY when requests are waiting for admission
+ * and their pairs plus this request's would exceed max_queued_pairs (the
+ * request is not queued; counted as rejected). */
+int locc_server_submit(locc_server *s, const locc_request *req, int64_t *id_out);
+
+/* Wait up to timeout_ms (< 0: no limit) for request `id`.  On completion
+ * fills *info (may be NULL), forgets the id and returns the request's status
+ * (0 or the failed launch's error code); TIMEOUT if it is still running
+ * (the id stays valid); INVALID_ARG for an unknown id. */
+int locc_server_wait(locc_server *s, int64_t id, int32_t timeout_ms,
+                     locc_request_info *info);
+
+/* Counters and latency percentiles since creation or the last reset. */
+int locc_server_stats(locc_server *s, locc_server_counters *st, int32_t reset);
+
+/* Finish every queued and admitted request, stop the scheduler and free the
+ * server (the handle stays).  Blocking. */
+void locc_server_destroy(locc_server *s);
 
 /* Release all device and host memory of the handle (blocking). */
 void locc_destroy(locc_handle *h);

@@ -19,7 +19,7 @@ from .abi import LoccError, LOCC_FP32, LOCC_BF16, LOCC_FP8, PRECISIONS
 KMAX = 64
 OUT_DIM = 8
 
-__all__ = ["Detector", "Trainer", "LoccError", "LOCC_FP32", "LOCC_BF16", "LOCC_FP8", "weights",
+__all__ = ["Detector", "Trainer", "Server", "LoccError", "LOCC_FP32", "LOCC_BF16", "LOCC_FP8", "weights",
            "abi", "KMAX", "OUT_DIM"]
 
 
@@ -299,6 +299,85 @@ class Trainer:
         _need(p, torch.float32, "params", self.det.device)
         abi.check(self._lib.locc_trainer_set_params(self._t, abi.ptr(p), abi.stream_ptr(stream)))
 
+    def set_lr(self, lr: float) -> None:
+        """Learning rate of the following steps."""
+        abi.check(self._lib.locc_trainer_set_lr(self._t, float(lr)))
+
     def commit(self) -> None:
         """Install the trained parameters as the detector's inference weights."""
         abi.check(self._lib.locc_trainer_commit(self._t))
+
+
+class Server:
+    """Owns one ``locc_server`` on a Detector (continuous batching of
+    contact-query batches from many clients; see ``locc_server_*``).
+
+    ``submit`` takes HOST numpy arrays (page-locked ones, e.g. from
+    ``torch.empty(..., pin_memory=True).numpy()``, let the copies overlap) and
+    keeps them alive until ``wait`` returns.  While the server exists it owns
+    the detector's handle."""
+
+    def __init__(self, det: Detector, arena_bytes: int = 0, max_batch_pairs: int = 131072,
+                 max_active: int = 256, max_queued_pairs: int = 0):
+        self._lib = abi.load()
+        self.det = det
+        cfg = abi.ServerConfig(int(arena_bytes), int(max_batch_pairs), int(max_active),
+                               int(max_queued_pairs))
+        self._s = ctypes.c_void_p()
+        abi.check(self._lib.locc_server_create(det._h, ctypes.byref(cfg), ctypes.byref(self._s)))
+        self._keep = {}
+
+    def close(self) -> None:
+        if getattr(self, "_s", None) is not None and self._s.value:
+            self._lib.locc_server_destroy(self._s)
+            self._s = None
+            self._keep.clear()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit(self, poses, obj_shape, pairs, out=None) -> int:
+        """Queue a request; returns its id.  ``out`` (float32 [n_pairs, 8],
+        host) receives the results; allocated when None (read it back with
+        ``result``)."""
+        import numpy as np
+        poses = np.ascontiguousarray(poses, np.float32)
+        obj_shape = np.ascontiguousarray(obj_shape, np.int32)
+        pairs = np.ascontiguousarray(pairs, np.int32)
+        if out is None:
+            out = np.empty((pairs.shape[0], OUT_DIM), np.float32)
+        if out.dtype != np.float32 or not out.flags.c_contiguous or \
+                out.shape != (pairs.shape[0], OUT_DIM):
+            raise ValueError("out must be a C-contiguous float32 [n_pairs, 8] array")
+        rq = abi.Request(poses.ctypes.data, obj_shape.ctypes.data, poses.shape[0],
+                         pairs.ctypes.data, pairs.shape[0], out.ctypes.data)
+        rid = ctypes.c_int64()
+        abi.check(self._lib.locc_server_submit(self._s, ctypes.byref(rq), ctypes.byref(rid)))
+        self._keep[rid.value] = (poses, obj_shape, pairs, out)
+        return rid.value
+
+    def wait(self, rid: int, timeout_ms: int = -1) -> dict:
+        """Block until request ``rid`` completes; returns its timeline
+        (admit_us, done_us, launches) and output array."""
+        info = abi.RequestInfo()
+        code = self._lib.locc_server_wait(self._s, int(rid), int(timeout_ms), ctypes.byref(info))
+        if code == -4:
+            raise TimeoutError(f"request {rid} still running")
+        keep = self._keep.pop(int(rid), None)
+        abi.check(code)
+        return {"admit_us": info.admit_us, "done_us": info.done_us, "launches": info.launches,
+                "out": keep[3] if keep else None}
+
+    def stats(self, reset: bool = False) -> dict:
+        c = abi.ServerCounters()
+        abi.check(self._lib.locc_server_stats(self._s, ctypes.byref(c), int(bool(reset))))
+        return {name: getattr(c, name) for name, _ in abi.ServerCounters._fields_}

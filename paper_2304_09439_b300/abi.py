@@ -18,7 +18,7 @@ from . import build as _build
 LOCC_FP32, LOCC_BF16, LOCC_FP8 = 0, 1, 2
 PRECISIONS = {"fp32": LOCC_FP32, "bf16": LOCC_BF16, "fp8": LOCC_FP8}
 ERRORS = {-1: "INVALID_ARG", -2: "OOM", -3: "CUDA", -4: "TIMEOUT",
-          -5: "BAD_WEIGHTS", -6: "BAD_INDEX"}
+          -5: "BAD_WEIGHTS", -6: "BAD_INDEX", -7: "BUSY"}
 
 # every symbol include/locc.h declares
 EXPORTS = ["locc_create", "locc_set_precision", "locc_detect", "locc_detect_host",
@@ -26,7 +26,9 @@ EXPORTS = ["locc_create", "locc_set_precision", "locc_detect", "locc_detect_host
            "locc_reserve", "locc_profile", "locc_stage_times", "locc_status", "locc_destroy",
            "locc_last_error", "locc_detect_noalloc", "locc_trainer_create", "locc_train_step",
            "locc_trainer_grad", "locc_trainer_params", "locc_trainer_set_params",
-           "locc_trainer_commit", "locc_trainer_destroy", "locc_set_pipeline", "locc_autotune"]
+           "locc_trainer_commit", "locc_trainer_set_lr", "locc_trainer_destroy", "locc_set_pipeline",
+           "locc_autotune", "locc_server_create", "locc_server_submit", "locc_server_wait",
+           "locc_server_stats", "locc_server_destroy"]
 NOALLOC_MAX_PAIRS = 1024
 
 
@@ -39,6 +41,31 @@ class LoccError(RuntimeError):
 class TrainConfig(ctypes.Structure):
     _fields_ = [(n, ctypes.c_float) for n in
                 ("lr", "beta1", "beta2", "eps", "w_pt", "w_n", "w_d", "huber_beta", "alpha")]
+
+
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("arena_bytes", ctypes.c_int64), ("max_batch_pairs", ctypes.c_int32),
+                ("max_active", ctypes.c_int32), ("max_queued_pairs", ctypes.c_int64)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("poses", ctypes.c_void_p), ("obj_shape", ctypes.c_void_p),
+                ("n_obj", ctypes.c_int32), ("pairs", ctypes.c_void_p),
+                ("n_pairs", ctypes.c_int32), ("out", ctypes.c_void_p)]
+
+
+class RequestInfo(ctypes.Structure):
+    _fields_ = [("admit_us", ctypes.c_double), ("done_us", ctypes.c_double),
+                ("launches", ctypes.c_int32), ("status", ctypes.c_int32)]
+
+
+class ServerCounters(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in
+                ("submitted", "rejected", "completed", "failed", "queued", "active",
+                 "pairs_completed", "launches", "arena_bytes", "arena_used", "arena_peak")] + \
+               [(n, ctypes.c_double) for n in
+                ("latency_p50_us", "latency_p99_us", "latency_max_us", "mean_pairs_per_launch")] + \
+               [("max_active_seen", ctypes.c_int32)]
 
 
 class _ShapeLibrary(ctypes.Structure):
@@ -87,13 +114,22 @@ def load(build_if_needed: bool = True) -> ctypes.CDLL:
         lib.locc_trainer_params.argtypes = [P, P, P]
         lib.locc_trainer_set_params.argtypes = [P, P, P]
         lib.locc_trainer_commit.argtypes = [P]
+        lib.locc_trainer_set_lr.argtypes = [P, ctypes.c_float]
         lib.locc_trainer_destroy.argtypes = [P]
         lib.locc_trainer_destroy.restype = None
+        lib.locc_server_create.argtypes = [P, ctypes.POINTER(ServerConfig), ctypes.POINTER(P)]
+        lib.locc_server_submit.argtypes = [P, ctypes.POINTER(Request),
+                                           ctypes.POINTER(ctypes.c_int64)]
+        lib.locc_server_wait.argtypes = [P, ctypes.c_int64, I, ctypes.POINTER(RequestInfo)]
+        lib.locc_server_stats.argtypes = [P, ctypes.POINTER(ServerCounters), I]
+        lib.locc_server_destroy.argtypes = [P]
+        lib.locc_server_destroy.restype = None
         lib.locc_destroy.argtypes = [P]
         lib.locc_destroy.restype = None
         lib.locc_last_error.restype = ctypes.c_char_p
         for name in EXPORTS:
-            if name not in ("locc_destroy", "locc_last_error", "locc_trainer_destroy"):
+            if name not in ("locc_destroy", "locc_last_error", "locc_trainer_destroy",
+                            "locc_server_destroy"):
                 getattr(lib, name).restype = ctypes.c_int
         _lib = lib
         return lib

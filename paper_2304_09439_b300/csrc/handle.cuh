@@ -74,6 +74,10 @@ int broadphase_run(locc_handle* h, const float* poses, const int32_t* obj_shape,
                    const int32_t* env_offsets, int n_env, int32_t* pairs_out,
                    int32_t* n_pairs_out, int max_pairs, cudaStream_t stream);
 DevLibrary dev_library(const locc_handle* h);
+// Crop gather and network of the pairs [0, n) (n = min(*n_dev, n_cap), or
+// n_cap when n_dev is NULL), chunked as set by locc_set_pipeline.
+int run_path(locc_handle* h, const PairInputs& in, int n_cap, const int* n_dev, float* out,
+             cudaStream_t s);
 // Encoder then head for the pairs of `rg`; mid (nullable): event recorded
 // between the encoder and the head.
 int run_network(locc_handle* h, const float4* xyz, const PairRange& rg, const PairInputs* in,

@@ -554,6 +554,13 @@ int locc_trainer_commit(locc_trainer* t) {
   return upload_params(t->h, flat);
 }
 
+int locc_trainer_set_lr(locc_trainer* t, float lr) {
+  if (!t) return tfail(LOCC_ERR_INVALID_ARG, "trainer is NULL");
+  if (!(lr >= 0.f) || !std::isfinite(lr)) return tfail(LOCC_ERR_INVALID_ARG, "lr must be finite and >= 0");
+  t->cfg.lr = lr;
+  return LOCC_OK;
+}
+
 void locc_trainer_destroy(locc_trainer* t) {
   if (!t) return;
   cudaDeviceSynchronize();

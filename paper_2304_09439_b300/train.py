@@ -1,6 +1,6 @@
 """Train the crop network on the GPU and evaluate it against geometric labels.
 
-    python -m paper_2304_09439_b300.train --data data/train64.npz \
+    python -m paper_2304_09439_b300.train --data data/train64.npz data/train64b.npz \
         --test data/test_known.npz data/test_unknown.npz \
         --steps 20000 --batch 256 --out paper_2304_09439_b300/weights/locc_trained.bin
 
@@ -39,6 +39,33 @@ def load_dataset(path):
     return {k: d[k] for k in ("poses", "obj_shape", "pairs", "targets")}, str(d["library"])
 
 
+def concat(parts):
+    """Concatenate datasets whose objects are numbered per file."""
+    out = {"poses": [], "obj_shape": [], "pairs": [], "targets": []}
+    base = 0
+    for d in parts:
+        out["poses"].append(d["poses"])
+        out["obj_shape"].append(d["obj_shape"])
+        out["pairs"].append(d["pairs"] + base)
+        out["targets"].append(d["targets"])
+        base += len(d["poses"])
+    return {k: np.concatenate(v) for k, v in out.items()}
+
+
+def split(data, n_val, rng):
+    """Hold out n_val pairs (with their two objects) for checkpoint selection.
+    Training files store pair i as objects (2i, 2i+1)."""
+    n = len(data["pairs"])
+    perm = rng.permutation(n)
+    parts = []
+    for idx in (perm[n_val:], perm[:n_val]):
+        objs = data["pairs"][idx].ravel()
+        parts.append({"poses": data["poses"][objs], "obj_shape": data["obj_shape"][objs],
+                      "pairs": np.arange(2 * len(idx), dtype=np.int32).reshape(-1, 2),
+                      "targets": data["targets"][idx]})
+    return parts
+
+
 def make_library(name):
     import synth
     n, seed = LIBRARIES[name]
@@ -75,8 +102,35 @@ def metrics(pred, tgt, near=0.05):
     ang = float(np.degrees(np.arccos(np.clip(cosv, -1, 1))).mean()) if m.any() else float("nan")
     nm = tgt[:, 7] > -near
     mae = float(np.abs(pred[nm, 7] - tgt[nm, 7]).mean()) if nm.any() else float("nan")
+    mn = m & (np.abs(tgt[:, 7]) < near)
+    cosn = np.sum(pred[mn, 4:7] * tgt[mn, 4:7], axis=1)
+    ang_near = (float(np.degrees(np.arccos(np.clip(cosn, -1, 1))).mean())
+                if mn.any() else float("nan"))
     return {"accuracy": acc, "precision": prec, "recall": rec, "f1": f1,
-            "normal_angle_deg": ang, "depth_mae": mae, "n": int(len(tgt))}
+            "normal_angle_deg": ang, "normal_angle_deg_near": ang_near,
+            "depth_mae": mae, "n": int(len(tgt))}
+
+
+def aabb_overlap(lib, data):
+    """The method without the network: a pair collides when the world AABBs
+    of the two posed OBBs overlap (the broadphase test).  Returns [n, 8] with
+    +1/-1 logits and zero regression outputs, so ``metrics`` applies."""
+    q = data["poses"][:, :4].astype(np.float64)
+    w, x, y, z = q.T
+    R = np.stack([1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y),
+                  2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x),
+                  2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)],
+                 axis=1).reshape(-1, 3, 3)
+    box = np.asarray(lib.aabb, np.float64)[data["obj_shape"]]
+    c = 0.5 * (box[:, :3] + box[:, 3:])
+    h = 0.5 * (box[:, 3:] - box[:, :3])
+    wc = np.einsum("nij,nj->ni", R, c) + data["poses"][:, 4:]
+    wh = np.einsum("nij,nj->ni", np.abs(R), h)
+    a, b = data["pairs"][:, 0], data["pairs"][:, 1]
+    hit = np.all(np.abs(wc[a] - wc[b]) <= wh[a] + wh[b], axis=1)
+    out = np.zeros((len(a), 8), np.float32)
+    out[:, 0] = np.where(hit, 1.0, -1.0)
+    return out
 
 
 def evaluate(det, lib_name, data, dev, cache):
@@ -104,12 +158,16 @@ def _run(det, data, dev):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--data", required=True)
+    ap.add_argument("--data", nargs="+", required=True)
     ap.add_argument("--test", nargs="*", default=[])
     ap.add_argument("--steps", type=int, default=20000)
     ap.add_argument("--batch", type=int, default=256)
     ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--lr-final", type=float, default=0.02,
+                    help="cosine decay to lr * lr_final at the last step (1 = constant)")
+    ap.add_argument("--val", type=int, default=4096, help="held-out pairs for checkpoint selection")
     ap.add_argument("--eval-every", type=int, default=5000)
+    ap.add_argument("--val-every", type=int, default=1000)
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--out", default=None)
     ap.add_argument("--report", default=None)
@@ -121,7 +179,12 @@ def main():
 
     dev = torch.device("cuda:0")
     torch.cuda.set_device(dev)
-    train, lib_name = load_dataset(args.data)
+    loaded = [load_dataset(p) for p in args.data]
+    lib_name = loaded[0][1]
+    if any(n != lib_name for _, n in loaded):
+        raise SystemExit("all --data files must use one shape library")
+    rng = np.random.default_rng(args.seed)
+    train, val = split(concat([d for d, _ in loaded]), args.val, rng)
     lib = make_library(lib_name)
     tests = [(p,) + load_dataset(p) for p in args.test]
     det = Detector(lib.points, lib.aabb, synth.xavier_weights(args.seed), RADIUS, "fp32")
@@ -129,32 +192,42 @@ def main():
     cache = {"train_lib": lib_name, "blob": lambda: weights.pack(
         weights.from_flat(tr.params().cpu().numpy()))}
 
-    report = {"train": args.data, "n_train": int(len(train["pairs"])), "batch": args.batch,
-              "steps": args.steps, "lr": args.lr, "evals": []}
+    report = {"train": args.data, "n_train": int(len(train["pairs"])),
+              "n_val": int(len(val["pairs"])), "batch": args.batch, "steps": args.steps,
+              "lr": args.lr, "lr_final": args.lr_final, "schedule": "cosine", "evals": [],
+              "val": []}
 
     def run_eval(step):
         row = {"step": step}
         for path, data, name in tests:
             tr.commit()
-            for prec in ("fp32", "bf16"):
+            for prec in ("fp32", "bf16", "fp8"):
                 det.set_precision(prec)
                 row[f"{os.path.basename(path)}:{prec}"] = metrics(
                     evaluate(det, name, data, dev, cache), data["targets"])
             det.set_precision("fp32")
+            tl = lib if name == lib_name else cache.setdefault(name, make_library(name))
+            row[f"{os.path.basename(path)}:aabb"] = metrics(aabb_overlap(tl, data),
+                                                            data["targets"])
         report["evals"].append(row)
         print(json.dumps(row), flush=True)
+
+    def run_val():
+        tr.commit()
+        return metrics(_run(det, val, dev), val["targets"])
 
     run_eval(0)
     P = len(train["pairs"])
     d_poses = torch.from_numpy(train["poses"]).to(dev)
     d_shape = torch.from_numpy(train["obj_shape"]).to(dev)
     d_tgt = torch.from_numpy(train["targets"]).to(dev)
-    rng = np.random.default_rng(args.seed)
     B = args.batch
     loss = torch.zeros(1, dtype=torch.float32, device=dev)
     hist = []
+    best = (-1.0, 0, None)
     t0 = time.time()
     for step in range(1, args.steps + 1):
+        tr.set_lr(tr_lr(args, step))
         idx = rng.integers(0, P, B)
         objs = np.stack([2 * idx, 2 * idx + 1], 1).ravel()
         bp = d_poses[torch.from_numpy(objs).to(dev)]
@@ -165,20 +238,37 @@ def main():
         tr.step(bp.contiguous(), bs.contiguous(), pairs, bt.contiguous(), rot, True, loss)
         if step % 200 == 0:
             hist.append((step, float(loss.item())))
+        if step % args.val_every == 0 or step == args.steps:
+            v = run_val()
+            report["val"].append({"step": step, **v})
+            # checkpoint selection: collision accuracy first, regression error second
+            score = v["f1"] - 1e-3 * v["depth_mae"]
+            if score > best[0]:
+                best = (score, step, tr.params().clone())
         if step % args.eval_every == 0 or step == args.steps:
-            print(f"step {step} loss {hist[-1][1]:.4f} {time.time() - t0:.0f} s", flush=True)
+            print(f"step {step} loss {hist[-1][1]:.4f} lr {tr_lr(args, step):.2e} "
+                  f"{time.time() - t0:.0f} s", flush=True)
             run_eval(step)
     report["loss_history"] = hist
     report["train_seconds"] = time.time() - t0
+    report["best_step"] = best[1]
+    tr.set_params(best[2])
+    run_eval(-best[1])
     if args.out:
         os.makedirs(os.path.dirname(os.path.abspath(args.out)), exist_ok=True)
         with open(args.out, "wb") as f:
-            f.write(weights.pack(weights.from_flat(tr.params().cpu().numpy())))
+            f.write(weights.pack(weights.from_flat(best[2].cpu().numpy())))
     if args.report:
         with open(args.report, "w") as f:
             json.dump(report, f, indent=1)
     tr.close()
     det.close()
+
+
+def tr_lr(args, step):
+    """Cosine decay from lr to lr * lr_final over the run."""
+    frac = (step - 1) / max(args.steps - 1, 1)
+    return args.lr * (args.lr_final + (1 - args.lr_final) * 0.5 * (1 + np.cos(np.pi * frac)))
 
 
 if __name__ == "__main__":

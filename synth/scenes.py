@@ -118,3 +118,21 @@ def sweep_pairs(lib: ShapeLibrary, n_pairs: int, seed: int,
     pairs = np.stack([np.arange(0, 2 * n, 2), np.arange(1, 2 * n, 2)],
                      axis=1).astype(np.int32)
     return poses, obj_shape, pairs, near
+
+
+def client_batch(n_shapes: int, n_env: int, n_pairs: int, seed: int,
+                 lam: float = 8.0, extent: float = 1.0):
+    """A simulator client's contact-query batch: ``n_env`` environments of
+    Poisson(lam) objects (clipped to [2, 25]) at uniform poses in
+    [-extent, extent]^3, and ``n_pairs`` candidate pairs, each two distinct
+    objects of one uniformly drawn environment.  Returns (poses f32 [n_obj,7],
+    obj_shape i32 [n_obj], pairs i32 [n_pairs,2])."""
+    rng = np.random.default_rng(seed)
+    poses, obj_shape, off = uneven_scene(n_env, n_shapes, int(rng.integers(1 << 30)), lam,
+                                         n_min=2, n_max=25, extent=extent)
+    e = rng.integers(0, n_env, size=n_pairs)
+    k = (off[e + 1] - off[e]).astype(np.int64)
+    a = rng.integers(0, k)
+    b = (a + 1 + rng.integers(0, k - 1)) % k
+    pairs = np.stack([off[e] + a, off[e] + b], axis=1).astype(np.int32)
+    return poses, obj_shape, pairs
