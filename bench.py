@@ -13,6 +13,12 @@ the launching stream.
     python bench.py [--gpus N] [--steps K] [--warmup W] [--precision bf16|fp32|fp8]
     python bench.py --impl reference ...   # the CPU oracle on the same workload
 
+After the timed steps (rank 0): ``e2e`` through the host-buffer call, the
+oracle on a bounded sample of the same scene (``cpu_baseline``) and a serving
+leg (``--serve-seconds`` each: Poisson arrivals of client batches at
+``--serve-rate`` requests/s through the request server, then at half of the
+capacity measured there; p50/p99 latency).
+
 Under torchrun every rank runs its own scene (weak scaling, no collective on
 the data path); the timing is the max over ranks.
 """
@@ -42,6 +48,19 @@ MAX_PAIRS = 400_000
 FLOP_ENC = 2 * 128 * (3 * 64 + 64 * 128 + 128 * 256)       # per pair
 FLOP_HEAD = 2 * (512 * 256 + 256 * 256 + 256 * 8)          # per pair
 WORKLOAD = "uneven_scenes_8192env_poisson8_64shapes"
+# DRAM bytes (read + write) per pair of the encoder kernel from one ncu capture
+# of the bench's scene 1 (154,924 pairs; profiles/kernels_bf16_fp8_uneven8192.md):
+# scaled by the pairs of a launch to give the per-launch traffic.
+ENC_DRAM_BYTES_PER_PAIR = {"bf16": (317.465344e6 + 275.488768e6) / 154924,
+                           "fp8": (317.382144e6 + 274.932480e6) / 154924}
+WEIGHTS = os.path.join(ROOT, "paper_2304_09439_b300", "weights", "locc_trained.bin")
+
+
+def trained_layers():
+    """The committed trained network (trained on the GPU by this library)."""
+    from paper_2304_09439_b300 import weights
+    with open(WEIGHTS, "rb") as f:
+        return weights.unpack(f.read())
 
 
 def _peaks():
@@ -126,7 +145,7 @@ def run_reference(args, rank: int, world: int) -> None:
     lib, scenes = make_inputs(0, 1)
     poses, osh, env = scenes[0]
     pairs = oracle.broadphase(lib.aabb, poses, osh, env)
-    params = oracle.flatten_params(synth.xavier_weights(1))
+    params = oracle.flatten_params(trained_layers())
     cores = os.cpu_count() or 1
     sample = int(args.ref_sample)
     rng = np.random.default_rng(0)
@@ -265,7 +284,7 @@ def cpu_baseline(lib, scene, seconds: float = 12.0):
     import oracle
     poses, osh, env = scene
     pairs = oracle.broadphase(lib.aabb, poses, osh, env)
-    params = oracle.flatten_params(synth.xavier_weights(1))
+    params = oracle.flatten_params(trained_layers())
     cores = os.cpu_count() or 1
     rng = np.random.default_rng(1)
     n, dt = 512, 0.0
@@ -322,7 +341,7 @@ def main():
         dist.init_process_group("nccl", device_id=dev)
 
     lib, scenes = make_inputs(rank, args.sets)
-    layers = synth.xavier_weights(1)
+    layers = trained_layers()
     det = Detector(lib.points, lib.aabb, layers, RADIUS, args.precision)
     det.reserve(MAX_PAIRS, N_ENV)
     dsc = []
@@ -465,6 +484,7 @@ def main():
                        "l2": "flushed between steps (256 MiB write)",
                        "cuda_graph": use_graph, "pipeline_chunks": chunks,
                        "crop_ctas_per_sm": cap, "autotune_ms": tune_ms,
+                       "weights": "trained (paper_2304_09439_b300/weights/locc_trained.bin)",
                        "parallelism": f"replicas{world}"},
             "stage_ms": {"broadphase": stage[0] / args.steps, "crop": stage[1] / args.steps,
                          "encoder": enc_ms, "head": stage[3] / args.steps,
@@ -472,7 +492,10 @@ def main():
                          "note": "crop / encoder / head summed over pipeline chunks; they overlap"},
             "roofline": {"kernel": "encoder", "bound": bound, "achieved": achieved,
                          "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                         "traffic": None, "peak_source": peak_src,
+                         "traffic": (ENC_DRAM_BYTES_PER_PAIR[args.precision] * per_step_pairs
+                                     if args.precision in ENC_DRAM_BYTES_PER_PAIR else None),
+                         "traffic_unit": "bytes per launch (ncu dram read+write per pair x pairs)",
+                         "peak_source": peak_src,
                          "algorithmic": f"{FLOP_ENC} FLOP per pair x pairs per launch"},
             "e2e": {"value": e2e_pairs_all / e2e_max, "unit": "pairs/s",
                     "h2d_bytes_per_step": h2d // args.steps, "d2h_bytes_per_step": d2h // args.steps},

@@ -86,8 +86,10 @@ typedef struct {
  * crop selection are float32 in every mode.
  *   LOCC_FP32: float32 CUDA-core products (the plain path);
  *   LOCC_BF16: bf16 operands on the tensor cores, float32 accumulation;
- *   LOCC_FP8:  e4m3 operands with per-channel weight scales and per-row
- *              activation scales on the tensor cores, float32 accumulation. */
+ *   LOCC_FP8:  e4m3 operands on the tensor cores, float32 accumulation;
+ *              per-output-channel weight scales, and static per-channel
+ *              activation scales (bounds that follow from the crop radius and
+ *              the weights) folded into the next layer's weights. */
 typedef enum { LOCC_FP32 = 0, LOCC_BF16 = 1, LOCC_FP8 = 2 } locc_precision;
 
 /* Create a detector on the current CUDA device.
@@ -130,8 +132,11 @@ int locc_detect_host(locc_handle *h, const float *poses,
 
 /* Steps 1-3 only (device pointers).  Outputs (idx_out / centre_out may be NULL):
  *   xyz_out:    float32 [n_pairs][2][64][4]: canonical x, y, z and 1.0 for a
- *               selected point, all zeros for padding; object A then B, nearest
- *               point first;
+ *               selected point, all zeros for padding; object A then B.  The
+ *               selected set is the min(64, n) in-ball samples nearest to the
+ *               centre (ties to the lower sample index); their order within a
+ *               crop is deterministic but not part of the result (the encoder
+ *               max-pools over points);
  *   idx_out:    int32 [n_pairs][2][64] library point index, -1 for padding;
  *   cnt_out:    int32 [n_pairs][2] number of selected points;
  *   centre_out: float32 [n_pairs][4] crop centre in A's body frame (w = 0). */

@@ -18,12 +18,21 @@
 //     with a bounding box per block; a warp first tests the ball against the
 //     block boxes (conservatively) and streams only the blocks that may hold
 //     in-ball points, one coalesced 512-byte float4 load per block;
-//   * in-ball points become 64-bit keys (d^2 bits, sample index, slot) and are
-//     appended to a per-warp shared-memory list by ballot + popc compaction;
-//     when the list is about to overflow it is bitonic-sorted in registers
-//     and cut to its 64 smallest keys, whose largest then bounds new arrivals
-//     (an exact streaming top-64);
-//   * the final list is sorted and its first min(64, n) keys are written out.
+//   * in-ball points become 64-bit keys (d^2 bits, sample index, storage
+//     position) and are appended to a per-warp shared-memory list by ballot +
+//     popc compaction, in one pass over the culled blocks (two block loads in
+//     flight per round);
+//   * at most 64 in-ball points: all are kept, nothing is sorted;
+//   * more: a 64-bin histogram of d^2 over [0, r^2] built from the list gives
+//     the bin b* that holds the 64th smallest key; every key of a lower bin is
+//     kept, and rank selection among the few keys of bin b* picks the rest
+//     (exact: the bin is a monotone function of d^2, keys are unique);
+//   * when the list fills up during the pass, the same histogram bounds the
+//     bins that can still matter: the list keeps those bins and later keys of
+//     higher bins are skipped; only if one bin alone overflows the list is it
+//     sorted and cut to its 64 smallest keys (an exact streaming top-64);
+//   * the kept keys are written in list order (storage order), which is not
+//     part of the result: the encoder max-pools over points.
 #include <algorithm>
 
 #include "common.cuh"
@@ -33,6 +42,7 @@ namespace {
 
 constexpr int CAND_CAP = 256;
 constexpr int NBINS = 64;  // d^2 histogram bins of the exact top-64 selection
+constexpr int EBUF = 64;   // keys of the cut bin resolved by rank
 constexpr unsigned FULL = 0xffffffffu;
 
 // One compare-exchange stage between lanes (partner lane ^ lj) for all R
@@ -158,17 +168,138 @@ __device__ __forceinline__ float box_dist2(float4 lo, float4 hi, float cx, float
   return dx * dx + dy * dy + dz * dz;
 }
 
+__device__ __forceinline__ float point_d2(float4 q, float cx, float cy, float cz) {
+  const float d0 = fsub(q.x, cx), d1 = fsub(q.y, cy), d2 = fsub(q.z, cz);
+  float s = fmul(d0, d0);
+  s = fadd(s, fmul(d1, d1));
+  return fadd(s, fmul(d2, d2));
+}
+
+// Selection key: d^2 bits (non-negative floats order as their bit patterns),
+// then the sample's library index (ties go to the lower index), then its
+// storage position (to find the point again).
+__device__ __forceinline__ unsigned long long make_key(float s, float4 q, int pos) {
+  return ((unsigned long long)__float_as_uint(s) << 32) |
+         ((unsigned long long)(__float_as_uint(q.w) & 0xffffu) << 16) | (unsigned)pos;
+}
+
+__device__ __forceinline__ int d2_bin(float s, float inv_w) {
+  return min(NBINS - 1, (int)fmul(s, inv_w));
+}
+
+__device__ __forceinline__ int key_bin(unsigned long long key, float inv_w) {
+  return d2_bin(__uint_as_float((unsigned)(key >> 32)), inv_w);
+}
+
+// The first bin b* at which the cumulative histogram count reaches KMAX
+// (requires a total above KMAX) and the count of the bins below it.
+__device__ __forceinline__ void cut_bin(const int* hist, int lane, int* bstar, int* below) {
+  const int h0 = hist[2 * lane], h1 = hist[2 * lane + 1];
+  int c = h0 + h1;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int t = __shfl_up_sync(FULL, c, o);
+    if (lane >= o) c += t;
+  }
+  const int L = __ffs(__ballot_sync(FULL, c >= KMAX)) - 1;
+  const int cL = __shfl_sync(FULL, c, L), h0L = __shfl_sync(FULL, h0, L),
+            h1L = __shfl_sync(FULL, h1, L);
+  const int excl = cL - h0L - h1L;
+  if (excl + h0L >= KMAX) {
+    *bstar = 2 * L;
+    *below = excl;
+  } else {
+    *bstar = 2 * L + 1;
+    *below = excl + h0L;
+  }
+}
+
+// Histogram of the d^2 bins of buf[0, n) (NBINS counters in shared memory).
+__device__ __forceinline__ void bin_histogram(const unsigned long long* buf, int n, float inv_w,
+                                              int* hist, int lane) {
+  hist[lane] = 0;
+  hist[lane + 32] = 0;
+  __syncwarp();
+  for (int j = lane; j < n; j += 32) atomicAdd(&hist[key_bin(buf[j], inv_w)], 1);
+  __syncwarp();
+}
+
+// Keep the keys of buf[0, n) whose bin is below `lim`, in order; returns
+// their number.
+__device__ __forceinline__ int keep_bins_below(unsigned long long* buf, int n, float inv_w, int lim,
+                                               int lane) {
+  const unsigned lt = (1u << lane) - 1u;
+  int w = 0;
+  for (int base = 0; base < n; base += 32) {
+    const int j = base + lane;
+    const unsigned long long key = j < n ? buf[j] : ~0ull;
+    const bool keep = j < n && key_bin(key, inv_w) < lim;
+    const unsigned km = __ballot_sync(FULL, keep);
+    __syncwarp();
+    if (keep) buf[w + __popc(km & lt)] = key;
+    w += __popc(km);
+    __syncwarp();
+  }
+  return w;
+}
+
+// Keep, in list order, the keys of buf[0, n) that are among the KMAX
+// smallest: every key of a bin below b* and the `need` smallest keys of bin
+// b* (rank selection over that bin's keys, which are unique).  buf must hold
+// every in-ball key of bins <= b*.  Returns false, leaving buf unchanged, when
+// bin b* holds more than EBUF keys.
+__device__ __forceinline__ bool select_cut(unsigned long long* buf, int n, float inv_w, int bstar,
+                                        int need, int lane, unsigned long long* ebuf,
+                                        unsigned long long* tsh) {
+  const unsigned lt = (1u << lane) - 1u;
+  int m = 0;
+  for (int base = 0; base < n; base += 32) {
+    const int j = base + lane;
+    const unsigned long long key = j < n ? buf[j] : ~0ull;
+    const bool e = j < n && key_bin(key, inv_w) == bstar;
+    const unsigned em = __ballot_sync(FULL, e);
+    if (m + __popc(em) > EBUF) return false;
+    if (e) ebuf[m + __popc(em & lt)] = key;
+    m += __popc(em);
+  }
+  __syncwarp();
+  for (int e = lane; e < m; e += 32) {
+    const unsigned long long k = ebuf[e];
+    int rank = 0;
+    for (int i = 0; i < m; ++i) rank += ebuf[i] < k;
+    if (rank == need - 1) *tsh = k;
+  }
+  __syncwarp();
+  const unsigned long long T = *tsh;
+  int w = 0;
+  for (int base = 0; base < n; base += 32) {
+    const int j = base + lane;
+    const unsigned long long key = j < n ? buf[j] : ~0ull;
+    int bin = NBINS;
+    if (j < n) bin = key_bin(key, inv_w);
+    const bool keep = bin < bstar || (bin == bstar && key <= T);
+    const unsigned km = __ballot_sync(FULL, keep);
+    __syncwarp();
+    if (keep) buf[w + __popc(km & lt)] = key;
+    w += __popc(km);
+    __syncwarp();
+  }
+  return true;
+}
+
 __device__ __forceinline__ void crop_pair(const DevLibrary& lib, const PairInputs& in, int p, int warp,
                                           int lane, float r, float4* __restrict__ xyz_out,
                                           int32_t* __restrict__ idx_out,
                                           int32_t* __restrict__ cnt_out,
                                           float4* __restrict__ centre_out, int* __restrict__ err,
-                                          unsigned long long* buf, int* hist) {
+                                          unsigned long long* buf, int* hist,
+                                          unsigned long long* ebuf, unsigned long long* tsh,
+                                          float* rsh) {
   int a, b, sa, sb;
   const bool ok = load_pair(in, lib.n_shapes, p, &a, &b, &sa, &sb, (warp == 0 && lane == 0) ? err : nullptr);
-  float4* xo = xyz_out + ((size_t)p * 2 + warp) * KMAX;
-  int32_t* io = idx_out ? idx_out + ((size_t)p * 2 + warp) * KMAX : nullptr;
   if (!ok) {
+    float4* xo = xyz_out + ((size_t)p * 2 + warp) * KMAX;
+    int32_t* io = idx_out ? idx_out + ((size_t)p * 2 + warp) * KMAX : nullptr;
     const float nan = __int_as_float(0x7fc00000);
     xo[lane] = xo[lane + 32] = make_float4(0.f, 0.f, 0.f, 0.f);
     if (io) io[lane] = io[lane + 32] = -1;
@@ -181,6 +312,9 @@ __device__ __forceinline__ void crop_pair(const DevLibrary& lib, const PairInput
              lib.aabb[2 * sa + 1], lib.aabb[2 * sb], lib.aabb[2 * sb + 1], f);
   if (warp == 0 && lane == 0 && centre_out) centre_out[p] = make_float4(f.c[0], f.c[1], f.c[2], 0.f);
 
+  // B's canonical coordinates need R_rel at the very end: park it in shared
+  // memory instead of keeping nine registers live through the selection
+  if (warp == 1 && lane < 9) rsh[lane] = f.rrel[lane];
   const int shape = warp == 0 ? sa : sb;
   const float cx = warp == 0 ? f.c[0] : f.cb[0];
   const float cy = warp == 0 ? f.c[1] : f.cb[1];
@@ -189,88 +323,96 @@ __device__ __forceinline__ void crop_pair(const DevLibrary& lib, const PairInput
   const float r2_cull = r2 * 1.001f + 1e-30f;  // conservative block test
   const float4* pts = lib.points + (size_t)shape * lib.n_pad;
   const float4* blk = lib.blocks + (size_t)shape * lib.n_blocks * 2;
-  unsigned long long bound = ~0ull;  // keys >= bound cannot reach the top 64
-  int n = 0;
-  // Pass 1: histogram of d^2 over NBINS equal bins of [0, r^2].  The bin is a
-  // non-decreasing function of d^2, so every key of a lower bin is smaller
-  // than every key of a higher bin, and the first bin b* at which the
-  // cumulative count reaches 64 bounds the 64 smallest keys: pass 2 keeps
-  // only keys of bins <= b* (about 64 + n / NBINS of them).
+  const unsigned lt = (1u << lane) - 1u;  // lanes below this one
+  int n = 0;      // keys in buf
+  int n_in = 0;   // in-ball points seen
   const float inv_w = (float)NBINS / r2;
-  hist[lane] = 0;
-  hist[lane + 32] = 0;
-  __syncwarp();
-  int n_in = 0;
+  // Keys of bins >= bcut, and keys >= bound, cannot be among the KMAX
+  // smallest any more: both only tighten while the pass runs.
+  int bcut = NBINS;
+  unsigned long long bound = ~0ull;
+  bool streamed = false;
+  // One pass over the culled blocks: the keys of in-ball points are appended
+  // to buf in visiting order.  When buf fills up, its histogram of d^2 over
+  // NBINS equal bins of [0, r^2] gives the first bin b' at which its
+  // cumulative count reaches KMAX; bins are a monotone function of d^2, so no
+  // key of a higher bin can be among the KMAX smallest: buf keeps the keys of
+  // bins <= b' (in order) and later keys of higher bins are skipped.  If even
+  // that leaves no room (one bin holding most keys), buf is sorted and cut to
+  // its KMAX smallest keys, whose largest bounds later arrivals.
+  float lim2 = r2_cull;  // blocks farther than this hold no key that can still matter
   for (int bg = 0; bg < lib.n_blocks; bg += 32) {
     const int bi = bg + lane;
-    bool hit = false;
-    if (bi < lib.n_blocks) hit = box_dist2(blk[2 * bi], blk[2 * bi + 1], cx, cy, cz) <= r2_cull;
-    unsigned mask = __ballot_sync(FULL, hit);
+    const float bd2 =
+        bi < lib.n_blocks ? box_dist2(blk[2 * bi], blk[2 * bi + 1], cx, cy, cz) : INFINITY;
+    unsigned mask = __ballot_sync(FULL, bd2 <= lim2);
     while (mask) {
-      const int bb = bg + __ffs(mask) - 1;
+      // two blocks per round: both loads are in flight together
+      const int pos0 = (bg + __ffs(mask) - 1) * BLOCK_PTS + lane;
       mask &= mask - 1;
-      const float4 q = pts[bb * BLOCK_PTS + lane];
-      const float d0 = fsub(q.x, cx), d1 = fsub(q.y, cy), d2 = fsub(q.z, cz);
-      float s = fmul(d0, d0);
-      s = fadd(s, fmul(d1, d1));
-      s = fadd(s, fmul(d2, d2));
-      const bool in = s <= r2;
-      if (in) atomicAdd(&hist[min(NBINS - 1, (int)(s * inv_w))], 1);
-      n_in += __popc(__ballot_sync(FULL, in));
-    }
-  }
-  __syncwarp();
-  int bstar = NBINS - 1;
-  if (n_in > KMAX) {
-    const int h0 = hist[2 * lane], h1 = hist[2 * lane + 1];
-    int c = h0 + h1;
+      const int pos1 = mask ? (bg + __ffs(mask) - 1) * BLOCK_PTS + lane : -1;
+      if (mask) mask &= mask - 1;
+      const float4 q0 = pts[pos0];
+      const float4 q1 = pts[pos1 >= 0 ? pos1 : pos0];
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int t = __shfl_up_sync(FULL, c, o);
-      if (lane >= o) c += t;
-    }
-    const int first_half = (c - h1) >= KMAX ? 0 : 1;  // does bin 2*lane already reach 64?
-    const int L = __ffs(__ballot_sync(FULL, c >= KMAX)) - 1;
-    bstar = 2 * L + __shfl_sync(FULL, first_half, L);
-  }
-  // Pass 2: collect the keys of bins <= b* (streaming top-64 if they overflow)
-  for (int bg = 0; bg < lib.n_blocks; bg += 32) {
-    const int bi = bg + lane;
-    bool hit = false;
-    if (bi < lib.n_blocks) hit = box_dist2(blk[2 * bi], blk[2 * bi + 1], cx, cy, cz) <= r2_cull;
-    unsigned mask = __ballot_sync(FULL, hit);
-    while (mask) {
-      const int bb = bg + __ffs(mask) - 1;
-      mask &= mask - 1;
-      const int pos = bb * BLOCK_PTS + lane;
-      const float4 q = pts[pos];
-      const float d0 = fsub(q.x, cx), d1 = fsub(q.y, cy), d2 = fsub(q.z, cz);
-      float s = fmul(d0, d0);
-      s = fadd(s, fmul(d1, d1));
-      s = fadd(s, fmul(d2, d2));
-      const unsigned long long key =
-          ((unsigned long long)__float_as_uint(s) << 32) |
-          ((unsigned long long)(__float_as_uint(q.w) & 0xffffu) << 16) | (unsigned)pos;
-      const bool in = s <= r2;
-      const int bin = in ? min(NBINS - 1, (int)(s * inv_w)) : NBINS;
-      const bool take = in && bin <= bstar && key < bound;
-      const unsigned tm = __ballot_sync(FULL, take);
-      if (tm == 0) continue;
-      if (n + __popc(tm) > CAND_CAP) {
-        sort_list<8>(buf, n, lane);
-        n = KMAX;
-        bound = buf[KMAX - 1];
+      for (int u = 0; u < 2; ++u) {
+        const int pos = u ? pos1 : pos0;
+        if (pos < 0) break;
+        const float4 q = u ? q1 : q0;
+        const float s = point_d2(q, cx, cy, cz);
+        const bool in = s <= r2;
+        n_in += __popc(__ballot_sync(FULL, in));
+        const unsigned long long key = make_key(s, q, pos);
+        bool take = in && d2_bin(s, inv_w) < bcut && key < bound;
+        unsigned tm = __ballot_sync(FULL, take);
+        if (tm == 0) continue;
+        if (n + __popc(tm) > CAND_CAP) {
+          int below;
+          bin_histogram(buf, n, inv_w, hist, lane);
+          cut_bin(hist, lane, &bcut, &below);
+          n = keep_bins_below(buf, n, inv_w, bcut + 1, lane);
+          bcut += 1;
+          // a key of bin >= bcut has d^2 >= bcut / inv_w (up to rounding):
+          // skip the blocks whose box lies farther (with a safety margin)
+          lim2 = fminf(lim2, (float)bcut / inv_w * 1.001f + 1e-30f);
+          mask &= __ballot_sync(FULL, bd2 <= lim2);
+          take = take && d2_bin(s, inv_w) < bcut;
+          tm = __ballot_sync(FULL, take);
+          if (n + __popc(tm) > CAND_CAP) {
+            sort_list<8>(buf, n, lane);
+            n = KMAX;
+            bound = buf[KMAX - 1];
+            streamed = true;
+            take = take && key < bound;
+            tm = __ballot_sync(FULL, take);
+          }
+        }
+        if (take) buf[n + __popc(tm & lt)] = key;
+        n += __popc(tm);
       }
-      const bool take2 = take && key < bound;
-      const unsigned tm2 = __ballot_sync(FULL, take2);
-      if (take2) buf[n + __popc(tm2 & ((1u << lane) - 1u))] = key;
-      n += __popc(tm2);
-      __syncwarp();
     }
   }
-  sort_any(buf, n, lane);
-  const int cnt = n < KMAX ? n : KMAX;
-  const float* R = f.rrel;
+  __syncwarp();
+  int cnt = n_in;  // n_in <= KMAX: every in-ball point is in buf, nothing to choose
+  if (n_in > KMAX) {
+    cnt = KMAX;
+    // buf holds every in-ball key of the bins that can still matter; the
+    // histogram of buf gives the bin b* that holds the KMAX-th smallest key:
+    // every key of a lower bin is kept, and rank selection among the few
+    // keys of bin b* picks the rest
+    bool sorted = streamed;
+    if (!sorted) {
+      int bstar, below;
+      bin_histogram(buf, n, inv_w, hist, lane);
+      cut_bin(hist, lane, &bstar, &below);
+      sorted = !select_cut(buf, n, inv_w, bstar, KMAX - below, lane, ebuf, tsh);
+    }
+    if (sorted) sort_any(buf, n, lane);
+  }
+  __syncwarp();
+  const float R[9] = {rsh[0], rsh[1], rsh[2], rsh[3], rsh[4], rsh[5], rsh[6], rsh[7], rsh[8]};
+  float4* xo = xyz_out + ((size_t)p * 2 + warp) * KMAX;
+  int32_t* io = idx_out ? idx_out + ((size_t)p * 2 + warp) * KMAX : nullptr;
 #pragma unroll
   for (int h = 0; h < 2; ++h) {
     const int s = lane + 32 * h;
@@ -304,13 +446,16 @@ __global__ void __launch_bounds__(64, 16) crop_kernel(DevLibrary lib, PairInputs
                                                       float4* __restrict__ centre_out,
                                                       int* __restrict__ err) {
   __shared__ unsigned long long cand[2][CAND_CAP];
+  __shared__ unsigned long long ebuf[2][EBUF];
+  __shared__ unsigned long long tsh[2];
   __shared__ int hist[2][NBINS];
+  __shared__ float rsh[2][12];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int lo, hi;
   range_bounds(rg, &lo, &hi);
   for (int p = lo + blockIdx.x; p < hi; p += gridDim.x) {
     crop_pair(lib, in, p, warp, lane, r, xyz_out, idx_out, cnt_out, centre_out, err, cand[warp],
-              hist[warp]);
+              hist[warp], ebuf[warp], &tsh[warp], rsh[warp]);
   }
 }
 

@@ -6,10 +6,17 @@
 // 3 -> 64 -> 128 -> 256, max-pool over the valid crop points of each object,
 // head 512 -> 256 -> 256 -> 8, world-frame epilogue.
 //
-// encoder_tc_kernel (persistent, one CTA of 128 threads per SM, one pair at a
-// time):
-//   * the bf16 images of W1, W2, W3 (82 KB) and the biases are copied into
-//     shared memory once and stay there for the life of the CTA;
+// encoder_tc_kernel (persistent, one CTA of 544 threads per SM, warp
+// specialised, NSLOT = 4 pairs in flight per CTA):
+//   * warp 16 (one elected lane) copies the bf16 images of W1, W2, W3 (82 KB)
+//     and the biases into shared memory once (cp.async.bulk), then streams the
+//     128 crop rows of each pair into its slot's staging buffer (bulk copies
+//     on an mbarrier) and issues every tcgen05.mma; warps 4s..4s+3 are the
+//     epilogue warpgroup of slot s (one thread per TMEM lane / crop row);
+//   * each slot owns 128 TMEM columns and one 32 KB shared operand region that
+//     holds X (layer-1 A operand), then H1, then H2 as the pair moves through
+//     the layers, so four pairs overlap: while one slot's epilogue converts a
+//     layer's accumulators, the tensor pipe works on the other slots;
 //   * the 128 crop rows of a pair (64 of A, 64 of B) form the M = 128 tile;
 //   * layer 1 packs K = 16: coordinates and weights are split into bf16 hi/lo
 //     parts, x.W ~ x_hi W_hi + x_lo W_hi + x_hi W_lo (9 of the 16 columns);
@@ -17,8 +24,10 @@
 //     epilogue adds the bias, applies ReLU and writes the bf16 row as the next
 //     layer's A operand;
 //   * layer 3 is computed transposed, D^T = W3 . H2^T (M = 128 channels per
-//     half, N = 128 points): thread r owns channel r, so the max-pool over the
-//     valid points of each object is a register reduction over TMEM columns.
+//     half, N = 128 points) in two halves that reuse the slot's 128 columns:
+//     thread r owns channel r, so the max-pool over the valid points of each
+//     object is a register reduction over TMEM columns; the second half is
+//     issued once the first has been pooled.
 // head_tc_kernel (persistent over tiles of 128 pairs): layer 1 streams W_h1 in
 // K-chunks of 64 through shared memory, layers 2 and 3 likewise; activations
 // stay on chip (TMEM -> bf16 in shared memory); the epilogue maps outputs to
