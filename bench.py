@@ -132,8 +132,7 @@ class ClockSampler:
 
 def make_inputs(rank: int, n_sets: int):
     lib = synth.make_library(N_SHAPES, LIB_SEED)
-    scenes = [synth.uneven_scene(N_ENV, N_SHAPES, seed=LIB_SEED + 1000 * rank + i)
-              for i in range(n_sets)]
+    scenes = [synth.uneven_scene(N_ENV, N_SHAPES, seed=sd) for sd in rank_scene_seeds(rank, n_sets)]
     return lib, scenes
 
 
@@ -277,6 +276,27 @@ def serving_leg(det, seconds: float, rate: float, max_queued: int, seed: int = 6
             "pool_batches": len(pool), "mean_pairs_per_request": mean_pairs,
             "max_batch_pairs": 131072, "max_queued_pairs": max_queued,
             "arena_bytes": 8 << 30, "overload": over, "half_capacity": half}
+
+
+def combine_ranks(ms, pairs, e2e_s, e2e_pairs, world: int, device):
+    """Whole-job figures over the ranks: the slowest rank's times (MAX) and
+    everyone's pairs (SUM) -- weak scaling, each rank runs its own scenes."""
+    import torch
+    if world <= 1:
+        return float(ms), float(pairs), float(e2e_s), float(e2e_pairs)
+    import torch.distributed as dist
+    stats = torch.tensor([ms, float(pairs), e2e_s, float(e2e_pairs)], dtype=torch.float64,
+                         device=device)
+    mx = stats.clone()
+    dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+    sm = stats.clone()
+    dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+    return mx[0].item(), sm[1].item(), mx[2].item(), sm[3].item()
+
+
+def rank_scene_seeds(rank: int, n_sets: int):
+    """Seeds of the scenes a rank runs: distinct per rank (no shared work)."""
+    return [LIB_SEED + 1000 * rank + i for i in range(n_sets)]
 
 
 def cpu_baseline(lib, scene, seconds: float = 12.0):
@@ -427,30 +447,25 @@ def main():
     det.status()
 
     # end to end through the host-buffer C call: H2D inputs, step, D2H outputs
-    host_scenes = scenes
-    det.step_host(*host_scenes[0], MAX_PAIRS)
+    # inputs and outputs in page-locked host memory (what a simulator feeding
+    # the detector keeps them in), allocated once
+    host_scenes = [tuple(_pinned_like(a) for a in sc) for sc in scenes]
+    h_pairs = _pinned_like(np.zeros((MAX_PAIRS, 2), np.int32))
+    h_out = _pinned_like(np.zeros((MAX_PAIRS, 8), np.float32))
+    det.step_host(*host_scenes[0], MAX_PAIRS, pairs_out=h_pairs, out=h_out)
     e2e_t, e2e_pairs, h2d, d2h = 0.0, 0, 0, 0
     for i in range(args.steps):
         poses, osh, env = host_scenes[i % len(host_scenes)]
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        pr, out, n = det.step_host(poses, osh, env, MAX_PAIRS)
+        pr, out, n = det.step_host(poses, osh, env, MAX_PAIRS, pairs_out=h_pairs, out=h_out)
         e2e_t += time.perf_counter() - t0
         e2e_pairs += n
         h2d += poses.nbytes + osh.nbytes + env.nbytes
         d2h += 4 + pr.nbytes + out.nbytes
 
-    stats = torch.tensor([ms, float(total_pairs), e2e_t, float(e2e_pairs)], dtype=torch.float64,
-                         device=dev)
-    if world > 1:
-        mx = stats.clone()
-        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-        sm = stats.clone()
-        dist.all_reduce(sm, op=dist.ReduceOp.SUM)
-        ms_max, pairs_all = mx[0].item(), sm[1].item()
-        e2e_max, e2e_pairs_all = mx[2].item(), sm[3].item()
-    else:
-        ms_max, pairs_all, e2e_max, e2e_pairs_all = ms, float(total_pairs), e2e_t, float(e2e_pairs)
+    ms_max, pairs_all, e2e_max, e2e_pairs_all = combine_ranks(ms, total_pairs, e2e_t, e2e_pairs,
+                                                              world, dev)
 
     if rank == 0:
         peaks, src = _peaks()

@@ -123,8 +123,9 @@ int locc_detect(locc_handle *h, const float *poses, const int32_t *obj_shape,
                 float *out, void *stream);
 
 /* Same as locc_detect with HOST arrays: copies inputs to the device, runs,
- * copies out back, and waits for the stream.  Uses pinned staging owned by
- * the handle. */
+ * copies out back, and waits for the stream.  Page-locked (pinned) arrays are
+ * copied directly; pageable ones go through pinned staging owned by the
+ * handle. */
 int locc_detect_host(locc_handle *h, const float *poses,
                      const int32_t *obj_shape, int32_t n_obj,
                      const int32_t *pairs, int32_t n_pairs, float *out,
@@ -179,7 +180,8 @@ int locc_step(locc_handle *h, const float *poses, const int32_t *obj_shape,
  * env_offsets [n_env+1] to the device, runs the step, waits, and copies back
  * the pair count (*n_pairs_out, host), the first min(count, max_pairs) pairs
  * (pairs_out, host int32 [max_pairs][2]) and their outputs (out, host float32
- * [max_pairs][8]). */
+ * [max_pairs][8]).  Page-locked arrays are copied directly, pageable ones
+ * through the handle's pinned staging. */
 int locc_step_host(locc_handle *h, const float *poses, const int32_t *obj_shape,
                    int32_t n_obj, const int32_t *env_offsets, int32_t n_env,
                    int32_t *pairs_out, int32_t *n_pairs_out, int32_t max_pairs,

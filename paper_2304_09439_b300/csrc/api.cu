@@ -41,6 +41,18 @@ uint32_t spread10(uint32_t v) {
   return v;
 }
 
+// Page-locked (pinned) host memory: copies can go straight between it and
+// the device, without the handle's staging buffer.
+bool is_pinned(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeHost;
+}
+
 template <typename T>
 cudaError_t upload(T** dptr, const std::vector<T>& host) {
   cudaError_t e = cudaMalloc(reinterpret_cast<void**>(dptr), host.size() * sizeof(T));
@@ -463,10 +475,16 @@ int locc_step_host(locc_handle* h, const float* poses, const int32_t* obj_shape,
   if (st) return st;
   char* hs = static_cast<char*>(h->h_stage);
   char* ds = static_cast<char*>(h->d_stage);
-  std::memcpy(hs, poses, b_poses);
-  std::memcpy(hs + o_shape, obj_shape, b_shape);
-  std::memcpy(hs + o_env, env_offsets, b_env);
-  CUDA_TRY(cudaMemcpyAsync(ds, hs, in_bytes, cudaMemcpyHostToDevice, s));
+  if (is_pinned(poses) && is_pinned(obj_shape) && is_pinned(env_offsets)) {
+    CUDA_TRY(cudaMemcpyAsync(ds, poses, b_poses, cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(ds + o_shape, obj_shape, b_shape, cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(ds + o_env, env_offsets, b_env, cudaMemcpyHostToDevice, s));
+  } else {
+    std::memcpy(hs, poses, b_poses);
+    std::memcpy(hs + o_shape, obj_shape, b_shape);
+    std::memcpy(hs + o_env, env_offsets, b_env);
+    CUDA_TRY(cudaMemcpyAsync(ds, hs, in_bytes, cudaMemcpyHostToDevice, s));
+  }
   st = locc_step(h, reinterpret_cast<float*>(ds), reinterpret_cast<int32_t*>(ds + o_shape), n_obj,
                  reinterpret_cast<int32_t*>(ds + o_env), n_env,
                  reinterpret_cast<int32_t*>(ds + o_pairs), reinterpret_cast<int32_t*>(ds + o_cnt),
@@ -479,11 +497,17 @@ int locc_step_host(locc_handle* h, const float* poses, const int32_t* obj_shape,
   *n_pairs_out = n;
   const int32_t m = std::min(n, max_pairs);
   if (m > 0) {
-    CUDA_TRY(cudaMemcpyAsync(hs + o_pairs, ds + o_pairs, (size_t)m * 8, cudaMemcpyDeviceToHost, s));
-    CUDA_TRY(cudaMemcpyAsync(hs + o_out, ds + o_out, (size_t)m * 32, cudaMemcpyDeviceToHost, s));
-    CUDA_TRY(cudaStreamSynchronize(s));
-    std::memcpy(pairs_out, hs + o_pairs, (size_t)m * 8);
-    std::memcpy(out, hs + o_out, (size_t)m * 32);
+    if (is_pinned(pairs_out) && is_pinned(out)) {
+      CUDA_TRY(cudaMemcpyAsync(pairs_out, ds + o_pairs, (size_t)m * 8, cudaMemcpyDeviceToHost, s));
+      CUDA_TRY(cudaMemcpyAsync(out, ds + o_out, (size_t)m * 32, cudaMemcpyDeviceToHost, s));
+      CUDA_TRY(cudaStreamSynchronize(s));
+    } else {
+      CUDA_TRY(cudaMemcpyAsync(hs + o_pairs, ds + o_pairs, (size_t)m * 8, cudaMemcpyDeviceToHost, s));
+      CUDA_TRY(cudaMemcpyAsync(hs + o_out, ds + o_out, (size_t)m * 32, cudaMemcpyDeviceToHost, s));
+      CUDA_TRY(cudaStreamSynchronize(s));
+      std::memcpy(pairs_out, hs + o_pairs, (size_t)m * 8);
+      std::memcpy(out, hs + o_out, (size_t)m * 32);
+    }
   }
   return LOCC_OK;
 }
@@ -555,17 +579,29 @@ int locc_detect_host(locc_handle* h, const float* poses, const int32_t* obj_shap
   if (st0) return st0;
   char* hs = static_cast<char*>(h->h_stage);
   char* ds = static_cast<char*>(h->d_stage);
-  std::memcpy(hs, poses, b_poses);
-  std::memcpy(hs + al(b_poses), obj_shape, b_shape);
-  std::memcpy(hs + al(b_poses) + al(b_shape), pairs, b_pairs);
-  CUDA_TRY(cudaMemcpyAsync(ds, hs, in_bytes, cudaMemcpyHostToDevice, s));
+  if (is_pinned(poses) && is_pinned(obj_shape) && is_pinned(pairs)) {
+    CUDA_TRY(cudaMemcpyAsync(ds, poses, b_poses, cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(ds + al(b_poses), obj_shape, b_shape, cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(ds + al(b_poses) + al(b_shape), pairs, b_pairs,
+                             cudaMemcpyHostToDevice, s));
+  } else {
+    std::memcpy(hs, poses, b_poses);
+    std::memcpy(hs + al(b_poses), obj_shape, b_shape);
+    std::memcpy(hs + al(b_poses) + al(b_shape), pairs, b_pairs);
+    CUDA_TRY(cudaMemcpyAsync(ds, hs, in_bytes, cudaMemcpyHostToDevice, s));
+  }
   int st = locc_detect(h, reinterpret_cast<float*>(ds), reinterpret_cast<int32_t*>(ds + al(b_poses)),
                        n_obj, reinterpret_cast<int32_t*>(ds + al(b_poses) + al(b_shape)), n_pairs,
                        reinterpret_cast<float*>(ds + in_bytes), stream);
   if (st) return st;
-  CUDA_TRY(cudaMemcpyAsync(hs + in_bytes, ds + in_bytes, b_out, cudaMemcpyDeviceToHost, s));
-  CUDA_TRY(cudaStreamSynchronize(s));
-  std::memcpy(out, hs + in_bytes, b_out);
+  if (is_pinned(out)) {
+    CUDA_TRY(cudaMemcpyAsync(out, ds + in_bytes, b_out, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+  } else {
+    CUDA_TRY(cudaMemcpyAsync(hs + in_bytes, ds + in_bytes, b_out, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    std::memcpy(out, hs + in_bytes, b_out);
+  }
   return LOCC_OK;
 }
 
