@@ -349,22 +349,18 @@ constexpr int HT = 128;                                   // pairs per tile
 constexpr int H_W3 = 0;                                    // [16 x 256] 8 KB
 constexpr int H_BIAS = H_W3 + 16 * 256 * 2;                // hb1 256, hb2 256, hb3 16
 constexpr int H_RES_BYTES = H_BIAS + (256 + 256 + 16) * 4; // resident part of the image
-constexpr int H_A = (H_RES_BYTES + 127) / 128 * 128;       // A chunk [128 x 64] 16 KB
-constexpr int H_B = H_A + 128 * 64 * 2;                    // B chunk [256 x 64] 32 KB
-constexpr int H_G = H_B + 256 * 64 * 2;                    // G [128 x 256] 64 KB
-constexpr int H_CTRL = H_G + 128 * 256 * 2;
-constexpr int H_SMEM = H_CTRL + 64;
 constexpr int H_CHUNK = 256 * 64 * 2;                      // bytes of one B chunk
+constexpr int H_A0 = (H_RES_BYTES + 1023) / 1024 * 1024;   // A stages [128 x 64] 16 KB each
+constexpr int H_B0 = H_A0 + 2 * 128 * 64 * 2;              // B stages [256 x 64] 32 KB each
+constexpr int H_G = H_B0 + 2 * H_CHUNK;                    // G [128 x 256] 64 KB
+constexpr int H_CTRL = H_G + 128 * 256 * 2;                // 7 mbarriers, TMEM address, abort
+constexpr int H_SMEM = H_CTRL + 80;
 // global image: [resident][W_h1 chunks x 8][W_h2 chunks x 4]
 constexpr int H_IMG_W1 = (H_RES_BYTES + 127) / 128 * 128;
 constexpr int H_IMG_W2 = H_IMG_W1 + 8 * H_CHUNK;
 constexpr int H_IMG_BYTES = H_IMG_W2 + 4 * H_CHUNK;
 static_assert(H_RES_BYTES % 16 == 0, "resident image must be 16-byte chunks");
-
-__device__ __forceinline__ void copy_chunk(unsigned char* dst, const unsigned char* src, int bytes) {
-  for (int i = threadIdx.x; i < bytes / 16; i += 128)
-    reinterpret_cast<uint4*>(dst)[i] = ld_global_v4(src + 16 * (size_t)i);
-}
+static_assert(H_IMG_W1 % 16 == 0 && H_CHUNK % 16 == 0, "bulk copies need 16-byte chunks");
 
 // Epilogue of a 256-wide layer: TMEM row tid, columns [col0, col0 + 256) ->
 // relu(x + b) as bf16 into G (K = 256).
@@ -386,6 +382,12 @@ __device__ __forceinline__ void head_epi_256(uint32_t taddr, const float* b, uns
   }
 }
 
+// Head over tiles of HT = 128 pairs (one pair per thread / TMEM lane).
+// Layers 1 and 2 run as 12 K-chunks of 64 (8 of W_h1 against the features, 4
+// of W_h2 against G) through two operand stages: while the MMAs of chunk c
+// run, chunk c + 1's weights arrive by bulk copy (thread 0) and its features
+// are converted to bf16 (all threads).  A stage is refilled once the MMAs that
+// read it have completed (tcgen05.commit on the stage's mbarrier).
 __global__ void __launch_bounds__(128, 1)
     head_tc_kernel(const float* __restrict__ feat, PairRange rg,
                    const unsigned char* __restrict__ img, PairInputs in, int have_in,
@@ -397,98 +399,119 @@ __global__ void __launch_bounds__(128, 1)
   range_bounds(rg, &lo, &n);  // this launch's pairs: [lo, n)
   const int n_tiles = (n - lo + HT - 1) / HT;
   if ((int)blockIdx.x >= n_tiles) return;
-  for (int i = tid; i < H_RES_BYTES / 16; i += 128)
-    reinterpret_cast<uint4*>(smem)[i] = ld_global_v4(img + 16 * (size_t)i);
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + H_CTRL);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + H_CTRL + 8);
-  const uint32_t bar = smem_u32(mbar);
+  // mbarriers: 0, 1 weights of stage s landed; 2, 3 MMAs of stage s done;
+  // 4 layer 3 done; 5 resident image landed; 6 drain
+  const uint32_t bar0 = smem_u32(smem + H_CTRL);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + H_CTRL + 56);
+  volatile int* abort = reinterpret_cast<volatile int*>(smem + H_CTRL + 60);
+  const uint32_t B_L3 = bar0 + 32, B_RES = bar0 + 40, B_DRAIN = bar0 + 48;
   if (tid == 0) {
-    mbar_init(bar, 1);
+    for (int i = 0; i < 7; ++i) mbar_init(bar0 + 8 * i, 1);
+    *abort = 0;
     fence_mbar_init();
   }
   if (warp == 0) {
     tmem_alloc(smem_u32(tmem_slot), 512);
     tmem_relinquish();
   }
-  fence_async_smem();
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tbase = *tmem_slot;
+  if (tid == 0) {
+    mbar_expect_tx(B_RES, H_RES_BYTES);
+    bulk_g2s(smem_u32(smem), img, H_RES_BYTES, B_RES);
+  }
   const uint32_t lane_off = (uint32_t)(32 * warp) << 16;
   const float* hb1 = reinterpret_cast<const float*>(smem + H_BIAS);
   const float* hb2 = hb1 + 256;
   const float* hb3 = hb2 + 256;
-  unsigned char* A = smem + H_A;
-  unsigned char* B = smem + H_B;
   unsigned char* G = smem + H_G;
-  const uint32_t sA = smem_u32(A), sB = smem_u32(B), sG = smem_u32(G), sW3 = smem_u32(smem + H_W3);
-  uint32_t phase = 0;
-  bool ok = true;
+  const uint32_t sG = smem_u32(G), sW3 = smem_u32(smem + H_W3);
+  int nb[2] = {0, 0}, nm[2] = {0, 0}, n3 = 0;  // bulk loads / MMA commits per stage
+  bool ok = mbar_wait_or_abort(B_RES, 0, abort, WAIT_CYCLES);
 
   for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
     const int q0 = lo + tile * HT;
     const int pr = q0 + tid;  // this thread's pair (row)
     const bool row_ok = pr < n;
-    // ---- layer 1: D1[128 x 256] = F[128 x 512] . Wh1^T, K in chunks of 64
 #pragma unroll 1
-    for (int kc = 0; kc < 8; ++kc) {
-      const float* src = feat + (size_t)pr * 512 + 64 * kc;
+    for (int c = 0; c < 12; ++c) {
+      const int st = c & 1;
+      unsigned char* A = smem + H_A0 + st * (128 * 64 * 2);
+      const uint32_t sA = smem_u32(A), sB = smem_u32(smem + H_B0 + st * H_CHUNK);
+      // the MMAs that last read this stage have completed
+      if (nm[st] > 0) ok = mbar_wait_or_abort(bar0 + 16 + 8 * st, (nm[st] - 1) & 1, abort, WAIT_CYCLES);
+      if (!__syncthreads_and(ok)) {
+        ok = false;
+        break;
+      }
+      if (tid == 0) {
+        const unsigned char* w = img + (c < 8 ? H_IMG_W1 + (size_t)c * H_CHUNK
+                                              : H_IMG_W2 + (size_t)(c - 8) * H_CHUNK);
+        mbar_expect_tx(bar0 + 8 * st, H_CHUNK);
+        bulk_g2s(sB, w, H_CHUNK, bar0 + 8 * st);
+      }
+      ++nb[st];
+      if (c < 8) {
+        // features [pr][64c, 64c + 64) -> bf16 A operand row tid
+        const float* src = feat + (size_t)pr * 512 + 64 * c;
 #pragma unroll
-      for (int c = 0; c < 8; ++c) {
-        float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f), a1 = a0;
-        if (row_ok) {
-          a0 = __ldg(reinterpret_cast<const float4*>(src + 8 * c));
-          a1 = __ldg(reinterpret_cast<const float4*>(src + 8 * c + 4));
+        for (int k = 0; k < 8; ++k) {
+          float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f), a1 = a0;
+          if (row_ok) {
+            a0 = __ldg(reinterpret_cast<const float4*>(src + 8 * k));
+            a1 = __ldg(reinterpret_cast<const float4*>(src + 8 * k + 4));
+          }
+          uint4 w;
+          w.x = pack_bf16(a0.x, a0.y);
+          w.y = pack_bf16(a0.z, a0.w);
+          w.z = pack_bf16(a1.x, a1.y);
+          w.w = pack_bf16(a1.z, a1.w);
+          *reinterpret_cast<uint4*>(A + kmajor_off(tid, 8 * k, 64)) = w;
         }
-        uint4 w;
-        w.x = pack_bf16(a0.x, a0.y);
-        w.y = pack_bf16(a0.z, a0.w);
-        w.z = pack_bf16(a1.x, a1.y);
-        w.w = pack_bf16(a1.z, a1.w);
-        *reinterpret_cast<uint4*>(A + kmajor_off(tid, 8 * c, 64)) = w;
+      } else if (c == 8) {
+        // layer-1 accumulators are final once the MMAs of chunk 7 (stage 1)
+        // have completed (tcgen05 operations complete in order)
+        ok = mbar_wait_or_abort(bar0 + 24, (nm[1] - 1) & 1, abort, WAIT_CYCLES);
+        if (!__syncthreads_and(ok)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        head_epi_256(tbase + lane_off + 0, hb1, G, tid);
       }
-      copy_chunk(B, img + H_IMG_W1 + (size_t)kc * H_CHUNK, H_CHUNK);
       fence_async_smem();
       tc_fence_before();
       __syncthreads();
-      if (tid == 0) {
-        tc_fence_after();
+      if (tid == 0 && !*abort) {
+        if (mbar_wait_or_abort(bar0 + 8 * st, (nb[st] - 1) & 1, abort, WAIT_CYCLES)) {
+          tc_fence_after();
+          if (c < 8) {
 #pragma unroll
-        for (int kk = 0; kk < 4; ++kk)
-          mma_bf16(tbase + 0, sdesc(sA + 256 * kk, 128, 1024), sdesc(sB + 256 * kk, 128, 1024),
-                   idesc_bf16(128, 256), (kc > 0 || kk > 0) ? 1u : 0u);
-        mma_commit(bar);
+            for (int kk = 0; kk < 4; ++kk)
+              mma_bf16(tbase + 0, sdesc(sA + 256 * kk, 128, 1024), sdesc(sB + 256 * kk, 128, 1024),
+                       idesc_bf16(128, 256), (c > 0 || kk > 0) ? 1u : 0u);
+          } else {
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk)
+              mma_bf16(tbase + 256, sdesc(sG + 1024 * (c - 8) + 256 * kk, 128, 4096),
+                       sdesc(sB + 256 * kk, 128, 1024), idesc_bf16(128, 256),
+                       (c > 8 || kk > 0) ? 1u : 0u);
+          }
+          mma_commit(bar0 + 16 + 8 * st);
+        }
       }
-      ok = mbar_wait(bar, phase, WAIT_CYCLES);
-      phase ^= 1;
-      if (!__syncthreads_and(ok)) { ok = false; break; }
-      tc_fence_after();
+      ++nm[st];
     }
     if (!ok) break;
-    head_epi_256(tbase + lane_off + 0, hb1, G, tid);
-    // ---- layer 2: D2[128 x 256] = G[128 x 256] . Wh2^T
-#pragma unroll 1
-    for (int kc = 0; kc < 4; ++kc) {
-      copy_chunk(B, img + H_IMG_W2 + (size_t)kc * H_CHUNK, H_CHUNK);
-      fence_async_smem();
-      tc_fence_before();
-      __syncthreads();
-      if (tid == 0) {
-        tc_fence_after();
-#pragma unroll
-        for (int kk = 0; kk < 4; ++kk)
-          mma_bf16(tbase + 256, sdesc(sG + 1024 * kc + 256 * kk, 128, 4096),
-                   sdesc(sB + 256 * kk, 128, 1024), idesc_bf16(128, 256),
-                   (kc > 0 || kk > 0) ? 1u : 0u);
-        mma_commit(bar);
-      }
-      ok = mbar_wait(bar, phase, WAIT_CYCLES);
-      phase ^= 1;
-      if (!__syncthreads_and(ok)) { ok = false; break; }
-      tc_fence_after();
+    // layer-2 accumulators are final with the MMAs of chunk 11 (stage 1)
+    ok = mbar_wait_or_abort(bar0 + 24, (nm[1] - 1) & 1, abort, WAIT_CYCLES);
+    if (!__syncthreads_and(ok)) {
+      ok = false;
+      break;
     }
-    if (!ok) break;
+    tc_fence_after();
     head_epi_256(tbase + lane_off + 256, hb2, G, tid);
     fence_async_smem();
     tc_fence_before();
@@ -500,11 +523,14 @@ __global__ void __launch_bounds__(128, 1)
       for (int kk = 0; kk < 16; ++kk)
         mma_bf16(tbase + 0, sdesc(sG + 256 * kk, 128, 4096), sdesc(sW3 + 256 * kk, 128, 4096),
                  idesc_bf16(128, 16), kk > 0);
-      mma_commit(bar);
+      mma_commit(B_L3);
     }
-    ok = mbar_wait(bar, phase, WAIT_CYCLES);
-    phase ^= 1;
-    if (!__syncthreads_and(ok)) { ok = false; break; }
+    ok = mbar_wait_or_abort(B_L3, n3 & 1, abort, WAIT_CYCLES);
+    ++n3;
+    if (!__syncthreads_and(ok)) {
+      ok = false;
+      break;
+    }
     tc_fence_after();
     {
       float v[16];
@@ -520,9 +546,9 @@ __global__ void __launch_bounds__(128, 1)
         if (out) {
           float o8[8];
           const int a = have_in ? in.pairs[2 * pr] : -1;
-          const float4 c = centre[pr];
-          if (a >= 0 && a < in.n_obj && !isnan(c.x)) {
-            epilogue_world(y, in.poses + 7 * (size_t)a, c, o8);
+          const float4 cc = centre[pr];
+          if (a >= 0 && a < in.n_obj && !isnan(cc.x)) {
+            epilogue_world(y, in.poses + 7 * (size_t)a, cc, o8);
           } else {
 #pragma unroll
             for (int o = 0; o < 8; ++o) o8[o] = __int_as_float(0x7fc00000);
@@ -535,7 +561,14 @@ __global__ void __launch_bounds__(128, 1)
     tc_fence_before();
     __syncthreads();
   }
-  if (!ok && tid == 0) atomicOr(err, 2);
+  if (tid == 0 && (!ok || *abort)) {
+    // drain: wait (bounded) for this thread's MMAs and bulk copies
+    atomicOr(err, 2);
+    mma_commit(B_DRAIN);
+    mbar_wait(B_DRAIN, 0, WAIT_CYCLES);
+    for (int st = 0; st < 2; ++st)
+      if (nb[st] > 0) mbar_wait(bar0 + 8 * st, (nb[st] - 1) & 1, WAIT_CYCLES);
+  }
   tc_fence_before();
   __syncthreads();
   if (warp == 0) {
