@@ -348,16 +348,12 @@ constexpr int G_CHUNK = 256 * 128;       // one B chunk [256 x 128] e4m3, 32 KB
 constexpr int G_IMG_W1 = G_RES_BYTES;    // 4 chunks
 constexpr int G_IMG_W2 = G_IMG_W1 + 4 * G_CHUNK;  // 2 chunks
 constexpr int G_IMG_BYTES = G_IMG_W2 + 2 * G_CHUNK;
-constexpr int G_A = G_RES_BYTES;         // A chunk [128 x 128] e4m3, 16 KB
-constexpr int G_B = G_A + 128 * 128;     // B chunk 32 KB
-constexpr int G_G = G_B + G_CHUNK;       // G [128 x 256] e4m3, 32 KB
-constexpr int G_CTRL = G_G + 128 * 256;
-constexpr int G_SMEM = G_CTRL + 64;
-
-__device__ __forceinline__ void copy_chunk(unsigned char* dst, const unsigned char* src, int bytes) {
-  for (int i = threadIdx.x; i < bytes / 16; i += 128)
-    reinterpret_cast<uint4*>(dst)[i] = ldg_v4(src + 16 * (size_t)i);
-}
+constexpr int G_A0 = (G_RES_BYTES + 1023) / 1024 * 1024;  // A stages [128 x 128] e4m3, 16 KB each
+constexpr int G_B0 = G_A0 + 2 * 128 * 128;                 // B stages, 32 KB each
+constexpr int G_G = G_B0 + 2 * G_CHUNK;                    // G [128 x 256] e4m3, 32 KB
+constexpr int G_CTRL = G_G + 128 * 256;                    // 7 mbarriers, TMEM address, abort
+constexpr int G_SMEM = G_CTRL + 80;
+static_assert(G_RES_BYTES % 16 == 0 && G_IMG_W1 % 16 == 0, "bulk copies need 16-byte chunks");
 
 __device__ __forceinline__ void head_epi_fp8(uint32_t taddr, const float* alpha, const float* beta,
                                              unsigned char* G, int row) {
@@ -369,6 +365,9 @@ __device__ __forceinline__ void head_epi_fp8(uint32_t taddr, const float* alpha,
   }
 }
 
+// Same pipeline as the BF16 head (two operand stages, weights by bulk copy,
+// features of chunk c + 1 quantised while chunk c's MMAs run) over 6 K-chunks
+// of 128: 4 of W_h1 against the features, 2 of W_h2 against G.
 __global__ void __launch_bounds__(128, 1)
     head_fp8_kernel(const float* __restrict__ feat, PairRange rg,
                     const unsigned char* __restrict__ img, PairInputs in, int have_in,
@@ -380,24 +379,29 @@ __global__ void __launch_bounds__(128, 1)
   range_bounds(rg, &lo, &n);  // this launch's pairs: [lo, n)
   const int n_tiles = (n - lo + HT - 1) / HT;
   if ((int)blockIdx.x >= n_tiles) return;
-  for (int i = tid; i < G_RES_BYTES / 16; i += 128)
-    reinterpret_cast<uint4*>(smem)[i] = ldg_v4(img + 16 * (size_t)i);
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + G_CTRL);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + G_CTRL + 8);
-  const uint32_t bar = smem_u32(mbar);
+  // mbarriers: 0, 1 weights of stage s landed; 2, 3 MMAs of stage s done;
+  // 4 layer 3 done; 5 resident image landed; 6 drain
+  const uint32_t bar0 = smem_u32(smem + G_CTRL);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + G_CTRL + 56);
+  volatile int* abort = reinterpret_cast<volatile int*>(smem + G_CTRL + 60);
+  const uint32_t B_L3 = bar0 + 32, B_RES = bar0 + 40, B_DRAIN = bar0 + 48;
   if (tid == 0) {
-    mbar_init(bar, 1);
+    for (int i = 0; i < 7; ++i) mbar_init(bar0 + 8 * i, 1);
+    *abort = 0;
     fence_mbar_init();
   }
   if (warp == 0) {
     tmem_alloc(smem_u32(tmem_slot), 512);
     tmem_relinquish();
   }
-  fence_async_smem();
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tbase = *tmem_slot;
+  if (tid == 0) {
+    mbar_expect_tx(B_RES, G_RES_BYTES);
+    bulk_g2s(smem_u32(smem), img, G_RES_BYTES, B_RES);
+  }
   const uint32_t lane_off = (uint32_t)(32 * warp) << 16;
   const float* finv = reinterpret_cast<const float*>(smem + G_EP);
   const float* a4 = finv + 256;
@@ -406,83 +410,101 @@ __global__ void __launch_bounds__(128, 1)
   const float* c5 = a5 + 256;
   const float* w6 = c5 + 256;
   const float* hb3 = w6 + 16;
-  unsigned char* A = smem + G_A;
-  unsigned char* B = smem + G_B;
   unsigned char* G = smem + G_G;
-  const uint32_t sA = smem_u32(A), sB = smem_u32(B), sG = smem_u32(G), sW3 = smem_u32(smem + G_W3);
+  const uint32_t sG = smem_u32(G), sW3 = smem_u32(smem + G_W3);
   const uint32_t id256 = idesc_e4m3(128, 256), id16 = idesc_e4m3(128, 16);
-  uint32_t phase = 0;
-  bool ok = true;
+  int nb[2] = {0, 0}, nm[2] = {0, 0}, n3 = 0;  // bulk loads / MMA commits per stage
+  bool ok = mbar_wait_or_abort(B_RES, 0, abort, WAIT_CYCLES);
 
   for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
     const int pr = lo + tile * HT + tid;
     const bool row_ok = pr < n;
     const float* src = feat + (size_t)pr * 512;
 #pragma unroll 1
-    for (int kc = 0; kc < 4; ++kc) {
-      const float* fi = finv + (128 * kc) % 256;
+    for (int c = 0; c < 6; ++c) {
+      const int st = c & 1;
+      unsigned char* A = smem + G_A0 + st * (128 * 128);
+      const uint32_t sA = smem_u32(A), sB = smem_u32(smem + G_B0 + st * G_CHUNK);
+      // the MMAs that last read this stage have completed
+      if (nm[st] > 0) ok = mbar_wait_or_abort(bar0 + 16 + 8 * st, (nm[st] - 1) & 1, abort, WAIT_CYCLES);
+      if (!__syncthreads_and(ok)) {
+        ok = false;
+        break;
+      }
+      if (tid == 0) {
+        const unsigned char* w = img + (c < 4 ? G_IMG_W1 + (size_t)c * G_CHUNK
+                                              : G_IMG_W2 + (size_t)(c - 4) * G_CHUNK);
+        mbar_expect_tx(bar0 + 8 * st, G_CHUNK);
+        bulk_g2s(sB, w, G_CHUNK, bar0 + 8 * st);
+      }
+      ++nb[st];
+      if (c < 4) {
+        // features [pr][128c, 128c + 128) scaled by 1 / s_k -> e4m3 A row tid
+        const float* fi = finv + (128 * c) % 256;
 #pragma unroll
-      for (int c = 0; c < 8; ++c) {
-        float t[16];
-        if (row_ok) {
+        for (int k = 0; k < 8; ++k) {
+          float t[16];
+          if (row_ok) {
 #pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const float4 f = __ldg(reinterpret_cast<const float4*>(src + 128 * kc + 16 * c + 4 * q));
-            t[4 * q + 0] = f.x * fi[16 * c + 4 * q + 0];
-            t[4 * q + 1] = f.y * fi[16 * c + 4 * q + 1];
-            t[4 * q + 2] = f.z * fi[16 * c + 4 * q + 2];
-            t[4 * q + 3] = f.w * fi[16 * c + 4 * q + 3];
+            for (int q = 0; q < 4; ++q) {
+              const float4 f = __ldg(reinterpret_cast<const float4*>(src + 128 * c + 16 * k + 4 * q));
+              t[4 * q + 0] = f.x * fi[16 * k + 4 * q + 0];
+              t[4 * q + 1] = f.y * fi[16 * k + 4 * q + 1];
+              t[4 * q + 2] = f.z * fi[16 * k + 4 * q + 2];
+              t[4 * q + 3] = f.w * fi[16 * k + 4 * q + 3];
+            }
+          } else {
+#pragma unroll
+            for (int q = 0; q < 16; ++q) t[q] = 0.f;
           }
-        } else {
-#pragma unroll
-          for (int q = 0; q < 16; ++q) t[q] = 0.f;
+          uint4 w;
+          w.x = pack_e4m3x4(t[0], t[1], t[2], t[3]);
+          w.y = pack_e4m3x4(t[4], t[5], t[6], t[7]);
+          w.z = pack_e4m3x4(t[8], t[9], t[10], t[11]);
+          w.w = pack_e4m3x4(t[12], t[13], t[14], t[15]);
+          *reinterpret_cast<uint4*>(A + kmajor_off8(tid, 16 * k, 128)) = w;
         }
-        uint4 w;
-        w.x = pack_e4m3x4(t[0], t[1], t[2], t[3]);
-        w.y = pack_e4m3x4(t[4], t[5], t[6], t[7]);
-        w.z = pack_e4m3x4(t[8], t[9], t[10], t[11]);
-        w.w = pack_e4m3x4(t[12], t[13], t[14], t[15]);
-        *reinterpret_cast<uint4*>(A + kmajor_off8(tid, 16 * c, 128)) = w;
+      } else if (c == 4) {
+        // layer-1 accumulators are final once the MMAs of chunk 3 (stage 1)
+        // have completed (tcgen05 operations complete in order)
+        ok = mbar_wait_or_abort(bar0 + 24, (nm[1] - 1) & 1, abort, WAIT_CYCLES);
+        if (!__syncthreads_and(ok)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        head_epi_fp8(tbase + lane_off + 0, a4, c4, G, tid);
       }
-      copy_chunk(B, img + G_IMG_W1 + (size_t)kc * G_CHUNK, G_CHUNK);
       fence_async_smem();
       tc_fence_before();
       __syncthreads();
-      if (tid == 0) {
-        tc_fence_after();
+      if (tid == 0 && !*abort) {
+        if (mbar_wait_or_abort(bar0 + 8 * st, (nb[st] - 1) & 1, abort, WAIT_CYCLES)) {
+          tc_fence_after();
+          if (c < 4) {
 #pragma unroll
-        for (int kk = 0; kk < 4; ++kk)
-          mma_e4m3(tbase + 0, sdesc(sA + 256 * kk, 128, 1024), sdesc(sB + 256 * kk, 128, 1024), id256,
-                   (kc > 0 || kk > 0) ? 1u : 0u);
-        mma_commit(bar);
+            for (int kk = 0; kk < 4; ++kk)
+              mma_e4m3(tbase + 0, sdesc(sA + 256 * kk, 128, 1024), sdesc(sB + 256 * kk, 128, 1024),
+                       id256, (c > 0 || kk > 0) ? 1u : 0u);
+          } else {
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk)
+              mma_e4m3(tbase + 256, sdesc(sG + 1024 * (c - 4) + 256 * kk, 128, 2048),
+                       sdesc(sB + 256 * kk, 128, 1024), id256, (c > 4 || kk > 0) ? 1u : 0u);
+          }
+          mma_commit(bar0 + 16 + 8 * st);
+        }
       }
-      ok = mbar_wait(bar, phase, WAIT_CYCLES);
-      phase ^= 1;
-      if (!__syncthreads_and(ok)) { ok = false; break; }
-      tc_fence_after();
+      ++nm[st];
     }
     if (!ok) break;
-    head_epi_fp8(tbase + lane_off + 0, a4, c4, G, tid);
-#pragma unroll 1
-    for (int kc = 0; kc < 2; ++kc) {
-      copy_chunk(B, img + G_IMG_W2 + (size_t)kc * G_CHUNK, G_CHUNK);
-      fence_async_smem();
-      tc_fence_before();
-      __syncthreads();
-      if (tid == 0) {
-        tc_fence_after();
-#pragma unroll
-        for (int kk = 0; kk < 4; ++kk)
-          mma_e4m3(tbase + 256, sdesc(sG + 1024 * kc + 256 * kk, 128, 2048),
-                   sdesc(sB + 256 * kk, 128, 1024), id256, (kc > 0 || kk > 0) ? 1u : 0u);
-        mma_commit(bar);
-      }
-      ok = mbar_wait(bar, phase, WAIT_CYCLES);
-      phase ^= 1;
-      if (!__syncthreads_and(ok)) { ok = false; break; }
-      tc_fence_after();
+    // layer-2 accumulators are final with the MMAs of chunk 5 (stage 1)
+    ok = mbar_wait_or_abort(bar0 + 24, (nm[1] - 1) & 1, abort, WAIT_CYCLES);
+    if (!__syncthreads_and(ok)) {
+      ok = false;
+      break;
     }
-    if (!ok) break;
+    tc_fence_after();
     head_epi_fp8(tbase + lane_off + 256, a5, c5, G, tid);
     fence_async_smem();
     tc_fence_before();
@@ -493,11 +515,14 @@ __global__ void __launch_bounds__(128, 1)
       for (int kk = 0; kk < 8; ++kk)
         mma_e4m3(tbase + 0, sdesc(sG + 256 * kk, 128, 2048), sdesc(sW3 + 256 * kk, 128, 2048), id16,
                  kk > 0);
-      mma_commit(bar);
+      mma_commit(B_L3);
     }
-    ok = mbar_wait(bar, phase, WAIT_CYCLES);
-    phase ^= 1;
-    if (!__syncthreads_and(ok)) { ok = false; break; }
+    ok = mbar_wait_or_abort(B_L3, n3 & 1, abort, WAIT_CYCLES);
+    ++n3;
+    if (!__syncthreads_and(ok)) {
+      ok = false;
+      break;
+    }
     tc_fence_after();
     {
       float v[16];
@@ -513,9 +538,9 @@ __global__ void __launch_bounds__(128, 1)
         if (out) {
           float o8[8];
           const int a = have_in ? in.pairs[2 * pr] : -1;
-          const float4 c = centre[pr];
-          if (a >= 0 && a < in.n_obj && !isnan(c.x)) {
-            epilogue_world(y, in.poses + 7 * (size_t)a, c, o8);
+          const float4 cc = centre[pr];
+          if (a >= 0 && a < in.n_obj && !isnan(cc.x)) {
+            epilogue_world(y, in.poses + 7 * (size_t)a, cc, o8);
           } else {
 #pragma unroll
             for (int o = 0; o < 8; ++o) o8[o] = __int_as_float(0x7fc00000);
@@ -528,7 +553,14 @@ __global__ void __launch_bounds__(128, 1)
     tc_fence_before();
     __syncthreads();
   }
-  if (!ok && tid == 0) atomicOr(err, 2);
+  if (tid == 0 && (!ok || *abort)) {
+    // drain: wait (bounded) for this thread's MMAs and bulk copies
+    atomicOr(err, 2);
+    mma_commit(B_DRAIN);
+    mbar_wait(B_DRAIN, 0, WAIT_CYCLES);
+    for (int st = 0; st < 2; ++st)
+      if (nb[st] > 0) mbar_wait(bar0 + 8 * st, (nb[st] - 1) & 1, WAIT_CYCLES);
+  }
   tc_fence_before();
   __syncthreads();
   if (warp == 0) {
