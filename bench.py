@@ -392,7 +392,8 @@ def main():
         chunks, cap = (int(x) for x in args.pipeline.split(","))
         det.set_pipeline(chunks, cap)
         tune_ms = None
-    launches_per_step = 3 + 3 * (chunks if max(n_pairs) >= 4096 else 1)
+    # broadphase (3 kernels), then per chunk: crop, crop fallback, encoder, head
+    launches_per_step = 3 + 4 * (chunks if max(n_pairs) >= 4096 else 1)
 
     def step_plain(i):
         p, s, e = dsc[i % len(dsc)]

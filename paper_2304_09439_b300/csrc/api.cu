@@ -74,7 +74,8 @@ int ensure_capacity(locc_handle* h, int n_pairs, cudaStream_t stream) {
   if (cudaMalloc(&h->d_xyz, P * ROWS * sizeof(float4)) != cudaSuccess ||
       cudaMalloc(&h->d_cnt, P * 2 * sizeof(int32_t)) != cudaSuccess ||
       cudaMalloc(&h->d_centre, P * sizeof(float4)) != cudaSuccess ||
-      cudaMalloc(&h->d_feat, P * 512 * sizeof(float)) != cudaSuccess) {
+      cudaMalloc(&h->d_feat, P * 512 * sizeof(float)) != cudaSuccess ||
+      cudaMalloc(&h->d_defer, (1 + 2 * P) * sizeof(int)) != cudaSuccess) {
     cudaGetLastError();
     free_scratch(h);
     return fail(LOCC_ERR_OOM, "cannot allocate scratch for %d pairs", n_pairs);
@@ -88,7 +89,9 @@ void free_scratch(locc_handle* h) {
   cudaFree(h->d_cnt);
   cudaFree(h->d_centre);
   cudaFree(h->d_feat);
+  cudaFree(h->d_defer);
   h->d_xyz = nullptr, h->d_cnt = nullptr, h->d_centre = nullptr, h->d_feat = nullptr;
+  h->d_defer = nullptr;
   h->cap_pairs = 0;
 }
 
@@ -174,6 +177,7 @@ int run_path(locc_handle* h, const PairInputs& in, int n_cap, const int* n_dev, 
     const PairRange rg = whole_range(n_cap, n_dev);
     if (prof) CUDA_TRY(cudaEventRecord(h->ev_c0[0], s));
     CUDA_TRY(launch_crop(lib, in, rg, h->radius, h->d_xyz, nullptr, h->d_cnt, h->d_centre, h->d_err,
+                         h->d_defer,
                          h->n_sm, h->crop_cap, s));
     if (prof) {
       CUDA_TRY(cudaEventRecord(h->ev_c1[0], s));
@@ -193,6 +197,7 @@ int run_path(locc_handle* h, const PairInputs& in, int n_cap, const int* n_dev, 
     const PairRange rg{n_cap, n_dev, i, C};
     if (prof) CUDA_TRY(cudaEventRecord(h->ev_c0[i], s));
     CUDA_TRY(launch_crop(lib, in, rg, h->radius, h->d_xyz, nullptr, h->d_cnt, h->d_centre, h->d_err,
+                         h->d_defer,
                          h->n_sm, h->crop_cap, s));
     if (prof) CUDA_TRY(cudaEventRecord(h->ev_c1[i], s));
     CUDA_TRY(cudaEventRecord(h->ev_crop[i], s));
@@ -520,10 +525,12 @@ int locc_crop(locc_handle* h, const float* poses, const int32_t* obj_shape, int3
   if (n_pairs == 0) return LOCC_OK;
   if (!poses || !obj_shape || !pairs || !xyz_out || !cnt_out)
     return fail(LOCC_ERR_INVALID_ARG, "NULL array");
+  int st = ensure_capacity(h, n_pairs, (cudaStream_t)stream);  // fallback scratch
+  if (st) return st;
   PairInputs in{poses, obj_shape, pairs, n_obj, n_pairs};
   CUDA_TRY(launch_crop(dev_library(h), in, whole_range(n_pairs, nullptr), h->radius,
                        reinterpret_cast<float4*>(xyz_out), idx_out, cnt_out,
-                       reinterpret_cast<float4*>(centre_out), h->d_err, h->n_sm, 0,
+                       reinterpret_cast<float4*>(centre_out), h->d_err, h->d_defer, h->n_sm, 0,
                        (cudaStream_t)stream));
   return LOCC_OK;
 }

@@ -146,9 +146,11 @@ namespace locc {
 // n_dev (nullable): device count of pairs actually present (<= n_pairs), read
 // by the kernels so that a fixed launch serves a count produced on the device.
 // grid_cap (crop): at most this many resident CTAs per SM (0 = occupancy limit).
+// defer (crop): device int [1 + 2 * (pairs of one launch)], scratch for the
+// objects left to the exact fallback kernel (defer[0] = their count).
 cudaError_t launch_crop(const DevLibrary& lib, const PairInputs& in, const PairRange& rg,
                         float r, float4* xyz, int32_t* idx, int32_t* cnt, float4* centre,
-                        int* err, int n_sm, int grid_cap, cudaStream_t stream);
+                        int* err, int* defer, int n_sm, int grid_cap, cudaStream_t stream);
 cudaError_t launch_encoder_fp32(const float4* xyz, const PairRange& rg,
                                 const Fp32Params& prm, float* feat, int n_sm,
                                 cudaStream_t stream);

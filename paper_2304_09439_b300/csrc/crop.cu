@@ -287,6 +287,35 @@ __device__ __forceinline__ bool select_cut(unsigned long long* buf, int n, float
   return true;
 }
 
+// Rows of one object crop: the points of the first cnt keys of buf in the
+// canonical frame (A: p - c; B: R_rel (p - c_B)), w = 1; zeros beyond.
+__device__ __forceinline__ void write_crop(const unsigned long long* buf, int cnt,
+                                           const float4* pts, float cx, float cy, float cz,
+                                           const float* R, float4* xo, int32_t* io, int lane) {
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int s = lane + 32 * h;
+    float4 o = make_float4(0.f, 0.f, 0.f, 0.f);
+    int oi = -1;
+    if (s < cnt) {
+      const unsigned long long key = buf[s];
+      const int pos = (int)(key & 0xffffu);
+      oi = (int)((key >> 16) & 0xffffu);
+      const float4 q = pts[pos];
+      const float d0 = fsub(q.x, cx), d1 = fsub(q.y, cy), d2 = fsub(q.z, cz);
+      if (!R) {
+        o = make_float4(d0, d1, d2, 1.0f);
+      } else {
+        o = make_float4(dot3_rn(R[0], R[1], R[2], d0, d1, d2),
+                        dot3_rn(R[3], R[4], R[5], d0, d1, d2),
+                        dot3_rn(R[6], R[7], R[8], d0, d1, d2), 1.0f);
+      }
+    }
+    xo[s] = o;
+    if (io) io[s] = oi;
+  }
+}
+
 __device__ __forceinline__ void crop_pair(const DevLibrary& lib, const PairInputs& in, int p, int warp,
                                           int lane, float r, float4* __restrict__ xyz_out,
                                           int32_t* __restrict__ idx_out,
@@ -294,7 +323,7 @@ __device__ __forceinline__ void crop_pair(const DevLibrary& lib, const PairInput
                                           float4* __restrict__ centre_out, int* __restrict__ err,
                                           unsigned long long* buf, int* hist,
                                           unsigned long long* ebuf, unsigned long long* tsh,
-                                          float* rsh) {
+                                          float* rsh, int* defer, int defer_cap) {
   int a, b, sa, sb;
   const bool ok = load_pair(in, lib.n_shapes, p, &a, &b, &sa, &sb, (warp == 0 && lane == 0) ? err : nullptr);
   if (!ok) {
@@ -327,26 +356,25 @@ __device__ __forceinline__ void crop_pair(const DevLibrary& lib, const PairInput
   int n = 0;      // keys in buf
   int n_in = 0;   // in-ball points seen
   const float inv_w = (float)NBINS / r2;
-  // Keys of bins >= bcut, and keys >= bound, cannot be among the KMAX
-  // smallest any more: both only tighten while the pass runs.
+  // Keys of bins >= bcut cannot be among the KMAX smallest any more (the
+  // bound only tightens while the pass runs).
   int bcut = NBINS;
-  unsigned long long bound = ~0ull;
-  bool streamed = false;
+  bool deferred = false;  // left to the exact fallback kernel
   // One pass over the culled blocks: the keys of in-ball points are appended
   // to buf in visiting order.  When buf fills up, its histogram of d^2 over
   // NBINS equal bins of [0, r^2] gives the first bin b' at which its
   // cumulative count reaches KMAX; bins are a monotone function of d^2, so no
   // key of a higher bin can be among the KMAX smallest: buf keeps the keys of
-  // bins <= b' (in order) and later keys of higher bins are skipped.  If even
-  // that leaves no room (one bin holding most keys), buf is sorted and cut to
-  // its KMAX smallest keys, whose largest bounds later arrivals.
+  // bins <= b' (in order), later keys of higher bins are skipped and blocks
+  // whose box lies beyond bin b' are no longer loaded.  If even that leaves no
+  // room (one bin holding most keys), the object is deferred.
   float lim2 = r2_cull;  // blocks farther than this hold no key that can still matter
-  for (int bg = 0; bg < lib.n_blocks; bg += 32) {
+  for (int bg = 0; bg < lib.n_blocks && !deferred; bg += 32) {
     const int bi = bg + lane;
     const float bd2 =
         bi < lib.n_blocks ? box_dist2(blk[2 * bi], blk[2 * bi + 1], cx, cy, cz) : INFINITY;
     unsigned mask = __ballot_sync(FULL, bd2 <= lim2);
-    while (mask) {
+    while (mask && !deferred) {
       // two blocks per round: both loads are in flight together
       const int pos0 = (bg + __ffs(mask) - 1) * BLOCK_PTS + lane;
       mask &= mask - 1;
@@ -357,13 +385,12 @@ __device__ __forceinline__ void crop_pair(const DevLibrary& lib, const PairInput
 #pragma unroll
       for (int u = 0; u < 2; ++u) {
         const int pos = u ? pos1 : pos0;
-        if (pos < 0) break;
+        if (pos < 0 || deferred) break;
         const float4 q = u ? q1 : q0;
         const float s = point_d2(q, cx, cy, cz);
         const bool in = s <= r2;
         n_in += __popc(__ballot_sync(FULL, in));
-        const unsigned long long key = make_key(s, q, pos);
-        bool take = in && d2_bin(s, inv_w) < bcut && key < bound;
+        bool take = in && d2_bin(s, inv_w) < bcut;
         unsigned tm = __ballot_sync(FULL, take);
         if (tm == 0) continue;
         if (n + __popc(tm) > CAND_CAP) {
@@ -379,63 +406,105 @@ __device__ __forceinline__ void crop_pair(const DevLibrary& lib, const PairInput
           take = take && d2_bin(s, inv_w) < bcut;
           tm = __ballot_sync(FULL, take);
           if (n + __popc(tm) > CAND_CAP) {
-            sort_list<8>(buf, n, lane);
-            n = KMAX;
-            bound = buf[KMAX - 1];
-            streamed = true;
-            take = take && key < bound;
-            tm = __ballot_sync(FULL, take);
+            deferred = true;
+            break;
           }
         }
-        if (take) buf[n + __popc(tm & lt)] = key;
+        if (take) buf[n + __popc(tm & lt)] = make_key(s, q, pos);
         n += __popc(tm);
       }
     }
   }
   __syncwarp();
   int cnt = n_in;  // n_in <= KMAX: every in-ball point is in buf, nothing to choose
-  if (n_in > KMAX) {
+  if (!deferred && n_in > KMAX) {
     cnt = KMAX;
     // buf holds every in-ball key of the bins that can still matter; the
     // histogram of buf gives the bin b* that holds the KMAX-th smallest key:
     // every key of a lower bin is kept, and rank selection among the few
     // keys of bin b* picks the rest
-    bool sorted = streamed;
-    if (!sorted) {
-      int bstar, below;
-      bin_histogram(buf, n, inv_w, hist, lane);
-      cut_bin(hist, lane, &bstar, &below);
-      sorted = !select_cut(buf, n, inv_w, bstar, KMAX - below, lane, ebuf, tsh);
+    int bstar, below;
+    bin_histogram(buf, n, inv_w, hist, lane);
+    cut_bin(hist, lane, &bstar, &below);
+    deferred = !select_cut(buf, n, inv_w, bstar, KMAX - below, lane, ebuf, tsh);
+  }
+  if (deferred) {
+    // rare: one d^2 bin holds more keys than the list or the rank buffer;
+    // crop_fallback_kernel redoes this object with an exact streaming sort
+    if (lane == 0) {
+      const int slot = atomicAdd(defer, 1);
+      if (slot < defer_cap) defer[1 + slot] = 2 * p + warp;
     }
-    if (sorted) sort_any(buf, n, lane);
+    return;
   }
   __syncwarp();
-  const float R[9] = {rsh[0], rsh[1], rsh[2], rsh[3], rsh[4], rsh[5], rsh[6], rsh[7], rsh[8]};
-  float4* xo = xyz_out + ((size_t)p * 2 + warp) * KMAX;
-  int32_t* io = idx_out ? idx_out + ((size_t)p * 2 + warp) * KMAX : nullptr;
-#pragma unroll
-  for (int h = 0; h < 2; ++h) {
-    const int s = lane + 32 * h;
-    float4 o = make_float4(0.f, 0.f, 0.f, 0.f);
-    int oi = -1;
-    if (s < cnt) {
-      const unsigned long long key = buf[s];
-      const int pos = (int)(key & 0xffffu);
-      oi = (int)((key >> 16) & 0xffffu);
-      const float4 q = pts[pos];
-      const float d0 = fsub(q.x, cx), d1 = fsub(q.y, cy), d2 = fsub(q.z, cz);
-      if (warp == 0) {
-        o = make_float4(d0, d1, d2, 1.0f);
-      } else {
-        o = make_float4(dot3_rn(R[0], R[1], R[2], d0, d1, d2),
-                        dot3_rn(R[3], R[4], R[5], d0, d1, d2),
-                        dot3_rn(R[6], R[7], R[8], d0, d1, d2), 1.0f);
-      }
-    }
-    xo[s] = o;
-    if (io) io[s] = oi;
-  }
+  write_crop(buf, cnt, pts, cx, cy, cz, warp == 1 ? rsh : nullptr,
+             xyz_out + ((size_t)p * 2 + warp) * KMAX,
+             idx_out ? idx_out + ((size_t)p * 2 + warp) * KMAX : nullptr, lane);
   if (lane == 0) cnt_out[2 * p + warp] = cnt;
+  __syncwarp();
+}
+
+// Exact fallback for the objects crop_kernel deferred: the classic streaming
+// top-KMAX -- keys collected into the list, and whenever it is full it is
+// sorted and cut to its KMAX smallest keys, whose largest bounds later keys.
+__device__ __forceinline__ void fallback_object(const DevLibrary& lib, const PairInputs& in, int p,
+                                                int obj, int lane, float r,
+                                                float4* __restrict__ xyz_out,
+                                                int32_t* __restrict__ idx_out,
+                                                int32_t* __restrict__ cnt_out,
+                                                unsigned long long* buf) {
+  int a, b, sa, sb;
+  if (!load_pair(in, lib.n_shapes, p, &a, &b, &sa, &sb, nullptr)) return;
+  Frame f;
+  pair_frame(in.poses + 7 * (size_t)a, in.poses + 7 * (size_t)b, lib.aabb[2 * sa],
+             lib.aabb[2 * sa + 1], lib.aabb[2 * sb], lib.aabb[2 * sb + 1], f);
+  const int shape = obj == 0 ? sa : sb;
+  const float cx = obj == 0 ? f.c[0] : f.cb[0];
+  const float cy = obj == 0 ? f.c[1] : f.cb[1];
+  const float cz = obj == 0 ? f.c[2] : f.cb[2];
+  const float r2 = fmul(r, r);
+  const float r2_cull = r2 * 1.001f + 1e-30f;
+  const float4* pts = lib.points + (size_t)shape * lib.n_pad;
+  const float4* blk = lib.blocks + (size_t)shape * lib.n_blocks * 2;
+  const unsigned lt = (1u << lane) - 1u;
+  unsigned long long bound = ~0ull;
+  int n = 0, n_in = 0;
+  for (int bg = 0; bg < lib.n_blocks; bg += 32) {
+    const int bi = bg + lane;
+    bool hit = false;
+    if (bi < lib.n_blocks) hit = box_dist2(blk[2 * bi], blk[2 * bi + 1], cx, cy, cz) <= r2_cull;
+    unsigned mask = __ballot_sync(FULL, hit);
+    while (mask) {
+      const int pos = (bg + __ffs(mask) - 1) * BLOCK_PTS + lane;
+      mask &= mask - 1;
+      const float4 q = pts[pos];
+      const float s = point_d2(q, cx, cy, cz);
+      const bool in = s <= r2;
+      n_in += __popc(__ballot_sync(FULL, in));
+      const unsigned long long key = make_key(s, q, pos);
+      bool take = in && key < bound;
+      unsigned tm = __ballot_sync(FULL, take);
+      if (tm == 0) continue;
+      if (n + __popc(tm) > CAND_CAP) {
+        sort_list<8>(buf, n, lane);
+        n = KMAX;
+        bound = buf[KMAX - 1];
+        take = take && key < bound;
+        tm = __ballot_sync(FULL, take);
+      }
+      if (take) buf[n + __popc(tm & lt)] = key;
+      n += __popc(tm);
+      __syncwarp();
+    }
+  }
+  __syncwarp();
+  sort_any(buf, n, lane);
+  const int cnt = n_in < KMAX ? n_in : KMAX;
+  write_crop(buf, cnt, pts, cx, cy, cz, obj == 1 ? f.rrel : nullptr,
+             xyz_out + ((size_t)p * 2 + obj) * KMAX,
+             idx_out ? idx_out + ((size_t)p * 2 + obj) * KMAX : nullptr, lane);
+  if (lane == 0) cnt_out[2 * p + obj] = cnt;
   __syncwarp();
 }
 
@@ -444,7 +513,8 @@ __global__ void __launch_bounds__(64, 16) crop_kernel(DevLibrary lib, PairInputs
                                                       int32_t* __restrict__ idx_out,
                                                       int32_t* __restrict__ cnt_out,
                                                       float4* __restrict__ centre_out,
-                                                      int* __restrict__ err) {
+                                                      int* __restrict__ err, int* __restrict__ defer,
+                                                      int defer_cap) {
   __shared__ unsigned long long cand[2][CAND_CAP];
   __shared__ unsigned long long ebuf[2][EBUF];
   __shared__ unsigned long long tsh[2];
@@ -455,7 +525,23 @@ __global__ void __launch_bounds__(64, 16) crop_kernel(DevLibrary lib, PairInputs
   range_bounds(rg, &lo, &hi);
   for (int p = lo + blockIdx.x; p < hi; p += gridDim.x) {
     crop_pair(lib, in, p, warp, lane, r, xyz_out, idx_out, cnt_out, centre_out, err, cand[warp],
-              hist[warp], ebuf[warp], &tsh[warp], rsh[warp]);
+              hist[warp], ebuf[warp], &tsh[warp], rsh[warp], defer, defer_cap);
+  }
+}
+
+// One warp per deferred object (defer[0] = count, defer[1 + i] = 2 p + object).
+__global__ void __launch_bounds__(64) crop_fallback_kernel(DevLibrary lib, PairInputs in, float r,
+                                                           float4* __restrict__ xyz_out,
+                                                           int32_t* __restrict__ idx_out,
+                                                           int32_t* __restrict__ cnt_out,
+                                                           const int* __restrict__ defer,
+                                                           int defer_cap) {
+  __shared__ unsigned long long cand[2][CAND_CAP];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int n = min(defer[0], defer_cap);
+  for (int e = 2 * blockIdx.x + warp; e < n; e += 2 * gridDim.x) {
+    const int code = defer[1 + e];
+    fallback_object(lib, in, code >> 1, code & 1, lane, r, xyz_out, idx_out, cnt_out, cand[warp]);
   }
 }
 
@@ -463,7 +549,7 @@ __global__ void __launch_bounds__(64, 16) crop_kernel(DevLibrary lib, PairInputs
 
 cudaError_t launch_crop(const DevLibrary& lib, const PairInputs& in, const PairRange& rg, float r,
                         float4* xyz, int32_t* idx, int32_t* cnt, float4* centre, int* err,
-                        int n_sm, int grid_cap, cudaStream_t stream) {
+                        int* defer, int n_sm, int grid_cap, cudaStream_t stream) {
   if (in.n_pairs <= 0) return cudaSuccess;
   // one wave of resident CTAs (at most grid_cap per SM); each strides over its pairs
   static int per_sm = 0;
@@ -474,7 +560,14 @@ cudaError_t launch_crop(const DevLibrary& lib, const PairInputs& in, const PairR
   const int cap = grid_cap > 0 ? std::min(grid_cap, per_sm) : per_sm;
   const int span = (in.n_pairs + rg.n_chunks - 1) / rg.n_chunks + 1;
   const int grid = std::max(1, std::min(span, n_sm * cap));
-  crop_kernel<<<grid, 64, 0, stream>>>(lib, in, rg, r, xyz, idx, cnt, centre, err);
+  const int defer_cap = 2 * (span - 1);  // both objects of every pair of one chunk
+  cudaError_t e = cudaMemsetAsync(defer, 0, sizeof(int), stream);
+  if (e != cudaSuccess) return e;
+  crop_kernel<<<grid, 64, 0, stream>>>(lib, in, rg, r, xyz, idx, cnt, centre, err, defer,
+                                       defer_cap);
+  // a fixed grid that reads the count on the device (graph-capturable); it
+  // finds nothing to do unless some object was deferred
+  crop_fallback_kernel<<<n_sm, 64, 0, stream>>>(lib, in, r, xyz, idx, cnt, defer, defer_cap);
   return cudaGetLastError();
 }
 

@@ -34,6 +34,7 @@ struct locc_handle {
   int32_t* d_cnt = nullptr;
   float4* d_centre = nullptr;
   float* d_feat = nullptr;
+  int* d_defer = nullptr;  // crop objects left to the exact fallback kernel
   void* d_feat_tc = nullptr;
   size_t feat_tc_bytes = 0;
   int* d_err = nullptr;

@@ -25,7 +25,8 @@ constexpr size_t kXyzBytes = (size_t)kMaxPairs * locc::ROWS * sizeof(float4);
 constexpr size_t kFeatBytes = (size_t)kMaxPairs * 512 * sizeof(float);
 constexpr size_t kCentreBytes = (size_t)kMaxPairs * sizeof(float4);
 constexpr size_t kCntBytes = (size_t)kMaxPairs * 2 * sizeof(int32_t);
-constexpr size_t kScratchBytes = kXyzBytes + kFeatBytes + kCentreBytes + kCntBytes;
+constexpr size_t kDeferBytes = (1 + (size_t)kMaxPairs * 2) * sizeof(int32_t);
+constexpr size_t kScratchBytes = kXyzBytes + kFeatBytes + kCentreBytes + kCntBytes + kDeferBytes;
 
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
@@ -95,11 +96,12 @@ extern "C" int locc_detect_noalloc(locc_handle* h, const float* poses, const int
   float* feat = reinterpret_cast<float*>(base + kXyzBytes);
   float4* centre = reinterpret_cast<float4*>(base + kXyzBytes + kFeatBytes);
   int32_t* cnt = reinterpret_cast<int32_t*>(base + kXyzBytes + kFeatBytes + kCentreBytes);
+  int* defer = reinterpret_cast<int*>(base + kXyzBytes + kFeatBytes + kCentreBytes + kCntBytes);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   PairInputs in{poses, obj_shape, pairs, n_obj, n_pairs};
   const PairRange rg = whole_range(n_pairs, nullptr);
   cudaError_t e = launch_crop(dev_library(h), in, rg, h->radius, xyz, nullptr, cnt, centre,
-                              h->d_err, h->n_sm, 0, s);
+                              h->d_err, defer, h->n_sm, 0, s);
   if (e == cudaSuccess) e = launch_encoder_fp32(xyz, rg, h->fp32, feat, h->n_sm, s);
   if (e == cudaSuccess)
     e = launch_head_fp32(feat, rg, h->fp32, &in, centre, out, nullptr, h->n_sm, s);

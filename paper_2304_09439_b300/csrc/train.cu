@@ -38,6 +38,7 @@ struct locc_trainer {
   float4* xyz = nullptr;  // crops from the gather kernel [P][128]
   int32_t* cnt = nullptr;
   float4* centre = nullptr;
+  int* defer = nullptr;   // crop objects left to the exact fallback kernel
   float* X = nullptr;      // augmented crop rows [M][4]
   float* T = nullptr;      // canonical targets [P][8]
   float* H1 = nullptr;     // [M][64]
@@ -381,7 +382,7 @@ int tfail(int code, const char* msg) {
   } while (0)
 
 void trainer_free(locc_trainer* t) {
-  void* ptrs[] = {t->params, t->grad, t->m, t->v, t->xyz, t->cnt, t->centre, t->X, t->T, t->H1,
+  void* ptrs[] = {t->params, t->grad, t->m, t->v, t->xyz, t->cnt, t->centre, t->defer, t->X, t->T, t->H1,
                   t->H2, t->Z3, t->F, t->amax, t->G1, t->G2, t->Y, t->dY, t->dG1, t->dG2, t->dF,
                   t->dH1, t->dH2, t->loss};
   for (void* p : ptrs) cudaFree(p);
@@ -404,6 +405,7 @@ int locc_trainer_create(locc_handle* h, int32_t max_batch, const locc_train_conf
   bool ok = cudaMalloc(&t->params, NP * 4) == cudaSuccess && cudaMalloc(&t->grad, NP * 4) == cudaSuccess &&
             cudaMalloc(&t->m, NP * 4) == cudaSuccess && cudaMalloc(&t->v, NP * 4) == cudaSuccess &&
             cudaMalloc(&t->xyz, M * 16) == cudaSuccess && cudaMalloc(&t->cnt, P * 8) == cudaSuccess &&
+            cudaMalloc(&t->defer, (1 + 2 * P) * sizeof(int)) == cudaSuccess &&
             cudaMalloc(&t->centre, P * 16) == cudaSuccess && cudaMalloc(&t->X, M * 16) == cudaSuccess &&
             cudaMalloc(&t->T, P * 32) == cudaSuccess && cudaMalloc(&t->H1, M * 64 * 4) == cudaSuccess &&
             cudaMalloc(&t->H2, M * 128 * 4) == cudaSuccess &&
@@ -458,7 +460,7 @@ int locc_train_step(locc_trainer* t, const float* poses, const int32_t* obj_shap
   auto gB = [&](int l) { return g + PARAM_OFF_B[l]; };
   PairInputs in{poses, obj_shape, pairs, n_obj, n_pairs};
   TCU(launch_crop(dev_library(h), in, whole_range(n_pairs, nullptr), h->radius, t->xyz, nullptr,
-                  t->cnt, t->centre, h->d_err, h->n_sm, 0, s));
+                  t->cnt, t->centre, h->d_err, t->defer, h->n_sm, 0, s));
   TCU(cudaMemsetAsync(t->loss, 0, 4, s));
   TCU(cudaMemsetAsync(g, 0, (size_t)LOCC_N_PARAMS * 4, s));
   prep_kernel<<<P, ROWS, 0, s>>>(t->xyz, t->centre, poses, pairs, n_obj, targets, rot, t->X, t->T, P);
