@@ -343,7 +343,10 @@ __device__ __forceinline__ void crop_pair(const DevLibrary& lib, const PairInput
 
   // B's canonical coordinates need R_rel at the very end: park it in shared
   // memory instead of keeping nine registers live through the selection
-  if (warp == 1 && lane < 9) rsh[lane] = f.rrel[lane];
+  if (warp == 1 && lane == 0) {
+#pragma unroll
+    for (int i = 0; i < 9; ++i) rsh[i] = f.rrel[i];
+  }
   const int shape = warp == 0 ? sa : sb;
   const float cx = warp == 0 ? f.c[0] : f.cb[0];
   const float cy = warp == 0 ? f.c[1] : f.cb[1];
@@ -508,7 +511,7 @@ __device__ __forceinline__ void fallback_object(const DevLibrary& lib, const Pai
   __syncwarp();
 }
 
-__global__ void __launch_bounds__(64, 16) crop_kernel(DevLibrary lib, PairInputs in, PairRange rg,
+__global__ void __launch_bounds__(64, 20) crop_kernel(DevLibrary lib, PairInputs in, PairRange rg,
                                                       float r, float4* __restrict__ xyz_out,
                                                       int32_t* __restrict__ idx_out,
                                                       int32_t* __restrict__ cnt_out,
