@@ -35,8 +35,7 @@ struct locc_handle {
   float4* d_centre = nullptr;
   float* d_feat = nullptr;
   int* d_defer = nullptr;  // crop objects left to the exact fallback kernel
-  void* d_feat_tc = nullptr;
-  size_t feat_tc_bytes = 0;
+  void* d_feat_tc = nullptr;  // bf16 pooled features in the head's operand tiles
   int* d_err = nullptr;
   // broadphase per-environment counts / offsets
   int32_t* d_env_counts = nullptr;

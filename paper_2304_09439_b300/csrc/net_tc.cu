@@ -133,10 +133,23 @@ __device__ __forceinline__ void enc_pool(uint32_t taddr, int cntA, int cntB, flo
   *mB = b;
 }
 
+// Pooled feature k of pair p (rel = p - first pair of the launch): float32
+// [P][512] when feat is given (the network's feature output), and always
+// bf16 in the head's operand layout -- tiles of 128 pairs, each 8 K-chunks of
+// 64 features in the K-major core-matrix layout (16 KB per chunk) -- so that
+// the head loads A chunks with bulk copies.
+__device__ __forceinline__ void put_feat(float* feat, __nv_bfloat16* ftile, int p, int rel, int k,
+                                         float v) {
+  if (feat) feat[(size_t)p * 512 + k] = v;
+  unsigned char* t = reinterpret_cast<unsigned char*>(ftile) + (size_t)(rel >> 7) * (128 * 512 * 2) +
+                     (size_t)(k >> 6) * (128 * 64 * 2);
+  *reinterpret_cast<__nv_bfloat16*>(t + kmajor_off(rel & 127, k & 63, 64)) = __float2bfloat16_rn(v);
+}
+
 __global__ void __launch_bounds__(E_THREADS, 1)
     encoder_tc_kernel(const float4* __restrict__ xyz, PairRange rg,
                       const unsigned char* __restrict__ img, float* __restrict__ feat,
-                      int* __restrict__ err) {
+                      __nv_bfloat16* __restrict__ ftile, int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char smem[];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   int lo, hi;
@@ -322,16 +335,16 @@ __global__ void __launch_bounds__(E_THREADS, 1)
       mbar_arrive(BAR(B_E3A + s));
       {
         const float bias = b3[row];
-        feat[(size_t)p * 512 + row] = cntA > 0 ? fmaxf(mA + bias, 0.f) : 0.f;
-        feat[(size_t)p * 512 + 256 + row] = cntB > 0 ? fmaxf(mB + bias, 0.f) : 0.f;
+        put_feat(feat, ftile, p, p - lo, row, cntA > 0 ? fmaxf(mA + bias, 0.f) : 0.f);
+        put_feat(feat, ftile, p, p - lo, 256 + row, cntB > 0 ? fmaxf(mB + bias, 0.f) : 0.f);
       }
       if (!(ok = mbar_wait_or_abort(BAR(B_D3B + s), ph, abort, WAIT_CYCLES))) break;
       tc_fence_after();
       enc_pool(tslot, cntA, cntB, &mA, &mB);
       {
         const float bias = b3[128 + row];
-        feat[(size_t)p * 512 + 128 + row] = cntA > 0 ? fmaxf(mA + bias, 0.f) : 0.f;
-        feat[(size_t)p * 512 + 384 + row] = cntB > 0 ? fmaxf(mB + bias, 0.f) : 0.f;
+        put_feat(feat, ftile, p, p - lo, 128 + row, cntA > 0 ? fmaxf(mA + bias, 0.f) : 0.f);
+        put_feat(feat, ftile, p, p - lo, 384 + row, cntB > 0 ? fmaxf(mB + bias, 0.f) : 0.f);
       }
       tc_fence_before();
     }
@@ -350,17 +363,20 @@ constexpr int H_W3 = 0;                                    // [16 x 256] 8 KB
 constexpr int H_BIAS = H_W3 + 16 * 256 * 2;                // hb1 256, hb2 256, hb3 16
 constexpr int H_RES_BYTES = H_BIAS + (256 + 256 + 16) * 4; // resident part of the image
 constexpr int H_CHUNK = 256 * 64 * 2;                      // bytes of one B chunk
+constexpr int H_ACHUNK = 128 * 64 * 2;                     // bytes of one A (feature) chunk
+constexpr int H_NST = 3;                                   // operand stages
 constexpr int H_A0 = (H_RES_BYTES + 1023) / 1024 * 1024;   // A stages [128 x 64] 16 KB each
-constexpr int H_B0 = H_A0 + 2 * 128 * 64 * 2;              // B stages [256 x 64] 32 KB each
-constexpr int H_G = H_B0 + 2 * H_CHUNK;                    // G [128 x 256] 64 KB
-constexpr int H_CTRL = H_G + 128 * 256 * 2;                // 7 mbarriers, TMEM address, abort
-constexpr int H_SMEM = H_CTRL + 80;
+constexpr int H_B0 = H_A0 + H_NST * H_ACHUNK;              // B stages [256 x 64] 32 KB each
+constexpr int H_G = H_B0 + H_NST * H_CHUNK;                // G [128 x 256] 64 KB
+constexpr int H_CTRL = H_G + 128 * 256 * 2;                // mbarriers, TMEM address, abort
+constexpr int H_SMEM = H_CTRL + 128;
 // global image: [resident][W_h1 chunks x 8][W_h2 chunks x 4]
 constexpr int H_IMG_W1 = (H_RES_BYTES + 127) / 128 * 128;
 constexpr int H_IMG_W2 = H_IMG_W1 + 8 * H_CHUNK;
 constexpr int H_IMG_BYTES = H_IMG_W2 + 4 * H_CHUNK;
 static_assert(H_RES_BYTES % 16 == 0, "resident image must be 16-byte chunks");
 static_assert(H_IMG_W1 % 16 == 0 && H_CHUNK % 16 == 0, "bulk copies need 16-byte chunks");
+static_assert(H_SMEM <= 227 * 1024, "head shared memory");
 
 // Epilogue of a 256-wide layer: TMEM row tid, columns [col0, col0 + 256) ->
 // relu(x + b) as bf16 into G (K = 256).
@@ -382,14 +398,19 @@ __device__ __forceinline__ void head_epi_256(uint32_t taddr, const float* b, uns
   }
 }
 
-// Head over tiles of HT = 128 pairs (one pair per thread / TMEM lane).
-// Layers 1 and 2 run as 12 K-chunks of 64 (8 of W_h1 against the features, 4
-// of W_h2 against G) through two operand stages: while the MMAs of chunk c
-// run, chunk c + 1's weights arrive by bulk copy (thread 0) and its features
-// are converted to bf16 (all threads).  A stage is refilled once the MMAs that
-// read it have completed (tcgen05.commit on the stage's mbarrier).
-__global__ void __launch_bounds__(128, 1)
-    head_tc_kernel(const float* __restrict__ feat, PairRange rg,
+// Head over tiles of HT = 128 pairs (one pair per epilogue thread / TMEM
+// lane; warps 0-3), plus a producer warp (warp 4, one elected lane).
+// Layers 1 and 2 are 12 K-chunks of 64 per tile (8 of W_h1 against the bf16
+// features the encoder wrote in operand layout, 4 of W_h2 against G); every
+// operand chunk arrives by bulk copy.  The producer runs the chunk stream
+// across tiles through H_NST stages: the copies of chunk g + 2 are issued as
+// soon as the MMAs of chunk g - 1 have freed their stage, so two chunks are in
+// flight while one multiplies.  The epilogue warps signal an mbarrier (EPI)
+// when G holds layer 1, when it holds layer 2, and when the tile's outputs
+// have been read out of TMEM.
+constexpr int H_THREADS = 160;
+__global__ void __launch_bounds__(H_THREADS, 1)
+    head_tc_kernel(const __nv_bfloat16* __restrict__ ftile, PairRange rg,
                    const unsigned char* __restrict__ img, PairInputs in, int have_in,
                    const float4* __restrict__ centre, float* __restrict__ out,
                    float* __restrict__ y_raw, int* __restrict__ err) {
@@ -399,14 +420,22 @@ __global__ void __launch_bounds__(128, 1)
   range_bounds(rg, &lo, &n);  // this launch's pairs: [lo, n)
   const int n_tiles = (n - lo + HT - 1) / HT;
   if ((int)blockIdx.x >= n_tiles) return;
-  // mbarriers: 0, 1 weights of stage s landed; 2, 3 MMAs of stage s done;
-  // 4 layer 3 done; 5 resident image landed; 6 drain
+  const int my_tiles = (n_tiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
+  // mbarriers: [0, 3) operands of stage s landed; [3, 6) MMAs of stage s done;
+  // 6 layer 3 done; 7 epilogue progress (3 per tile); 8 resident image;
+  // 9 drain; 10 / 11 layer 1 / layer 2 of the tile done (one commit per tile
+  // each: a waiter is never more than one phase behind)
   const uint32_t bar0 = smem_u32(smem + H_CTRL);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + H_CTRL + 56);
-  volatile int* abort = reinterpret_cast<volatile int*>(smem + H_CTRL + 60);
-  const uint32_t B_L3 = bar0 + 32, B_RES = bar0 + 40, B_DRAIN = bar0 + 48;
+  const uint32_t B_L3 = bar0 + 48, B_EPI = bar0 + 56, B_RES = bar0 + 64, B_DRAIN = bar0 + 72;
+  const uint32_t B_L1D = bar0 + 80, B_L2D = bar0 + 88;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + H_CTRL + 96);
+  volatile int* abort = reinterpret_cast<volatile int*>(smem + H_CTRL + 100);
   if (tid == 0) {
-    for (int i = 0; i < 7; ++i) mbar_init(bar0 + 8 * i, 1);
+    for (int i = 0; i < 8; ++i) mbar_init(bar0 + 8 * i, i == 7 ? 128 : 1);
+    mbar_init(B_RES, 1);
+    mbar_init(B_DRAIN, 1);
+    mbar_init(B_L1D, 1);
+    mbar_init(B_L2D, 1);
     *abort = 0;
     fence_mbar_init();
   }
@@ -418,119 +447,111 @@ __global__ void __launch_bounds__(128, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tbase = *tmem_slot;
-  if (tid == 0) {
-    mbar_expect_tx(B_RES, H_RES_BYTES);
-    bulk_g2s(smem_u32(smem), img, H_RES_BYTES, B_RES);
-  }
   const uint32_t lane_off = (uint32_t)(32 * warp) << 16;
   const float* hb1 = reinterpret_cast<const float*>(smem + H_BIAS);
   const float* hb2 = hb1 + 256;
   const float* hb3 = hb2 + 256;
   unsigned char* G = smem + H_G;
   const uint32_t sG = smem_u32(G), sW3 = smem_u32(smem + H_W3);
-  int nb[2] = {0, 0}, nm[2] = {0, 0}, n3 = 0;  // bulk loads / MMA commits per stage
-  bool ok = mbar_wait_or_abort(B_RES, 0, abort, WAIT_CYCLES);
+  const int n_chunks = 12 * my_tiles;  // this CTA's chunk stream
+  bool ok = true;
+  int g_issued = 0;  // chunks whose copies the producer has issued
 
-  for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
-    const int q0 = lo + tile * HT;
-    const int pr = q0 + tid;  // this thread's pair (row)
-    const bool row_ok = pr < n;
-#pragma unroll 1
-    for (int c = 0; c < 12; ++c) {
-      const int st = c & 1;
-      unsigned char* A = smem + H_A0 + st * (128 * 64 * 2);
-      const uint32_t sA = smem_u32(A), sB = smem_u32(smem + H_B0 + st * H_CHUNK);
-      // the MMAs that last read this stage have completed
-      if (nm[st] > 0) ok = mbar_wait_or_abort(bar0 + 16 + 8 * st, (nm[st] - 1) & 1, abort, WAIT_CYCLES);
-      if (!__syncthreads_and(ok)) {
-        ok = false;
-        break;
-      }
-      if (tid == 0) {
-        const unsigned char* w = img + (c < 8 ? H_IMG_W1 + (size_t)c * H_CHUNK
-                                              : H_IMG_W2 + (size_t)(c - 8) * H_CHUNK);
-        mbar_expect_tx(bar0 + 8 * st, H_CHUNK);
-        bulk_g2s(sB, w, H_CHUNK, bar0 + 8 * st);
-      }
-      ++nb[st];
+  if (tid == 128) {
+    mbar_expect_tx(B_RES, H_RES_BYTES);
+    bulk_g2s(smem_u32(smem), img, H_RES_BYTES, B_RES);
+    // copies of global chunk g into stage g % H_NST
+    auto issue = [&](int g) {
+      const int st = g % H_NST, c = g % 12;
+      const int tile = (int)blockIdx.x + (g / 12) * (int)gridDim.x;
+      const uint32_t bw = bar0 + 8 * st;
       if (c < 8) {
-        // features [pr][64c, 64c + 64) -> bf16 A operand row tid
-        const float* src = feat + (size_t)pr * 512 + 64 * c;
+        mbar_expect_tx(bw, H_ACHUNK + H_CHUNK);
+        bulk_g2s(smem_u32(smem + H_A0 + st * H_ACHUNK),
+                 reinterpret_cast<const unsigned char*>(ftile) + (size_t)tile * (128 * 512 * 2) +
+                     (size_t)c * H_ACHUNK,
+                 H_ACHUNK, bw);
+        bulk_g2s(smem_u32(smem + H_B0 + st * H_CHUNK), img + H_IMG_W1 + (size_t)c * H_CHUNK,
+                 H_CHUNK, bw);
+      } else {
+        mbar_expect_tx(bw, H_CHUNK);
+        bulk_g2s(smem_u32(smem + H_B0 + st * H_CHUNK), img + H_IMG_W2 + (size_t)(c - 8) * H_CHUNK,
+                 H_CHUNK, bw);
+      }
+      g_issued = g + 1;
+    };
+    for (int g = 0; g < 2 && g < n_chunks; ++g) issue(g);
+    ok = mbar_wait_or_abort(B_RES, 0, abort, WAIT_CYCLES);
+    for (int g = 0; g < n_chunks && ok; ++g) {
+      const int st = g % H_NST, c = g % 12, t = g / 12;
+      // the stage of chunk g + 2 was last read by the MMAs of chunk g - 1
+      if (g + 2 < n_chunks) {
+        if (g >= 1)
+          ok = mbar_wait_or_abort(bar0 + 24 + 8 * ((g - 1) % H_NST), ((g - 1) / H_NST) & 1, abort,
+                                  WAIT_CYCLES);
+        if (!ok) break;
+        issue(g + 2);
+      }
+      // chunk 0 of a tile: the previous tile's outputs have left TMEM;
+      // chunk 8: G holds layer 1
+      if (c == 0 && t > 0) ok = mbar_wait_or_abort(B_EPI, (3 * t - 1) & 1, abort, WAIT_CYCLES);
+      if (c == 8) ok = ok && mbar_wait_or_abort(B_EPI, (3 * t) & 1, abort, WAIT_CYCLES);
+      ok = ok && mbar_wait_or_abort(bar0 + 8 * st, (g / H_NST) & 1, abort, WAIT_CYCLES);
+      if (!ok) break;
+      tc_fence_after();
+      const uint32_t sA = smem_u32(smem + H_A0 + st * H_ACHUNK);
+      const uint32_t sB = smem_u32(smem + H_B0 + st * H_CHUNK);
+      if (c < 8) {
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-          float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f), a1 = a0;
-          if (row_ok) {
-            a0 = __ldg(reinterpret_cast<const float4*>(src + 8 * k));
-            a1 = __ldg(reinterpret_cast<const float4*>(src + 8 * k + 4));
-          }
-          uint4 w;
-          w.x = pack_bf16(a0.x, a0.y);
-          w.y = pack_bf16(a0.z, a0.w);
-          w.z = pack_bf16(a1.x, a1.y);
-          w.w = pack_bf16(a1.z, a1.w);
-          *reinterpret_cast<uint4*>(A + kmajor_off(tid, 8 * k, 64)) = w;
-        }
-      } else if (c == 8) {
-        // layer-1 accumulators are final once the MMAs of chunk 7 (stage 1)
-        // have completed (tcgen05 operations complete in order)
-        ok = mbar_wait_or_abort(bar0 + 24, (nm[1] - 1) & 1, abort, WAIT_CYCLES);
-        if (!__syncthreads_and(ok)) {
-          ok = false;
-          break;
-        }
+        for (int kk = 0; kk < 4; ++kk)
+          mma_bf16(tbase + 0, sdesc(sA + 256 * kk, 128, 1024), sdesc(sB + 256 * kk, 128, 1024),
+                   idesc_bf16(128, 256), (c > 0 || kk > 0) ? 1u : 0u);
+      } else {
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk)
+          mma_bf16(tbase + 256, sdesc(sG + 1024 * (c - 8) + 256 * kk, 128, 4096),
+                   sdesc(sB + 256 * kk, 128, 1024), idesc_bf16(128, 256),
+                   (c > 8 || kk > 0) ? 1u : 0u);
+      }
+      mma_commit(bar0 + 24 + 8 * st);
+      if (c == 7) mma_commit(B_L1D);
+      if (c == 11) mma_commit(B_L2D);
+      if (c == 11) {
+        // layer 3 once G holds layer 2: D3[128 x 16] = G . Wh3img^T (rows 8..15 zero)
+        ok = mbar_wait_or_abort(B_EPI, (3 * t + 1) & 1, abort, WAIT_CYCLES);
+        if (!ok) break;
         tc_fence_after();
-        head_epi_256(tbase + lane_off + 0, hb1, G, tid);
-      }
-      fence_async_smem();
-      tc_fence_before();
-      __syncthreads();
-      if (tid == 0 && !*abort) {
-        if (mbar_wait_or_abort(bar0 + 8 * st, (nb[st] - 1) & 1, abort, WAIT_CYCLES)) {
-          tc_fence_after();
-          if (c < 8) {
 #pragma unroll
-            for (int kk = 0; kk < 4; ++kk)
-              mma_bf16(tbase + 0, sdesc(sA + 256 * kk, 128, 1024), sdesc(sB + 256 * kk, 128, 1024),
-                       idesc_bf16(128, 256), (c > 0 || kk > 0) ? 1u : 0u);
-          } else {
-#pragma unroll
-            for (int kk = 0; kk < 4; ++kk)
-              mma_bf16(tbase + 256, sdesc(sG + 1024 * (c - 8) + 256 * kk, 128, 4096),
-                       sdesc(sB + 256 * kk, 128, 1024), idesc_bf16(128, 256),
-                       (c > 8 || kk > 0) ? 1u : 0u);
-          }
-          mma_commit(bar0 + 16 + 8 * st);
-        }
+        for (int kk = 0; kk < 16; ++kk)
+          mma_bf16(tbase + 0, sdesc(sG + 256 * kk, 128, 4096), sdesc(sW3 + 256 * kk, 128, 4096),
+                   idesc_bf16(128, 16), kk > 0);
+        mma_commit(B_L3);
       }
-      ++nm[st];
     }
+    if (!ok) *abort = 1;
+  }
+  // epilogue warps
+  if (tid < 128) ok = mbar_wait_or_abort(B_RES, 0, abort, WAIT_CYCLES);
+  for (int t = 0; tid < 128 && t < my_tiles && ok; ++t) {
+    const int pr = lo + ((int)blockIdx.x + t * (int)gridDim.x) * HT + tid;
+    const bool row_ok = pr < n;
+    // layer 1 final with the MMAs of chunk 12 t + 7, layer 2 with 12 t + 11
+    ok = mbar_wait_or_abort(B_L1D, t & 1, abort, WAIT_CYCLES);
     if (!ok) break;
-    // layer-2 accumulators are final with the MMAs of chunk 11 (stage 1)
-    ok = mbar_wait_or_abort(bar0 + 24, (nm[1] - 1) & 1, abort, WAIT_CYCLES);
-    if (!__syncthreads_and(ok)) {
-      ok = false;
-      break;
-    }
+    tc_fence_after();
+    head_epi_256(tbase + lane_off + 0, hb1, G, tid);
+    fence_async_smem();
+    tc_fence_before();
+    mbar_arrive(B_EPI);
+    ok = mbar_wait_or_abort(B_L2D, t & 1, abort, WAIT_CYCLES);
+    if (!ok) break;
     tc_fence_after();
     head_epi_256(tbase + lane_off + 256, hb2, G, tid);
     fence_async_smem();
     tc_fence_before();
-    __syncthreads();
-    // ---- layer 3: D3[128 x 16] = G[128 x 256] . Wh3img^T (rows 8..15 zero)
-    if (tid == 0) {
-      tc_fence_after();
-#pragma unroll
-      for (int kk = 0; kk < 16; ++kk)
-        mma_bf16(tbase + 0, sdesc(sG + 256 * kk, 128, 4096), sdesc(sW3 + 256 * kk, 128, 4096),
-                 idesc_bf16(128, 16), kk > 0);
-      mma_commit(B_L3);
-    }
-    ok = mbar_wait_or_abort(B_L3, n3 & 1, abort, WAIT_CYCLES);
-    ++n3;
-    if (!__syncthreads_and(ok)) {
-      ok = false;
-      break;
-    }
+    mbar_arrive(B_EPI);
+    ok = mbar_wait_or_abort(B_L3, t & 1, abort, WAIT_CYCLES);
+    if (!ok) break;
     tc_fence_after();
     {
       float v[16];
@@ -559,15 +580,16 @@ __global__ void __launch_bounds__(128, 1)
       }
     }
     tc_fence_before();
-    __syncthreads();
+    mbar_arrive(B_EPI);
   }
-  if (tid == 0 && (!ok || *abort)) {
-    // drain: wait (bounded) for this thread's MMAs and bulk copies
+  __syncthreads();
+  if (tid == 128 && *abort) {
+    // drain: wait (bounded) for the producer's MMAs and bulk copies
     atomicOr(err, 2);
     mma_commit(B_DRAIN);
     mbar_wait(B_DRAIN, 0, WAIT_CYCLES);
-    for (int st = 0; st < 2; ++st)
-      if (nb[st] > 0) mbar_wait(bar0 + 8 * st, (nb[st] - 1) & 1, WAIT_CYCLES);
+    for (int g = g_issued - H_NST; g < g_issued; ++g)
+      if (g >= 0) mbar_wait(bar0 + 8 * (g % H_NST), (g / H_NST) & 1, WAIT_CYCLES);
   }
   tc_fence_before();
   __syncthreads();
@@ -671,9 +693,10 @@ int run_network_tc(locc_handle* h, const float4* xyz, const PairRange& rg, const
     }
     attr = true;
   }
-  float* feat = feat_out ? feat_out : h->d_feat;
+  __nv_bfloat16* ftile = static_cast<__nv_bfloat16*>(h->d_feat_tc);
   const int grid_e = std::min(n_pairs, h->n_sm);
-  encoder_tc_kernel<<<grid_e, E_THREADS, E_SMEM, stream>>>(xyz, rg, h->wtc_enc, feat, h->d_err);
+  encoder_tc_kernel<<<grid_e, E_THREADS, E_SMEM, stream>>>(xyz, rg, h->wtc_enc, feat_out, ftile,
+                                                           h->d_err);
   if (cudaGetLastError() != cudaSuccess) {
     set_error("encoder_tc_kernel launch failed");
     return LOCC_ERR_CUDA;
@@ -682,8 +705,8 @@ int run_network_tc(locc_handle* h, const float4* xyz, const PairRange& rg, const
   PairInputs pin{};
   if (in) pin = *in;
   const int grid_h = std::min((n_pairs + HT - 1) / HT, h->n_sm);
-  head_tc_kernel<<<grid_h, 128, H_SMEM, stream>>>(feat, rg, h->wtc_head, pin, in != nullptr,
-                                                  centre, out, y_raw, h->d_err);
+  head_tc_kernel<<<grid_h, H_THREADS, H_SMEM, stream>>>(ftile, rg, h->wtc_head, pin, in != nullptr,
+                                                        centre, out, y_raw, h->d_err);
   if (cudaGetLastError() != cudaSuccess) {
     set_error("head_tc_kernel launch failed");
     return LOCC_ERR_CUDA;

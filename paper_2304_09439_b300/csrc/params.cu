@@ -92,9 +92,8 @@ int upload_params(locc_handle* h, const std::vector<float>& params) {
 void free_params(locc_handle* h) {
   cudaFree(h->d_w32);
   cudaFree(h->d_wtc);
-  cudaFree(h->d_feat_tc);
   cudaFree(h->d_wf8);
-  h->d_w32 = nullptr, h->d_wtc = nullptr, h->d_feat_tc = nullptr, h->d_wf8 = nullptr;
+  h->d_w32 = nullptr, h->d_wtc = nullptr, h->d_wf8 = nullptr;
 }
 
 }  // namespace locc
