@@ -51,8 +51,7 @@ WORKLOAD = "uneven_scenes_8192env_poisson8_64shapes"
 # DRAM bytes (read + write) per pair of the encoder kernel from one ncu capture
 # of the bench's scene 1 (154,924 pairs; profiles/kernels_bf16_fp8_uneven8192.md):
 # scaled by the pairs of a launch to give the per-launch traffic.
-ENC_DRAM_BYTES_PER_PAIR = {"bf16": (317.465344e6 + 275.488768e6) / 154924,
-                           "fp8": (317.382144e6 + 274.932480e6) / 154924}
+ENC_DRAM_BYTES_PER_PAIR = {}  # re-captured after the feature layout change
 WEIGHTS = os.path.join(ROOT, "paper_2304_09439_b300", "weights", "locc_trained.bin")
 
 

@@ -54,8 +54,8 @@ __global__ void quant_e4m3_kernel(const float* __restrict__ W, const float* __re
 constexpr int F_W1 = 0;                        // [64 x 16] bf16 (hi/lo)   2 KB
 constexpr int F_W2 = F_W1 + 64 * 16 * 2;       // [128 x 64] e4m3          8 KB
 constexpr int F_W3 = F_W2 + 128 * 64;          // [256 x 128] e4m3        32 KB
-constexpr int F_EP = F_W3 + 256 * 128;         // a1 c1 [64], a2 c2 [128], w3 b3 [256] (f32)
-constexpr int F_IMG_BYTES = F_EP + (2 * 64 + 2 * 128 + 2 * 256) * 4;
+constexpr int F_EP = F_W3 + 256 * 128;         // a1 c1 [64], a2 c2 [128], w3 b3 finv [256] (f32)
+constexpr int F_IMG_BYTES = F_EP + (2 * 64 + 2 * 128 + 3 * 256) * 4;
 static_assert(F_IMG_BYTES % 16 == 0, "encoder fp8 image must be 16-byte chunks");
 // NSLOT pair slots; each: raw crop rows (2 KB) and a 16 KB operand region
 // holding in turn X (bf16, 4 KB), H1 (e4m3, 8 KB) and H2 (e4m3, 16 KB).
@@ -122,10 +122,21 @@ __device__ __forceinline__ void pool8(uint32_t taddr, int cntA, int cntB, float*
   *mB = b;
 }
 
+// Pooled feature k of pair p (rel = p - first pair of the launch): float32
+// [P][512] when feat is given, and always e4m3 of v / s_k (the head's input
+// scale) in the head's operand layout -- tiles of 128 pairs, each 4 K-chunks
+// of 128 features, K-major (16 KB per chunk) -- for bulk copies into the head.
+__device__ __forceinline__ void put_feat8(float* feat, unsigned char* ftile, int p, int rel, int k,
+                                          float v, float inv_s) {
+  if (feat) feat[(size_t)p * 512 + k] = v;
+  unsigned char* t = ftile + (size_t)(rel >> 7) * (128 * 512) + (size_t)(k >> 7) * (128 * 128);
+  t[kmajor_off8(rel & 127, k & 127, 128)] = (unsigned char)(pack_e4m3x4(v * inv_s, 0.f, 0.f, 0.f) & 0xffu);
+}
+
 __global__ void __launch_bounds__(F_THREADS, 1)
     encoder_fp8_kernel(const float4* __restrict__ xyz, PairRange rg,
                        const unsigned char* __restrict__ img, float* __restrict__ feat,
-                       int* __restrict__ err) {
+                       unsigned char* __restrict__ ftile, int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char smem[];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   int lo, hi;
@@ -172,6 +183,7 @@ __global__ void __launch_bounds__(F_THREADS, 1)
   const float* c2 = a2 + 128;
   const float* w3 = c2 + 128;
   const float* b3 = w3 + 256;
+  const float* fin = b3 + 256;
 
   if (warp == MMA_WARP) {
     if (lane == 0) {
@@ -315,17 +327,20 @@ __global__ void __launch_bounds__(F_THREADS, 1)
       tc_fence_before();
       mbar_arrive(BAR(B_E3A + s));
       {
-        const float sc = w3[row], bias = b3[row];
-        feat[(size_t)p * 512 + row] = cntA > 0 ? fmaxf(fmaf(mA, sc, bias), 0.f) : 0.f;
-        feat[(size_t)p * 512 + 256 + row] = cntB > 0 ? fmaxf(fmaf(mB, sc, bias), 0.f) : 0.f;
+        const float sc = w3[row], bias = b3[row], fi = fin[row];
+        put_feat8(feat, ftile, p, p - lo, row, cntA > 0 ? fmaxf(fmaf(mA, sc, bias), 0.f) : 0.f, fi);
+        put_feat8(feat, ftile, p, p - lo, 256 + row, cntB > 0 ? fmaxf(fmaf(mB, sc, bias), 0.f) : 0.f,
+                  fi);
       }
       if (!(ok = mbar_wait_or_abort(BAR(B_D3B + s), ph, abort, WAIT_CYCLES))) break;
       tc_fence_after();
       pool8(tslot, cntA, cntB, &mA, &mB);
       {
-        const float sc = w3[128 + row], bias = b3[128 + row];
-        feat[(size_t)p * 512 + 128 + row] = cntA > 0 ? fmaxf(fmaf(mA, sc, bias), 0.f) : 0.f;
-        feat[(size_t)p * 512 + 384 + row] = cntB > 0 ? fmaxf(fmaf(mB, sc, bias), 0.f) : 0.f;
+        const float sc = w3[128 + row], bias = b3[128 + row], fi = fin[128 + row];
+        put_feat8(feat, ftile, p, p - lo, 128 + row, cntA > 0 ? fmaxf(fmaf(mA, sc, bias), 0.f) : 0.f,
+                  fi);
+        put_feat8(feat, ftile, p, p - lo, 384 + row, cntB > 0 ? fmaxf(fmaf(mB, sc, bias), 0.f) : 0.f,
+                  fi);
       }
       tc_fence_before();
     }
@@ -348,12 +363,16 @@ constexpr int G_CHUNK = 256 * 128;       // one B chunk [256 x 128] e4m3, 32 KB
 constexpr int G_IMG_W1 = G_RES_BYTES;    // 4 chunks
 constexpr int G_IMG_W2 = G_IMG_W1 + 4 * G_CHUNK;  // 2 chunks
 constexpr int G_IMG_BYTES = G_IMG_W2 + 2 * G_CHUNK;
+constexpr int G_ACHUNK = 128 * 128;                       // one A (feature) chunk, e4m3
+constexpr int G_NST = 3;                                   // operand stages
 constexpr int G_A0 = (G_RES_BYTES + 1023) / 1024 * 1024;  // A stages [128 x 128] e4m3, 16 KB each
-constexpr int G_B0 = G_A0 + 2 * 128 * 128;                 // B stages, 32 KB each
-constexpr int G_G = G_B0 + 2 * G_CHUNK;                    // G [128 x 256] e4m3, 32 KB
-constexpr int G_CTRL = G_G + 128 * 256;                    // 7 mbarriers, TMEM address, abort
-constexpr int G_SMEM = G_CTRL + 80;
+constexpr int G_B0 = G_A0 + G_NST * G_ACHUNK;              // B stages, 32 KB each
+constexpr int G_G = G_B0 + G_NST * G_CHUNK;                // G [128 x 256] e4m3, 32 KB
+constexpr int G_CTRL = G_G + 128 * 256;                    // mbarriers, TMEM address, abort
+constexpr int G_SMEM = G_CTRL + 128;
+constexpr int G_THREADS = 160;
 static_assert(G_RES_BYTES % 16 == 0 && G_IMG_W1 % 16 == 0, "bulk copies need 16-byte chunks");
+static_assert(G_SMEM <= 227 * 1024, "fp8 head shared memory");
 
 __device__ __forceinline__ void head_epi_fp8(uint32_t taddr, const float* alpha, const float* beta,
                                              unsigned char* G, int row) {
@@ -365,11 +384,12 @@ __device__ __forceinline__ void head_epi_fp8(uint32_t taddr, const float* alpha,
   }
 }
 
-// Same pipeline as the BF16 head (two operand stages, weights by bulk copy,
-// features of chunk c + 1 quantised while chunk c's MMAs run) over 6 K-chunks
-// of 128: 4 of W_h1 against the features, 2 of W_h2 against G.
-__global__ void __launch_bounds__(128, 1)
-    head_fp8_kernel(const float* __restrict__ feat, PairRange rg,
+// Same stream as the BF16 head (producer warp 4 feeding three operand stages
+// by bulk copy across tiles; epilogue warps 0-3) over 6 K-chunks of 128 per
+// tile: 4 of W_h1 against the e4m3 features the encoder wrote in operand
+// layout, 2 of W_h2 against G.
+__global__ void __launch_bounds__(G_THREADS, 1)
+    head_fp8_kernel(const unsigned char* __restrict__ ftile, PairRange rg,
                     const unsigned char* __restrict__ img, PairInputs in, int have_in,
                     const float4* __restrict__ centre, float* __restrict__ out,
                     float* __restrict__ y_raw, int* __restrict__ err) {
@@ -379,14 +399,21 @@ __global__ void __launch_bounds__(128, 1)
   range_bounds(rg, &lo, &n);  // this launch's pairs: [lo, n)
   const int n_tiles = (n - lo + HT - 1) / HT;
   if ((int)blockIdx.x >= n_tiles) return;
-  // mbarriers: 0, 1 weights of stage s landed; 2, 3 MMAs of stage s done;
-  // 4 layer 3 done; 5 resident image landed; 6 drain
+  const int my_tiles = (n_tiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
+  // mbarriers: [0, 3) operands of stage s landed; [3, 6) MMAs of stage s done;
+  // 6 layer 3 done; 7 epilogue progress (3 per tile); 8 resident image;
+  // 9 drain; 10 / 11 layer 1 / layer 2 of the tile done
   const uint32_t bar0 = smem_u32(smem + G_CTRL);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + G_CTRL + 56);
-  volatile int* abort = reinterpret_cast<volatile int*>(smem + G_CTRL + 60);
-  const uint32_t B_L3 = bar0 + 32, B_RES = bar0 + 40, B_DRAIN = bar0 + 48;
+  const uint32_t B_L3 = bar0 + 48, B_EPI = bar0 + 56, B_RES = bar0 + 64, B_DRAIN = bar0 + 72;
+  const uint32_t B_L1D = bar0 + 80, B_L2D = bar0 + 88;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + G_CTRL + 96);
+  volatile int* abort = reinterpret_cast<volatile int*>(smem + G_CTRL + 100);
   if (tid == 0) {
-    for (int i = 0; i < 7; ++i) mbar_init(bar0 + 8 * i, 1);
+    for (int i = 0; i < 8; ++i) mbar_init(bar0 + 8 * i, i == 7 ? 128 : 1);
+    mbar_init(B_RES, 1);
+    mbar_init(B_DRAIN, 1);
+    mbar_init(B_L1D, 1);
+    mbar_init(B_L2D, 1);
     *abort = 0;
     fence_mbar_init();
   }
@@ -398,10 +425,6 @@ __global__ void __launch_bounds__(128, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tbase = *tmem_slot;
-  if (tid == 0) {
-    mbar_expect_tx(B_RES, G_RES_BYTES);
-    bulk_g2s(smem_u32(smem), img, G_RES_BYTES, B_RES);
-  }
   const uint32_t lane_off = (uint32_t)(32 * warp) << 16;
   const float* finv = reinterpret_cast<const float*>(smem + G_EP);
   const float* a4 = finv + 256;
@@ -413,116 +436,96 @@ __global__ void __launch_bounds__(128, 1)
   unsigned char* G = smem + G_G;
   const uint32_t sG = smem_u32(G), sW3 = smem_u32(smem + G_W3);
   const uint32_t id256 = idesc_e4m3(128, 256), id16 = idesc_e4m3(128, 16);
-  int nb[2] = {0, 0}, nm[2] = {0, 0}, n3 = 0;  // bulk loads / MMA commits per stage
-  bool ok = mbar_wait_or_abort(B_RES, 0, abort, WAIT_CYCLES);
+  const int n_chunks = 6 * my_tiles;  // this CTA's chunk stream
+  bool ok = true;
+  int g_issued = 0;
 
-  for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
-    const int pr = lo + tile * HT + tid;
-    const bool row_ok = pr < n;
-    const float* src = feat + (size_t)pr * 512;
-#pragma unroll 1
-    for (int c = 0; c < 6; ++c) {
-      const int st = c & 1;
-      unsigned char* A = smem + G_A0 + st * (128 * 128);
-      const uint32_t sA = smem_u32(A), sB = smem_u32(smem + G_B0 + st * G_CHUNK);
-      // the MMAs that last read this stage have completed
-      if (nm[st] > 0) ok = mbar_wait_or_abort(bar0 + 16 + 8 * st, (nm[st] - 1) & 1, abort, WAIT_CYCLES);
-      if (!__syncthreads_and(ok)) {
-        ok = false;
-        break;
-      }
-      if (tid == 0) {
-        const unsigned char* w = img + (c < 4 ? G_IMG_W1 + (size_t)c * G_CHUNK
-                                              : G_IMG_W2 + (size_t)(c - 4) * G_CHUNK);
-        mbar_expect_tx(bar0 + 8 * st, G_CHUNK);
-        bulk_g2s(sB, w, G_CHUNK, bar0 + 8 * st);
-      }
-      ++nb[st];
+  if (tid == 128) {
+    mbar_expect_tx(B_RES, G_RES_BYTES);
+    bulk_g2s(smem_u32(smem), img, G_RES_BYTES, B_RES);
+    auto issue = [&](int g) {
+      const int st = g % G_NST, c = g % 6;
+      const int tile = (int)blockIdx.x + (g / 6) * (int)gridDim.x;
+      const uint32_t bw = bar0 + 8 * st;
       if (c < 4) {
-        // features [pr][128c, 128c + 128) scaled by 1 / s_k -> e4m3 A row tid
-        const float* fi = finv + (128 * c) % 256;
+        mbar_expect_tx(bw, G_ACHUNK + G_CHUNK);
+        bulk_g2s(smem_u32(smem + G_A0 + st * G_ACHUNK),
+                 ftile + (size_t)tile * (128 * 512) + (size_t)c * G_ACHUNK, G_ACHUNK, bw);
+        bulk_g2s(smem_u32(smem + G_B0 + st * G_CHUNK), img + G_IMG_W1 + (size_t)c * G_CHUNK,
+                 G_CHUNK, bw);
+      } else {
+        mbar_expect_tx(bw, G_CHUNK);
+        bulk_g2s(smem_u32(smem + G_B0 + st * G_CHUNK), img + G_IMG_W2 + (size_t)(c - 4) * G_CHUNK,
+                 G_CHUNK, bw);
+      }
+      g_issued = g + 1;
+    };
+    for (int g = 0; g < 2 && g < n_chunks; ++g) issue(g);
+    ok = mbar_wait_or_abort(B_RES, 0, abort, WAIT_CYCLES);
+    for (int g = 0; g < n_chunks && ok; ++g) {
+      const int st = g % G_NST, c = g % 6, t = g / 6;
+      if (g + 2 < n_chunks) {
+        if (g >= 1)
+          ok = mbar_wait_or_abort(bar0 + 24 + 8 * ((g - 1) % G_NST), ((g - 1) / G_NST) & 1, abort,
+                                  WAIT_CYCLES);
+        if (!ok) break;
+        issue(g + 2);
+      }
+      if (c == 0 && t > 0) ok = mbar_wait_or_abort(B_EPI, (3 * t - 1) & 1, abort, WAIT_CYCLES);
+      if (c == 4) ok = ok && mbar_wait_or_abort(B_EPI, (3 * t) & 1, abort, WAIT_CYCLES);
+      ok = ok && mbar_wait_or_abort(bar0 + 8 * st, (g / G_NST) & 1, abort, WAIT_CYCLES);
+      if (!ok) break;
+      tc_fence_after();
+      const uint32_t sA = smem_u32(smem + G_A0 + st * G_ACHUNK);
+      const uint32_t sB = smem_u32(smem + G_B0 + st * G_CHUNK);
+      if (c < 4) {
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-          float t[16];
-          if (row_ok) {
+        for (int kk = 0; kk < 4; ++kk)
+          mma_e4m3(tbase + 0, sdesc(sA + 256 * kk, 128, 1024), sdesc(sB + 256 * kk, 128, 1024), id256,
+                   (c > 0 || kk > 0) ? 1u : 0u);
+      } else {
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-              const float4 f = __ldg(reinterpret_cast<const float4*>(src + 128 * c + 16 * k + 4 * q));
-              t[4 * q + 0] = f.x * fi[16 * k + 4 * q + 0];
-              t[4 * q + 1] = f.y * fi[16 * k + 4 * q + 1];
-              t[4 * q + 2] = f.z * fi[16 * k + 4 * q + 2];
-              t[4 * q + 3] = f.w * fi[16 * k + 4 * q + 3];
-            }
-          } else {
-#pragma unroll
-            for (int q = 0; q < 16; ++q) t[q] = 0.f;
-          }
-          uint4 w;
-          w.x = pack_e4m3x4(t[0], t[1], t[2], t[3]);
-          w.y = pack_e4m3x4(t[4], t[5], t[6], t[7]);
-          w.z = pack_e4m3x4(t[8], t[9], t[10], t[11]);
-          w.w = pack_e4m3x4(t[12], t[13], t[14], t[15]);
-          *reinterpret_cast<uint4*>(A + kmajor_off8(tid, 16 * k, 128)) = w;
-        }
-      } else if (c == 4) {
-        // layer-1 accumulators are final once the MMAs of chunk 3 (stage 1)
-        // have completed (tcgen05 operations complete in order)
-        ok = mbar_wait_or_abort(bar0 + 24, (nm[1] - 1) & 1, abort, WAIT_CYCLES);
-        if (!__syncthreads_and(ok)) {
-          ok = false;
-          break;
-        }
+        for (int kk = 0; kk < 4; ++kk)
+          mma_e4m3(tbase + 256, sdesc(sG + 1024 * (c - 4) + 256 * kk, 128, 2048),
+                   sdesc(sB + 256 * kk, 128, 1024), id256, (c > 4 || kk > 0) ? 1u : 0u);
+      }
+      mma_commit(bar0 + 24 + 8 * st);
+      if (c == 3) mma_commit(B_L1D);
+      if (c == 5) {
+        mma_commit(B_L2D);
+        // layer 3 once G holds layer 2: D3[128 x 16] = G . Wh3'^T (rows 8..15 zero)
+        ok = mbar_wait_or_abort(B_EPI, (3 * t + 1) & 1, abort, WAIT_CYCLES);
+        if (!ok) break;
         tc_fence_after();
-        head_epi_fp8(tbase + lane_off + 0, a4, c4, G, tid);
-      }
-      fence_async_smem();
-      tc_fence_before();
-      __syncthreads();
-      if (tid == 0 && !*abort) {
-        if (mbar_wait_or_abort(bar0 + 8 * st, (nb[st] - 1) & 1, abort, WAIT_CYCLES)) {
-          tc_fence_after();
-          if (c < 4) {
 #pragma unroll
-            for (int kk = 0; kk < 4; ++kk)
-              mma_e4m3(tbase + 0, sdesc(sA + 256 * kk, 128, 1024), sdesc(sB + 256 * kk, 128, 1024),
-                       id256, (c > 0 || kk > 0) ? 1u : 0u);
-          } else {
-#pragma unroll
-            for (int kk = 0; kk < 4; ++kk)
-              mma_e4m3(tbase + 256, sdesc(sG + 1024 * (c - 4) + 256 * kk, 128, 2048),
-                       sdesc(sB + 256 * kk, 128, 1024), id256, (c > 4 || kk > 0) ? 1u : 0u);
-          }
-          mma_commit(bar0 + 16 + 8 * st);
-        }
+        for (int kk = 0; kk < 8; ++kk)
+          mma_e4m3(tbase + 0, sdesc(sG + 256 * kk, 128, 2048), sdesc(sW3 + 256 * kk, 128, 2048),
+                   id16, kk > 0);
+        mma_commit(B_L3);
       }
-      ++nm[st];
     }
+    if (!ok) *abort = 1;
+  }
+  if (tid < 128) ok = mbar_wait_or_abort(B_RES, 0, abort, WAIT_CYCLES);
+  for (int t = 0; tid < 128 && t < my_tiles && ok; ++t) {
+    const int pr = lo + ((int)blockIdx.x + t * (int)gridDim.x) * HT + tid;
+    const bool row_ok = pr < n;
+    ok = mbar_wait_or_abort(B_L1D, t & 1, abort, WAIT_CYCLES);
     if (!ok) break;
-    // layer-2 accumulators are final with the MMAs of chunk 5 (stage 1)
-    ok = mbar_wait_or_abort(bar0 + 24, (nm[1] - 1) & 1, abort, WAIT_CYCLES);
-    if (!__syncthreads_and(ok)) {
-      ok = false;
-      break;
-    }
+    tc_fence_after();
+    head_epi_fp8(tbase + lane_off + 0, a4, c4, G, tid);
+    fence_async_smem();
+    tc_fence_before();
+    mbar_arrive(B_EPI);
+    ok = mbar_wait_or_abort(B_L2D, t & 1, abort, WAIT_CYCLES);
+    if (!ok) break;
     tc_fence_after();
     head_epi_fp8(tbase + lane_off + 256, a5, c5, G, tid);
     fence_async_smem();
     tc_fence_before();
-    __syncthreads();
-    if (tid == 0) {
-      tc_fence_after();
-#pragma unroll
-      for (int kk = 0; kk < 8; ++kk)
-        mma_e4m3(tbase + 0, sdesc(sG + 256 * kk, 128, 2048), sdesc(sW3 + 256 * kk, 128, 2048), id16,
-                 kk > 0);
-      mma_commit(B_L3);
-    }
-    ok = mbar_wait_or_abort(B_L3, n3 & 1, abort, WAIT_CYCLES);
-    ++n3;
-    if (!__syncthreads_and(ok)) {
-      ok = false;
-      break;
-    }
+    mbar_arrive(B_EPI);
+    ok = mbar_wait_or_abort(B_L3, t & 1, abort, WAIT_CYCLES);
+    if (!ok) break;
     tc_fence_after();
     {
       float v[16];
@@ -551,15 +554,16 @@ __global__ void __launch_bounds__(128, 1)
       }
     }
     tc_fence_before();
-    __syncthreads();
+    mbar_arrive(B_EPI);
   }
-  if (tid == 0 && (!ok || *abort)) {
-    // drain: wait (bounded) for this thread's MMAs and bulk copies
+  __syncthreads();
+  if (tid == 128 && *abort) {
+    // drain: wait (bounded) for the producer's MMAs and bulk copies
     atomicOr(err, 2);
     mma_commit(B_DRAIN);
     mbar_wait(B_DRAIN, 0, WAIT_CYCLES);
-    for (int st = 0; st < 2; ++st)
-      if (nb[st] > 0) mbar_wait(bar0 + 8 * st, (nb[st] - 1) & 1, WAIT_CYCLES);
+    for (int g = g_issued - G_NST; g < g_issued; ++g)
+      if (g >= 0) mbar_wait(bar0 + 8 * (g % G_NST), (g / G_NST) & 1, WAIT_CYCLES);
   }
   tc_fence_before();
   __syncthreads();
@@ -676,6 +680,7 @@ int upload_fp8_params(locc_handle* h, const std::vector<float>& params) {
   for (int c = 0; c < 256; ++c) {
     ep[384 + c] = (float)L3.w[c];                     // w3
     ep[640 + c] = P[offb[2] + c];                     // b3
+    ep[896 + c] = (float)(1.0 / s3[c]);               // feature inverse scale (head input)
   }
   unsigned char* hd = img.data() + enc_bytes;
   float* hp = reinterpret_cast<float*>(hd + G_EP);
@@ -740,9 +745,9 @@ int run_network_fp8(locc_handle* h, const float4* xyz, const PairRange& rg, cons
     }
     attr = true;
   }
-  float* feat = feat_out ? feat_out : h->d_feat;
+  unsigned char* ftile = static_cast<unsigned char*>(h->d_feat_tc);
   encoder_fp8_kernel<<<std::min(n_pairs, h->n_sm), F_THREADS, F_SMEM, stream>>>(
-      xyz, rg, h->wf8_enc, feat, h->d_err);
+      xyz, rg, h->wf8_enc, feat_out, ftile, h->d_err);
   if (cudaGetLastError() != cudaSuccess) {
     set_error("encoder_fp8_kernel launch failed");
     return LOCC_ERR_CUDA;
@@ -750,8 +755,8 @@ int run_network_fp8(locc_handle* h, const float4* xyz, const PairRange& rg, cons
   if (mid && cudaEventRecord(mid, stream) != cudaSuccess) return LOCC_ERR_CUDA;
   PairInputs pin{};
   if (in) pin = *in;
-  head_fp8_kernel<<<std::min((n_pairs + HT - 1) / HT, h->n_sm), 128, G_SMEM, stream>>>(
-      feat, rg, h->wf8_head, pin, in != nullptr, centre, out, y_raw, h->d_err);
+  head_fp8_kernel<<<std::min((n_pairs + HT - 1) / HT, h->n_sm), G_THREADS, G_SMEM, stream>>>(
+      ftile, rg, h->wf8_head, pin, in != nullptr, centre, out, y_raw, h->d_err);
   if (cudaGetLastError() != cudaSuccess) {
     set_error("head_fp8_kernel launch failed");
     return LOCC_ERR_CUDA;
