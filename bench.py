@@ -51,7 +51,8 @@ WORKLOAD = "uneven_scenes_8192env_poisson8_64shapes"
 # DRAM bytes (read + write) per pair of the encoder kernel from one ncu capture
 # of the bench's scene 1 (154,924 pairs; profiles/kernels_bf16_fp8_uneven8192.md):
 # scaled by the pairs of a launch to give the per-launch traffic.
-ENC_DRAM_BYTES_PER_PAIR = {}  # re-captured after the feature layout change
+ENC_DRAM_BYTES_PER_PAIR = {"bf16": (317.457152e6 + 128.659200e6) / 154924,
+                           "fp8": (317.384704e6 + 63.287552e6) / 154924}
 WEIGHTS = os.path.join(ROOT, "paper_2304_09439_b300", "weights", "locc_trained.bin")
 
 
