@@ -471,7 +471,10 @@ __global__ void __launch_bounds__(G_THREADS, 1)
         if (!ok) break;
         issue(g + 2);
       }
-      if (c == 0 && t > 0) ok = mbar_wait_or_abort(B_EPI, (3 * t - 1) & 1, abort, WAIT_CYCLES);
+      // layer 2 of tile t: the previous tile's outputs have left TMEM (they sit
+      // in the layer-2 columns) and G holds layer 1 of tile t; the EPI phases
+      // are waited one after the other, never skipping one
+      if (c == 4 && t > 0) ok = mbar_wait_or_abort(B_EPI, (3 * t - 1) & 1, abort, WAIT_CYCLES);
       if (c == 4) ok = ok && mbar_wait_or_abort(B_EPI, (3 * t) & 1, abort, WAIT_CYCLES);
       ok = ok && mbar_wait_or_abort(bar0 + 8 * st, (g / G_NST) & 1, abort, WAIT_CYCLES);
       if (!ok) break;
@@ -499,7 +502,7 @@ __global__ void __launch_bounds__(G_THREADS, 1)
         tc_fence_after();
 #pragma unroll
         for (int kk = 0; kk < 8; ++kk)
-          mma_e4m3(tbase + 0, sdesc(sG + 256 * kk, 128, 2048), sdesc(sW3 + 256 * kk, 128, 2048),
+          mma_e4m3(tbase + 256, sdesc(sG + 256 * kk, 128, 2048), sdesc(sW3 + 256 * kk, 128, 2048),
                    id16, kk > 0);
         mma_commit(B_L3);
       }
@@ -529,7 +532,7 @@ __global__ void __launch_bounds__(G_THREADS, 1)
     tc_fence_after();
     {
       float v[16];
-      tmem_ld16(tbase + lane_off + 0, v);
+      tmem_ld16(tbase + lane_off + 256, v);  // layer 3 sits in the layer-2 columns
       if (row_ok) {
         float y[8];
 #pragma unroll
