@@ -258,13 +258,14 @@ def serving_run(srv, pool, rate: float, seconds: float, seed: int):
             "window_s": window}
 
 
-def serving_leg(det, seconds: float, rate: float, max_queued: int, seed: int = 6):
+def serving_leg(det, seconds: float, rate: float, max_queued: int, max_active: int = 256,
+                seed: int = 6):
     """Serving workload: an overloaded run at `rate` requests/s, then a run at
     half of the capacity measured there."""
     from paper_2304_09439_b300 import Server
     pool = serving_pool(48, seed)
     mean_pairs = float(np.mean([len(x[2]) for x in pool]))
-    with Server(det, arena_bytes=8 << 30, max_batch_pairs=131072, max_active=256,
+    with Server(det, arena_bytes=8 << 30, max_batch_pairs=131072, max_active=max_active,
                 max_queued_pairs=max_queued) as srv:
         # warm-up: one pass over a few batches
         for p, s, q, o in pool[:4]:
@@ -274,7 +275,7 @@ def serving_leg(det, seconds: float, rate: float, max_queued: int, seed: int = 6
         half = serving_run(srv, pool, 0.5 * cap / mean_pairs, seconds, seed + 2)
     return {"workload": "clients: envs log-U[64,16384], pairs log-U[1e2,1e6], Poisson arrivals",
             "pool_batches": len(pool), "mean_pairs_per_request": mean_pairs,
-            "max_batch_pairs": 131072, "max_queued_pairs": max_queued,
+            "max_batch_pairs": 131072, "max_queued_pairs": max_queued, "max_active": max_active,
             "arena_bytes": 8 << 30, "overload": over, "half_capacity": half}
 
 
@@ -340,6 +341,8 @@ def main():
     ap.add_argument("--serve-rate", type=float, default=2000.0, help="offered requests/s")
     ap.add_argument("--serve-max-queued", type=int, default=8_000_000,
                     help="queued pairs beyond which requests are refused")
+    ap.add_argument("--serve-max-active", type=int, default=256,
+                    help="requests admitted at once (sharing the launches)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -487,7 +490,7 @@ def main():
         serving = None
         if args.serve_seconds > 0:
             serving = serving_leg(det, args.serve_seconds, args.serve_rate,
-                                  args.serve_max_queued)
+                                  args.serve_max_queued, args.serve_max_active)
         line = {
             "metric": "contact pairs/sec", "value": pairs_all / (ms_max * 1e-3),
             "unit": "pairs/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,

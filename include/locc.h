@@ -305,7 +305,9 @@ void locc_trainer_destroy(locc_trainer *t);
  * which the paper does not describe.
  *   - Admission by device memory: a request's inputs are copied into a device
  *     arena of arena_bytes (a budget of HBM) when a block large enough is
- *     free; queued requests are admitted in arrival order as blocks free up.
+ *     free; queued requests are admitted in arrival order as blocks free up,
+ *     at most max_active at once and while the admitted requests' pairs left
+ *     to launch (each counted up to one launch) stay below max_active_pairs.
  *   - Continuous batching: every launch packs the pending pairs of all
  *     admitted requests, up to max_batch_pairs: each request first gets an
  *     equal share, the room left goes in admission order.  A large request
@@ -326,6 +328,13 @@ typedef struct {
   int64_t max_queued_pairs; /* pairs waiting for admission beyond which
                                locc_server_submit rejects (an empty queue
                                always accepts); 0 -> no limit */
+  int64_t max_active_pairs; /* admission pauses while the admitted requests'
+                               pairs still to launch, each counted up to
+                               max_batch_pairs, reach this (one request is
+                               always admitted): bounds how many requests
+                               share the launches without keeping small
+                               requests out behind a large one;
+                               0 -> 4 x max_batch_pairs */
 } locc_server_config;
 
 /* A request: HOST arrays, read until the request completes; `out` is written

@@ -318,11 +318,11 @@ class Server:
     the detector's handle."""
 
     def __init__(self, det: Detector, arena_bytes: int = 0, max_batch_pairs: int = 131072,
-                 max_active: int = 256, max_queued_pairs: int = 0):
+                 max_active: int = 256, max_queued_pairs: int = 0, max_active_pairs: int = 0):
         self._lib = abi.load()
         self.det = det
         cfg = abi.ServerConfig(int(arena_bytes), int(max_batch_pairs), int(max_active),
-                               int(max_queued_pairs))
+                               int(max_queued_pairs), int(max_active_pairs))
         self._s = ctypes.c_void_p()
         abi.check(self._lib.locc_server_create(det._h, ctypes.byref(cfg), ctypes.byref(self._s)))
         self._keep = {}

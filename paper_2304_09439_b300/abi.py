@@ -45,7 +45,8 @@ class TrainConfig(ctypes.Structure):
 
 class ServerConfig(ctypes.Structure):
     _fields_ = [("arena_bytes", ctypes.c_int64), ("max_batch_pairs", ctypes.c_int32),
-                ("max_active", ctypes.c_int32), ("max_queued_pairs", ctypes.c_int64)]
+                ("max_active", ctypes.c_int32), ("max_queued_pairs", ctypes.c_int64),
+                ("max_active_pairs", ctypes.c_int64)]
 
 
 class Request(ctypes.Structure):

@@ -288,12 +288,20 @@ void locc_server::scheduler() {
       std::unique_lock<std::mutex> lk(mu);
       for (;;) {
         // admission in arrival order while the arena has room
-        while (!queue.empty() && (int)active.size() < cfg.max_active && !free_events.empty()) {
+        // launch pressure of the admitted requests: the pairs each still has to
+        // launch, counted up to one launch, so a large request does not keep
+        // small ones out while many large ones are bounded
+        int64_t pressure = 0;
+        for (Request* r : active)
+          pressure += std::min<int64_t>(r->rq.n_pairs - r->cursor, cfg.max_batch_pairs);
+        while (!queue.empty() && (int)active.size() < cfg.max_active && !free_events.empty() &&
+               (active.empty() || pressure < cfg.max_active_pairs)) {
           Request* r = queue.front();
           size_t off = 0;
           if (!arena.alloc(r->bytes, &off)) break;
           queue.pop_front();
           queued_pairs -= r->rq.n_pairs;
+          pressure += std::min<int64_t>(r->rq.n_pairs, cfg.max_batch_pairs);
           r->off = off;
           r->off_shape = off + (((size_t)r->rq.n_obj * 28 + 255) / 256 * 256);
           r->off_pairs = r->off_shape + (((size_t)r->rq.n_obj * 4 + 255) / 256 * 256);
@@ -365,10 +373,11 @@ int locc_server_create(locc_handle* h, const locc_server_config* cfg_in, locc_se
   if (cfg_in) cfg = *cfg_in;
   if (cfg.max_batch_pairs == 0) cfg.max_batch_pairs = 131072;
   if (cfg.max_active == 0) cfg.max_active = 256;
+  if (cfg.max_active_pairs == 0) cfg.max_active_pairs = 4 * (int64_t)cfg.max_batch_pairs;
   if (cfg.max_batch_pairs < 1 || cfg.max_active < 1 || cfg.max_active > kMaxActive ||
-      cfg.arena_bytes < 0 || cfg.max_queued_pairs < 0) {
+      cfg.arena_bytes < 0 || cfg.max_queued_pairs < 0 || cfg.max_active_pairs < 0) {
     set_error("locc_server_create: max_batch_pairs >= 1, 1 <= max_active <= 1024, "
-              "arena_bytes >= 0 and max_queued_pairs >= 0 are required");
+              "arena_bytes, max_queued_pairs and max_active_pairs >= 0 are required");
     return LOCC_ERR_INVALID_ARG;
   }
   if (cudaSetDevice(h->device) != cudaSuccess) {
