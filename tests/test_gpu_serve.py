@@ -206,3 +206,27 @@ def test_bad_requests_and_shutdown(lib):
     srv.close()
     assert np.array_equal(_alone(det, (p, s, q)).view(np.uint32), o.view(np.uint32))
     det.close()
+
+
+def test_launch_pressure_bounds_admission(lib):
+    # many large requests: each counts up to one launch (max_batch_pairs) of
+    # pressure, so only a few are admitted at once (more only as the admitted
+    # ones near their end); a small request is still admitted beside them
+    from paper_2304_09439_b300 import Detector, Server
+    _dev()
+    det = Detector(lib.points, lib.aabb, synth.xavier_weights(1), R, "bf16")
+    big = _requests([(2000, 40000)] * 12, 700)
+    small = _requests([(64, 150)], 800)[0]
+    with Server(det, max_batch_pairs=8192, max_active_pairs=4 * 8192) as srv:
+        outs = [_out(40000) for _ in big]
+        ids = [srv.submit(*r, out=o) for r, o in zip(big, outs)]
+        o_s = _out(150)
+        i_s = srv.submit(*small, out=o_s)
+        infos = [srv.wait(i) for i in ids]
+        info_s = srv.wait(i_s)
+        st = srv.stats()
+    assert 2 <= st["max_active_seen"] <= 8, st  # without the bound all 13 would be
+    assert info_s["launches"] == 1
+    for r, o in zip(big[:2], outs[:2]):
+        assert np.array_equal(_alone(det, r).view(np.uint32), o.view(np.uint32))
+    det.close()
