@@ -31,10 +31,6 @@ using namespace tc;
 
 constexpr long long WAIT_CYCLES = 2000000000LL;  // ~1 s at 2 GHz
 
-__device__ __forceinline__ uint4 ldg_v4(const void* p) {
-  return __ldg(reinterpret_cast<const uint4*>(p));
-}
-
 // ------------------------------------------------------ weight quantisation
 // Row r of W [rows][K] (float32, row-major) times inv[r] -> e4m3 bytes in
 // K-chunks of chunkK columns, each chunk a K-major no-swizzle tile
@@ -370,22 +366,24 @@ constexpr int G_B0 = G_A0 + G_NST * G_ACHUNK;              // B stages, 32 KB ea
 constexpr int G_G = G_B0 + G_NST * G_CHUNK;                // G [128 x 256] e4m3, 32 KB
 constexpr int G_CTRL = G_G + 128 * 256;                    // mbarriers, TMEM address, abort
 constexpr int G_SMEM = G_CTRL + 128;
-constexpr int G_THREADS = 160;
+constexpr int G_THREADS = 288;  // 8 epilogue warps + the producer warp
 static_assert(G_RES_BYTES % 16 == 0 && G_IMG_W1 % 16 == 0, "bulk copies need 16-byte chunks");
 static_assert(G_SMEM <= 227 * 1024, "fp8 head shared memory");
 
+// Half of a 256-wide layer: 128 columns from taddr -> e4m3 G columns
+// [k0, k0 + 128).
 __device__ __forceinline__ void head_epi_fp8(uint32_t taddr, const float* alpha, const float* beta,
-                                             unsigned char* G, int row) {
+                                             unsigned char* G, int row, int k0) {
   float v[32];
 #pragma unroll 2
-  for (int h = 0; h < 8; ++h) {
+  for (int h = 0; h < 4; ++h) {
     tmem_ld32(taddr + 32 * h, v);
-    epi_e4m3_32<256>(v, alpha + 32 * h, beta + 32 * h, G, row, 32 * h);
+    epi_e4m3_32<256>(v, alpha + 32 * h, beta + 32 * h, G, row, k0 + 32 * h);
   }
 }
 
-// Same stream as the BF16 head (producer warp 4 feeding three operand stages
-// by bulk copy across tiles; epilogue warps 0-3) over 6 K-chunks of 128 per
+// Same stream as the BF16 head (producer warp 8 feeding three operand stages
+// by bulk copy across tiles; epilogue warps 0-7) over 6 K-chunks of 128 per
 // tile: 4 of W_h1 against the e4m3 features the encoder wrote in operand
 // layout, 2 of W_h2 against G.
 __global__ void __launch_bounds__(G_THREADS, 1)
@@ -409,7 +407,7 @@ __global__ void __launch_bounds__(G_THREADS, 1)
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + G_CTRL + 96);
   volatile int* abort = reinterpret_cast<volatile int*>(smem + G_CTRL + 100);
   if (tid == 0) {
-    for (int i = 0; i < 8; ++i) mbar_init(bar0 + 8 * i, i == 7 ? 128 : 1);
+    for (int i = 0; i < 8; ++i) mbar_init(bar0 + 8 * i, i == 7 ? 256 : 1);
     mbar_init(B_RES, 1);
     mbar_init(B_DRAIN, 1);
     mbar_init(B_L1D, 1);
@@ -425,7 +423,10 @@ __global__ void __launch_bounds__(G_THREADS, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tbase = *tmem_slot;
-  const uint32_t lane_off = (uint32_t)(32 * warp) << 16;
+  // epilogue warps w and w + 4 share TMEM lane quarter w % 4 and split the
+  // columns between them
+  const uint32_t lane_off = (uint32_t)(32 * (warp & 3)) << 16;
+  const int row = tid & 127, half = (tid >> 7) & 1;
   const float* finv = reinterpret_cast<const float*>(smem + G_EP);
   const float* a4 = finv + 256;
   const float* c4 = a4 + 256;
@@ -440,7 +441,7 @@ __global__ void __launch_bounds__(G_THREADS, 1)
   bool ok = true;
   int g_issued = 0;
 
-  if (tid == 128) {
+  if (tid == 256) {
     mbar_expect_tx(B_RES, G_RES_BYTES);
     bulk_g2s(smem_u32(smem), img, G_RES_BYTES, B_RES);
     auto issue = [&](int g) {
@@ -509,28 +510,29 @@ __global__ void __launch_bounds__(G_THREADS, 1)
     }
     if (!ok) *abort = 1;
   }
-  if (tid < 128) ok = mbar_wait_or_abort(B_RES, 0, abort, WAIT_CYCLES);
-  for (int t = 0; tid < 128 && t < my_tiles && ok; ++t) {
-    const int pr = lo + ((int)blockIdx.x + t * (int)gridDim.x) * HT + tid;
+  if (tid < 256) ok = mbar_wait_or_abort(B_RES, 0, abort, WAIT_CYCLES);
+  for (int t = 0; tid < 256 && t < my_tiles && ok; ++t) {
+    const int pr = lo + ((int)blockIdx.x + t * (int)gridDim.x) * HT + row;
     const bool row_ok = pr < n;
     ok = mbar_wait_or_abort(B_L1D, t & 1, abort, WAIT_CYCLES);
     if (!ok) break;
     tc_fence_after();
-    head_epi_fp8(tbase + lane_off + 0, a4, c4, G, tid);
+    head_epi_fp8(tbase + lane_off + 128 * half, a4 + 128 * half, c4 + 128 * half, G, row, 128 * half);
     fence_async_smem();
     tc_fence_before();
     mbar_arrive(B_EPI);
     ok = mbar_wait_or_abort(B_L2D, t & 1, abort, WAIT_CYCLES);
     if (!ok) break;
     tc_fence_after();
-    head_epi_fp8(tbase + lane_off + 256, a5, c5, G, tid);
+    head_epi_fp8(tbase + lane_off + 256 + 128 * half, a5 + 128 * half, c5 + 128 * half, G, row,
+                 128 * half);
     fence_async_smem();
     tc_fence_before();
     mbar_arrive(B_EPI);
     ok = mbar_wait_or_abort(B_L3, t & 1, abort, WAIT_CYCLES);
     if (!ok) break;
     tc_fence_after();
-    {
+    if (half == 0) {
       float v[16];
       tmem_ld16(tbase + lane_off + 256, v);  // layer 3 sits in the layer-2 columns
       if (row_ok) {
@@ -560,7 +562,7 @@ __global__ void __launch_bounds__(G_THREADS, 1)
     mbar_arrive(B_EPI);
   }
   __syncthreads();
-  if (tid == 128 && *abort) {
+  if (tid == 256 && *abort) {
     // drain: wait (bounded) for the producer's MMAs and bulk copies
     atomicOr(err, 2);
     mma_commit(B_DRAIN);

@@ -80,10 +80,6 @@ constexpr int B_FULLX = 0, B_XRDY = NSLOT, B_H1RDY = 2 * NSLOT, B_H2RDY = 3 * NS
               B_E3A = 4 * NSLOT, B_D1 = 5 * NSLOT, B_D2 = 6 * NSLOT, B_D3A = 7 * NSLOT,
               B_D3B = 8 * NSLOT, B_W = 9 * NSLOT, B_DRAIN = 9 * NSLOT + 1;
 
-__device__ __forceinline__ uint4 ld_global_v4(const void* p) {
-  return __ldg(reinterpret_cast<const uint4*>(p));
-}
-
 // Epilogue of layers 1 and 2: TMEM row -> relu(x + b) -> bf16 row of the next
 // A operand (K = NCOL).
 template <int NCOL>
@@ -378,12 +374,13 @@ static_assert(H_RES_BYTES % 16 == 0, "resident image must be 16-byte chunks");
 static_assert(H_IMG_W1 % 16 == 0 && H_CHUNK % 16 == 0, "bulk copies need 16-byte chunks");
 static_assert(H_SMEM <= 227 * 1024, "head shared memory");
 
-// Epilogue of a 256-wide layer: TMEM row tid, columns [col0, col0 + 256) ->
-// relu(x + b) as bf16 into G (K = 256).
-__device__ __forceinline__ void head_epi_256(uint32_t taddr, const float* b, unsigned char* G, int row) {
+// Epilogue of half of a 256-wide layer: TMEM row `row`, 128 columns from
+// taddr -> relu(x + b) as bf16 into G columns [k0, k0 + 128) (K = 256).
+__device__ __forceinline__ void head_epi_256(uint32_t taddr, const float* b, unsigned char* G, int row,
+                                             int k0) {
   float v[32];
 #pragma unroll 1
-  for (int h = 0; h < 8; ++h) {
+  for (int h = 0; h < 4; ++h) {
     tmem_ld32(taddr + 32 * h, v);
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
@@ -393,13 +390,14 @@ __device__ __forceinline__ void head_epi_256(uint32_t taddr, const float* b, uns
       w.y = pack_bf16(fmaxf(v[j + 2] + b[o + 2], 0.f), fmaxf(v[j + 3] + b[o + 3], 0.f));
       w.z = pack_bf16(fmaxf(v[j + 4] + b[o + 4], 0.f), fmaxf(v[j + 5] + b[o + 5], 0.f));
       w.w = pack_bf16(fmaxf(v[j + 6] + b[o + 6], 0.f), fmaxf(v[j + 7] + b[o + 7], 0.f));
-      *reinterpret_cast<uint4*>(G + kmajor_off(row, o, 256)) = w;
+      *reinterpret_cast<uint4*>(G + kmajor_off(row, k0 + o, 256)) = w;
     }
   }
 }
 
-// Head over tiles of HT = 128 pairs (one pair per epilogue thread / TMEM
-// lane; warps 0-3), plus a producer warp (warp 4, one elected lane).
+// Head over tiles of HT = 128 pairs (one pair per TMEM lane).  Warps 0-7 are
+// the epilogue (warps w and w + 4 read lane quarter w % 4, half of the
+// columns each); warp 8 is the producer (one elected lane).
 // Layers 1 and 2 are 12 K-chunks of 64 per tile (8 of W_h1 against the bf16
 // features the encoder wrote in operand layout, 4 of W_h2 against G); every
 // operand chunk arrives by bulk copy.  The producer runs the chunk stream
@@ -408,7 +406,7 @@ __device__ __forceinline__ void head_epi_256(uint32_t taddr, const float* b, uns
 // flight while one multiplies.  The epilogue warps signal an mbarrier (EPI)
 // when G holds layer 1, when it holds layer 2, and when the tile's outputs
 // have been read out of TMEM.
-constexpr int H_THREADS = 160;
+constexpr int H_THREADS = 288;  // 8 epilogue warps + the producer warp
 __global__ void __launch_bounds__(H_THREADS, 1)
     head_tc_kernel(const __nv_bfloat16* __restrict__ ftile, PairRange rg,
                    const unsigned char* __restrict__ img, PairInputs in, int have_in,
@@ -431,7 +429,7 @@ __global__ void __launch_bounds__(H_THREADS, 1)
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + H_CTRL + 96);
   volatile int* abort = reinterpret_cast<volatile int*>(smem + H_CTRL + 100);
   if (tid == 0) {
-    for (int i = 0; i < 8; ++i) mbar_init(bar0 + 8 * i, i == 7 ? 128 : 1);
+    for (int i = 0; i < 8; ++i) mbar_init(bar0 + 8 * i, i == 7 ? 256 : 1);
     mbar_init(B_RES, 1);
     mbar_init(B_DRAIN, 1);
     mbar_init(B_L1D, 1);
@@ -447,7 +445,10 @@ __global__ void __launch_bounds__(H_THREADS, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tbase = *tmem_slot;
-  const uint32_t lane_off = (uint32_t)(32 * warp) << 16;
+  // epilogue warps w and w + 4 share TMEM lane quarter w % 4 and split the
+  // columns between them
+  const uint32_t lane_off = (uint32_t)(32 * (warp & 3)) << 16;
+  const int row = tid & 127, half = (tid >> 7) & 1;
   const float* hb1 = reinterpret_cast<const float*>(smem + H_BIAS);
   const float* hb2 = hb1 + 256;
   const float* hb3 = hb2 + 256;
@@ -457,7 +458,7 @@ __global__ void __launch_bounds__(H_THREADS, 1)
   bool ok = true;
   int g_issued = 0;  // chunks whose copies the producer has issued
 
-  if (tid == 128) {
+  if (tid == 256) {
     mbar_expect_tx(B_RES, H_RES_BYTES);
     bulk_g2s(smem_u32(smem), img, H_RES_BYTES, B_RES);
     // copies of global chunk g into stage g % H_NST
@@ -534,29 +535,29 @@ __global__ void __launch_bounds__(H_THREADS, 1)
     if (!ok) *abort = 1;
   }
   // epilogue warps
-  if (tid < 128) ok = mbar_wait_or_abort(B_RES, 0, abort, WAIT_CYCLES);
-  for (int t = 0; tid < 128 && t < my_tiles && ok; ++t) {
-    const int pr = lo + ((int)blockIdx.x + t * (int)gridDim.x) * HT + tid;
+  if (tid < 256) ok = mbar_wait_or_abort(B_RES, 0, abort, WAIT_CYCLES);
+  for (int t = 0; tid < 256 && t < my_tiles && ok; ++t) {
+    const int pr = lo + ((int)blockIdx.x + t * (int)gridDim.x) * HT + row;
     const bool row_ok = pr < n;
     // layer 1 final with the MMAs of chunk 12 t + 7, layer 2 with 12 t + 11
     ok = mbar_wait_or_abort(B_L1D, t & 1, abort, WAIT_CYCLES);
     if (!ok) break;
     tc_fence_after();
-    head_epi_256(tbase + lane_off + 0, hb1, G, tid);
+    head_epi_256(tbase + lane_off + 128 * half, hb1 + 128 * half, G, row, 128 * half);
     fence_async_smem();
     tc_fence_before();
     mbar_arrive(B_EPI);
     ok = mbar_wait_or_abort(B_L2D, t & 1, abort, WAIT_CYCLES);
     if (!ok) break;
     tc_fence_after();
-    head_epi_256(tbase + lane_off + 256, hb2, G, tid);
+    head_epi_256(tbase + lane_off + 256 + 128 * half, hb2 + 128 * half, G, row, 128 * half);
     fence_async_smem();
     tc_fence_before();
     mbar_arrive(B_EPI);
     ok = mbar_wait_or_abort(B_L3, t & 1, abort, WAIT_CYCLES);
     if (!ok) break;
     tc_fence_after();
-    {
+    if (half == 0) {
       float v[16];
       tmem_ld16(tbase + lane_off + 256, v);  // layer 3 sits in the layer-2 columns
       if (row_ok) {
@@ -586,7 +587,7 @@ __global__ void __launch_bounds__(H_THREADS, 1)
     mbar_arrive(B_EPI);
   }
   __syncthreads();
-  if (tid == 128 && *abort) {
+  if (tid == 256 && *abort) {
     // drain: wait (bounded) for the producer's MMAs and bulk copies
     atomicOr(err, 2);
     mma_commit(B_DRAIN);
