@@ -31,8 +31,9 @@
 //     bins that can still matter: the list keeps those bins and later keys of
 //     higher bins are skipped; only if one bin alone overflows the list is it
 //     sorted and cut to its 64 smallest keys (an exact streaming top-64);
-//   * the kept keys are written in list order (storage order), which is not
-//     part of the result: the encoder max-pools over points.
+//   * the kept keys are written in list order (storage order), the chosen
+//     keys of bin b* last; the order is not part of the result: the encoder
+//     max-pools over points.
 #include <algorithm>
 
 #include "common.cuh"
@@ -243,47 +244,37 @@ __device__ __forceinline__ int keep_bins_below(unsigned long long* buf, int n, f
   return w;
 }
 
-// Keep, in list order, the keys of buf[0, n) that are among the KMAX
-// smallest: every key of a bin below b* and the `need` smallest keys of bin
-// b* (rank selection over that bin's keys, which are unique).  buf must hold
-// every in-ball key of bins <= b*.  Returns false, leaving buf unchanged, when
-// bin b* holds more than EBUF keys.
+// Keep the keys of buf[0, n) that are among the KMAX smallest: every key of
+// a bin below b* (compacted in place, in list order) and then the `need`
+// smallest keys of bin b* (rank selection over that bin's keys, which are
+// unique).  buf must hold every in-ball key of bins <= b*.  Returns false when
+// bin b* holds more than EBUF keys; buf is then partly overwritten and the
+// caller defers the object.
 __device__ __forceinline__ bool select_cut(unsigned long long* buf, int n, float inv_w, int bstar,
-                                        int need, int lane, unsigned long long* ebuf,
-                                        unsigned long long* tsh) {
+                                           int need, int lane, unsigned long long* ebuf) {
   const unsigned lt = (1u << lane) - 1u;
-  int m = 0;
+  int w = 0, m = 0;
   for (int base = 0; base < n; base += 32) {
     const int j = base + lane;
     const unsigned long long key = j < n ? buf[j] : ~0ull;
-    const bool e = j < n && key_bin(key, inv_w) == bstar;
-    const unsigned em = __ballot_sync(FULL, e);
-    if (m + __popc(em) > EBUF) return false;
-    if (e) ebuf[m + __popc(em & lt)] = key;
-    m += __popc(em);
+    const int bin = j < n ? key_bin(key, inv_w) : NBINS;
+    const unsigned bm = __ballot_sync(FULL, bin < bstar);
+    const unsigned am = __ballot_sync(FULL, bin == bstar);
+    if (m + __popc(am) > EBUF) return false;
+    __syncwarp();  // every lane has read its key before any is overwritten
+    if (bin < bstar) buf[w + __popc(bm & lt)] = key;
+    if (bin == bstar) ebuf[m + __popc(am & lt)] = key;
+    w += __popc(bm);
+    m += __popc(am);
+    __syncwarp();
   }
-  __syncwarp();
   for (int e = lane; e < m; e += 32) {
     const unsigned long long k = ebuf[e];
     int rank = 0;
     for (int i = 0; i < m; ++i) rank += ebuf[i] < k;
-    if (rank == need - 1) *tsh = k;
+    if (rank < need) buf[w + rank] = k;
   }
   __syncwarp();
-  const unsigned long long T = *tsh;
-  int w = 0;
-  for (int base = 0; base < n; base += 32) {
-    const int j = base + lane;
-    const unsigned long long key = j < n ? buf[j] : ~0ull;
-    int bin = NBINS;
-    if (j < n) bin = key_bin(key, inv_w);
-    const bool keep = bin < bstar || (bin == bstar && key <= T);
-    const unsigned km = __ballot_sync(FULL, keep);
-    __syncwarp();
-    if (keep) buf[w + __popc(km & lt)] = key;
-    w += __popc(km);
-    __syncwarp();
-  }
   return true;
 }
 
@@ -322,8 +313,8 @@ __device__ __forceinline__ void crop_pair(const DevLibrary& lib, const PairInput
                                           int32_t* __restrict__ cnt_out,
                                           float4* __restrict__ centre_out, int* __restrict__ err,
                                           unsigned long long* buf, int* hist,
-                                          unsigned long long* ebuf, unsigned long long* tsh,
-                                          float* rsh, int* defer, int defer_cap) {
+                                          unsigned long long* ebuf, float* rsh, int* defer,
+                                          int defer_cap) {
   int a, b, sa, sb;
   const bool ok = load_pair(in, lib.n_shapes, p, &a, &b, &sa, &sb, (warp == 0 && lane == 0) ? err : nullptr);
   if (!ok) {
@@ -429,7 +420,7 @@ __device__ __forceinline__ void crop_pair(const DevLibrary& lib, const PairInput
     int bstar, below;
     bin_histogram(buf, n, inv_w, hist, lane);
     cut_bin(hist, lane, &bstar, &below);
-    deferred = !select_cut(buf, n, inv_w, bstar, KMAX - below, lane, ebuf, tsh);
+    deferred = !select_cut(buf, n, inv_w, bstar, KMAX - below, lane, ebuf);
   }
   if (deferred) {
     // rare: one d^2 bin holds more keys than the list or the rank buffer;
@@ -520,7 +511,6 @@ __global__ void __launch_bounds__(64, 20) crop_kernel(DevLibrary lib, PairInputs
                                                       int defer_cap) {
   __shared__ unsigned long long cand[2][CAND_CAP];
   __shared__ unsigned long long ebuf[2][EBUF];
-  __shared__ unsigned long long tsh[2];
   __shared__ int hist[2][NBINS];
   __shared__ float rsh[2][12];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -528,7 +518,7 @@ __global__ void __launch_bounds__(64, 20) crop_kernel(DevLibrary lib, PairInputs
   range_bounds(rg, &lo, &hi);
   for (int p = lo + blockIdx.x; p < hi; p += gridDim.x) {
     crop_pair(lib, in, p, warp, lane, r, xyz_out, idx_out, cnt_out, centre_out, err, cand[warp],
-              hist[warp], ebuf[warp], &tsh[warp], rsh[warp], defer, defer_cap);
+              hist[warp], ebuf[warp], rsh[warp], defer, defer_cap);
   }
 }
 
