@@ -305,6 +305,28 @@ def rank_scene_seeds(rank: int, n_sets: int):
     return [LIB_SEED + 1000 * rank + i for i in range(n_sets)]
 
 
+def cpu_baseline_geometric(lib, scene, seconds: float = 6.0):
+    """Oracle (a), the float64 geometric contact detector, on a bounded sample
+    of the same scene's broadphase pairs (host cores)."""
+    import oracle
+    poses, osh, env = scene
+    pairs = oracle.broadphase(lib.aabb, poses, osh, env)
+    cores = os.cpu_count() or 1
+    rng = np.random.default_rng(2)
+    n, dt = 64, 0.0
+    while True:
+        sel = np.sort(rng.choice(len(pairs), min(n, len(pairs)), replace=False))
+        t0 = time.perf_counter()
+        oracle.contact(lib.meshes, lib.points, poses, osh, pairs[sel], n_threads=cores)
+        dt = time.perf_counter() - t0
+        if dt > seconds / 4 or n >= len(pairs):
+            break
+        n = min(len(pairs), int(n * max(2.0, seconds / 4 / max(dt, 1e-3))))
+    return {"value": len(sel) / dt, "unit": "pairs/s", "cores": cores, "kind": "oracle",
+            "sample": f"{len(sel)} random broadphase pairs of one scene (float64 triangle-pair "
+                      f"contact: label, point, normal, depth), {dt:.1f} s"}
+
+
 def cpu_baseline(lib, scene, seconds: float = 12.0):
     """Oracle (b) on a bounded sample of the workload (host cores)."""
     import oracle
@@ -489,9 +511,10 @@ def main():
             bound, peak_src = "tensor", f"{src} bf16_tflops_sustained" + \
                 (" x 2 (fp8/bf16 nominal ratio)" if args.precision == "fp8" else "")
         achieved = FLOP_ENC * per_step_pairs / (enc_ms * 1e-3) / 1e12
-        cpu = None
+        cpu = cpu_geo = None
         if not args.no_cpu_baseline and world == 1:
             cpu = cpu_baseline(lib, scenes[0])
+            cpu_geo = cpu_baseline_geometric(lib, scenes[0])
         serving = None
         if args.serve_seconds > 0:
             serving = serving_leg(det, args.serve_seconds, args.serve_rate,
@@ -526,6 +549,10 @@ def main():
             "gpu_launches": launches_per_step * args.steps,
             "clocks": clk.summary(),
             "cpu_baseline": cpu,
+            "cpu_baseline_geometric": cpu_geo,
+            "context": "paper: 5-10x over its uniform-flow GJK at comparable accuracy (Sec. I, "
+                       "IV-B); the only GPU it names is an RTX A6000 (training machine, "
+                       "hyper-parameter table); quoted as context, not a target",
             "serving": serving,
             "wall_s_timed": t_wall,
         }
