@@ -51,8 +51,11 @@ WORKLOAD = "uneven_scenes_8192env_poisson8_64shapes"
 # DRAM bytes (read + write) per pair of the encoder kernel from one ncu capture
 # of the bench's scene 1 (154,924 pairs; profiles/kernels_bf16_fp8_uneven8192.md):
 # scaled by the pairs of a launch to give the per-launch traffic.
-ENC_DRAM_BYTES_PER_PAIR = {"bf16": (317.457152e6 + 128.659200e6) / 154924,
-                           "fp8": (317.384704e6 + 63.287552e6) / 154924}
+ENC_DRAM_BYTES_PER_PAIR = {"bf16": (317.428992e6 + 128.546048e6) / 154924,
+                           "fp8": (317.391104e6 + 63.572480e6) / 154924}
+# the same for the head kernel (same capture)
+HEAD_DRAM_BYTES_PER_PAIR = {"bf16": (164.734464e6 + 4.893440e6) / 154924,
+                            "fp8": (85.178368e6 + 2.168832e6) / 154924}
 WEIGHTS = os.path.join(ROOT, "paper_2304_09439_b300", "weights", "locc_trained.bin")
 
 
@@ -511,6 +514,8 @@ def main():
             bound, peak_src = "tensor", f"{src} bf16_tflops_sustained" + \
                 (" x 2 (fp8/bf16 nominal ratio)" if args.precision == "fp8" else "")
         achieved = FLOP_ENC * per_step_pairs / (enc_ms * 1e-3) / 1e12
+        head_ms = stage[3] / args.steps
+        achieved_head = FLOP_HEAD * per_step_pairs / (head_ms * 1e-3) / 1e12
         cpu = cpu_geo = None
         if not args.no_cpu_baseline and world == 1:
             cpu = cpu_baseline(lib, scenes[0])
@@ -544,6 +549,15 @@ def main():
                          "traffic_unit": "bytes per launch (ncu dram read+write per pair x pairs)",
                          "peak_source": peak_src,
                          "algorithmic": f"{FLOP_ENC} FLOP per pair x pairs per launch"},
+            # the head GEMMs on their own (the second tensor-core kernel)
+            "roofline_head": {"kernel": "head", "bound": bound, "achieved": achieved_head,
+                              "peak": peak, "unit": "TFLOP/s", "frac": achieved_head / peak,
+                              "traffic": (HEAD_DRAM_BYTES_PER_PAIR[args.precision] * per_step_pairs
+                                          if args.precision in HEAD_DRAM_BYTES_PER_PAIR else None),
+                              "traffic_unit": "bytes per launch (ncu dram read+write per pair x "
+                                              "pairs)",
+                              "peak_source": peak_src,
+                              "algorithmic": f"{FLOP_HEAD} FLOP per pair x pairs per launch"},
             "e2e": {"value": e2e_pairs_all / e2e_max, "unit": "pairs/s",
                     "h2d_bytes_per_step": h2d // args.steps, "d2h_bytes_per_step": d2h // args.steps},
             "gpu_launches": launches_per_step * args.steps,

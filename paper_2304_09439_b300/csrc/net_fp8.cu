@@ -120,13 +120,13 @@ __device__ __forceinline__ void pool8(uint32_t taddr, int cntA, int cntB, float*
 
 // Pooled feature k of pair p (rel = p - first pair of the launch): float32
 // [P][512] when feat is given, and always e4m3 of v / s_k (the head's input
-// scale) in the head's operand layout -- tiles of 128 pairs, each 4 K-chunks
-// of 128 features, K-major (16 KB per chunk) -- for bulk copies into the head.
+// scale) in the head's operand layout -- tiles of 128 pairs, each 8 K-chunks
+// of 64 features, K-major (8 KB per chunk) -- for bulk copies into the head.
 __device__ __forceinline__ void put_feat8(float* feat, unsigned char* ftile, int p, int rel, int k,
                                           float v, float inv_s) {
   if (feat) feat[(size_t)p * 512 + k] = v;
-  unsigned char* t = ftile + (size_t)(rel >> 7) * (128 * 512) + (size_t)(k >> 7) * (128 * 128);
-  t[kmajor_off8(rel & 127, k & 127, 128)] = (unsigned char)(pack_e4m3x4(v * inv_s, 0.f, 0.f, 0.f) & 0xffu);
+  unsigned char* t = ftile + (size_t)(rel >> 7) * (128 * 512) + (size_t)(k >> 6) * (128 * 64);
+  t[kmajor_off8(rel & 127, k & 63, 64)] = (unsigned char)(pack_e4m3x4(v * inv_s, 0.f, 0.f, 0.f) & 0xffu);
 }
 
 __global__ void __launch_bounds__(F_THREADS, 1)
@@ -182,74 +182,90 @@ __global__ void __launch_bounds__(F_THREADS, 1)
   const float* fin = b3 + 256;
 
   if (warp == MMA_WARP) {
+    // MMA issuer + TMA producer warp: warp-uniform control flow, copies by
+    // lane 0, MMAs by an elected lane
+    const uint32_t sW1 = smem_u32(smem + F_W1), sW2 = smem_u32(smem + F_W2);
+    const uint32_t sW3 = smem_u32(smem + F_W3);
     if (lane == 0) {
-      const uint32_t sW1 = smem_u32(smem + F_W1), sW2 = smem_u32(smem + F_W2);
-      const uint32_t sW3 = smem_u32(smem + F_W3);
       mbar_expect_tx(BAR(B_W), F_IMG_BYTES);
       for (int off = 0; off < F_IMG_BYTES; off += 32768)
         bulk_g2s(smem_u32(smem + off), img + off, min(32768, F_IMG_BYTES - off), BAR(B_W));
-      int issued[NSLOT] = {};
-      auto load_pair = [&](int i) {
-        const int s = i % NSLOT;
-        const int p = lo + blockIdx.x + i * gridDim.x;
+    }
+    int issued[NSLOT] = {};
+    auto load_pair = [&](int i) {
+      const int s = i % NSLOT;
+      const int p = lo + blockIdx.x + i * gridDim.x;
+      if (lane == 0) {
         mbar_expect_tx(BAR(B_FULLX + s), ROWS * 16);
         bulk_g2s(smem_u32(smem + F_SLOT0 + s * F_SLOT_BYTES + FS_STG), xyz + (size_t)p * ROWS,
                  ROWS * 16, BAR(B_FULLX + s));
-        ++issued[s];
-      };
-      for (int i = 0; i < NSLOT && i < my_pairs; ++i) load_pair(i);
-      bool ok = mbar_wait_or_abort(BAR(B_W), 0, abort, WAIT_CYCLES);
-      tc_fence_after();
-      const uint32_t id64 = idesc_bf16(128, 64), id128 = idesc_e4m3(128, 128);
-      for (int r = 0; ok && NSLOT * r < my_pairs; ++r) {
-        const uint32_t ph = r & 1;
-        const int ns = min(NSLOT, my_pairs - NSLOT * r);
-        for (int s = 0; s < ns && ok; ++s) {
-          if (!(ok = mbar_wait_or_abort(BAR(B_XRDY + s), ph, abort, WAIT_CYCLES))) break;
-          tc_fence_after();
-          const int i = NSLOT * r + s;
-          if (i + NSLOT < my_pairs) load_pair(i + NSLOT);
-          const uint32_t sX = smem_u32(smem + F_SLOT0 + s * F_SLOT_BYTES + FS_OPD);
+      }
+      ++issued[s];
+    };
+    for (int i = 0; i < NSLOT && i < my_pairs; ++i) load_pair(i);
+    bool ok = mbar_wait_warp(BAR(B_W), 0, abort, WAIT_CYCLES);
+    tc_fence_after();
+    const uint32_t id64 = idesc_bf16(128, 64), id128 = idesc_e4m3(128, 128);
+    for (int r = 0; ok && NSLOT * r < my_pairs; ++r) {
+      const uint32_t ph = r & 1;
+      const int ns = min(NSLOT, my_pairs - NSLOT * r);
+      for (int s = 0; s < ns && ok; ++s) {
+        if (!(ok = mbar_wait_warp(BAR(B_XRDY + s), ph, abort, WAIT_CYCLES))) break;
+        tc_fence_after();
+        const int i = NSLOT * r + s;
+        if (i + NSLOT < my_pairs) load_pair(i + NSLOT);
+        const uint32_t sX = smem_u32(smem + F_SLOT0 + s * F_SLOT_BYTES + FS_OPD);
+        if (elect_one()) {
           mma_bf16(tbase + s * SLOT_COLS, sdesc(sX, 128, 256), sdesc(sW1, 128, 256), id64, 0);
           mma_commit(BAR(B_D1 + s));
         }
-        for (int s = 0; s < ns && ok; ++s) {
-          if (!(ok = mbar_wait_or_abort(BAR(B_H1RDY + s), ph, abort, WAIT_CYCLES))) break;
-          tc_fence_after();
-          const uint32_t sH = smem_u32(smem + F_SLOT0 + s * F_SLOT_BYTES + FS_OPD);
+        __syncwarp();
+      }
+      for (int s = 0; s < ns && ok; ++s) {
+        if (!(ok = mbar_wait_warp(BAR(B_H1RDY + s), ph, abort, WAIT_CYCLES))) break;
+        tc_fence_after();
+        const uint32_t sH = smem_u32(smem + F_SLOT0 + s * F_SLOT_BYTES + FS_OPD);
+        if (elect_one()) {
 #pragma unroll
           for (int kk = 0; kk < 2; ++kk)
             mma_e4m3(tbase + s * SLOT_COLS, sdesc(sH + 256 * kk, 128, 512),
                      sdesc(sW2 + 256 * kk, 128, 512), id128, kk > 0);
           mma_commit(BAR(B_D2 + s));
         }
-        for (int s = 0; s < ns && ok; ++s) {
-          if (!(ok = mbar_wait_or_abort(BAR(B_H2RDY + s), ph, abort, WAIT_CYCLES))) break;
-          tc_fence_after();
-          const uint32_t sH = smem_u32(smem + F_SLOT0 + s * F_SLOT_BYTES + FS_OPD);
+        __syncwarp();
+      }
+      for (int s = 0; s < ns && ok; ++s) {
+        if (!(ok = mbar_wait_warp(BAR(B_H2RDY + s), ph, abort, WAIT_CYCLES))) break;
+        tc_fence_after();
+        const uint32_t sH = smem_u32(smem + F_SLOT0 + s * F_SLOT_BYTES + FS_OPD);
+        if (elect_one()) {
 #pragma unroll
           for (int kk = 0; kk < 4; ++kk)
             mma_e4m3(tbase + s * SLOT_COLS, sdesc(sW3 + 256 * kk, 128, 1024),
                      sdesc(sH + 256 * kk, 128, 1024), id128, kk > 0);
           mma_commit(BAR(B_D3A + s));
         }
-        for (int s = 0; s < ns && ok; ++s) {
-          if (!(ok = mbar_wait_or_abort(BAR(B_E3A + s), ph, abort, WAIT_CYCLES))) break;
-          tc_fence_after();
-          const uint32_t sH = smem_u32(smem + F_SLOT0 + s * F_SLOT_BYTES + FS_OPD);
+        __syncwarp();
+      }
+      for (int s = 0; s < ns && ok; ++s) {
+        if (!(ok = mbar_wait_warp(BAR(B_E3A + s), ph, abort, WAIT_CYCLES))) break;
+        tc_fence_after();
+        const uint32_t sH = smem_u32(smem + F_SLOT0 + s * F_SLOT_BYTES + FS_OPD);
+        if (elect_one()) {
 #pragma unroll
           for (int kk = 0; kk < 4; ++kk)
             mma_e4m3(tbase + s * SLOT_COLS, sdesc(sW3 + 16384 + 256 * kk, 128, 1024),
                      sdesc(sH + 256 * kk, 128, 1024), id128, kk > 0);
           mma_commit(BAR(B_D3B + s));
         }
+        __syncwarp();
       }
-      if (*abort) {
-        mma_commit(BAR(B_DRAIN));
-        mbar_wait(BAR(B_DRAIN), 0, WAIT_CYCLES);
-        for (int s = 0; s < NSLOT; ++s)
-          if (issued[s] > 0) mbar_wait(BAR(B_FULLX + s), (issued[s] - 1) & 1, WAIT_CYCLES);
-      }
+    }
+    if (__any_sync(0xffffffffu, *abort) && elect_one()) {
+      mma_commit(BAR(B_DRAIN));
+      mbar_wait(BAR(B_DRAIN), 0, WAIT_CYCLES);
+      for (int s = 0; s < NSLOT; ++s)
+        if (issued[s] > 0) mbar_wait(BAR(B_FULLX + s), (issued[s] - 1) & 1, WAIT_CYCLES);
     }
     __syncwarp();
   } else {
@@ -355,18 +371,21 @@ constexpr int G_W3 = 0;                  // Wh3' [16 x 256] e4m3 (rows 8.. zero)
 constexpr int G_EP = G_W3 + 16 * 256;    // f_inv [256], a4 c4 [256], a5 c5 [256], w6 hb3 [16]
 constexpr int G_RES_BYTES = G_EP + (5 * 256 + 2 * 16) * 4;
 static_assert(G_RES_BYTES % 128 == 0, "fp8 head resident image");
-constexpr int G_CHUNK = 256 * 128;       // one B chunk [256 x 128] e4m3, 32 KB
-constexpr int G_IMG_W1 = G_RES_BYTES;    // 4 chunks
-constexpr int G_IMG_W2 = G_IMG_W1 + 4 * G_CHUNK;  // 2 chunks
-constexpr int G_IMG_BYTES = G_IMG_W2 + 2 * G_CHUNK;
-constexpr int G_ACHUNK = 128 * 128;                       // one A (feature) chunk, e4m3
-constexpr int G_NST = 3;                                   // operand stages
-constexpr int G_A0 = (G_RES_BYTES + 1023) / 1024 * 1024;  // A stages [128 x 128] e4m3, 16 KB each
-constexpr int G_B0 = G_A0 + G_NST * G_ACHUNK;              // B stages, 32 KB each
+constexpr int GK = 64;                    // K of one streamed chunk (bytes per row)
+constexpr int G_CHUNK = 256 * GK;        // one B chunk [256 x 64] e4m3, 16 KB
+constexpr int G_L1C = 512 / GK, G_NCH = G_L1C + 256 / GK;  // chunks per tile: 8 + 4
+constexpr int G_IMG_W1 = G_RES_BYTES;    // 8 chunks
+constexpr int G_IMG_W2 = G_IMG_W1 + G_L1C * G_CHUNK;  // 4 chunks
+constexpr int G_IMG_BYTES = G_IMG_W2 + (G_NCH - G_L1C) * G_CHUNK;
+constexpr int G_ACHUNK = 128 * GK;                        // one A (feature) chunk, e4m3, 8 KB
+constexpr int G_NST = 6;                                   // operand stages
+constexpr int G_A0 = (G_RES_BYTES + 1023) / 1024 * 1024;  // A stages [128 x 64] e4m3
+constexpr int G_B0 = G_A0 + G_NST * G_ACHUNK;              // B stages [256 x 64] e4m3
 constexpr int G_G = G_B0 + G_NST * G_CHUNK;                // G [128 x 256] e4m3, 32 KB
 constexpr int G_CTRL = G_G + 128 * 256;                    // mbarriers, TMEM address, abort
-constexpr int G_SMEM = G_CTRL + 128;
-constexpr int G_THREADS = 288;  // 8 epilogue warps + the producer warp
+constexpr int G_SMEM = G_CTRL + 256;
+constexpr int G_THREADS = 320;  // 8 epilogue warps, the copy warp, the MMA warp
+constexpr int G_COPY = 256, G_MMA_WARP = 9;
 static_assert(G_RES_BYTES % 16 == 0 && G_IMG_W1 % 16 == 0, "bulk copies need 16-byte chunks");
 static_assert(G_SMEM <= 227 * 1024, "fp8 head shared memory");
 
@@ -382,10 +401,13 @@ __device__ __forceinline__ void head_epi_fp8(uint32_t taddr, const float* alpha,
   }
 }
 
-// Same stream as the BF16 head (producer warp 8 feeding three operand stages
-// by bulk copy across tiles; epilogue warps 0-7) over 6 K-chunks of 128 per
-// tile: 4 of W_h1 against the e4m3 features the encoder wrote in operand
-// layout, 2 of W_h2 against G.
+// Same schedule as the BF16 head (a copy thread in warp 8 streaming operand
+// chunks through G_NST stages by bulk copy, an MMA thread in warp 9, layer 3
+// of tile t deferred behind the layer-1 MMAs of tile t + 1; epilogue warps
+// 0-7) over 12 K-chunks of 64 per tile: 8 of W_h1 against the e4m3 features
+// the encoder wrote in operand layout, 4 of W_h2 against G.  The layer-1
+// epilogue fills G in four 64-column chunks (mbarriers GC0-GC3); layer-2 chunk
+// j starts once G chunk j is ready.
 __global__ void __launch_bounds__(G_THREADS, 1)
     head_fp8_kernel(const unsigned char* __restrict__ ftile, PairRange rg,
                     const unsigned char* __restrict__ img, PairInputs in, int have_in,
@@ -398,21 +420,21 @@ __global__ void __launch_bounds__(G_THREADS, 1)
   const int n_tiles = (n - lo + HT - 1) / HT;
   if ((int)blockIdx.x >= n_tiles) return;
   const int my_tiles = (n_tiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
-  // mbarriers: [0, 3) operands of stage s landed; [3, 6) MMAs of stage s done;
-  // 6 layer 3 done; 7 epilogue progress (3 per tile); 8 resident image;
-  // 9 drain; 10 / 11 layer 1 / layer 2 of the tile done
+  // mbarriers: [0, 6) operands of stage s landed; [6, 12) MMAs of stage s
+  // done; 12 layer 3 done; 13 EPI (two per tile: G holds layer 2; outputs
+  // left TMEM); 14 resident image; 15 drain; 16 / 17 layer 1 / layer 2 of the
+  // tile done; [18, 22) G chunk k holds layer 1
   const uint32_t bar0 = smem_u32(smem + G_CTRL);
-  const uint32_t B_L3 = bar0 + 48, B_EPI = bar0 + 56, B_RES = bar0 + 64, B_DRAIN = bar0 + 72;
-  const uint32_t B_L1D = bar0 + 80, B_L2D = bar0 + 88;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + G_CTRL + 96);
-  volatile int* abort = reinterpret_cast<volatile int*>(smem + G_CTRL + 100);
+  const uint32_t B_FULL = bar0, B_DONE = bar0 + 48;
+  const uint32_t B_L3 = bar0 + 96, B_EPI = bar0 + 104, B_RES = bar0 + 112, B_DRAIN = bar0 + 120;
+  const uint32_t B_L1D = bar0 + 128, B_L2D = bar0 + 136, B_GC = bar0 + 144;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + G_CTRL + 192);
+  volatile int* abort = reinterpret_cast<volatile int*>(smem + G_CTRL + 196);
+  int* s_issued = reinterpret_cast<int*>(smem + G_CTRL + 200);
   if (tid == 0) {
-    for (int i = 0; i < 8; ++i) mbar_init(bar0 + 8 * i, i == 7 ? 256 : 1);
-    mbar_init(B_RES, 1);
-    mbar_init(B_DRAIN, 1);
-    mbar_init(B_L1D, 1);
-    mbar_init(B_L2D, 1);
+    for (int i = 0; i < 22; ++i) mbar_init(bar0 + 8 * i, (i == 13 || i >= 18) ? 256 : 1);
     *abort = 0;
+    *s_issued = 0;
     fence_mbar_init();
   }
   if (warp == 0) {
@@ -437,76 +459,101 @@ __global__ void __launch_bounds__(G_THREADS, 1)
   unsigned char* G = smem + G_G;
   const uint32_t sG = smem_u32(G), sW3 = smem_u32(smem + G_W3);
   const uint32_t id256 = idesc_e4m3(128, 256), id16 = idesc_e4m3(128, 16);
-  const int n_chunks = 6 * my_tiles;  // this CTA's chunk stream
+  const int n_chunks = G_NCH * my_tiles;  // this CTA's chunk stream
   bool ok = true;
-  int g_issued = 0;
 
-  if (tid == 256) {
+  if (tid == G_COPY) {
     mbar_expect_tx(B_RES, G_RES_BYTES);
     bulk_g2s(smem_u32(smem), img, G_RES_BYTES, B_RES);
-    auto issue = [&](int g) {
-      const int st = g % G_NST, c = g % 6;
-      const int tile = (int)blockIdx.x + (g / 6) * (int)gridDim.x;
-      const uint32_t bw = bar0 + 8 * st;
-      if (c < 4) {
-        mbar_expect_tx(bw, G_ACHUNK + G_CHUNK);
+    for (int g = 0; g < n_chunks; ++g) {
+      const int st = g % G_NST, c = g % G_NCH;
+      if (g >= G_NST &&
+          !(ok = mbar_wait_or_abort(B_DONE + 8 * st, (g / G_NST - 1) & 1, abort, WAIT_CYCLES)))
+        break;
+      const int tile = (int)blockIdx.x + (g / G_NCH) * (int)gridDim.x;
+      const uint32_t bf = B_FULL + 8 * st;
+      if (c < G_L1C) {
+        mbar_expect_tx(bf, G_ACHUNK + G_CHUNK);
         bulk_g2s(smem_u32(smem + G_A0 + st * G_ACHUNK),
-                 ftile + (size_t)tile * (128 * 512) + (size_t)c * G_ACHUNK, G_ACHUNK, bw);
+                 ftile + (size_t)tile * (128 * 512) + (size_t)c * G_ACHUNK, G_ACHUNK, bf);
         bulk_g2s(smem_u32(smem + G_B0 + st * G_CHUNK), img + G_IMG_W1 + (size_t)c * G_CHUNK,
-                 G_CHUNK, bw);
+                 G_CHUNK, bf);
       } else {
-        mbar_expect_tx(bw, G_CHUNK);
-        bulk_g2s(smem_u32(smem + G_B0 + st * G_CHUNK), img + G_IMG_W2 + (size_t)(c - 4) * G_CHUNK,
-                 G_CHUNK, bw);
+        mbar_expect_tx(bf, G_CHUNK);
+        bulk_g2s(smem_u32(smem + G_B0 + st * G_CHUNK),
+                 img + G_IMG_W2 + (size_t)(c - G_L1C) * G_CHUNK, G_CHUNK, bf);
       }
-      g_issued = g + 1;
-    };
-    for (int g = 0; g < 2 && g < n_chunks; ++g) issue(g);
-    ok = mbar_wait_or_abort(B_RES, 0, abort, WAIT_CYCLES);
-    for (int g = 0; g < n_chunks && ok; ++g) {
-      const int st = g % G_NST, c = g % 6, t = g / 6;
-      if (g + 2 < n_chunks) {
-        if (g >= 1)
-          ok = mbar_wait_or_abort(bar0 + 24 + 8 * ((g - 1) % G_NST), ((g - 1) / G_NST) & 1, abort,
-                                  WAIT_CYCLES);
-        if (!ok) break;
-        issue(g + 2);
-      }
-      // layer 2 of tile t: the previous tile's outputs have left TMEM (they sit
-      // in the layer-2 columns) and G holds layer 1 of tile t; the EPI phases
-      // are waited one after the other, never skipping one
-      if (c == 4 && t > 0) ok = mbar_wait_or_abort(B_EPI, (3 * t - 1) & 1, abort, WAIT_CYCLES);
-      if (c == 4) ok = ok && mbar_wait_or_abort(B_EPI, (3 * t) & 1, abort, WAIT_CYCLES);
-      ok = ok && mbar_wait_or_abort(bar0 + 8 * st, (g / G_NST) & 1, abort, WAIT_CYCLES);
-      if (!ok) break;
+      *s_issued = g + 1;
+    }
+    if (!ok) *abort = 1;
+  } else if (warp == G_MMA_WARP) {
+    // layer 3: D3[128 x 16] = G . Wh3'^T (rows 8..15 zero), in the layer-2 columns
+    auto layer3 = [&]() {
       tc_fence_after();
-      const uint32_t sA = smem_u32(smem + G_A0 + st * G_ACHUNK);
-      const uint32_t sB = smem_u32(smem + G_B0 + st * G_CHUNK);
-      if (c < 4) {
-#pragma unroll
-        for (int kk = 0; kk < 4; ++kk)
-          mma_e4m3(tbase + 0, sdesc(sA + 256 * kk, 128, 1024), sdesc(sB + 256 * kk, 128, 1024), id256,
-                   (c > 0 || kk > 0) ? 1u : 0u);
-      } else {
-#pragma unroll
-        for (int kk = 0; kk < 4; ++kk)
-          mma_e4m3(tbase + 256, sdesc(sG + 1024 * (c - 4) + 256 * kk, 128, 2048),
-                   sdesc(sB + 256 * kk, 128, 1024), id256, (c > 4 || kk > 0) ? 1u : 0u);
-      }
-      mma_commit(bar0 + 24 + 8 * st);
-      if (c == 3) mma_commit(B_L1D);
-      if (c == 5) {
-        mma_commit(B_L2D);
-        // layer 3 once G holds layer 2: D3[128 x 16] = G . Wh3'^T (rows 8..15 zero)
-        ok = mbar_wait_or_abort(B_EPI, (3 * t + 1) & 1, abort, WAIT_CYCLES);
-        if (!ok) break;
-        tc_fence_after();
+      if (elect_one()) {
 #pragma unroll
         for (int kk = 0; kk < 8; ++kk)
           mma_e4m3(tbase + 256, sdesc(sG + 256 * kk, 128, 2048), sdesc(sW3 + 256 * kk, 128, 2048),
                    id16, kk > 0);
         mma_commit(B_L3);
       }
+      __syncwarp();
+    };
+    ok = mbar_wait_warp(B_RES, 0, abort, WAIT_CYCLES);
+    int l3 = -1;  // tile whose layer 3 waits for its layer-2 epilogue
+    // two chunks (four MMAs) per step, so that the per-step waits cost less
+    // than the tensor work they gate
+    for (int g = 0; g < n_chunks && ok; g += 2) {
+      const int st0 = g % G_NST, st1 = (g + 1) % G_NST, c = g % G_NCH, t = g / G_NCH;
+      if (l3 >= 0) {
+        // EPI phase 2 l3: G holds layer 2 of tile l3.  Layer 2 of the next
+        // tile needs its outputs out of TMEM, so by then it is waited for.
+        if (c == G_L1C) {
+          ok = mbar_wait_warp(B_EPI, (2 * l3) & 1, abort, WAIT_CYCLES);
+          if (!ok) break;
+        }
+        if (c == G_L1C || __all_sync(0xffffffffu, mbar_test_wait(B_EPI, (2 * l3) & 1))) {
+          layer3();
+          l3 = -1;
+        }
+      }
+      const bool l1 = c < G_L1C;
+      const int j = c - G_L1C;  // layer-2 chunk (even)
+      if (!l1) {
+        // the previous tile's outputs have left the layer-2 columns (EPI
+        // phase 2 t - 1), and G chunks j and j + 1 (64 columns each) hold
+        // layer 1
+        if (j == 0 && t > 0) ok = mbar_wait_warp(B_EPI, (2 * t - 1) & 1, abort, WAIT_CYCLES);
+        ok = ok && mbar_wait_warp(B_GC + 8 * j, t & 1, abort, WAIT_CYCLES);
+        ok = ok && mbar_wait_warp(B_GC + 8 * (j + 1), t & 1, abort, WAIT_CYCLES);
+      }
+      ok = ok && mbar_wait_warp(B_FULL + 8 * st0, (g / G_NST) & 1, abort, WAIT_CYCLES);
+      ok = ok && mbar_wait_warp(B_FULL + 8 * st1, ((g + 1) / G_NST) & 1, abort, WAIT_CYCLES);
+      if (!ok) break;
+      tc_fence_after();
+      // descriptors from warp-uniform values; one elected lane issues
+      const uint32_t sB0 = smem_u32(smem + G_B0 + st0 * G_CHUNK);
+      const uint32_t sB1 = smem_u32(smem + G_B0 + st1 * G_CHUNK);
+      const uint32_t sA0 = l1 ? smem_u32(smem + G_A0 + st0 * G_ACHUNK) : sG + 512 * j;
+      const uint32_t sA1 = l1 ? smem_u32(smem + G_A0 + st1 * G_ACHUNK) : sG + 512 * (j + 1);
+      const uint32_t dcol = l1 ? 0u : 256u, sbo = l1 ? 512u : 2048u;
+      const uint32_t acc0 = (l1 ? c : j) > 0 ? 1u : 0u;
+      if (elect_one()) {
+        mma_e4m3(tbase + dcol, sdesc(sA0, 128, sbo), sdesc(sB0, 128, 512), id256, acc0);
+        mma_e4m3(tbase + dcol, sdesc(sA0 + 256, 128, sbo), sdesc(sB0 + 256, 128, 512), id256, 1u);
+        mma_commit(B_DONE + 8 * st0);
+        mma_e4m3(tbase + dcol, sdesc(sA1, 128, sbo), sdesc(sB1, 128, 512), id256, 1u);
+        mma_e4m3(tbase + dcol, sdesc(sA1 + 256, 128, sbo), sdesc(sB1 + 256, 128, 512), id256, 1u);
+        mma_commit(B_DONE + 8 * st1);
+        if (c + 1 == G_L1C - 1) mma_commit(B_L1D);
+        if (c + 1 == G_NCH - 1) mma_commit(B_L2D);
+      }
+      __syncwarp();
+      if (c + 1 == G_NCH - 1) l3 = t;
+    }
+    if (ok && l3 >= 0) {
+      ok = mbar_wait_warp(B_EPI, (2 * l3) & 1, abort, WAIT_CYCLES);
+      if (ok) layer3();
     }
     if (!ok) *abort = 1;
   }
@@ -514,13 +561,29 @@ __global__ void __launch_bounds__(G_THREADS, 1)
   for (int t = 0; tid < 256 && t < my_tiles && ok; ++t) {
     const int pr = lo + ((int)blockIdx.x + t * (int)gridDim.x) * HT + row;
     const bool row_ok = pr < n;
+    bool geo = false;
+    float4 cc = make_float4(0.f, 0.f, 0.f, 0.f);
+    float pose[7];
+    if (half == 0 && row_ok && out) {
+      const int a = have_in ? in.pairs[2 * pr] : -1;
+      cc = centre[pr];
+      geo = a >= 0 && a < in.n_obj && !isnan(cc.x);
+#pragma unroll
+      for (int i = 0; i < 7; ++i) pose[i] = geo ? in.poses[7 * (size_t)a + i] : 0.f;
+    }
     ok = mbar_wait_or_abort(B_L1D, t & 1, abort, WAIT_CYCLES);
     if (!ok) break;
     tc_fence_after();
-    head_epi_fp8(tbase + lane_off + 128 * half, a4 + 128 * half, c4 + 128 * half, G, row, 128 * half);
-    fence_async_smem();
-    tc_fence_before();
-    mbar_arrive(B_EPI);
+#pragma unroll 1
+    for (int k = 0; k < 4; ++k) {
+      const int col = 64 * k + 32 * half;
+      float v[32];
+      tmem_ld32(tbase + lane_off + col, v);
+      epi_e4m3_32<256>(v, a4 + col, c4 + col, G, row, col);
+      fence_async_smem();
+      tc_fence_before();
+      mbar_arrive(B_GC + 8 * k);
+    }
     ok = mbar_wait_or_abort(B_L2D, t & 1, abort, WAIT_CYCLES);
     if (!ok) break;
     tc_fence_after();
@@ -545,10 +608,8 @@ __global__ void __launch_bounds__(G_THREADS, 1)
         }
         if (out) {
           float o8[8];
-          const int a = have_in ? in.pairs[2 * pr] : -1;
-          const float4 cc = centre[pr];
-          if (a >= 0 && a < in.n_obj && !isnan(cc.x)) {
-            epilogue_world(y, in.poses + 7 * (size_t)a, cc, o8);
+          if (geo) {
+            epilogue_world(y, pose, cc, o8);
           } else {
 #pragma unroll
             for (int o = 0; o < 8; ++o) o8[o] = __int_as_float(0x7fc00000);
@@ -562,13 +623,19 @@ __global__ void __launch_bounds__(G_THREADS, 1)
     mbar_arrive(B_EPI);
   }
   __syncthreads();
-  if (tid == 256 && *abort) {
-    // drain: wait (bounded) for the producer's MMAs and bulk copies
-    atomicOr(err, 2);
-    mma_commit(B_DRAIN);
-    mbar_wait(B_DRAIN, 0, WAIT_CYCLES);
-    for (int g = g_issued - G_NST; g < g_issued; ++g)
-      if (g >= 0) mbar_wait(bar0 + 8 * (g % G_NST), (g / G_NST) & 1, WAIT_CYCLES);
+  if (*abort) {
+    // drain (bounded): the MMA thread waits for its MMAs, the copy thread for
+    // the copies it issued
+    if (tid == 0) atomicOr(err, 2);
+    if (warp == G_MMA_WARP && (tid & 31) == 0) {
+      mma_commit(B_DRAIN);
+      mbar_wait(B_DRAIN, 0, WAIT_CYCLES);
+    }
+    if (tid == G_COPY) {
+      const int issued = *s_issued;
+      for (int g = issued - G_NST; g < issued; ++g)
+        if (g >= 0) mbar_wait(B_FULL + 8 * (g % G_NST), (g / G_NST) & 1, WAIT_CYCLES);
+    }
   }
   tc_fence_before();
   __syncthreads();
@@ -719,8 +786,8 @@ int upload_fp8_params(locc_handle* h, const std::vector<float>& params) {
     unsigned char* dh = de + enc_bytes;
     quant_e4m3_kernel<<<128, 128>>>(d_fw + o2, d_fw + o2 + 128 * 64, 128, 64, 64, de + F_W2);
     quant_e4m3_kernel<<<256, 128>>>(d_fw + o3, d_fw + o3 + 256 * 128, 256, 128, 128, de + F_W3);
-    quant_e4m3_kernel<<<256, 128>>>(d_fw + o4, d_fw + o4 + 256 * 512, 256, 512, 128, dh + G_IMG_W1);
-    quant_e4m3_kernel<<<256, 128>>>(d_fw + o5, d_fw + o5 + 256 * 256, 256, 256, 128, dh + G_IMG_W2);
+    quant_e4m3_kernel<<<256, 128>>>(d_fw + o4, d_fw + o4 + 256 * 512, 256, 512, GK, dh + G_IMG_W1);
+    quant_e4m3_kernel<<<256, 128>>>(d_fw + o5, d_fw + o5 + 256 * 256, 256, 256, GK, dh + G_IMG_W2);
     quant_e4m3_kernel<<<8, 128>>>(d_fw + o6, d_fw + o6 + 8 * 256, 8, 256, 256, dh + G_W3);
     ok = cudaGetLastError() == cudaSuccess && cudaDeviceSynchronize() == cudaSuccess;
     h->wf8_enc = de;

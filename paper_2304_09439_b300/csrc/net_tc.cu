@@ -131,15 +131,15 @@ __device__ __forceinline__ void enc_pool(uint32_t taddr, int cntA, int cntB, flo
 
 // Pooled feature k of pair p (rel = p - first pair of the launch): float32
 // [P][512] when feat is given (the network's feature output), and always
-// bf16 in the head's operand layout -- tiles of 128 pairs, each 8 K-chunks of
-// 64 features in the K-major core-matrix layout (16 KB per chunk) -- so that
+// bf16 in the head's operand layout -- tiles of 128 pairs, each 16 K-chunks
+// of 32 features in the K-major core-matrix layout (8 KB per chunk) -- so that
 // the head loads A chunks with bulk copies.
 __device__ __forceinline__ void put_feat(float* feat, __nv_bfloat16* ftile, int p, int rel, int k,
                                          float v) {
   if (feat) feat[(size_t)p * 512 + k] = v;
   unsigned char* t = reinterpret_cast<unsigned char*>(ftile) + (size_t)(rel >> 7) * (128 * 512 * 2) +
-                     (size_t)(k >> 6) * (128 * 64 * 2);
-  *reinterpret_cast<__nv_bfloat16*>(t + kmajor_off(rel & 127, k & 63, 64)) = __float2bfloat16_rn(v);
+                     (size_t)(k >> 5) * (128 * 32 * 2);
+  *reinterpret_cast<__nv_bfloat16*>(t + kmajor_off(rel & 127, k & 31, 32)) = __float2bfloat16_rn(v);
 }
 
 __global__ void __launch_bounds__(E_THREADS, 1)
@@ -191,83 +191,98 @@ __global__ void __launch_bounds__(E_THREADS, 1)
   const float* b3 = b2 + 128;
 
   if (warp == MMA_WARP) {
-    // ------------------------------------------------ MMA issuer + TMA producer
+    // ------------------------------------------ MMA issuer + TMA producer warp
+    // (warp-uniform control flow; copies by lane 0, MMAs by an elected lane)
+    const uint32_t sW1 = smem_u32(smem + E_W1), sW2 = smem_u32(smem + E_W2);
+    const uint32_t sW3 = smem_u32(smem + E_W3);
+    // resident weights, in bulk copies of at most 32 KB
     if (lane == 0) {
-      const uint32_t sW1 = smem_u32(smem + E_W1), sW2 = smem_u32(smem + E_W2);
-      const uint32_t sW3 = smem_u32(smem + E_W3);
-      // resident weights, in bulk copies of at most 32 KB
       mbar_expect_tx(BAR(B_W), E_IMG_BYTES);
       for (int off = 0; off < E_IMG_BYTES; off += 32768) {
         const int bytes = min(32768, E_IMG_BYTES - off);
         bulk_g2s(smem_u32(smem + off), img + off, bytes, BAR(B_W));
       }
-      int issued[NSLOT] = {};
-      auto load_pair = [&](int i) {
-        const int s = i % NSLOT;
-        const int p = lo + blockIdx.x + i * gridDim.x;
+    }
+    int issued[NSLOT] = {};
+    auto load_pair = [&](int i) {
+      const int s = i % NSLOT;
+      const int p = lo + blockIdx.x + i * gridDim.x;
+      if (lane == 0) {
         mbar_expect_tx(BAR(B_FULLX + s), ROWS * 16);
         bulk_g2s(smem_u32(smem + E_SLOT0 + s * SLOT_BYTES + S_STG), xyz + (size_t)p * ROWS,
                  ROWS * 16, BAR(B_FULLX + s));
-        ++issued[s];
-      };
-      for (int i = 0; i < NSLOT && i < my_pairs; ++i) load_pair(i);
-      bool ok = mbar_wait_or_abort(BAR(B_W), 0, abort, WAIT_CYCLES);
-      tc_fence_after();
-      const uint32_t id64 = idesc_bf16(128, 64), id128 = idesc_bf16(128, 128);
-      for (int r = 0; ok && NSLOT * r < my_pairs; ++r) {
-        const uint32_t ph = r & 1;
-        const int ns = min(NSLOT, my_pairs - NSLOT * r);  // slots in use this round
-        // layer 1: D1[128 x 64] = X[128 x 16] . W1img^T
-        for (int s = 0; s < ns && ok; ++s) {
-          if (!(ok = mbar_wait_or_abort(BAR(B_XRDY + s), ph, abort, WAIT_CYCLES))) break;
-          tc_fence_after();
-          const int i = NSLOT * r + s;
-          if (i + NSLOT < my_pairs) load_pair(i + NSLOT);  // staging rows of slot s are free
-          const uint32_t sX = smem_u32(smem + E_SLOT0 + s * SLOT_BYTES + S_OPD);
+      }
+      ++issued[s];
+    };
+    for (int i = 0; i < NSLOT && i < my_pairs; ++i) load_pair(i);
+    bool ok = mbar_wait_warp(BAR(B_W), 0, abort, WAIT_CYCLES);
+    tc_fence_after();
+    const uint32_t id64 = idesc_bf16(128, 64), id128 = idesc_bf16(128, 128);
+    for (int r = 0; ok && NSLOT * r < my_pairs; ++r) {
+      const uint32_t ph = r & 1;
+      const int ns = min(NSLOT, my_pairs - NSLOT * r);  // slots in use this round
+      // layer 1: D1[128 x 64] = X[128 x 16] . W1img^T
+      for (int s = 0; s < ns && ok; ++s) {
+        if (!(ok = mbar_wait_warp(BAR(B_XRDY + s), ph, abort, WAIT_CYCLES))) break;
+        tc_fence_after();
+        const int i = NSLOT * r + s;
+        if (i + NSLOT < my_pairs) load_pair(i + NSLOT);  // staging rows of slot s are free
+        const uint32_t sX = smem_u32(smem + E_SLOT0 + s * SLOT_BYTES + S_OPD);
+        if (elect_one()) {
           mma_bf16(tbase + s * SLOT_COLS, sdesc(sX, 128, 256), sdesc(sW1, 128, 256), id64, 0);
           mma_commit(BAR(B_D1 + s));
         }
-        // layer 2: D2[128 x 128] = H1[128 x 64] . W2img^T
-        for (int s = 0; s < ns && ok; ++s) {
-          if (!(ok = mbar_wait_or_abort(BAR(B_H1RDY + s), ph, abort, WAIT_CYCLES))) break;
-          tc_fence_after();
-          const uint32_t sH = smem_u32(smem + E_SLOT0 + s * SLOT_BYTES + S_OPD);
+        __syncwarp();
+      }
+      // layer 2: D2[128 x 128] = H1[128 x 64] . W2img^T
+      for (int s = 0; s < ns && ok; ++s) {
+        if (!(ok = mbar_wait_warp(BAR(B_H1RDY + s), ph, abort, WAIT_CYCLES))) break;
+        tc_fence_after();
+        const uint32_t sH = smem_u32(smem + E_SLOT0 + s * SLOT_BYTES + S_OPD);
+        if (elect_one()) {
 #pragma unroll
           for (int kk = 0; kk < 4; ++kk)
             mma_bf16(tbase + s * SLOT_COLS, sdesc(sH + 256 * kk, 128, 1024),
                      sdesc(sW2 + 256 * kk, 128, 1024), id128, kk > 0);
           mma_commit(BAR(B_D2 + s));
         }
-        // layer 3, half 0 (channels 0..127), transposed: D3^T = W3img[0:128] . H2^T
-        for (int s = 0; s < ns && ok; ++s) {
-          if (!(ok = mbar_wait_or_abort(BAR(B_H2RDY + s), ph, abort, WAIT_CYCLES))) break;
-          tc_fence_after();
-          const uint32_t sH = smem_u32(smem + E_SLOT0 + s * SLOT_BYTES + S_OPD);
+        __syncwarp();
+      }
+      // layer 3, half 0 (channels 0..127), transposed: D3^T = W3img[0:128] . H2^T
+      for (int s = 0; s < ns && ok; ++s) {
+        if (!(ok = mbar_wait_warp(BAR(B_H2RDY + s), ph, abort, WAIT_CYCLES))) break;
+        tc_fence_after();
+        const uint32_t sH = smem_u32(smem + E_SLOT0 + s * SLOT_BYTES + S_OPD);
+        if (elect_one()) {
 #pragma unroll
           for (int kk = 0; kk < 8; ++kk)
             mma_bf16(tbase + s * SLOT_COLS, sdesc(sW3 + 256 * kk, 128, 2048),
                      sdesc(sH + 256 * kk, 128, 2048), id128, kk > 0);
           mma_commit(BAR(B_D3A + s));
         }
-        // layer 3, half 1 (channels 128..255), once half 0 has been pooled
-        for (int s = 0; s < ns && ok; ++s) {
-          if (!(ok = mbar_wait_or_abort(BAR(B_E3A + s), ph, abort, WAIT_CYCLES))) break;
-          tc_fence_after();
-          const uint32_t sH = smem_u32(smem + E_SLOT0 + s * SLOT_BYTES + S_OPD);
+        __syncwarp();
+      }
+      // layer 3, half 1 (channels 128..255), once half 0 has been pooled
+      for (int s = 0; s < ns && ok; ++s) {
+        if (!(ok = mbar_wait_warp(BAR(B_E3A + s), ph, abort, WAIT_CYCLES))) break;
+        tc_fence_after();
+        const uint32_t sH = smem_u32(smem + E_SLOT0 + s * SLOT_BYTES + S_OPD);
+        if (elect_one()) {
 #pragma unroll
           for (int kk = 0; kk < 8; ++kk)
             mma_bf16(tbase + s * SLOT_COLS, sdesc(sW3 + 32768 + 256 * kk, 128, 2048),
                      sdesc(sH + 256 * kk, 128, 2048), id128, kk > 0);
           mma_commit(BAR(B_D3B + s));
         }
+        __syncwarp();
       }
-      if (*abort) {
-        // drain: wait (bounded) for every MMA and bulk copy this thread issued
-        mma_commit(BAR(B_DRAIN));
-        mbar_wait(BAR(B_DRAIN), 0, WAIT_CYCLES);
-        for (int s = 0; s < NSLOT; ++s)
-          if (issued[s] > 0) mbar_wait(BAR(B_FULLX + s), (issued[s] - 1) & 1, WAIT_CYCLES);
-      }
+    }
+    if (__any_sync(0xffffffffu, *abort) && elect_one()) {
+      // drain: wait (bounded) for every MMA and bulk copy this warp issued
+      mma_commit(BAR(B_DRAIN));
+      mbar_wait(BAR(B_DRAIN), 0, WAIT_CYCLES);
+      for (int s = 0; s < NSLOT; ++s)
+        if (issued[s] > 0) mbar_wait(BAR(B_FULLX + s), (issued[s] - 1) & 1, WAIT_CYCLES);
     }
     __syncwarp();
   } else {
@@ -358,21 +373,41 @@ constexpr int HT = 128;                                   // pairs per tile
 constexpr int H_W3 = 0;                                    // [16 x 256] 8 KB
 constexpr int H_BIAS = H_W3 + 16 * 256 * 2;                // hb1 256, hb2 256, hb3 16
 constexpr int H_RES_BYTES = H_BIAS + (256 + 256 + 16) * 4; // resident part of the image
-constexpr int H_CHUNK = 256 * 64 * 2;                      // bytes of one B chunk
-constexpr int H_ACHUNK = 128 * 64 * 2;                     // bytes of one A (feature) chunk
-constexpr int H_NST = 3;                                   // operand stages
-constexpr int H_A0 = (H_RES_BYTES + 1023) / 1024 * 1024;   // A stages [128 x 64] 16 KB each
-constexpr int H_B0 = H_A0 + H_NST * H_ACHUNK;              // B stages [256 x 64] 32 KB each
+constexpr int HK = 32;                                     // K of one streamed chunk
+constexpr int H_CHUNK = 256 * HK * 2;                      // bytes of one B chunk [256 x 32]
+constexpr int H_ACHUNK = 128 * HK * 2;                     // bytes of one A (feature) chunk
+constexpr int H_NST = 6;                                   // operand stages
+constexpr int H_L1C = 512 / HK, H_NCH = H_L1C + 256 / HK;  // chunks per tile: 16 + 8
+constexpr int H_A0 = (H_RES_BYTES + 1023) / 1024 * 1024;   // A stages [128 x 32] 8 KB each
+constexpr int H_B0 = H_A0 + H_NST * H_ACHUNK;              // B stages [256 x 32] 16 KB each
 constexpr int H_G = H_B0 + H_NST * H_CHUNK;                // G [128 x 256] 64 KB
 constexpr int H_CTRL = H_G + 128 * 256 * 2;                // mbarriers, TMEM address, abort
-constexpr int H_SMEM = H_CTRL + 128;
-// global image: [resident][W_h1 chunks x 8][W_h2 chunks x 4]
+constexpr int H_SMEM = H_CTRL + 256;
+// global image: [resident][W_h1 chunks x 16][W_h2 chunks x 8]
 constexpr int H_IMG_W1 = (H_RES_BYTES + 127) / 128 * 128;
-constexpr int H_IMG_W2 = H_IMG_W1 + 8 * H_CHUNK;
-constexpr int H_IMG_BYTES = H_IMG_W2 + 4 * H_CHUNK;
+constexpr int H_IMG_W2 = H_IMG_W1 + H_L1C * H_CHUNK;
+constexpr int H_IMG_BYTES = H_IMG_W2 + (H_NCH - H_L1C) * H_CHUNK;
 static_assert(H_RES_BYTES % 16 == 0, "resident image must be 16-byte chunks");
 static_assert(H_IMG_W1 % 16 == 0 && H_CHUNK % 16 == 0, "bulk copies need 16-byte chunks");
 static_assert(H_SMEM <= 227 * 1024, "head shared memory");
+
+// One 32-column group of a 256-wide layer: TMEM row `row` at taddr ->
+// relu(x + b) as bf16 into G columns [k0, k0 + 32) (K = 256).
+__device__ __forceinline__ void head_epi_32(uint32_t taddr, const float* b, unsigned char* G, int row,
+                                            int k0) {
+  float v[32];
+  tmem_ld32(taddr, v);
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    uint4 w;
+    const int j = 8 * c;
+    w.x = pack_bf16(fmaxf(v[j + 0] + b[j + 0], 0.f), fmaxf(v[j + 1] + b[j + 1], 0.f));
+    w.y = pack_bf16(fmaxf(v[j + 2] + b[j + 2], 0.f), fmaxf(v[j + 3] + b[j + 3], 0.f));
+    w.z = pack_bf16(fmaxf(v[j + 4] + b[j + 4], 0.f), fmaxf(v[j + 5] + b[j + 5], 0.f));
+    w.w = pack_bf16(fmaxf(v[j + 6] + b[j + 6], 0.f), fmaxf(v[j + 7] + b[j + 7], 0.f));
+    *reinterpret_cast<uint4*>(G + kmajor_off(row, k0 + j, 256)) = w;
+  }
+}
 
 // Epilogue of half of a 256-wide layer: TMEM row `row`, 128 columns from
 // taddr -> relu(x + b) as bf16 into G columns [k0, k0 + 128) (K = 256).
@@ -396,17 +431,28 @@ __device__ __forceinline__ void head_epi_256(uint32_t taddr, const float* b, uns
 }
 
 // Head over tiles of HT = 128 pairs (one pair per TMEM lane).  Warps 0-7 are
-// the epilogue (warps w and w + 4 read lane quarter w % 4, half of the
-// columns each); warp 8 is the producer (one elected lane).
-// Layers 1 and 2 are 12 K-chunks of 64 per tile (8 of W_h1 against the bf16
-// features the encoder wrote in operand layout, 4 of W_h2 against G); every
-// operand chunk arrives by bulk copy.  The producer runs the chunk stream
-// across tiles through H_NST stages: the copies of chunk g + 2 are issued as
-// soon as the MMAs of chunk g - 1 have freed their stage, so two chunks are in
-// flight while one multiplies.  The epilogue warps signal an mbarrier (EPI)
-// when G holds layer 1, when it holds layer 2, and when the tile's outputs
-// have been read out of TMEM.
-constexpr int H_THREADS = 288;  // 8 epilogue warps + the producer warp
+// the epilogue (warps w and w + 4 read lane quarter w % 4 and split the
+// columns); one lane of warp 8 streams operands, one lane of warp 9 issues the
+// MMAs.  Layers 1 and 2 are 24 K-chunks of 32 per tile (16 of W_h1 against the
+// bf16 features the encoder wrote in operand layout, 8 of W_h2 against G);
+// every operand chunk arrives by bulk copy through H_NST stages.  The stream
+// is bound by the rate at which operands arrive (the weights are streamed
+// again for every tile), so the copy thread keeps H_NST - 1 chunks in flight
+// and refills a stage as soon as the MMAs that read it have completed,
+// independently of the MMA thread.  TMEM: layer 1 accumulates in columns
+// [0, 256), layer 2 and layer 3 in [256, 512).  The layer-1 epilogue fills G
+// in four 64-column chunks, each announced on its own mbarrier (GC0-GC3);
+// layer-2 chunk j starts once G chunk j / 2 is ready.  Layer 3 of tile t waits
+// for the layer-2 epilogue without blocking the stream: the MMA thread polls
+// for it between the layer-1 chunks of tile t + 1 (whose accumulator columns
+// are already free), so the layer-2 and output epilogues of tile t overlap
+// the layer-1 MMAs of tile t + 1.
+// mbarrier phases (one waiter each, never more than one phase behind):
+//   full[s] / done[s]: one per chunk in stage s; L1D, L2D, L3: one per tile;
+//   GC0-GC3: one per tile (G chunk k holds layer 1); EPI: two per tile (G
+//   holds layer 2; outputs have left TMEM).
+constexpr int H_THREADS = 320;  // 8 epilogue warps, the copy warp, the MMA warp
+constexpr int H_COPY = 256, H_MMA_WARP = 9;
 __global__ void __launch_bounds__(H_THREADS, 1)
     head_tc_kernel(const __nv_bfloat16* __restrict__ ftile, PairRange rg,
                    const unsigned char* __restrict__ img, PairInputs in, int have_in,
@@ -419,22 +465,20 @@ __global__ void __launch_bounds__(H_THREADS, 1)
   const int n_tiles = (n - lo + HT - 1) / HT;
   if ((int)blockIdx.x >= n_tiles) return;
   const int my_tiles = (n_tiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
-  // mbarriers: [0, 3) operands of stage s landed; [3, 6) MMAs of stage s done;
-  // 6 layer 3 done; 7 epilogue progress (3 per tile); 8 resident image;
-  // 9 drain; 10 / 11 layer 1 / layer 2 of the tile done (one commit per tile
-  // each: a waiter is never more than one phase behind)
+  // mbarriers: [0, 6) operands of stage s landed; [6, 12) MMAs of stage s
+  // done; 12 layer 3 done; 13 EPI; 14 resident image; 15 drain; 16 / 17 layer
+  // 1 / layer 2 of the tile done; [18, 22) G chunk k holds layer 1
   const uint32_t bar0 = smem_u32(smem + H_CTRL);
-  const uint32_t B_L3 = bar0 + 48, B_EPI = bar0 + 56, B_RES = bar0 + 64, B_DRAIN = bar0 + 72;
-  const uint32_t B_L1D = bar0 + 80, B_L2D = bar0 + 88;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + H_CTRL + 96);
-  volatile int* abort = reinterpret_cast<volatile int*>(smem + H_CTRL + 100);
+  const uint32_t B_FULL = bar0, B_DONE = bar0 + 48;
+  const uint32_t B_L3 = bar0 + 96, B_EPI = bar0 + 104, B_RES = bar0 + 112, B_DRAIN = bar0 + 120;
+  const uint32_t B_L1D = bar0 + 128, B_L2D = bar0 + 136, B_GC = bar0 + 144;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + H_CTRL + 192);
+  volatile int* abort = reinterpret_cast<volatile int*>(smem + H_CTRL + 196);
+  int* s_issued = reinterpret_cast<int*>(smem + H_CTRL + 200);
   if (tid == 0) {
-    for (int i = 0; i < 8; ++i) mbar_init(bar0 + 8 * i, i == 7 ? 256 : 1);
-    mbar_init(B_RES, 1);
-    mbar_init(B_DRAIN, 1);
-    mbar_init(B_L1D, 1);
-    mbar_init(B_L2D, 1);
+    for (int i = 0; i < 22; ++i) mbar_init(bar0 + 8 * i, (i == 13 || i >= 18) ? 256 : 1);
     *abort = 0;
+    *s_issued = 0;
     fence_mbar_init();
   }
   if (warp == 0) {
@@ -445,8 +489,6 @@ __global__ void __launch_bounds__(H_THREADS, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tbase = *tmem_slot;
-  // epilogue warps w and w + 4 share TMEM lane quarter w % 4 and split the
-  // columns between them
   const uint32_t lane_off = (uint32_t)(32 * (warp & 3)) << 16;
   const int row = tid & 127, half = (tid >> 7) & 1;
   const float* hb1 = reinterpret_cast<const float*>(smem + H_BIAS);
@@ -454,83 +496,106 @@ __global__ void __launch_bounds__(H_THREADS, 1)
   const float* hb3 = hb2 + 256;
   unsigned char* G = smem + H_G;
   const uint32_t sG = smem_u32(G), sW3 = smem_u32(smem + H_W3);
-  const int n_chunks = 12 * my_tiles;  // this CTA's chunk stream
+  const int n_chunks = H_NCH * my_tiles;  // this CTA's chunk stream
   bool ok = true;
-  int g_issued = 0;  // chunks whose copies the producer has issued
 
-  if (tid == 256) {
+  if (tid == H_COPY) {
+    // ---------------------------------------------------------- copy thread
     mbar_expect_tx(B_RES, H_RES_BYTES);
     bulk_g2s(smem_u32(smem), img, H_RES_BYTES, B_RES);
-    // copies of global chunk g into stage g % H_NST
-    auto issue = [&](int g) {
-      const int st = g % H_NST, c = g % 12;
-      const int tile = (int)blockIdx.x + (g / 12) * (int)gridDim.x;
-      const uint32_t bw = bar0 + 8 * st;
-      if (c < 8) {
-        mbar_expect_tx(bw, H_ACHUNK + H_CHUNK);
+    for (int g = 0; g < n_chunks; ++g) {
+      const int st = g % H_NST, c = g % H_NCH;
+      // the stage was last read by the MMAs of chunk g - H_NST
+      if (g >= H_NST &&
+          !(ok = mbar_wait_or_abort(B_DONE + 8 * st, (g / H_NST - 1) & 1, abort, WAIT_CYCLES)))
+        break;
+      const int tile = (int)blockIdx.x + (g / H_NCH) * (int)gridDim.x;
+      const uint32_t bf = B_FULL + 8 * st;
+      if (c < H_L1C) {
+        mbar_expect_tx(bf, H_ACHUNK + H_CHUNK);
         bulk_g2s(smem_u32(smem + H_A0 + st * H_ACHUNK),
                  reinterpret_cast<const unsigned char*>(ftile) + (size_t)tile * (128 * 512 * 2) +
                      (size_t)c * H_ACHUNK,
-                 H_ACHUNK, bw);
+                 H_ACHUNK, bf);
         bulk_g2s(smem_u32(smem + H_B0 + st * H_CHUNK), img + H_IMG_W1 + (size_t)c * H_CHUNK,
-                 H_CHUNK, bw);
+                 H_CHUNK, bf);
       } else {
-        mbar_expect_tx(bw, H_CHUNK);
-        bulk_g2s(smem_u32(smem + H_B0 + st * H_CHUNK), img + H_IMG_W2 + (size_t)(c - 8) * H_CHUNK,
-                 H_CHUNK, bw);
+        mbar_expect_tx(bf, H_CHUNK);
+        bulk_g2s(smem_u32(smem + H_B0 + st * H_CHUNK),
+                 img + H_IMG_W2 + (size_t)(c - H_L1C) * H_CHUNK, H_CHUNK, bf);
       }
-      g_issued = g + 1;
-    };
-    for (int g = 0; g < 2 && g < n_chunks; ++g) issue(g);
-    ok = mbar_wait_or_abort(B_RES, 0, abort, WAIT_CYCLES);
-    for (int g = 0; g < n_chunks && ok; ++g) {
-      const int st = g % H_NST, c = g % 12, t = g / 12;
-      // the stage of chunk g + 2 was last read by the MMAs of chunk g - 1
-      if (g + 2 < n_chunks) {
-        if (g >= 1)
-          ok = mbar_wait_or_abort(bar0 + 24 + 8 * ((g - 1) % H_NST), ((g - 1) / H_NST) & 1, abort,
-                                  WAIT_CYCLES);
-        if (!ok) break;
-        issue(g + 2);
-      }
-      // chunk 0 of a tile: the previous tile's outputs have left TMEM;
-      // chunk 8: G holds layer 1
-      // layer 2 of tile t: the previous tile's outputs have left TMEM (they sit
-      // in the layer-2 columns) and G holds layer 1 of tile t; the EPI phases
-      // are waited one after the other, never skipping one
-      if (c == 8 && t > 0) ok = mbar_wait_or_abort(B_EPI, (3 * t - 1) & 1, abort, WAIT_CYCLES);
-      if (c == 8) ok = ok && mbar_wait_or_abort(B_EPI, (3 * t) & 1, abort, WAIT_CYCLES);
-      ok = ok && mbar_wait_or_abort(bar0 + 8 * st, (g / H_NST) & 1, abort, WAIT_CYCLES);
-      if (!ok) break;
+      *s_issued = g + 1;
+    }
+    if (!ok) *abort = 1;
+  } else if (warp == H_MMA_WARP) {
+    // ------------------------------------------------------------- MMA warp
+    // layer 3 of a tile: D3[128 x 16] = G . Wh3img^T (rows 8..15 zero), in
+    // the layer-2 columns
+    auto layer3 = [&]() {
       tc_fence_after();
-      const uint32_t sA = smem_u32(smem + H_A0 + st * H_ACHUNK);
-      const uint32_t sB = smem_u32(smem + H_B0 + st * H_CHUNK);
-      if (c < 8) {
-#pragma unroll
-        for (int kk = 0; kk < 4; ++kk)
-          mma_bf16(tbase + 0, sdesc(sA + 256 * kk, 128, 1024), sdesc(sB + 256 * kk, 128, 1024),
-                   idesc_bf16(128, 256), (c > 0 || kk > 0) ? 1u : 0u);
-      } else {
-#pragma unroll
-        for (int kk = 0; kk < 4; ++kk)
-          mma_bf16(tbase + 256, sdesc(sG + 1024 * (c - 8) + 256 * kk, 128, 4096),
-                   sdesc(sB + 256 * kk, 128, 1024), idesc_bf16(128, 256),
-                   (c > 8 || kk > 0) ? 1u : 0u);
-      }
-      mma_commit(bar0 + 24 + 8 * st);
-      if (c == 7) mma_commit(B_L1D);
-      if (c == 11) mma_commit(B_L2D);
-      if (c == 11) {
-        // layer 3 once G holds layer 2: D3[128 x 16] = G . Wh3img^T (rows 8..15 zero)
-        ok = mbar_wait_or_abort(B_EPI, (3 * t + 1) & 1, abort, WAIT_CYCLES);
-        if (!ok) break;
-        tc_fence_after();
+      if (elect_one()) {
 #pragma unroll
         for (int kk = 0; kk < 16; ++kk)
           mma_bf16(tbase + 256, sdesc(sG + 256 * kk, 128, 4096), sdesc(sW3 + 256 * kk, 128, 4096),
                    idesc_bf16(128, 16), kk > 0);
         mma_commit(B_L3);
       }
+      __syncwarp();
+    };
+    ok = mbar_wait_warp(B_RES, 0, abort, WAIT_CYCLES);
+    int l3 = -1;  // tile whose layer 3 waits for its layer-2 epilogue
+    // two chunks (four MMAs) per step, so that the per-step waits cost less
+    // than the tensor work they gate
+    for (int g = 0; g < n_chunks && ok; g += 2) {
+      const int st0 = g % H_NST, st1 = (g + 1) % H_NST, c = g % H_NCH, t = g / H_NCH;
+      if (l3 >= 0) {
+        // EPI phase 2 l3: G holds layer 2 of tile l3.  Layer 2 of the next
+        // tile needs its outputs out of TMEM, so by then it is waited for.
+        if (c == H_L1C) {
+          ok = mbar_wait_warp(B_EPI, (2 * l3) & 1, abort, WAIT_CYCLES);
+          if (!ok) break;
+        }
+        if (c == H_L1C || __all_sync(0xffffffffu, mbar_test_wait(B_EPI, (2 * l3) & 1))) {
+          layer3();
+          l3 = -1;
+        }
+      }
+      const bool l1 = c < H_L1C;
+      const int j = c - H_L1C;  // layer-2 chunk (even)
+      if (!l1) {
+        // the previous tile's outputs have left the layer-2 columns (EPI
+        // phase 2 t - 1), and G chunk j / 2 (64 columns: K-chunks j and
+        // j + 1) holds layer 1
+        if (j == 0 && t > 0) ok = mbar_wait_warp(B_EPI, (2 * t - 1) & 1, abort, WAIT_CYCLES);
+        ok = ok && mbar_wait_warp(B_GC + 8 * (j >> 1), t & 1, abort, WAIT_CYCLES);
+      }
+      ok = ok && mbar_wait_warp(B_FULL + 8 * st0, (g / H_NST) & 1, abort, WAIT_CYCLES);
+      ok = ok && mbar_wait_warp(B_FULL + 8 * st1, ((g + 1) / H_NST) & 1, abort, WAIT_CYCLES);
+      if (!ok) break;
+      tc_fence_after();
+      // descriptors from warp-uniform values; one elected lane issues
+      const uint32_t sB0 = smem_u32(smem + H_B0 + st0 * H_CHUNK);
+      const uint32_t sB1 = smem_u32(smem + H_B0 + st1 * H_CHUNK);
+      const uint32_t sA0 = l1 ? smem_u32(smem + H_A0 + st0 * H_ACHUNK) : sG + 512 * j;
+      const uint32_t sA1 = l1 ? smem_u32(smem + H_A0 + st1 * H_ACHUNK) : sG + 512 * (j + 1);
+      const uint32_t dcol = l1 ? 0u : 256u, sbo = l1 ? 512u : 4096u;
+      const uint32_t acc0 = (l1 ? c : j) > 0 ? 1u : 0u;
+      if (elect_one()) {
+        mma_bf16(tbase + dcol, sdesc(sA0, 128, sbo), sdesc(sB0, 128, 512), idesc_bf16(128, 256), acc0);
+        mma_bf16(tbase + dcol, sdesc(sA0 + 256, 128, sbo), sdesc(sB0 + 256, 128, 512), idesc_bf16(128, 256), 1u);
+        mma_commit(B_DONE + 8 * st0);
+        mma_bf16(tbase + dcol, sdesc(sA1, 128, sbo), sdesc(sB1, 128, 512), idesc_bf16(128, 256), 1u);
+        mma_bf16(tbase + dcol, sdesc(sA1 + 256, 128, sbo), sdesc(sB1 + 256, 128, 512), idesc_bf16(128, 256), 1u);
+        mma_commit(B_DONE + 8 * st1);
+        if (c + 1 == H_L1C - 1) mma_commit(B_L1D);
+        if (c + 1 == H_NCH - 1) mma_commit(B_L2D);
+      }
+      __syncwarp();
+      if (c + 1 == H_NCH - 1) l3 = t;
+    }
+    if (ok && l3 >= 0) {
+      ok = mbar_wait_warp(B_EPI, (2 * l3) & 1, abort, WAIT_CYCLES);
+      if (ok) layer3();
     }
     if (!ok) *abort = 1;
   }
@@ -539,14 +604,28 @@ __global__ void __launch_bounds__(H_THREADS, 1)
   for (int t = 0; tid < 256 && t < my_tiles && ok; ++t) {
     const int pr = lo + ((int)blockIdx.x + t * (int)gridDim.x) * HT + row;
     const bool row_ok = pr < n;
-    // layer 1 final with the MMAs of chunk 12 t + 7, layer 2 with 12 t + 11
+    // operands of the world-frame epilogue, loaded while the MMAs run
+    bool geo = false;
+    float4 cc = make_float4(0.f, 0.f, 0.f, 0.f);
+    float pose[7];
+    if (half == 0 && row_ok && out) {
+      const int a = have_in ? in.pairs[2 * pr] : -1;
+      cc = centre[pr];
+      geo = a >= 0 && a < in.n_obj && !isnan(cc.x);
+#pragma unroll
+      for (int i = 0; i < 7; ++i) pose[i] = geo ? in.poses[7 * (size_t)a + i] : 0.f;
+    }
     ok = mbar_wait_or_abort(B_L1D, t & 1, abort, WAIT_CYCLES);
     if (!ok) break;
     tc_fence_after();
-    head_epi_256(tbase + lane_off + 128 * half, hb1 + 128 * half, G, row, 128 * half);
-    fence_async_smem();
-    tc_fence_before();
-    mbar_arrive(B_EPI);
+#pragma unroll 1
+    for (int k = 0; k < 4; ++k) {
+      const int col = 64 * k + 32 * half;
+      head_epi_32(tbase + lane_off + col, hb1 + col, G, row, col);
+      fence_async_smem();
+      tc_fence_before();
+      mbar_arrive(B_GC + 8 * k);
+    }
     ok = mbar_wait_or_abort(B_L2D, t & 1, abort, WAIT_CYCLES);
     if (!ok) break;
     tc_fence_after();
@@ -570,10 +649,8 @@ __global__ void __launch_bounds__(H_THREADS, 1)
         }
         if (out) {
           float o8[8];
-          const int a = have_in ? in.pairs[2 * pr] : -1;
-          const float4 cc = centre[pr];
-          if (a >= 0 && a < in.n_obj && !isnan(cc.x)) {
-            epilogue_world(y, in.poses + 7 * (size_t)a, cc, o8);
+          if (geo) {
+            epilogue_world(y, pose, cc, o8);
           } else {
 #pragma unroll
             for (int o = 0; o < 8; ++o) o8[o] = __int_as_float(0x7fc00000);
@@ -587,13 +664,19 @@ __global__ void __launch_bounds__(H_THREADS, 1)
     mbar_arrive(B_EPI);
   }
   __syncthreads();
-  if (tid == 256 && *abort) {
-    // drain: wait (bounded) for the producer's MMAs and bulk copies
-    atomicOr(err, 2);
-    mma_commit(B_DRAIN);
-    mbar_wait(B_DRAIN, 0, WAIT_CYCLES);
-    for (int g = g_issued - H_NST; g < g_issued; ++g)
-      if (g >= 0) mbar_wait(bar0 + 8 * (g % H_NST), (g / H_NST) & 1, WAIT_CYCLES);
+  if (*abort) {
+    // drain (bounded): the MMA thread waits for its MMAs, the copy thread for
+    // the copies it issued
+    if (tid == 0) atomicOr(err, 2);
+    if (warp == H_MMA_WARP && (tid & 31) == 0) {
+      mma_commit(B_DRAIN);
+      mbar_wait(B_DRAIN, 0, WAIT_CYCLES);
+    }
+    if (tid == H_COPY) {
+      const int issued = *s_issued;
+      for (int g = issued - H_NST; g < issued; ++g)
+        if (g >= 0) mbar_wait(B_FULL + 8 * (g % H_NST), (g / H_NST) & 1, WAIT_CYCLES);
+    }
   }
   tc_fence_before();
   __syncthreads();
@@ -662,12 +745,12 @@ int upload_tc_params(locc_handle* h, const std::vector<float>& params) {
   std::memcpy(hd + H_BIAS, &params[offb[3]], 256 * 4);
   std::memcpy(hd + H_BIAS + 256 * 4, &params[offb[4]], 256 * 4);
   std::memcpy(hd + H_BIAS + 512 * 4, &params[offb[5]], 8 * 4);
-  for (int kc = 0; kc < 8; ++kc)
-    put_tile(hd + H_IMG_W1 + (size_t)kc * H_CHUNK, 256, 64,
-             [&](int c, int k) { return W(3, c, 64 * kc + k); });
-  for (int kc = 0; kc < 4; ++kc)
-    put_tile(hd + H_IMG_W2 + (size_t)kc * H_CHUNK, 256, 64,
-             [&](int c, int k) { return W(4, c, 64 * kc + k); });
+  for (int kc = 0; kc < H_L1C; ++kc)
+    put_tile(hd + H_IMG_W1 + (size_t)kc * H_CHUNK, 256, HK,
+             [&](int c, int k) { return W(3, c, HK * kc + k); });
+  for (int kc = 0; kc < H_NCH - H_L1C; ++kc)
+    put_tile(hd + H_IMG_W2 + (size_t)kc * H_CHUNK, 256, HK,
+             [&](int c, int k) { return W(4, c, HK * kc + k); });
   if (cudaMalloc(&h->d_wtc, total) != cudaSuccess ||
       cudaMemcpy(h->d_wtc, img.data(), total, cudaMemcpyHostToDevice) != cudaSuccess) {
     cudaGetLastError();

@@ -29,6 +29,29 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
+// Non-blocking probe: true once the phase of the given parity has completed.
+__device__ __forceinline__ bool mbar_test_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// One lane of the (converged) warp returns true.  MMA-issuing loops run on a
+// whole warp with warp-uniform control flow and issue through elect_one(): a
+// tcgen05.mma whose descriptors come from per-thread (divergent) values issues
+// far more slowly than one whose operands the compiler can keep uniform.
+__device__ __forceinline__ bool elect_one() {
+  uint32_t pred = 0;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\telect.sync _|p, 0xffffffff;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(pred));
+  return pred != 0;
+}
 // Bounded wait: gives up after ~max_cycles SM cycles and returns false.
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long long max_cycles) {
   const long long t0 = clock64();
@@ -52,6 +75,7 @@ __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
 // timeout it raises *abort itself.  Returns false when giving up.
 __device__ __forceinline__ bool mbar_wait_or_abort(uint32_t bar, uint32_t parity, volatile int* abort,
                                                    long long max_cycles) {
+  if (mbar_test_wait(bar, parity)) return true;  // fast path: phase already complete
   const long long t0 = clock64();
   while (!mbar_try_wait(bar, parity)) {
     if (*abort) return false;
@@ -61,6 +85,14 @@ __device__ __forceinline__ bool mbar_wait_or_abort(uint32_t bar, uint32_t parity
     }
   }
   return true;
+}
+
+// Warp-wide bounded wait: every lane polls, and the result is made warp-uniform
+// by a vote (false on every lane if any lane gave up or saw the abort flag).
+__device__ __forceinline__ bool mbar_wait_warp(uint32_t bar, uint32_t parity, volatile int* abort,
+                                               long long max_cycles) {
+  if (__all_sync(0xffffffffu, mbar_test_wait(bar, parity))) return true;
+  return __all_sync(0xffffffffu, mbar_wait_or_abort(bar, parity, abort, max_cycles));
 }
 
 // ---- bulk copies (TMA engine, no tensor map) ------------------------------------
