@@ -399,6 +399,73 @@ void locc_server_destroy(locc_server *s);
 /* Release all device and host memory of the handle (blocking). */
 void locc_destroy(locc_handle *h);
 
+/* ------------------------------------------------ voxel-latent variant ----
+ * The paper's own design (Sec. III "Local Crop Collision Network"; appendix
+ * "Architecture Details"): a shape encoder computes, once per library shape,
+ * a latent of 6 x 6 x 6 cells x 16 features over the shape's AABB (per-point
+ * MLP 3 -> 256 -> 256 -> 256, cell-wise max pooling, a 3-D U-Net of four
+ * 128-channel 3x3x3 convolutions -- the first unpadded -- and four transposed
+ * convolutions with concatenated skips, a global [max || mean] feature tiled
+ * onto every cell, a linear layer to 16).  Per pair, each object's cells whose
+ * centre lies in the intersection of its box with the other object's box
+ * (seen as an axis-aligned box of its frame), widened by the cell's
+ * half-diagonal so that no cell touching the region is missed, are average
+ * pooled (no cell: 0); [pooled (16) || pose in A's frame (7)] of each object
+ * goes through 23 -> 128 -> 128 -> 128 (ReLU), the two results are max pooled,
+ * then 128 -> 128 -> 128 -> 128 (ReLU) -> 1 gives the collision logit
+ * (collision <=> logit > 0, i.e. sigmoid > 0.5).  A's pose input is
+ * (1, 0, 0, 0, 0, 0, 0), B's (q_A* q_B, R_A^T (t_B - t_A)).  Cells are
+ * numbered (i * 6 + j) * 6 + k along body axes 0, 1, 2.  Float32 on the CUDA
+ * cores; the cell selection is bit-reproducible (explicitly rounded float32 in
+ * a fixed order).  Same conventions as above: device pointers, asynchronous
+ * on `stream`, out-of-range indices give a NaN logit and raise the flag that
+ * locc_voxel_status reports. */
+#define LOCC_VOXEL_N_PARAMS 5533969 /* parameters of the voxel network */
+#define LOCC_VOXEL_CELLS 216        /* 6 x 6 x 6 cells per shape */
+#define LOCC_VOXEL_F 16             /* latent features per cell */
+
+typedef struct locc_voxel locc_voxel;
+
+/* Copy the library to the device, read the "LOCCV001" blob (8-byte magic,
+ * uint32 version 1, uint32 LOCC_VOXEL_N_PARAMS, then float32 parameters:
+ * e1 W[256][3] b, e2 W[256][256] b, e3 likewise, c1 W[128][256][3][3][3] b,
+ * c2..c4 W[128][128][3][3][3] b, d1 W[128][128][3][3][3] b (transposed
+ * convolutions are [in][out][3][3][3]), d2..d4 W[256][128][3][3][3] b,
+ * f W[16][384] b, p1 W[128][23] b, p2, p3, q1, q2, q3 W[128][128] b,
+ * q4 W[1][128] b) and encode every shape (blocking).  Errors:
+ * LOCC_ERR_INVALID_ARG, LOCC_ERR_BAD_WEIGHTS, LOCC_ERR_OOM, LOCC_ERR_CUDA. */
+int locc_voxel_create(const locc_shape_library *lib, const void *weights_blob,
+                      size_t blob_bytes, locc_voxel **out);
+
+/* Re-run the shape encoder on `stream` (the latents are already computed by
+ * locc_voxel_create; this is for timing and for callers that reload). */
+int locc_voxel_encode(locc_voxel *h, void *stream);
+
+/* Copy the latents to out: device float32 [n_shapes][216][16]. */
+int locc_voxel_latents(locc_voxel *h, float *out, void *stream);
+
+/* Collision logits of n_pairs pairs: poses [n_obj][7], obj_shape [n_obj],
+ * pairs [n_pairs][2] (A, B), logit [n_pairs] float32 (all device). */
+int locc_voxel_detect(locc_voxel *h, const float *poses, const int32_t *obj_shape,
+                      int32_t n_obj, const int32_t *pairs, int32_t n_pairs,
+                      float *logit, void *stream);
+
+/* locc_voxel_detect plus, when not NULL, the selected cells of each object as
+ * index ranges cell_ranges [n_pairs][2][6] int32 = (i0, i1, j0, j1, k0, k1),
+ * inclusive, i0 > i1 on an empty axis; and the pooled features
+ * pooled [n_pairs][2][16] float32. */
+int locc_voxel_detect_ex(locc_voxel *h, const float *poses, const int32_t *obj_shape,
+                         int32_t n_obj, const int32_t *pairs, int32_t n_pairs,
+                         float *logit, int32_t *cell_ranges, float *pooled,
+                         void *stream);
+
+/* Synchronise `stream` and report (then clear) the device error flag:
+ * 0 or LOCC_ERR_BAD_INDEX. */
+int locc_voxel_status(locc_voxel *h, void *stream);
+
+/* Release the handle (blocking). */
+void locc_voxel_destroy(locc_voxel *h);
+
 /* Message of the last failing call on this host thread ("" if none). */
 const char *locc_last_error(void);
 

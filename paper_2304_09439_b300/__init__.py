@@ -19,7 +19,7 @@ from .abi import LoccError, LOCC_FP32, LOCC_BF16, LOCC_FP8, PRECISIONS
 KMAX = 64
 OUT_DIM = 8
 
-__all__ = ["Detector", "Trainer", "Server", "LoccError", "LOCC_FP32", "LOCC_BF16", "LOCC_FP8", "weights",
+__all__ = ["Detector", "VoxelDetector", "Trainer", "Server", "LoccError", "LOCC_FP32", "LOCC_BF16", "LOCC_FP8", "weights",
            "abi", "KMAX", "OUT_DIM"]
 
 
@@ -237,6 +237,73 @@ class Detector:
                                            abi.ptr(n), M, abi.ptr(out), abi.stream_ptr(stream)))
         m = min(int(n[0]), M)
         return pairs_out[:m], out[:m], int(n[0])
+
+
+class VoxelDetector:
+    """Owns one ``locc_voxel`` handle (the voxel-latent variant) on the current
+    CUDA device: the library's latents are computed at construction."""
+
+    def __init__(self, points, aabb, params):
+        import torch
+        self._lib = abi.load()
+        self.device = torch.cuda.current_device()
+        blob = params if isinstance(params, (bytes, bytearray)) else weights.pack_voxel(params)
+        self._h = abi.voxel_create(points, aabb, bytes(blob))
+        self.n_shapes = int(len(aabb))
+
+    def close(self) -> None:
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.locc_voxel_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def encode(self, stream=None) -> None:
+        """Recompute the latents (asynchronous on ``stream``)."""
+        abi.check(self._lib.locc_voxel_encode(self._h, abi.stream_ptr(stream)))
+
+    def latents(self, stream=None):
+        import torch
+        out = torch.empty((self.n_shapes, 216, 16), dtype=torch.float32, device=self.device)
+        abi.check(self._lib.locc_voxel_latents(self._h, abi.ptr(out), abi.stream_ptr(stream)))
+        return out
+
+    def detect(self, poses, obj_shape, pairs, logit=None, details=False, stream=None):
+        """Logits [P] (and, with ``details``, cell ranges [P, 2, 6] and pooled
+        features [P, 2, 16])."""
+        import torch
+        _need(poses, torch.float32, "poses", self.device)
+        _need(obj_shape, torch.int32, "obj_shape", self.device)
+        _need(pairs, torch.int32, "pairs", self.device)
+        P = pairs.shape[0]
+        if logit is None:
+            logit = torch.empty(P, dtype=torch.float32, device=pairs.device)
+        _need(logit, torch.float32, "logit", self.device)
+        if not details:
+            abi.check(self._lib.locc_voxel_detect(self._h, abi.ptr(poses), abi.ptr(obj_shape),
+                                                  poses.shape[0], abi.ptr(pairs), P,
+                                                  abi.ptr(logit), abi.stream_ptr(stream)))
+            return logit
+        ranges = torch.empty((P, 2, 6), dtype=torch.int32, device=pairs.device)
+        pooled = torch.empty((P, 2, 16), dtype=torch.float32, device=pairs.device)
+        abi.check(self._lib.locc_voxel_detect_ex(self._h, abi.ptr(poses), abi.ptr(obj_shape),
+                                                 poses.shape[0], abi.ptr(pairs), P,
+                                                 abi.ptr(logit), abi.ptr(ranges), abi.ptr(pooled),
+                                                 abi.stream_ptr(stream)))
+        return logit, ranges, pooled
+
+    def status(self, stream=None) -> None:
+        abi.check(self._lib.locc_voxel_status(self._h, abi.stream_ptr(stream)))
 
 
 class Trainer:

@@ -28,7 +28,11 @@ EXPORTS = ["locc_create", "locc_set_precision", "locc_detect", "locc_detect_host
            "locc_trainer_grad", "locc_trainer_params", "locc_trainer_set_params",
            "locc_trainer_commit", "locc_trainer_set_lr", "locc_trainer_destroy", "locc_set_pipeline",
            "locc_autotune", "locc_server_create", "locc_server_submit", "locc_server_wait",
-           "locc_server_stats", "locc_server_destroy"]
+           "locc_server_stats", "locc_server_destroy", "locc_voxel_create", "locc_voxel_encode",
+           "locc_voxel_latents", "locc_voxel_detect", "locc_voxel_detect_ex", "locc_voxel_status",
+           "locc_voxel_destroy"]
+VOID_EXPORTS = ("locc_destroy", "locc_last_error", "locc_trainer_destroy", "locc_server_destroy",
+                "locc_voxel_destroy")
 NOALLOC_MAX_PAIRS = 1024
 
 
@@ -125,12 +129,20 @@ def load(build_if_needed: bool = True) -> ctypes.CDLL:
         lib.locc_server_stats.argtypes = [P, ctypes.POINTER(ServerCounters), I]
         lib.locc_server_destroy.argtypes = [P]
         lib.locc_server_destroy.restype = None
+        lib.locc_voxel_create.argtypes = [ctypes.POINTER(_ShapeLibrary), P, ctypes.c_size_t,
+                                          ctypes.POINTER(P)]
+        lib.locc_voxel_encode.argtypes = [P, P]
+        lib.locc_voxel_latents.argtypes = [P, P, P]
+        lib.locc_voxel_detect.argtypes = [P, P, P, I, P, I, P, P]
+        lib.locc_voxel_detect_ex.argtypes = [P, P, P, I, P, I, P, P, P, P]
+        lib.locc_voxel_status.argtypes = [P, P]
+        lib.locc_voxel_destroy.argtypes = [P]
+        lib.locc_voxel_destroy.restype = None
         lib.locc_destroy.argtypes = [P]
         lib.locc_destroy.restype = None
         lib.locc_last_error.restype = ctypes.c_char_p
         for name in EXPORTS:
-            if name not in ("locc_destroy", "locc_last_error", "locc_trainer_destroy",
-                            "locc_server_destroy"):
+            if name not in VOID_EXPORTS:
                 getattr(lib, name).restype = ctypes.c_int
         _lib = lib
         return lib
@@ -170,4 +182,19 @@ def create(points, aabb, blob: bytes, radius: float, precision: int):
     buf = ctypes.create_string_buffer(blob, len(blob))
     check(lib.locc_create(ctypes.byref(sl), ctypes.cast(buf, ctypes.c_void_p), len(blob),
                           float(radius), int(precision), ctypes.byref(h)))
+    return h
+
+
+def voxel_create(points, aabb, blob: bytes):
+    import numpy as np
+    lib = load()
+    points = np.ascontiguousarray(points, np.float32)
+    aabb = np.ascontiguousarray(aabb, np.float32)
+    if points.ndim != 3 or points.shape[2] != 3 or aabb.shape != (points.shape[0], 6):
+        raise ValueError("points must be [S, n_points, 3] and aabb [S, 6]")
+    sl = _ShapeLibrary(points.shape[0], points.shape[1], points.ctypes.data, aabb.ctypes.data)
+    h = ctypes.c_void_p()
+    buf = ctypes.create_string_buffer(blob, len(blob))
+    check(lib.locc_voxel_create(ctypes.byref(sl), ctypes.cast(buf, ctypes.c_void_p), len(blob),
+                                ctypes.byref(h)))
     return h

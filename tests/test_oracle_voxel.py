@@ -280,3 +280,16 @@ def test_empty_selection_pools_to_zero():
                  np.array([[0, 1]]), prm)
     assert r["cnt"].tolist() == [[216, 216]]
     np.testing.assert_allclose(r["feat"][0, 0], np.arange(1, 17))
+
+
+def test_voxel_blob_round_trip_and_layout():
+    # the product's blob layout lists the same tensors in the same order as
+    # the oracle, and packing / unpacking is lossless
+    from paper_2304_09439_b300 import weights as W
+    import synth
+    assert [(n, tuple(s)) for n, s in W.VOXEL_LAYERS] == [(n, tuple(s)) for n, s in V.LAYERS]
+    assert W.N_VOXEL_PARAMS == V.N_PARAMS
+    flat = synth.voxel_weights(V.LAYERS, 2)
+    blob = W.pack_voxel(flat)
+    assert blob[:8] == b"LOCCV001" and len(blob) == 16 + 4 * V.N_PARAMS
+    np.testing.assert_array_equal(W.unpack_voxel(blob), flat)
