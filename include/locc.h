@@ -399,6 +399,44 @@ void locc_server_destroy(locc_server *s);
 /* Release all device and host memory of the handle (blocking). */
 void locc_destroy(locc_handle *h);
 
+/* ------------------------------------------------------ simulation step ----
+ * Contact resolution driven by the detector (Sec. IV-C: the network inside a
+ * GPU simulator's step; Table 2: |signed distance| whenever a contact
+ * arises).  Penalty method (the paper cites its solver without describing
+ * it): a contact row {logit, point, normal (A -> B), depth} with logit > 0
+ * pushes B by F = max(0, k_contact max(depth, 0) - c_contact v_n) n at the
+ * point and A by -F, v_n the normal speed of B relative to A there; each body
+ * box corner below the ground plane z = 0 adds max(0, k_plane pen - c_plane
+ * v_z) upwards and -mu_plane (v_x, v_y); gravity; unit mass and the inertia
+ * of a solid box filling the body AABB; semi-implicit Euler with damping,
+ * quaternion renormalised. */
+typedef struct {
+  float dt, gravity;
+  float k_contact, c_contact;
+  float k_plane, c_plane, mu_plane;
+  float lin_damp, ang_damp;
+} locc_sim_params;
+
+/* One step of every object, in place: poses [n_obj][7] and velocities
+ * vel [n_obj][6] (linear, angular, world) on the device.  Contacts: the first
+ * min(*n_pairs_dev, max_pairs) rows (all max_pairs when n_pairs_dev is NULL)
+ * of pairs [.][2] and contacts [.][8] (the format of locc_detect's output,
+ * world frame).  acc: device scratch float32 [n_obj][6], zero on entry and
+ * left zero.  Asynchronous on `stream`. */
+int locc_sim_step(locc_handle *h, const locc_sim_params *prm, float *poses, float *vel,
+                  const int32_t *obj_shape, int32_t n_obj, const int32_t *pairs,
+                  const int32_t *n_pairs_dev, int32_t max_pairs, const float *contacts,
+                  float *acc, void *stream);
+
+/* Proxy-geometry contacts in the same row format from bounding spheres of
+ * radius radius[shape] (device float32 [n_shapes]) about each object's
+ * origin: logit = depth = r_A + r_B - |t_B - t_A|, normal along t_B - t_A,
+ * point halfway between the sphere surfaces.  A baseline contact source for
+ * locc_sim_step. */
+int locc_sphere_contacts(locc_handle *h, const float *poses, const int32_t *obj_shape,
+                         int32_t n_obj, const int32_t *pairs, const int32_t *n_pairs_dev,
+                         int32_t max_pairs, const float *radius, float *out, void *stream);
+
 /* ------------------------------------------------ voxel-latent variant ----
  * The paper's own design (Sec. III "Local Crop Collision Network"; appendix
  * "Architecture Details"): a shape encoder computes, once per library shape,

@@ -218,6 +218,29 @@ class Detector:
                                       abi.stream_ptr(stream)))
         return pairs_out, n_pairs_out, out
 
+    def sim_step(self, params, poses, vel, obj_shape, pairs, n_pairs_dev, contacts, acc,
+                 stream=None):
+        """One contact-resolution step of every object in place (poses, vel)
+        from contact rows in the detector's output format."""
+        import torch
+        _need(poses, torch.float32, "poses", self.device)
+        _need(vel, torch.float32, "vel", self.device)
+        _need(obj_shape, torch.int32, "obj_shape", self.device)
+        _need(acc, torch.float32, "acc", self.device)
+        abi.check(self._lib.locc_sim_step(self._h, ctypes.byref(params), abi.ptr(poses),
+                                          abi.ptr(vel), abi.ptr(obj_shape), poses.shape[0],
+                                          abi.ptr(pairs), abi.ptr(n_pairs_dev), pairs.shape[0],
+                                          abi.ptr(contacts), abi.ptr(acc),
+                                          abi.stream_ptr(stream)))
+
+    def sphere_contacts(self, poses, obj_shape, pairs, n_pairs_dev, radius, out, stream=None):
+        """Bounding-sphere contact rows (a proxy-geometry contact source)."""
+        abi.check(self._lib.locc_sphere_contacts(self._h, abi.ptr(poses), abi.ptr(obj_shape),
+                                                 poses.shape[0], abi.ptr(pairs),
+                                                 abi.ptr(n_pairs_dev), pairs.shape[0],
+                                                 abi.ptr(radius), abi.ptr(out),
+                                                 abi.stream_ptr(stream)))
+
     def step_host(self, poses, obj_shape, env_offsets, max_pairs: int, pairs_out=None,
                   out=None, stream=None):
         """Host arrays in and out; returns (pairs [n,2], out [n,8]) as numpy."""

@@ -30,7 +30,7 @@ EXPORTS = ["locc_create", "locc_set_precision", "locc_detect", "locc_detect_host
            "locc_autotune", "locc_server_create", "locc_server_submit", "locc_server_wait",
            "locc_server_stats", "locc_server_destroy", "locc_voxel_create", "locc_voxel_encode",
            "locc_voxel_latents", "locc_voxel_detect", "locc_voxel_detect_ex", "locc_voxel_status",
-           "locc_voxel_destroy"]
+           "locc_voxel_destroy", "locc_sim_step", "locc_sphere_contacts"]
 VOID_EXPORTS = ("locc_destroy", "locc_last_error", "locc_trainer_destroy", "locc_server_destroy",
                 "locc_voxel_destroy")
 NOALLOC_MAX_PAIRS = 1024
@@ -71,6 +71,12 @@ class ServerCounters(ctypes.Structure):
                [(n, ctypes.c_double) for n in
                 ("latency_p50_us", "latency_p99_us", "latency_max_us", "mean_pairs_per_launch")] + \
                [("max_active_seen", ctypes.c_int32)]
+
+
+class SimParams(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_float) for n in
+                ("dt", "gravity", "k_contact", "c_contact", "k_plane", "c_plane", "mu_plane",
+                 "lin_damp", "ang_damp")]
 
 
 class _ShapeLibrary(ctypes.Structure):
@@ -129,6 +135,8 @@ def load(build_if_needed: bool = True) -> ctypes.CDLL:
         lib.locc_server_stats.argtypes = [P, ctypes.POINTER(ServerCounters), I]
         lib.locc_server_destroy.argtypes = [P]
         lib.locc_server_destroy.restype = None
+        lib.locc_sim_step.argtypes = [P, ctypes.POINTER(SimParams), P, P, P, I, P, P, I, P, P, P]
+        lib.locc_sphere_contacts.argtypes = [P, P, P, I, P, P, I, P, P, P]
         lib.locc_voxel_create.argtypes = [ctypes.POINTER(_ShapeLibrary), P, ctypes.c_size_t,
                                           ctypes.POINTER(P)]
         lib.locc_voxel_encode.argtypes = [P, P]

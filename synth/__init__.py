@@ -19,12 +19,12 @@ from .poses import (random_quaternions, random_poses, quat_multiply,
                     compose_relative_tiny)
 from .weights import LAYER_DIMS, xavier_weights, voxel_weights
 from .scenes import uneven_scene, sweep_pairs, client_batch
-from .drop import drop_scene
+from .drop import drop_scene, drop_initial_state
 
 __all__ = [
     "Mesh", "box_mesh", "ellipsoid_mesh", "torus_mesh", "l_bracket",
     "random_union", "sample_surface", "ShapeLibrary", "make_library",
     "tiny_library", "random_quaternions", "random_poses", "quat_multiply",
     "compose_relative_tiny", "LAYER_DIMS", "xavier_weights", "voxel_weights", "uneven_scene",
-    "sweep_pairs", "client_batch", "drop_scene",
+    "sweep_pairs", "client_batch", "drop_scene", "drop_initial_state",
 ]

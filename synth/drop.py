@@ -73,3 +73,25 @@ def drop_scene(lib, n_env: int, n_steps: int, seed: int, dt: float = 1.0 / 240.0
             *(dq[:, 0:1] * q[:, 1:] + q[:, 0:1] * dq[:, 1:] + np.cross(dq[:, 1:], q[:, 1:])).T], 1)
         q = q + dt * qd
         q /= np.linalg.norm(q, axis=1, keepdims=True)
+
+
+def drop_initial_state(lib, n_env: int, seed: int):
+    """Initial state of drop scenes for a simulator driven by the detector:
+    two objects per environment drawn from the library, the second 1.2 m above
+    the first, random orientations and spins, small horizontal offsets (the
+    same recipe as ``drop_scene``).  Returns poses float32 [2 n_env, 7],
+    velocities float32 [2 n_env, 6] (linear, angular), obj_shape int32
+    [2 n_env] and env_offsets int32 [n_env + 1]."""
+    rng = np.random.default_rng(seed)
+    n = 2 * n_env
+    shape = rng.integers(0, lib.n_shapes, size=n).astype(np.int32)
+    q = random_quaternions(n, rng).astype(np.float32)
+    x = np.zeros((n, 3), np.float32)
+    x[:, 2] = 1.0 + rng.uniform(0.0, 0.5, n) + np.tile([0.0, 1.2], n_env)
+    x[:, :2] = rng.uniform(-0.3, 0.3, (n, 2))
+    x[1::2, :2] = x[0::2, :2] + rng.uniform(-0.2, 0.2, (n_env, 2))
+    vel = np.zeros((n, 6), np.float32)
+    vel[:, 3:] = rng.normal(0.0, 2.0, (n, 3))
+    poses = np.concatenate([q, x], 1).astype(np.float32)
+    env = np.arange(0, n + 1, 2, dtype=np.int32)
+    return poses, vel, shape, env
