@@ -65,6 +65,8 @@ extern "C" {
 #define LOCC_ERR_BUSY (-7)         /* server queue full: request rejected */
 
 #define LOCC_CROP_POINTS 64        /* points kept per object */
+#define LOCC_CROP_LOCAL 0          /* crop mode: nearest samples in the crop ball */
+#define LOCC_CROP_GLOBAL 1         /* crop mode: the first 64 samples of each shape */
 #define LOCC_OUT_DIM 8             /* logit, point xyz, normal xyz, depth */
 #define LOCC_N_PARAMS 240776       /* parameters of the crop network */
 
@@ -395,6 +397,14 @@ int locc_server_stats(locc_server *s, locc_server_counters *st, int32_t reset);
 /* Finish every queued and admitted request, stop the scheduler and free the
  * server (the handle stays).  Blocking. */
 void locc_server_destroy(locc_server *s);
+
+/* Crop mode of every later call on the handle (detection, crops, training):
+ * LOCC_CROP_LOCAL (default: the method's local crops) or LOCC_CROP_GLOBAL,
+ * the ablation without locality (Sec. IV-B, GLOBAL-OCN): each object keeps its
+ * first 64 surface samples -- an area-uniform subset of the whole surface,
+ * whatever the crop ball -- in the same canonical frame, count 64 (fewer if
+ * the shapes have fewer samples).  Errors: LOCC_ERR_INVALID_ARG. */
+int locc_set_crop_mode(locc_handle *h, int32_t mode);
 
 /* Release all device and host memory of the handle (blocking). */
 void locc_destroy(locc_handle *h);

@@ -64,6 +64,9 @@ def _load():
         lib.orb_run.argtypes = [P, P, I, I, P, P, I, P, I, ctypes.c_float, I,
                                 P, P, P, P, P, P, P, I]
         lib.orb_run.restype = I
+        lib.orb_run_global.argtypes = [P, P, I, I, P, P, I, P, I, ctypes.c_float, I,
+                                P, P, P, P, P, P, P, I]
+        lib.orb_run_global.restype = I
         lib.orb_network.argtypes = [P, P, P, I, I, P, P]
         lib.orb_network.restype = I
         lib.orb_loss_grad.argtypes = [P, P, P, P, I, I, P, P]
@@ -113,8 +116,10 @@ def unflatten_params(flat: np.ndarray):
 
 def crop_forward(points, aabb, poses, obj_shape, pairs, r: float,
                  params: Optional[np.ndarray] = None, kmax: int = KMAX,
-                 n_threads: int = 1):
+                 n_threads: int = 1, mode: str = "local"):
     """Oracle (b): crop selection (+ network forward when ``params`` given).
+    ``mode`` "global": each object's first kmax samples instead of the local
+    crop (the ablation without locality).
 
     Returns a dict with idx [P,2,kmax] int32 (-1 padded), cnt [P,2] int32,
     xyz [P,2,kmax,3] float32 canonical coordinates, centre [P,3] float32 and,
@@ -138,7 +143,8 @@ def crop_forward(points, aabb, poses, obj_shape, pairs, r: float,
         assert params.size == N_PARAMS
         out = np.empty((P, 8), np.float64)
         feat = np.empty((P, 512), np.float64)
-    st = lib.orb_run(_ptr(points), _ptr(aabb), S, NP, _ptr(poses), _ptr(obj_shape),
+    run = {"local": lib.orb_run, "global": lib.orb_run_global}[mode]
+    st = run(_ptr(points), _ptr(aabb), S, NP, _ptr(poses), _ptr(obj_shape),
                      poses.shape[0], _ptr(pairs), P, float(r), kmax, _ptr(params),
                      _ptr(idx), _ptr(cnt), _ptr(xyz), _ptr(centre), _ptr(out),
                      _ptr(feat), int(n_threads))

@@ -32,6 +32,12 @@ import synth  # noqa: E402
 LIBRARIES = {
     "train64": (64, 4),    # the benchmark library: "known objects"
     "unknown32": (32, 7),  # shapes never seen in training: "unknown objects"
+    # training libraries of the data-efficiency comparison (Sec. IV-B,
+    # Table I: 5 / 20 / 50 / 100 training objects)
+    "few5": (5, 31),
+    "few20": (20, 32),
+    "few50": (50, 33),
+    "few100": (100, 34),
 }
 
 

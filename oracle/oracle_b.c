@@ -176,6 +176,35 @@ static int orb_select(const float *pts, int n, const float c[3], float r2,
   return cnt;
 }
 
+/* Global crop of one object (the ablation without locality, Sec. IV-B
+ * GLOBAL-OCN): its first kmax samples in index order -- an area-uniform
+ * subset of the whole surface -- in the same canonical frame as orb_select.
+ * Returns the count. */
+static int orb_select_global(const float *pts, int n, const float c[3], int kmax,
+                             const float (*rot)[3], int32_t *idx_out, float *xyz_out) {
+  int cnt = n < kmax ? n : kmax;
+  for (int k = 0; k < kmax; ++k) {
+    if (k < cnt) {
+      float d0 = pts[3 * k] - c[0];
+      float d1 = pts[3 * k + 1] - c[1];
+      float d2 = pts[3 * k + 2] - c[2];
+      idx_out[k] = k;
+      if (rot == NULL) {
+        xyz_out[3 * k] = d0;
+        xyz_out[3 * k + 1] = d1;
+        xyz_out[3 * k + 2] = d2;
+      } else {
+        for (int a = 0; a < 3; ++a)
+          xyz_out[3 * k + a] = orb_dot3(rot[a][0], rot[a][1], rot[a][2], d0, d1, d2);
+      }
+    } else {
+      idx_out[k] = -1;
+      xyz_out[3 * k] = xyz_out[3 * k + 1] = xyz_out[3 * k + 2] = 0.0f;
+    }
+  }
+  return cnt;
+}
+
 /* ---------------------------------------------------------------- float64 */
 
 /* Parameter offsets into the flat float64 buffer, in this order:
@@ -291,6 +320,7 @@ typedef struct {
   double *out, *feat_out;
   int status;
   int lo, hi;
+  int global; /* 1: global crops (orb_select_global) */
 } orb_job;
 
 static int orb_pair_valid(const orb_job *j, int p) {
@@ -309,6 +339,12 @@ static void orb_crop_one(const orb_job *j, int p, orb_cand *scratch,
   const float *pb = j->points + (size_t)sb * j->n_points * 3;
   orb_pair_frame(j->poses + 7 * a, j->poses + 7 * b, j->aabb + 6 * sa,
                  j->aabb + 6 * sb, fr);
+  if (j->global) {
+    cnt[0] = orb_select_global(pa, j->n_points, fr->centre, j->kmax, NULL, idx, xyz);
+    cnt[1] = orb_select_global(pb, j->n_points, fr->cB, j->kmax, (const float(*)[3])fr->Rrel,
+                               idx + j->kmax, xyz + 3 * j->kmax);
+    return;
+  }
   float r2 = j->r * j->r;
   cnt[0] = orb_select(pa, j->n_points, fr->centre, r2, j->kmax, NULL, idx, xyz,
                       scratch);
@@ -359,12 +395,42 @@ static void *orb_worker(void *arg) {
  * outputs (each may be NULL): idx [P][2][kmax] (-1 padded), cnt [P][2],
  * xyz [P][2][kmax][3] canonical float32, centre [P][3], out [P][8] world
  * float64, feat [P][512] pooled float64.  Returns 0, -1 (bad index), -2 (OOM). */
+static int orb_run_mode(const float *points, const float *aabb, int n_shapes, int n_points,
+                        const float *poses, const int32_t *obj_shape, int n_obj,
+                        const int32_t *pairs, int n_pairs, float r, int kmax,
+                        const double *params, int32_t *idx_out, int32_t *cnt_out,
+                        float *xyz_out, float *centre_out, double *out, double *feat_out,
+                        int n_threads, int global);
+
 int orb_run(const float *points, const float *aabb, int n_shapes, int n_points,
             const float *poses, const int32_t *obj_shape, int n_obj,
             const int32_t *pairs, int n_pairs, float r, int kmax,
             const double *params, int32_t *idx_out, int32_t *cnt_out,
             float *xyz_out, float *centre_out, double *out, double *feat_out,
             int n_threads) {
+  return orb_run_mode(points, aabb, n_shapes, n_points, poses, obj_shape, n_obj, pairs,
+                      n_pairs, r, kmax, params, idx_out, cnt_out, xyz_out, centre_out, out,
+                      feat_out, n_threads, 0);
+}
+
+/* orb_run with global crops (orb_select_global) instead of local ones. */
+int orb_run_global(const float *points, const float *aabb, int n_shapes, int n_points,
+                   const float *poses, const int32_t *obj_shape, int n_obj,
+                   const int32_t *pairs, int n_pairs, float r, int kmax,
+                   const double *params, int32_t *idx_out, int32_t *cnt_out,
+                   float *xyz_out, float *centre_out, double *out, double *feat_out,
+                   int n_threads) {
+  return orb_run_mode(points, aabb, n_shapes, n_points, poses, obj_shape, n_obj, pairs,
+                      n_pairs, r, kmax, params, idx_out, cnt_out, xyz_out, centre_out, out,
+                      feat_out, n_threads, 1);
+}
+
+static int orb_run_mode(const float *points, const float *aabb, int n_shapes, int n_points,
+                        const float *poses, const int32_t *obj_shape, int n_obj,
+                        const int32_t *pairs, int n_pairs, float r, int kmax,
+                        const double *params, int32_t *idx_out, int32_t *cnt_out,
+                        float *xyz_out, float *centre_out, double *out, double *feat_out,
+                        int n_threads, int global) {
   if (n_threads < 1) n_threads = 1;
   if (n_threads > 256) n_threads = 256;
   pthread_t th[256];
@@ -378,7 +444,7 @@ int orb_run(const float *points, const float *aabb, int n_shapes, int n_points,
     j->n_pairs = n_pairs, j->kmax = kmax, j->r = r;
     j->idx_out = idx_out, j->cnt_out = cnt_out, j->xyz_out = xyz_out;
     j->centre_out = centre_out, j->params = params, j->out = out;
-    j->feat_out = feat_out, j->status = 0;
+    j->feat_out = feat_out, j->status = 0, j->global = global;
     j->lo = t * per;
     j->hi = (t + 1) * per < n_pairs ? (t + 1) * per : n_pairs;
     if (j->lo > j->hi) j->lo = j->hi;

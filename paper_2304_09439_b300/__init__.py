@@ -76,6 +76,10 @@ class Detector:
         abi.check(self._lib.locc_set_precision(self._h, _prec(precision)))
         self.precision = _prec(precision)
 
+    def set_crop_mode(self, mode: str) -> None:
+        """"local" (the method) or "global" (each object's first 64 samples)."""
+        abi.check(self._lib.locc_set_crop_mode(self._h, abi.CROP_MODES[mode]))
+
     def reserve(self, max_pairs: int, max_envs: int = 0) -> None:
         abi.check(self._lib.locc_reserve(self._h, int(max_pairs), int(max_envs)))
 

@@ -16,6 +16,7 @@ from typing import Optional
 from . import build as _build
 
 LOCC_FP32, LOCC_BF16, LOCC_FP8 = 0, 1, 2
+CROP_MODES = {"local": 0, "global": 1}
 PRECISIONS = {"fp32": LOCC_FP32, "bf16": LOCC_BF16, "fp8": LOCC_FP8}
 ERRORS = {-1: "INVALID_ARG", -2: "OOM", -3: "CUDA", -4: "TIMEOUT",
           -5: "BAD_WEIGHTS", -6: "BAD_INDEX", -7: "BUSY"}
@@ -30,7 +31,7 @@ EXPORTS = ["locc_create", "locc_set_precision", "locc_detect", "locc_detect_host
            "locc_autotune", "locc_server_create", "locc_server_submit", "locc_server_wait",
            "locc_server_stats", "locc_server_destroy", "locc_voxel_create", "locc_voxel_encode",
            "locc_voxel_latents", "locc_voxel_detect", "locc_voxel_detect_ex", "locc_voxel_status",
-           "locc_voxel_destroy", "locc_sim_step", "locc_sphere_contacts"]
+           "locc_voxel_destroy", "locc_sim_step", "locc_sphere_contacts", "locc_set_crop_mode"]
 VOID_EXPORTS = ("locc_destroy", "locc_last_error", "locc_trainer_destroy", "locc_server_destroy",
                 "locc_voxel_destroy")
 NOALLOC_MAX_PAIRS = 1024
@@ -135,6 +136,7 @@ def load(build_if_needed: bool = True) -> ctypes.CDLL:
         lib.locc_server_stats.argtypes = [P, ctypes.POINTER(ServerCounters), I]
         lib.locc_server_destroy.argtypes = [P]
         lib.locc_server_destroy.restype = None
+        lib.locc_set_crop_mode.argtypes = [P, I]
         lib.locc_sim_step.argtypes = [P, ctypes.POINTER(SimParams), P, P, P, I, P, P, I, P, P, P]
         lib.locc_sphere_contacts.argtypes = [P, P, P, I, P, P, I, P, P, P]
         lib.locc_voxel_create.argtypes = [ctypes.POINTER(_ShapeLibrary), P, ctypes.c_size_t,

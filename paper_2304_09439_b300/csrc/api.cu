@@ -130,6 +130,7 @@ DevLibrary dev_library(const locc_handle* h) {
   L.points = h->d_points;
   L.blocks = h->d_blocks;
   L.aabb = h->d_aabb;
+  L.inv = h->d_inv;
   L.n_shapes = h->n_shapes;
   L.n_points = h->n_points;
   L.n_pad = h->n_pad;
@@ -180,7 +181,7 @@ int run_path(locc_handle* h, const PairInputs& in, int n_cap, const int* n_dev, 
     if (prof) CUDA_TRY(cudaEventRecord(h->ev_c0[0], s));
     CUDA_TRY(launch_crop(lib, in, rg, h->radius, h->d_xyz, nullptr, h->d_cnt, h->d_centre, h->d_err,
                          h->d_defer,
-                         h->n_sm, h->crop_cap, s));
+                         h->n_sm, h->crop_cap, s, h->crop_mode));
     if (prof) {
       CUDA_TRY(cudaEventRecord(h->ev_c1[0], s));
       CUDA_TRY(cudaEventRecord(h->ev_e0[0], s));
@@ -200,7 +201,7 @@ int run_path(locc_handle* h, const PairInputs& in, int n_cap, const int* n_dev, 
     if (prof) CUDA_TRY(cudaEventRecord(h->ev_c0[i], s));
     CUDA_TRY(launch_crop(lib, in, rg, h->radius, h->d_xyz, nullptr, h->d_cnt, h->d_centre, h->d_err,
                          h->d_defer,
-                         h->n_sm, h->crop_cap, s));
+                         h->n_sm, h->crop_cap, s, h->crop_mode));
     if (prof) CUDA_TRY(cudaEventRecord(h->ev_c1[i], s));
     CUDA_TRY(cudaEventRecord(h->ev_crop[i], s));
     CUDA_TRY(cudaStreamWaitEvent(h->aux, h->ev_crop[i], 0));
@@ -258,6 +259,7 @@ int locc_create(const locc_shape_library* lib, const void* blob, size_t blob_byt
   // shape library: Morton-ordered blocks of 32 samples with block boxes
   const size_t S = (size_t)h->n_shapes, NP = (size_t)h->n_points, NPAD = (size_t)h->n_pad;
   std::vector<float4> pts(S * NPAD), blocks(S * h->n_blocks * 2), aabb(S * 2);
+  std::vector<int32_t> inv(S * NP);
   const float nanv = std::nanf("");
   std::vector<uint32_t> code(NP);
   std::vector<int> order(NP);
@@ -278,6 +280,7 @@ int locc_create(const locc_shape_library* lib, const void* blob, size_t blob_byt
     }
     std::iota(order.begin(), order.end(), 0);
     std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return code[x] < code[y]; });
+    for (size_t k = 0; k < NP; ++k) inv[s * NP + order[k]] = (int32_t)k;
     for (size_t k = 0; k < NPAD; ++k) {
       float4 v;
       if (k < NP) {
@@ -304,7 +307,7 @@ int locc_create(const locc_shape_library* lib, const void* blob, size_t blob_byt
   }
   int st = LOCC_OK;
   if (upload(&h->d_points, pts) != cudaSuccess || upload(&h->d_blocks, blocks) != cudaSuccess ||
-      upload(&h->d_aabb, aabb) != cudaSuccess) {
+      upload(&h->d_aabb, aabb) != cudaSuccess || upload(&h->d_inv, inv) != cudaSuccess) {
     st = fail(LOCC_ERR_OOM, "cannot upload the shape library: %s",
               cudaGetErrorString(cudaGetLastError()));
   }
@@ -400,6 +403,14 @@ int locc_stage_times(locc_handle* h, float* ms_out, int n) {
   int k = 0;
   for (; k < n && k < 5; ++k) ms_out[k] = t[k];
   return k;
+}
+
+int locc_set_crop_mode(locc_handle* h, int32_t mode) {
+  if (!h) return fail(LOCC_ERR_INVALID_ARG, "handle is NULL");
+  if (mode != LOCC_CROP_LOCAL && mode != LOCC_CROP_GLOBAL)
+    return fail(LOCC_ERR_INVALID_ARG, "crop mode must be LOCC_CROP_LOCAL or LOCC_CROP_GLOBAL");
+  h->crop_mode = mode;
+  return LOCC_OK;
 }
 
 int locc_set_pipeline(locc_handle* h, int32_t n_chunks, int32_t crop_ctas_per_sm) {
@@ -533,7 +544,7 @@ int locc_crop(locc_handle* h, const float* poses, const int32_t* obj_shape, int3
   CUDA_TRY(launch_crop(dev_library(h), in, whole_range(n_pairs, nullptr), h->radius,
                        reinterpret_cast<float4*>(xyz_out), idx_out, cnt_out,
                        reinterpret_cast<float4*>(centre_out), h->d_err, h->d_defer, h->n_sm, 0,
-                       (cudaStream_t)stream));
+                       (cudaStream_t)stream, h->crop_mode));
   return LOCC_OK;
 }
 
@@ -648,6 +659,7 @@ void locc_destroy(locc_handle* h) {
   free_params(h);
   cudaFree(h->d_points);
   cudaFree(h->d_blocks);
+  cudaFree(h->d_inv);
   cudaFree(h->d_aabb);
   cudaFree(h->d_err);
   cudaFree(h->d_env_counts);

@@ -28,6 +28,7 @@ struct DevLibrary {
   const float4* points;
   const float4* blocks;
   const float4* aabb;
+  const int32_t* inv;  // [S][n_points]: storage position of sample index i
   int n_shapes;
   int n_points;
   int n_pad;
@@ -148,9 +149,12 @@ namespace locc {
 // grid_cap (crop): at most this many resident CTAs per SM (0 = occupancy limit).
 // defer (crop): device int [1 + 2 * (pairs of one launch)], scratch for the
 // objects left to the exact fallback kernel (defer[0] = their count).
+// mode: LOCC_CROP_LOCAL (nearest-first within the ball) or LOCC_CROP_GLOBAL
+// (the first KMAX samples of each shape, same canonical frame).
 cudaError_t launch_crop(const DevLibrary& lib, const PairInputs& in, const PairRange& rg,
                         float r, float4* xyz, int32_t* idx, int32_t* cnt, float4* centre,
-                        int* err, int* defer, int n_sm, int grid_cap, cudaStream_t stream);
+                        int* err, int* defer, int n_sm, int grid_cap, cudaStream_t stream,
+                        int mode = LOCC_CROP_LOCAL);
 cudaError_t launch_encoder_fp32(const float4* xyz, const PairRange& rg,
                                 const Fp32Params& prm, float* feat, int n_sm,
                                 cudaStream_t stream);

@@ -538,12 +538,69 @@ __global__ void __launch_bounds__(64) crop_fallback_kernel(DevLibrary lib, PairI
   }
 }
 
+// Global crops (the ablation without locality): each object keeps its first
+// KMAX surface samples -- an area-uniform subset of the whole surface -- in
+// the same canonical frame as the local crop (A's body axes, origin at the
+// crop centre).  One CTA of two warps (A, B) per pair.
+__global__ void __launch_bounds__(64)
+    crop_global_kernel(DevLibrary lib, PairInputs in, PairRange rg, float4* __restrict__ xyz_out,
+                       int32_t* __restrict__ idx_out, int32_t* __restrict__ cnt_out,
+                       float4* __restrict__ centre_out, int* __restrict__ err) {
+  __shared__ unsigned long long keys[2][KMAX];
+  __shared__ float rsh[9];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int lo, hi;
+  range_bounds(rg, &lo, &hi);
+  for (int p = lo + blockIdx.x; p < hi; p += gridDim.x) {
+    int a, b, sa, sb;
+    const bool ok =
+        load_pair(in, lib.n_shapes, p, &a, &b, &sa, &sb, (warp == 0 && lane == 0) ? err : nullptr);
+    float4* xo = xyz_out + ((size_t)p * 2 + warp) * KMAX;
+    int32_t* io = idx_out ? idx_out + ((size_t)p * 2 + warp) * KMAX : nullptr;
+    if (!ok) {
+      const float nan = __int_as_float(0x7fc00000);
+      xo[lane] = xo[lane + 32] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (io) io[lane] = io[lane + 32] = -1;
+      if (lane == 0) cnt_out[2 * p + warp] = 0;
+      if (warp == 0 && lane == 0 && centre_out) centre_out[p] = make_float4(nan, nan, nan, nan);
+      __syncthreads();
+      continue;
+    }
+    Frame f;
+    pair_frame(in.poses + 7 * (size_t)a, in.poses + 7 * (size_t)b, lib.aabb[2 * sa],
+               lib.aabb[2 * sa + 1], lib.aabb[2 * sb], lib.aabb[2 * sb + 1], f);
+    if (warp == 0 && lane == 0 && centre_out) centre_out[p] = make_float4(f.c[0], f.c[1], f.c[2], 0.f);
+    if (warp == 1 && lane == 0) {
+#pragma unroll
+      for (int i = 0; i < 9; ++i) rsh[i] = f.rrel[i];
+    }
+    const int shape = warp == 0 ? sa : sb;
+    const int cnt = min(KMAX, lib.n_points);
+    for (int k = lane; k < cnt; k += 32) {
+      const int pos = lib.inv[(size_t)shape * lib.n_points + k];
+      keys[warp][k] = ((unsigned long long)k << 16) | (unsigned long long)pos;
+    }
+    __syncthreads();
+    write_crop(keys[warp], cnt, lib.points + (size_t)shape * lib.n_pad, warp == 0 ? f.c[0] : f.cb[0],
+               warp == 0 ? f.c[1] : f.cb[1], warp == 0 ? f.c[2] : f.cb[2], warp == 1 ? rsh : nullptr,
+               xo, io, lane);
+    if (lane == 0) cnt_out[2 * p + warp] = cnt;
+    __syncthreads();
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_crop(const DevLibrary& lib, const PairInputs& in, const PairRange& rg, float r,
                         float4* xyz, int32_t* idx, int32_t* cnt, float4* centre, int* err,
-                        int* defer, int n_sm, int grid_cap, cudaStream_t stream) {
+                        int* defer, int n_sm, int grid_cap, cudaStream_t stream, int mode) {
   if (in.n_pairs <= 0) return cudaSuccess;
+  if (mode == LOCC_CROP_GLOBAL) {
+    const int span = (in.n_pairs + rg.n_chunks - 1) / rg.n_chunks + 1;
+    crop_global_kernel<<<std::max(1, std::min(span, 16 * n_sm)), 64, 0, stream>>>(
+        lib, in, rg, xyz, idx, cnt, centre, err);
+    return cudaGetLastError();
+  }
   // one wave of resident CTAs (at most grid_cap per SM); each strides over its pairs
   static int per_sm = 0;
   if (per_sm == 0) {

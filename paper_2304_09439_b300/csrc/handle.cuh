@@ -17,6 +17,8 @@ struct locc_handle {
   float4* d_points = nullptr;
   float4* d_blocks = nullptr;
   float4* d_aabb = nullptr;
+  int32_t* d_inv = nullptr;  // [S][n_points]: storage position of each sample index
+  int crop_mode = LOCC_CROP_LOCAL;
   // parameters (device): float32 W^T / b for the CUDA-core path
   float* d_w32 = nullptr;
   locc::Fp32Params fp32{};

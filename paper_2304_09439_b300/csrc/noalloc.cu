@@ -101,7 +101,7 @@ extern "C" int locc_detect_noalloc(locc_handle* h, const float* poses, const int
   PairInputs in{poses, obj_shape, pairs, n_obj, n_pairs};
   const PairRange rg = whole_range(n_pairs, nullptr);
   cudaError_t e = launch_crop(dev_library(h), in, rg, h->radius, xyz, nullptr, cnt, centre,
-                              h->d_err, defer, h->n_sm, 0, s);
+                              h->d_err, defer, h->n_sm, 0, s, h->crop_mode);
   if (e == cudaSuccess) e = launch_encoder_fp32(xyz, rg, h->fp32, feat, h->n_sm, s);
   if (e == cudaSuccess)
     e = launch_head_fp32(feat, rg, h->fp32, &in, centre, out, nullptr, h->n_sm, s);

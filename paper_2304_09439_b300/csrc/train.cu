@@ -460,7 +460,7 @@ int locc_train_step(locc_trainer* t, const float* poses, const int32_t* obj_shap
   auto gB = [&](int l) { return g + PARAM_OFF_B[l]; };
   PairInputs in{poses, obj_shape, pairs, n_obj, n_pairs};
   TCU(launch_crop(dev_library(h), in, whole_range(n_pairs, nullptr), h->radius, t->xyz, nullptr,
-                  t->cnt, t->centre, h->d_err, t->defer, h->n_sm, 0, s));
+                  t->cnt, t->centre, h->d_err, t->defer, h->n_sm, 0, s, h->crop_mode));
   TCU(cudaMemsetAsync(t->loss, 0, 4, s));
   TCU(cudaMemsetAsync(g, 0, (size_t)LOCC_N_PARAMS * 4, s));
   prep_kernel<<<P, ROWS, 0, s>>>(t->xyz, t->centre, poses, pairs, n_obj, targets, rot, t->X, t->T, P);

@@ -30,7 +30,9 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 # procedural shape libraries by name: (number of shapes, seed)
-LIBRARIES = {"train64": (64, 4), "unknown32": (32, 7)}
+LIBRARIES = {"train64": (64, 4), "unknown32": (32, 7),
+             # the data-efficiency comparison (Sec. IV-B): 5 / 20 / 50 / 100 shapes
+             "few5": (5, 31), "few20": (20, 32), "few50": (50, 33), "few100": (100, 34)}
 RADIUS = 0.25
 
 
@@ -143,6 +145,7 @@ def evaluate(det, lib_name, data, dev, cache):
         lib = cache[lib_name]
         blob = cache["blob"]()
         with Detector(lib.points, lib.aabb, blob, RADIUS, det.precision) as d2:
+            d2.set_crop_mode(cache.get("crop_mode", "local"))
             return _run(d2, data, dev)
     return _run(det, data, dev)
 
@@ -171,6 +174,9 @@ def main():
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--out", default=None)
     ap.add_argument("--report", default=None)
+    ap.add_argument("--crop-mode", default="local", choices=["local", "global"],
+                    help="local crops (the method) or global crops (the ablation without "
+                         "locality)")
     args = ap.parse_args()
 
     import torch
@@ -188,13 +194,15 @@ def main():
     lib = make_library(lib_name)
     tests = [(p,) + load_dataset(p) for p in args.test]
     det = Detector(lib.points, lib.aabb, synth.xavier_weights(args.seed), RADIUS, "fp32")
+    det.set_crop_mode(args.crop_mode)
     tr = Trainer(det, args.batch, lr=args.lr)
-    cache = {"train_lib": lib_name, "blob": lambda: weights.pack(
+    cache = {"train_lib": lib_name, "crop_mode": args.crop_mode, "blob": lambda: weights.pack(
         weights.from_flat(tr.params().cpu().numpy()))}
 
     report = {"train": args.data, "n_train": int(len(train["pairs"])),
               "n_val": int(len(val["pairs"])), "batch": args.batch, "steps": args.steps,
-              "lr": args.lr, "lr_final": args.lr_final, "schedule": "cosine", "evals": [],
+              "lr": args.lr, "lr_final": args.lr_final, "schedule": "cosine",
+              "crop_mode": args.crop_mode, "evals": [],
               "val": []}
 
     def run_eval(step):
