@@ -447,6 +447,36 @@ int locc_sphere_contacts(locc_handle *h, const float *poses, const int32_t *obj_
                          int32_t n_obj, const int32_t *pairs, const int32_t *n_pairs_dev,
                          int32_t max_pairs, const float *radius, float *out, void *stream);
 
+/* --------------------------------------------------------------- UCF-GJK ----
+ * The analytical comparator (Sec. IV-B, Claim 1; "range of parameters in
+ * UCF-GJK" of the hyper-parameter table): each shape is a union of convex
+ * elements given by their vertices (a convex decomposition; body frame); a
+ * pair collides when any pair of elements intersects, each element pair being
+ * tested by GJK on the Minkowski difference for exactly `iterations`
+ * iterations (a uniform computational flow).  A pair the iterations leave
+ * undecided counts as colliding.  Float32. */
+typedef struct locc_gjk locc_gjk;
+
+/* Copy a convex decomposition to the device: shape s owns elements
+ * [elem_off[s], elem_off[s + 1]), element e owns vertices
+ * [vert_off[e], vert_off[e + 1]) of verts (host float32 [n][3]); every shape
+ * needs >= 1 element and every element >= 1 vertex.  Blocking.  Errors:
+ * LOCC_ERR_INVALID_ARG, LOCC_ERR_OOM. */
+int locc_gjk_create(int32_t n_shapes, const int32_t *elem_off, const int32_t *vert_off,
+                    const float *verts, locc_gjk **out);
+
+/* collide [n_pairs] uint8 (device): 1 collision, 0 none, 0xff out-of-range
+ * pair (which also raises the flag locc_gjk_status reports).  poses, obj_shape,
+ * pairs as for locc_detect; 1 <= iterations <= 1024.  Asynchronous. */
+int locc_gjk_detect(locc_gjk *h, const float *poses, const int32_t *obj_shape, int32_t n_obj,
+                    const int32_t *pairs, int32_t n_pairs, int32_t iterations,
+                    uint8_t *collide, void *stream);
+
+/* Synchronise `stream`; 0 or LOCC_ERR_BAD_INDEX (flag then cleared). */
+int locc_gjk_status(locc_gjk *h, void *stream);
+
+void locc_gjk_destroy(locc_gjk *h);
+
 /* ------------------------------------------------ voxel-latent variant ----
  * The paper's own design (Sec. III "Local Crop Collision Network"; appendix
  * "Architecture Details"): a shape encoder computes, once per library shape,

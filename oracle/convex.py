@@ -28,10 +28,13 @@ def hulls_intersect(A, B) -> bool:
     A_eq[3, :n] = 1.0
     A_eq[4, n:] = 1.0
     b_eq = np.array([0.0, 0.0, 0.0, 1.0, 1.0])
-    res = linprog(np.zeros(n + m), A_eq=A_eq, b_eq=b_eq, bounds=(0, None), method="highs")
-    if res.status not in (0, 2):
-        raise RuntimeError(f"linprog status {res.status}: {res.message}")
-    return res.status == 0
+    # HiGHS' default can end undecided on degenerate instances; the dual
+    # simplex and the interior-point solver are tried next
+    for method in ("highs", "highs-ds", "highs-ipm"):
+        res = linprog(np.zeros(n + m), A_eq=A_eq, b_eq=b_eq, bounds=(0, None), method=method)
+        if res.status in (0, 2):
+            return res.status == 0
+    raise RuntimeError(f"linprog undecided: {res.message}")
 
 
 def scaled(V, s):
@@ -44,9 +47,13 @@ def scaled(V, s):
 def robust_intersect(A, B, delta: float = 2e-3):
     """(answer, robust): robust when shrinking and growing both hulls by
     delta about their centroids does not change the answer."""
-    lo = hulls_intersect(scaled(A, 1 - delta), scaled(B, 1 - delta))
-    hi = hulls_intersect(scaled(A, 1 + delta), scaled(B, 1 + delta))
-    return hulls_intersect(A, B), lo == hi
+    try:
+        lo = hulls_intersect(scaled(A, 1 - delta), scaled(B, 1 - delta))
+        hi = hulls_intersect(scaled(A, 1 + delta), scaled(B, 1 + delta))
+        mid = hulls_intersect(A, B)
+    except RuntimeError:  # solver undecided: not a case to compare on
+        return False, False
+    return mid, lo == hi
 
 
 def posed(V, pose):

@@ -19,7 +19,7 @@ from .abi import LoccError, LOCC_FP32, LOCC_BF16, LOCC_FP8, PRECISIONS
 KMAX = 64
 OUT_DIM = 8
 
-__all__ = ["Detector", "VoxelDetector", "Trainer", "Server", "LoccError", "LOCC_FP32", "LOCC_BF16", "LOCC_FP8", "weights",
+__all__ = ["Detector", "VoxelDetector", "GJK", "Trainer", "Server", "LoccError", "LOCC_FP32", "LOCC_BF16", "LOCC_FP8", "weights",
            "abi", "KMAX", "OUT_DIM"]
 
 
@@ -331,6 +331,57 @@ class VoxelDetector:
 
     def status(self, stream=None) -> None:
         abi.check(self._lib.locc_voxel_status(self._h, abi.stream_ptr(stream)))
+
+
+class GJK:
+    """UCF-GJK comparator (``locc_gjk``): a convex decomposition on the current
+    CUDA device; ``detect`` tests every pair with a fixed GJK iteration count."""
+
+    def __init__(self, elem_off, vert_off, verts):
+        import numpy as np
+        import torch
+        self._lib = abi.load()
+        self.device = torch.cuda.current_device()
+        eo = np.ascontiguousarray(elem_off, np.int32)
+        vo = np.ascontiguousarray(vert_off, np.int32)
+        vv = np.ascontiguousarray(verts, np.float32)
+        self._h = ctypes.c_void_p()
+        abi.check(self._lib.locc_gjk_create(len(eo) - 1, eo.ctypes.data, vo.ctypes.data,
+                                            vv.ctypes.data, ctypes.byref(self._h)))
+
+    def close(self) -> None:
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.locc_gjk_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def detect(self, poses, obj_shape, pairs, iterations: int, collide=None, stream=None):
+        """uint8 [P] on the device: 1 collision, 0 none, 255 bad pair."""
+        import torch
+        _need(poses, torch.float32, "poses", self.device)
+        _need(obj_shape, torch.int32, "obj_shape", self.device)
+        _need(pairs, torch.int32, "pairs", self.device)
+        P = pairs.shape[0]
+        if collide is None:
+            collide = torch.empty(P, dtype=torch.uint8, device=pairs.device)
+        abi.check(self._lib.locc_gjk_detect(self._h, abi.ptr(poses), abi.ptr(obj_shape),
+                                            poses.shape[0], abi.ptr(pairs), P, int(iterations),
+                                            abi.ptr(collide), abi.stream_ptr(stream)))
+        return collide
+
+    def status(self, stream=None) -> None:
+        abi.check(self._lib.locc_gjk_status(self._h, abi.stream_ptr(stream)))
 
 
 class Trainer:

@@ -14,7 +14,7 @@ a torus).
 
 from .shapes import (Mesh, box_mesh, ellipsoid_mesh, torus_mesh, l_bracket,
                      random_union, sample_surface, ShapeLibrary, make_library,
-                     tiny_library)
+                     tiny_library, convex_elements)
 from .poses import (random_quaternions, random_poses, quat_multiply,
                     compose_relative_tiny)
 from .weights import LAYER_DIMS, xavier_weights, voxel_weights
@@ -26,5 +26,5 @@ __all__ = [
     "random_union", "sample_surface", "ShapeLibrary", "make_library",
     "tiny_library", "random_quaternions", "random_poses", "quat_multiply",
     "compose_relative_tiny", "LAYER_DIMS", "xavier_weights", "voxel_weights", "uneven_scene",
-    "sweep_pairs", "client_batch", "drop_scene", "drop_initial_state",
+    "sweep_pairs", "client_batch", "drop_scene", "drop_initial_state", "convex_elements",
 ]

@@ -316,3 +316,37 @@ def make_library(n_shapes: int, seed: int, n_points: int = N_POINTS,
     meshes = [random_union(rng, min_tris, max_tris) for _ in range(n_shapes)]
     return _finish(meshes, [f"union{i}" for i in range(n_shapes)], n_points,
                    rng)
+
+
+def convex_elements(lib: "ShapeLibrary", max_vertices: int = 0, max_elements: int = 0):
+    """Convex decomposition of every library shape from its components (each
+    component of a procedural shape is a box or an ellipsoid, so convex):
+    element e of shape s is the vertex set of one component, cut to
+    ``max_vertices`` by farthest-point sampling when > 0 (the convex hull of
+    the kept vertices is then an inner approximation), and at most
+    ``max_elements`` elements per shape (the largest, by vertex spread) when
+    > 0.  Returns elem_off int32 [S + 1], vert_off int32 [E + 1] and verts
+    float32 [V, 3] (body frame)."""
+    elem_off, vert_off, verts = [0], [0], []
+    for m in lib.meshes:
+        elems = []
+        for c in np.unique(m.comp):
+            v = m.vertices[np.unique(m.faces[m.comp == c].ravel())]
+            if max_vertices and len(v) > max_vertices:
+                keep = [int(np.argmax(np.linalg.norm(v - v.mean(0), axis=1)))]
+                d = np.linalg.norm(v - v[keep[0]], axis=1)
+                while len(keep) < max_vertices:
+                    i = int(np.argmax(d))
+                    keep.append(i)
+                    d = np.minimum(d, np.linalg.norm(v - v[i], axis=1))
+                v = v[keep]
+            elems.append(v)
+        if max_elements and len(elems) > max_elements:
+            spread = [np.ptp(e, axis=0).prod() for e in elems]
+            elems = [elems[i] for i in np.argsort(spread)[::-1][:max_elements]]
+        for e in elems:
+            verts.append(e.astype(np.float32))
+            vert_off.append(vert_off[-1] + len(e))
+        elem_off.append(elem_off[-1] + len(elems))
+    return (np.asarray(elem_off, np.int32), np.asarray(vert_off, np.int32),
+            np.concatenate(verts).astype(np.float32))
