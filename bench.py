@@ -380,24 +380,34 @@ def voxel_leg(lib, dsc, scene_pairs, stream, flush, steps, warmup, peaks):
             k = i % len(dsc)
             vd.detect(dsc[k][0], dsc[k][1], scene_pairs[k], logit=logits[k], stream=stream)
 
-        for i in range(warmup):
-            flush.zero_()
-            one(i)
-        torch.cuda.synchronize()
-        ms, pairs = 0.0, 0
-        for i in range(steps):
-            flush.zero_()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            one(i)
-            e1.record(stream)
-            e1.synchronize()
-            ms += e0.elapsed_time(e1)
-            pairs += len(scene_pairs[i % len(dsc)])
-        vd.status(stream)
+        def timed():
+            for i in range(warmup):
+                flush.zero_()
+                one(i)
+            torch.cuda.synchronize()
+            ms, pairs = 0.0, 0
+            for i in range(steps):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                one(i)
+                e1.record(stream)
+                e1.synchronize()
+                ms += e0.elapsed_time(e1)
+                pairs += len(scene_pairs[i % len(dsc)])
+            vd.status(stream)
+            return ms, pairs
+
+        ms, pairs = timed()
+        vd.set_precision("bf16")
+        ms16, pairs16 = timed()
+        vd.set_precision("fp32")
     per_launch = ms / steps
     achieved = FLOP_VOX * (pairs / steps) / (per_launch * 1e-3) / 1e12
     peak = 148 * 128 * 2 * peaks.get("sm_max_mhz", 2032.0) * 1e6 / 1e12
+    per16 = ms16 / steps
+    ach16 = FLOP_VOX * (pairs16 / steps) / (per16 * 1e-3) / 1e12
+    peak16 = peaks["bf16_tflops_sustained"]
     return {"what": "voxel-latent variant: per-pair cell selection + average pooling + "
                     "symmetric predictor over device-resident shape latents",
             "pairs_per_s": pairs / (ms * 1e-3), "ms_per_step": per_launch, "dtype": "f32",
@@ -408,7 +418,14 @@ def voxel_leg(lib, dsc, scene_pairs, stream, flush, steps, warmup, peaks):
                          "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                          "traffic": None,
                          "peak_source": "derived: 148 SM x 128 FP32 lanes x 2 x sm_max_mhz",
-                         "algorithmic": f"{FLOP_VOX} FLOP per pair x pairs per launch"}}
+                         "algorithmic": f"{FLOP_VOX} FLOP per pair x pairs per launch"},
+            "bf16": {"pairs_per_s": pairs16 / (ms16 * 1e-3), "ms_per_step": per16,
+                     "dtype": "bf16",
+                     "roofline": {"kernel": "vox_tc_kernel", "bound": "tensor",
+                                  "achieved": ach16, "peak": peak16, "unit": "TFLOP/s",
+                                  "frac": ach16 / peak16, "traffic": None,
+                                  "peak_source": "measured bf16_tflops_sustained",
+                                  "algorithmic": f"{FLOP_VOX} FLOP per pair x pairs per launch"}}}
 
 
 def main():

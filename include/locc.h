@@ -537,6 +537,12 @@ int locc_voxel_detect_ex(locc_voxel *h, const float *poses, const int32_t *obj_s
                          float *logit, int32_t *cell_ranges, float *pooled,
                          void *stream);
 
+/* Arithmetic of the predictor: LOCC_FP32 (CUDA cores, default) or LOCC_BF16
+ * (tcgen05 tensor cores: bf16 operands -- pooled features and pose included --
+ * with float32 accumulation; selection and pooling stay float32).  Errors:
+ * LOCC_ERR_INVALID_ARG. */
+int locc_voxel_set_precision(locc_voxel *h, int32_t precision);
+
 /* Synchronise `stream` and report (then clear) the device error flag:
  * 0 or LOCC_ERR_BAD_INDEX. */
 int locc_voxel_status(locc_voxel *h, void *stream);

@@ -295,6 +295,10 @@ class VoxelDetector:
     def __exit__(self, *a):
         self.close()
 
+    def set_precision(self, precision) -> None:
+        """"fp32" (CUDA cores) or "bf16" (tcgen05) for the predictor."""
+        abi.check(self._lib.locc_voxel_set_precision(self._h, _prec(precision)))
+
     def encode(self, stream=None) -> None:
         """Recompute the latents (asynchronous on ``stream``)."""
         abi.check(self._lib.locc_voxel_encode(self._h, abi.stream_ptr(stream)))

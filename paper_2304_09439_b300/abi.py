@@ -31,6 +31,7 @@ EXPORTS = ["locc_create", "locc_set_precision", "locc_detect", "locc_detect_host
            "locc_autotune", "locc_server_create", "locc_server_submit", "locc_server_wait",
            "locc_server_stats", "locc_server_destroy", "locc_voxel_create", "locc_voxel_encode",
            "locc_voxel_latents", "locc_voxel_detect", "locc_voxel_detect_ex", "locc_voxel_status",
+           "locc_voxel_set_precision",
            "locc_voxel_destroy", "locc_sim_step", "locc_sphere_contacts", "locc_set_crop_mode",
            "locc_gjk_create", "locc_gjk_detect", "locc_gjk_status", "locc_gjk_destroy"]
 VOID_EXPORTS = ("locc_destroy", "locc_last_error", "locc_trainer_destroy", "locc_server_destroy",
@@ -152,6 +153,7 @@ def load(build_if_needed: bool = True) -> ctypes.CDLL:
         lib.locc_voxel_detect.argtypes = [P, P, P, I, P, I, P, P]
         lib.locc_voxel_detect_ex.argtypes = [P, P, P, I, P, I, P, P, P, P]
         lib.locc_voxel_status.argtypes = [P, P]
+        lib.locc_voxel_set_precision.argtypes = [P, I]
         lib.locc_voxel_destroy.argtypes = [P]
         lib.locc_voxel_destroy.restype = None
         lib.locc_destroy.argtypes = [P]

@@ -38,6 +38,7 @@
 
 #include "common.cuh"
 #include "handle.cuh"
+#include "tc_ptx.cuh"
 
 namespace locc {
 namespace {
@@ -209,19 +210,45 @@ __device__ __forceinline__ int range_count(const int* r) {
   return (n0 > 0 && n1 > 0 && n2 > 0) ? n0 * n1 * n2 : 0;
 }
 
-// Mean latent over the cells of a range box, computed by one warp (lane =
-// feature + 16 x half; the halves take alternate cells); every lane returns
-// the mean of feature lane % 16.
+// Mean latent over the cells of a range box, computed by one warp: lane l
+// sums the 16 features of cells l, l + 32, ... (four 16-byte loads per cell,
+// all independent), then a butterfly exchange reduces the 16 partial sums
+// over the lanes in 16 shuffles, halving the features a lane keeps at each
+// step; every lane returns the mean of feature lane % 16.
 __device__ __forceinline__ float pool_range(const float* lat, const int* r, int lane) {
   const int n = range_count(r);
   const int n1 = r[3] - r[2] + 1, n2 = r[5] - r[4] + 1;
-  float sum = 0.f;
-  for (int q = lane >> 4; q < n; q += 2) {
+  float v[16];
+#pragma unroll
+  for (int f = 0; f < 16; ++f) v[f] = 0.f;
+  for (int q = lane; q < n; q += 32) {
     const int i = r[0] + q / (n1 * n2), j = r[2] + (q / n2) % n1, k = r[4] + q % n2;
-    sum += lat[((i * VM + j) * VM + k) * VF + (lane & 15)];
+    const float4* c = reinterpret_cast<const float4*>(lat + ((i * VM + j) * VM + k) * VF);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const float4 x = __ldg(c + u);
+      v[4 * u] += x.x;
+      v[4 * u + 1] += x.y;
+      v[4 * u + 2] += x.z;
+      v[4 * u + 3] += x.w;
+    }
   }
-  sum += __shfl_xor_sync(0xffffffffu, sum, 16);
-  return n > 0 ? __fdiv_rn(sum, (float)n) : 0.f;
+  // after the steps of offsets 16, 8, 4, 2 a lane holds feature (lane >> 1)
+#pragma unroll
+  for (int off = 16, w = 8; off >= 2; off >>= 1, w >>= 1) {
+    const bool up = (lane & off) != 0;
+#pragma unroll
+    for (int f = 0; f < 8; ++f) {
+      if (f < w) {
+        const float keep = up ? v[f + w] : v[f];
+        const float send = up ? v[f] : v[f + w];
+        v[f] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+      }
+    }
+  }
+  v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
+  const float mean = n > 0 ? __fdiv_rn(v[0], (float)n) : 0.f;
+  return __shfl_sync(0xffffffffu, mean, 2 * (lane & 15));
 }
 
 // act_out[r][c] = act(W^T-major layer over act_in rows [0, R)), 256 threads:
@@ -396,6 +423,386 @@ __global__ void __launch_bounds__(256, 2)
   }
 }
 
+// ------------------------------------------------ predictor on tcgen05 (BF16)
+// Tiles of 128 pairs (one pair per TMEM lane).  Warps 0-7 select and pool the
+// tile's pairs into the A operands X_A, X_B ([feature || pose || 0], K = 32,
+// bf16) and run every epilogue (two warps per TMEM lane quarter, half of the
+// columns each); one elected lane of warp 8 issues the MMAs (M = 128, N = 128)
+// and streams the weights of q1..q3 through two 32 KB stages.  TMEM columns:
+// object A [0, 128), object B [128, 256), the shared MLP [256, 384).
+//   p1..p3 (both objects) -> max -> q1 -> q2 -> q3 -> q4 on the CUDA cores.
+// Every mbarrier completes once per tile except the weight stages (stage 0
+// carries q1 and q3 of every tile: two phases per tile); no wait is ever more
+// than one phase behind.  Waits are bounded; on a timeout the CTA raises bit
+// 2 of the error flag, drains and returns.
+namespace vtc {
+using namespace tc;
+constexpr long long WAIT = 2000000000LL;
+constexpr int WQ = 128 * 128 * 2;                       // one 128 x 128 bf16 weight tile
+constexpr int S_WP1 = 0;                                // [128 x 32] bf16, 8 KB
+constexpr int S_WP2 = S_WP1 + 128 * 32 * 2;             // resident p2, p3
+constexpr int S_WP3 = S_WP2 + WQ;
+constexpr int S_QST = S_WP3 + WQ;                       // two stages for q1..q3
+constexpr int S_XA = S_QST + 2 * WQ;                    // [128 x 32] bf16
+constexpr int S_XB = S_XA + 128 * 32 * 2;
+constexpr int S_HA = S_XB + 128 * 32 * 2;               // [128 x 128] bf16 (also Z)
+constexpr int S_HB = S_HA + WQ;
+constexpr int S_BIAS = S_HB + WQ;                       // p1..p3, q1..q3 (128 each), q4 w (128), q4 b
+constexpr int BIAS_FLOATS = 7 * 128 + 4;
+constexpr int S_PART = S_BIAS + BIAS_FLOATS * 4;        // q4 partial sums [2][128]
+constexpr int S_VALID = S_PART + 2 * 128 * 4;           // [128] int
+constexpr int S_CTRL = S_VALID + 128 * 4;               // mbarriers, TMEM address, abort
+constexpr int SMEM = S_CTRL + 256;
+static_assert(SMEM <= 227 * 1024, "voxel tensor-core predictor shared memory");
+// global image: [p1][p2][p3][q1][q2][q3][biases] (the resident part first)
+constexpr int G_RES = S_QST;                            // p1, p2, p3 bytes
+constexpr int G_Q = G_RES;                              // q1 at G_Q, q2, q3 follow
+constexpr int G_BIAS = G_Q + 3 * WQ;
+constexpr int G_BYTES = G_BIAS + BIAS_FLOATS * 4;
+constexpr int THREADS = 288;
+
+// TMEM row -> relu(x + b) bf16 into a K = 128 operand, this thread's 64 columns
+__device__ __forceinline__ void epi64(uint32_t taddr, const float* b, unsigned char* dst, int row,
+                                      int c0) {
+  float v[32];
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    tmem_ld32(taddr + c0 + 32 * h, v);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int j = 8 * c, o = c0 + 32 * h + j;
+      uint4 w;
+      w.x = pack_bf16(fmaxf(v[j + 0] + b[o + 0], 0.f), fmaxf(v[j + 1] + b[o + 1], 0.f));
+      w.y = pack_bf16(fmaxf(v[j + 2] + b[o + 2], 0.f), fmaxf(v[j + 3] + b[o + 3], 0.f));
+      w.z = pack_bf16(fmaxf(v[j + 4] + b[o + 4], 0.f), fmaxf(v[j + 5] + b[o + 5], 0.f));
+      w.w = pack_bf16(fmaxf(v[j + 6] + b[o + 6], 0.f), fmaxf(v[j + 7] + b[o + 7], 0.f));
+      *reinterpret_cast<uint4*>(dst + kmajor_off(row, o, 128)) = w;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(THREADS, 1)
+    vox_tc_kernel(PairInputs in, int n_shapes, const float* __restrict__ aabb,
+                  const float* __restrict__ lat, const unsigned char* __restrict__ img,
+                  float* __restrict__ logit, int32_t* __restrict__ range_out,
+                  float* __restrict__ feat_out, int* __restrict__ err) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int n = in.n_pairs, n_tiles = (n + 127) / 128;
+  if ((int)blockIdx.x >= n_tiles) return;
+  const int my_tiles = (n_tiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
+  // barriers: 0 RES, 1 SF0, 2 SF1, 3 S0 (stage 0 read), 4 S1, 5 XR, 6 H1R, 7 H2R, 8 ZR0,
+  // 9 ZR1, 10 ZR2, 11 P1D, 12 P2D, 13 P3D, 14 Q1D, 15 Q2D, 16 Q3D, 17 DRAIN,
+  // 18 PART (both halves' partial logits written)
+  const uint32_t bar0 = smem_u32(smem + S_CTRL);
+  auto BAR = [&](int i) { return bar0 + 8u * (uint32_t)i; };
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + S_CTRL + 160);
+  volatile int* abort = reinterpret_cast<volatile int*>(smem + S_CTRL + 164);
+  static_assert(19 * 8 <= 160, "mbarriers overlap the TMEM slot");
+  if (tid == 0) {
+    for (int i = 0; i < 19; ++i) mbar_init(BAR(i), ((i >= 5 && i <= 10) || i == 18) ? 256 : 1);
+    *abort = 0;
+    fence_mbar_init();
+  }
+  if (warp == 0) {
+    tmem_alloc(smem_u32(tmem_slot), 512);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tbase = *tmem_slot;
+  const float* bias = reinterpret_cast<const float*>(smem + S_BIAS);
+  int* valid = reinterpret_cast<int*>(smem + S_VALID);
+  float* part = reinterpret_cast<float*>(smem + S_PART);
+  const uint32_t sWP1 = smem_u32(smem + S_WP1), sWP2 = smem_u32(smem + S_WP2),
+                 sWP3 = smem_u32(smem + S_WP3), sQ0 = smem_u32(smem + S_QST),
+                 sQ1 = smem_u32(smem + S_QST + WQ), sXA = smem_u32(smem + S_XA),
+                 sXB = smem_u32(smem + S_XB), sHA = smem_u32(smem + S_HA),
+                 sHB = smem_u32(smem + S_HB);
+  bool ok = true;
+
+  if (warp == 8) {
+    // ------------------------------------------------------------ MMA warp
+    if (lane == 0) {
+      mbar_expect_tx(BAR(0), G_RES + BIAS_FLOATS * 4);
+      for (int off = 0; off < G_RES; off += 32768)
+        bulk_g2s(smem_u32(smem + off), img + off, min(32768, G_RES - off), BAR(0));
+      bulk_g2s(smem_u32(smem + S_BIAS), img + G_BIAS, BIAS_FLOATS * 4, BAR(0));
+      // q1 -> stage 0, q2 -> stage 1 of the first tile
+      mbar_expect_tx(BAR(1), WQ);
+      bulk_g2s(sQ0, img + G_Q, WQ, BAR(1));
+      mbar_expect_tx(BAR(2), WQ);
+      bulk_g2s(sQ1, img + G_Q + WQ, WQ, BAR(2));
+    }
+    __syncwarp();
+    ok = mbar_wait_warp(BAR(0), 0, abort, WAIT);
+    const uint32_t id = idesc_bf16(128, 128);
+    auto chain = [&](uint32_t d, uint32_t a, uint32_t b, int K, uint32_t asbo) {
+      // D[128 x 128] = A[128 x K] . B[128 x K]^T, K-major, K in steps of 16
+      for (int kk = 0; kk < K / 16; ++kk)
+        mma_bf16(d, sdesc(a + 256 * kk, 128, asbo), sdesc(b + 256 * kk, 128, asbo), id, kk > 0);
+    };
+    for (int t = 0; t < my_tiles && ok; ++t) {
+      const uint32_t ph = t & 1;
+      // p1 for both objects
+      if (!(ok = mbar_wait_warp(BAR(5), ph, abort, WAIT))) break;
+      tc_fence_after();
+      if (elect_one()) {
+        chain(tbase + 0, sXA, sWP1, 32, 512);
+        chain(tbase + 128, sXB, sWP1, 32, 512);
+        mma_commit(BAR(11));
+      }
+      __syncwarp();
+      if (!(ok = mbar_wait_warp(BAR(6), ph, abort, WAIT))) break;
+      tc_fence_after();
+      if (elect_one()) {
+        chain(tbase + 0, sHA, sWP2, 128, 2048);
+        chain(tbase + 128, sHB, sWP2, 128, 2048);
+        mma_commit(BAR(12));
+      }
+      __syncwarp();
+      if (!(ok = mbar_wait_warp(BAR(7), ph, abort, WAIT))) break;
+      tc_fence_after();
+      if (elect_one()) {
+        chain(tbase + 0, sHA, sWP3, 128, 2048);
+        chain(tbase + 128, sHB, sWP3, 128, 2048);
+        mma_commit(BAR(13));
+      }
+      __syncwarp();
+      // q1 (stage 0, phase 2t), q2 (stage 1, phase t), q3 (stage 0, phase 2t + 1)
+      ok = mbar_wait_warp(BAR(8), ph, abort, WAIT) && mbar_wait_warp(BAR(1), 0, abort, WAIT);
+      if (!ok) break;
+      tc_fence_after();
+      if (elect_one()) {
+        chain(tbase + 256, sHA, sQ0, 128, 2048);
+        mma_commit(BAR(14));
+        mma_commit(BAR(3));
+      }
+      __syncwarp();
+      // stage 0 takes q3 once q1's MMAs are done
+      if (!(ok = mbar_wait_warp(BAR(3), (2 * t) & 1, abort, WAIT))) break;
+      if (lane == 0) {
+        mbar_expect_tx(BAR(1), WQ);
+        bulk_g2s(sQ0, img + G_Q + 2 * WQ, WQ, BAR(1));
+      }
+      __syncwarp();
+      ok = mbar_wait_warp(BAR(9), ph, abort, WAIT) && mbar_wait_warp(BAR(2), ph, abort, WAIT);
+      if (!ok) break;
+      tc_fence_after();
+      if (elect_one()) {
+        chain(tbase + 256, sHA, sQ1, 128, 2048);
+        mma_commit(BAR(15));
+        mma_commit(BAR(4));
+      }
+      __syncwarp();
+      ok = mbar_wait_warp(BAR(10), ph, abort, WAIT) && mbar_wait_warp(BAR(1), 1, abort, WAIT);
+      if (!ok) break;
+      tc_fence_after();
+      if (elect_one()) {
+        chain(tbase + 256, sHA, sQ0, 128, 2048);
+        mma_commit(BAR(16));
+        mma_commit(BAR(3));
+      }
+      __syncwarp();
+      // refill for the next tile: q1 -> stage 0 after q3's MMAs, q2 -> stage 1
+      // after q2's
+      if (t + 1 < my_tiles) {
+        ok = mbar_wait_warp(BAR(3), (2 * t + 1) & 1, abort, WAIT) &&
+             mbar_wait_warp(BAR(4), ph, abort, WAIT);
+        if (!ok) break;
+        if (lane == 0) {
+          mbar_expect_tx(BAR(1), WQ);
+          bulk_g2s(sQ0, img + G_Q, WQ, BAR(1));
+          mbar_expect_tx(BAR(2), WQ);
+          bulk_g2s(sQ1, img + G_Q + WQ, WQ, BAR(2));
+        }
+        __syncwarp();
+      }
+    }
+    if (!ok) *abort = 1;
+  } else {
+    // ------------------------------------------------------ epilogue warps
+    const uint32_t lane_off = (uint32_t)(32 * (warp & 3)) << 16;
+    const int row = tid & 127, half = tid >> 7, c0 = 64 * half;
+    unsigned char* XA = smem + S_XA;
+    unsigned char* XB = smem + S_XB;
+    unsigned char* HA = smem + S_HA;
+    unsigned char* HB = smem + S_HB;
+    ok = mbar_wait_or_abort(BAR(0), 0, abort, WAIT);
+    for (int t = 0; t < my_tiles && ok; ++t) {
+      const uint32_t ph = t & 1;
+      const int tile = (int)blockIdx.x + t * (int)gridDim.x;
+      // selection and pooling: warp w takes the tile's pairs w, w + 8, ...
+      for (int j = warp; j < 128; j += 8) {
+        const int p = tile * 128 + j;
+        int a = -1, b = -1, sa = -1, sb = -1;
+        const bool good = p < n && load_pair(in, n_shapes, p, &a, &b, &sa, &sb, lane == 0 ? err : nullptr);
+        float vA = 0.f, vB = 0.f;
+        if (good) {
+          const float* pa = in.poses + 7 * (size_t)a;
+          const float* pb = in.poses + 7 * (size_t)b;
+          float RA[9], RB[9], Rr[9], tr[3], dt[3];
+          quat_to_rot(pa, RA);
+          quat_to_rot(pb, RB);
+#pragma unroll
+          for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int k = 0; k < 3; ++k)
+              Rr[3 * i + k] = dot3_rn(RA[i], RA[3 + i], RA[6 + i], RB[k], RB[3 + k], RB[6 + k]);
+#pragma unroll
+          for (int d = 0; d < 3; ++d) dt[d] = fsub(pb[4 + d], pa[4 + d]);
+#pragma unroll
+          for (int i = 0; i < 3; ++i) tr[i] = dot3_rn(RA[i], RA[3 + i], RA[6 + i], dt[0], dt[1], dt[2]);
+          float boxA[6], boxB[6], loB[3], hiB[3], loA[3], hiA[3], cb[3], hb[3], ca[3], ha[3], e[3];
+#pragma unroll
+          for (int d = 0; d < 6; ++d) boxA[d] = aabb[6 * sa + d], boxB[d] = aabb[6 * sb + d];
+#pragma unroll
+          for (int d = 0; d < 3; ++d) {
+            cb[d] = fmul(fadd(boxB[d], boxB[3 + d]), 0.5f);
+            hb[d] = fmul(fsub(boxB[3 + d], boxB[d]), 0.5f);
+            ca[d] = fmul(fadd(boxA[d], boxA[3 + d]), 0.5f);
+            ha[d] = fmul(fsub(boxA[3 + d], boxA[d]), 0.5f);
+          }
+#pragma unroll
+          for (int i = 0; i < 3; ++i) {
+            const float c = fadd(dot3_rn(Rr[3 * i], Rr[3 * i + 1], Rr[3 * i + 2], cb[0], cb[1], cb[2]), tr[i]);
+            const float h = dot3_rn(fabsf(Rr[3 * i]), fabsf(Rr[3 * i + 1]), fabsf(Rr[3 * i + 2]), hb[0], hb[1], hb[2]);
+            loB[i] = fsub(c, h);
+            hiB[i] = fadd(c, h);
+          }
+#pragma unroll
+          for (int d = 0; d < 3; ++d) e[d] = fsub(ca[d], tr[d]);
+#pragma unroll
+          for (int k = 0; k < 3; ++k) {
+            const float c = dot3_rn(Rr[k], Rr[3 + k], Rr[6 + k], e[0], e[1], e[2]);
+            const float h = dot3_rn(fabsf(Rr[k]), fabsf(Rr[3 + k]), fabsf(Rr[6 + k]), ha[0], ha[1], ha[2]);
+            loA[k] = fsub(c, h);
+            hiA[k] = fadd(c, h);
+          }
+          int rA[6], rB[6];
+          cell_ranges(boxA, loB, hiB, rA);
+          cell_ranges(boxB, loA, hiA, rB);
+          const float fA = pool_range(lat + (size_t)sa * VCELLS * VF, rA, lane);
+          const float fB = pool_range(lat + (size_t)sb * VCELLS * VF, rB, lane);
+          const float aw = pa[0], ax = pa[1], ay = pa[2], az = pa[3];
+          const float bw = pb[0], bx = pb[1], by = pb[2], bz = pb[3];
+          const float pose[7] = {aw * bw + ax * bx + ay * by + az * bz, aw * bx - ax * bw - ay * bz + az * by,
+                                 aw * by + ax * bz - ay * bw - az * bx, aw * bz - ax * by + ay * bx - az * bw,
+                                 tr[0], tr[1], tr[2]};
+          if (lane < VF) {
+            vA = fA;
+            vB = fB;
+          } else if (lane < VPIN) {
+            vA = lane == VF ? 1.f : 0.f;
+#pragma unroll
+            for (int i = 0; i < 7; ++i)
+              if (lane == VF + i) vB = pose[i];
+          }
+          if (range_out && lane < 12) range_out[12 * (size_t)p + lane] = lane < 6 ? rA[lane] : rB[lane - 6];
+          if (feat_out && lane < VF) {
+            feat_out[32 * (size_t)p + lane] = fA;
+            feat_out[32 * (size_t)p + VF + lane] = fB;
+          }
+        }
+        const __nv_bfloat16 hA = __float2bfloat16_rn(vA), hB = __float2bfloat16_rn(vB);
+        *reinterpret_cast<__nv_bfloat16*>(XA + kmajor_off(j, lane, 32)) = hA;
+        *reinterpret_cast<__nv_bfloat16*>(XB + kmajor_off(j, lane, 32)) = hB;
+        if (lane == 0) valid[j] = good;
+      }
+      fence_async_smem();
+      tc_fence_before();
+      mbar_arrive(BAR(5));
+      // p1 .. p3
+      for (int l = 0; l < 3 && ok; ++l) {
+        if (!(ok = mbar_wait_or_abort(BAR(11 + l), ph, abort, WAIT))) break;
+        tc_fence_after();
+        if (l < 2) {
+          epi64(tbase + lane_off, bias + 128 * l, HA, row, c0);
+          epi64(tbase + lane_off + 128, bias + 128 * l, HB, row, c0);
+        } else {
+          // relu of both objects, max over the objects -> Z (in H_A)
+          float va[32], vb[32];
+          const float* b3 = bias + 256;
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            tmem_ld32(tbase + lane_off + c0 + 32 * h, va);
+            tmem_ld32(tbase + lane_off + 128 + c0 + 32 * h, vb);
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+              const int jj = 8 * c, o = c0 + 32 * h + jj;
+              float z[8];
+#pragma unroll
+              for (int q = 0; q < 8; ++q)
+                z[q] = fmaxf(fmaxf(va[jj + q] + b3[o + q], 0.f), fmaxf(vb[jj + q] + b3[o + q], 0.f));
+              uint4 w;
+              w.x = pack_bf16(z[0], z[1]);
+              w.y = pack_bf16(z[2], z[3]);
+              w.z = pack_bf16(z[4], z[5]);
+              w.w = pack_bf16(z[6], z[7]);
+              *reinterpret_cast<uint4*>(HA + kmajor_off(row, o, 128)) = w;
+            }
+          }
+        }
+        fence_async_smem();
+        tc_fence_before();
+        mbar_arrive(BAR(6 + l));  // H1R, H2R, ZR0
+      }
+      // q1, q2: Z <- relu(.) ; q3: the logit
+      for (int l = 0; l < 2 && ok; ++l) {
+        if (!(ok = mbar_wait_or_abort(BAR(14 + l), ph, abort, WAIT))) break;
+        tc_fence_after();
+        epi64(tbase + lane_off + 256, bias + 384 + 128 * l, HA, row, c0);
+        fence_async_smem();
+        tc_fence_before();
+        mbar_arrive(BAR(9 + l));  // ZR1, ZR2
+      }
+      if (!ok) break;
+      if (!(ok = mbar_wait_or_abort(BAR(16), ph, abort, WAIT))) break;
+      tc_fence_after();
+      {
+        const float* b6 = bias + 640;
+        const float* w4 = bias + 768;
+        float v[32], acc = 0.f;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          tmem_ld32(tbase + lane_off + 256 + c0 + 32 * h, v);
+#pragma unroll
+          for (int q = 0; q < 32; ++q) acc = fmaf(fmaxf(v[q] + b6[c0 + 32 * h + q], 0.f), w4[c0 + 32 * h + q], acc);
+        }
+        part[half * 128 + row] = acc;
+      }
+      tc_fence_before();
+      // (a bounded mbarrier handoff rather than a named barrier: a thread that
+      // gave up on a wait must not leave the others blocked.)  The next tile's
+      // partial sums cannot overwrite these before they are read: writing them
+      // needs that tile's MMAs, which need every thread's arrival on XR.
+      mbar_arrive(BAR(18));
+      if (half == 0) {
+        if (!(ok = mbar_wait_or_abort(BAR(18), ph, abort, WAIT))) break;
+        const int p = tile * 128 + row;
+        if (p < n) logit[p] = valid[row] ? part[row] + part[128 + row] + bias[896]
+                                         : __int_as_float(0x7fc00000);
+      }
+    }
+  }
+  __syncthreads();
+  if (*abort) {
+    if (tid == 0) atomicOr(err, 2);
+    if (warp == 8 && elect_one()) {
+      mma_commit(BAR(17));
+      mbar_wait(BAR(17), 0, WAIT);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    tmem_dealloc(tbase, 512);
+  }
+}
+}  // namespace vtc
+
 }  // namespace
 }  // namespace locc
 
@@ -403,6 +810,8 @@ using namespace locc;
 
 struct locc_voxel {
   int n_shapes = 0, n_points = 0, n_sm = 148;
+  int prec = LOCC_FP32;
+  unsigned char* d_img16 = nullptr;  // bf16 predictor image of the tensor-core kernel
   float* d_points = nullptr;  // [S][N][3]
   float* d_aabb = nullptr;    // [S][6]
   float* d_params = nullptr;  // device parameter images
@@ -449,6 +858,38 @@ std::vector<float> conv_image(const float* w, int cin, int cout, bool transposed
         t[((size_t)k * cin + i) * cout + o] = v;
       }
   return t;
+}
+
+uint16_t bf16_of(float f) {
+  uint32_t u;
+  std::memcpy(&u, &f, 4);
+  u += 0x7fffu + ((u >> 16) & 1u);  // round to nearest even (finite values)
+  return (uint16_t)(u >> 16);
+}
+
+// Predictor image of vox_tc_kernel: W [out][in] of p1 (K padded to 32), p2,
+// p3, q1, q2, q3 as K-major bf16 tiles [128][K], then float32 biases p1..q3,
+// q4's weights and bias.
+std::vector<unsigned char> tc_image(const float* p1w, const float* p1b, const float* const* w,
+                                    const float* const* b, const float* q4w, const float* q4b) {
+  std::vector<unsigned char> img(vtc::G_BYTES, 0);
+  auto put = [&](size_t off, const float* W, int K, int Kin) {
+    for (int n = 0; n < 128; ++n)
+      for (int k = 0; k < K; ++k) {
+        const uint16_t v = bf16_of(k < Kin ? W[(size_t)n * Kin + k] : 0.f);
+        std::memcpy(img.data() + off + tc::kmajor_off(n, k, K), &v, 2);
+      }
+  };
+  put(0, p1w, 32, VPIN);
+  put(vtc::S_WP2, w[0], 128, 128);
+  put(vtc::S_WP3, w[1], 128, 128);
+  for (int l = 0; l < 3; ++l) put(vtc::G_Q + (size_t)l * vtc::WQ, w[2 + l], 128, 128);
+  float* bias = reinterpret_cast<float*>(img.data() + vtc::G_BIAS);
+  std::memcpy(bias, p1b, 128 * 4);
+  for (int l = 0; l < 5; ++l) std::memcpy(bias + 128 * (l + 1), b[l], 128 * 4);
+  std::memcpy(bias + 768, q4w, 128 * 4);
+  bias[896] = q4b[0];
+  return img;
 }
 
 int vox_fail(int code, const char* msg) {
@@ -535,6 +976,20 @@ int locc_voxel_create(const locc_shape_library* lib, const void* blob, size_t bl
   for (int l = 0; l < 3; ++l) lin(VPW, VPW, VPW);  // q1..q3
   lin(1, VPW, VPW);                 // q4
   if (o != P.size()) return vox_fail(LOCC_ERR_BAD_WEIGHTS, "voxel weights: layout mismatch");
+  // predictor tensors in the blob (they close it): p1 w b, p2, p3, q1, q2, q3, q4
+  const size_t pred = P.size() - ((size_t)VPW * VPIN + VPW + 5 * ((size_t)VPW * VPW + VPW) + VPW + 1);
+  const float* pp = P.data() + pred;
+  const float* p1w = pp;
+  const float* p1b = p1w + VPW * VPIN;
+  const float* ws[5];
+  const float* bs[5];
+  const float* cur = p1b + VPW;
+  for (int l = 0; l < 5; ++l) {
+    ws[l] = cur;
+    bs[l] = cur + VPW * VPW;
+    cur = bs[l] + VPW;
+  }
+  const std::vector<unsigned char> img16 = tc_image(p1w, p1b, ws, bs, cur, cur + VPW);
 
   auto* h = new locc_voxel();
   h->n_shapes = lib->n_shapes;
@@ -554,13 +1009,15 @@ int locc_voxel_create(const locc_shape_library* lib, const void* blob, size_t bl
             cudaMalloc(&h->d_params, img.data.size() * sizeof(float)) == cudaSuccess &&
             cudaMalloc(&h->d_lat, (size_t)S * VCELLS * VF * sizeof(float)) == cudaSuccess &&
             cudaMalloc(&h->d_work, work_floats * sizeof(float)) == cudaSuccess &&
-            cudaMalloc(&h->d_err, sizeof(int)) == cudaSuccess;
+            cudaMalloc(&h->d_err, sizeof(int)) == cudaSuccess &&
+            cudaMalloc(&h->d_img16, img16.size()) == cudaSuccess;
   ok = ok && cudaMemcpy(h->d_points, lib->points, pts_bytes, cudaMemcpyHostToDevice) == cudaSuccess &&
        cudaMemcpy(h->d_aabb, lib->aabb, (size_t)S * 6 * sizeof(float), cudaMemcpyHostToDevice) ==
            cudaSuccess &&
        cudaMemcpy(h->d_params, img.data.data(), img.data.size() * sizeof(float),
                   cudaMemcpyHostToDevice) == cudaSuccess &&
-       cudaMemset(h->d_err, 0, sizeof(int)) == cudaSuccess;
+       cudaMemset(h->d_err, 0, sizeof(int)) == cudaSuccess &&
+       cudaMemcpy(h->d_img16, img16.data(), img16.size(), cudaMemcpyHostToDevice) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
     locc_voxel_destroy(h);
@@ -584,7 +1041,9 @@ int locc_voxel_create(const locc_shape_library* lib, const void* blob, size_t bl
   h->u[3] = w, w += (size_t)S * VCELLS * VC;
   h->g = w;
   if (cudaFuncSetAttribute(vox_detect_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)VOX_SMEM) != cudaSuccess) {
+                           (int)VOX_SMEM) != cudaSuccess ||
+      cudaFuncSetAttribute(vtc::vox_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           vtc::SMEM) != cudaSuccess) {
     cudaGetLastError();
     locc_voxel_destroy(h);
     return vox_fail(LOCC_ERR_CUDA, "cudaFuncSetAttribute failed for vox_detect_kernel");
@@ -624,6 +1083,14 @@ static int vox_launch(locc_voxel* h, const float* poses, const int32_t* obj_shap
   if (!poses || !obj_shape || !pairs || !logit)
     return vox_fail(LOCC_ERR_INVALID_ARG, "NULL array argument");
   PairInputs in{poses, obj_shape, pairs, n_obj, n_pairs};
+  if (h->prec == LOCC_BF16) {
+    const int tiles128 = (n_pairs + 127) / 128;
+    vtc::vox_tc_kernel<<<std::min(tiles128, h->n_sm), vtc::THREADS, vtc::SMEM,
+                         static_cast<cudaStream_t>(stream)>>>(in, h->n_shapes, h->d_aabb, h->d_lat,
+                                                              h->d_img16, logit, ranges, feat, h->d_err);
+    if (cudaGetLastError() != cudaSuccess) return vox_fail(LOCC_ERR_CUDA, "vox_tc_kernel launch failed");
+    return LOCC_OK;
+  }
   const int tiles = (n_pairs + VTILE - 1) / VTILE;
   const int grid = std::min(tiles, 2 * h->n_sm);
   vox_detect_kernel<<<grid, 256, VOX_SMEM, static_cast<cudaStream_t>(stream)>>>(
@@ -641,6 +1108,14 @@ int locc_voxel_detect_ex(locc_voxel* h, const float* poses, const int32_t* obj_s
                          const int32_t* pairs, int32_t n_pairs, float* logit, int32_t* cell_ranges,
                          float* pooled, void* stream) {
   return vox_launch(h, poses, obj_shape, n_obj, pairs, n_pairs, logit, cell_ranges, pooled, stream);
+}
+
+int locc_voxel_set_precision(locc_voxel* h, int32_t precision) {
+  if (!h) return vox_fail(LOCC_ERR_INVALID_ARG, "handle is NULL");
+  if (precision != LOCC_FP32 && precision != LOCC_BF16)
+    return vox_fail(LOCC_ERR_INVALID_ARG, "voxel predictor precision must be LOCC_FP32 or LOCC_BF16");
+  h->prec = precision;
+  return LOCC_OK;
 }
 
 int locc_voxel_status(locc_voxel* h, void* stream) {
@@ -667,6 +1142,7 @@ void locc_voxel_destroy(locc_voxel* h) {
   cudaFree(h->d_lat);
   cudaFree(h->d_work);
   cudaFree(h->d_err);
+  cudaFree(h->d_img16);
   delete h;
 }
 

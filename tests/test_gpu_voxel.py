@@ -144,3 +144,36 @@ def test_larger_library_sampled_against_oracle():
     np.testing.assert_array_equal(_masks_from_ranges(ranges.cpu().numpy()[sel]), ref["mask"])
     _close(pooled.cpu().numpy()[sel], ref["feat"])
     _close(logit.cpu().numpy()[sel], ref["logit"])
+
+
+def test_bf16_tensor_core_predictor(setup):
+    """tcgen05 predictor (bf16 operands, float32 accumulation): cell ranges
+    and pooled features unchanged (they stay float32), logits within 5e-2 of
+    max(|y|, rms) of the float64 oracle (seven layers of bf16 rounding,
+    ~2^-9 per operand), the same decision on >= 97 % of pairs, batch-size
+    invariant at tile edges; back to FP32 gives the FP32 results again."""
+    dev = torch.device("cuda:0")
+    det, pairs = setup["det"], setup["pairs"]
+    tp, ts, tq = (torch.from_numpy(a).to(dev) for a in (setup["poses"], setup["osh"], pairs))
+    l32, r32, f32 = det.detect(tp, ts, tq, details=True)
+    det.set_precision("bf16")
+    try:
+        l16, r16, f16 = det.detect(tp, ts, tq, details=True)
+        det.status()
+        np.testing.assert_array_equal(r16.cpu().numpy(), r32.cpu().numpy())
+        np.testing.assert_array_equal(f16.cpu().numpy(), f32.cpu().numpy())
+        ref = V.detect(setup["lat_ref"], setup["lib"].aabb, setup["poses"], setup["osh"], pairs,
+                       setup["prm"])["logit"]
+        _close(l16.cpu().numpy(), ref, tol=5e-2)
+        agree = np.mean((l16.cpu().numpy() > 0) == (ref > 0))
+        assert agree >= 0.97, agree
+        full = l16.cpu().numpy()
+        for n in (1, 127, 128, 129, 255, 257):
+            part = det.detect(tp, ts, torch.from_numpy(np.ascontiguousarray(pairs[:n])).to(dev))
+            np.testing.assert_array_equal(part.cpu().numpy(), full[:n])
+        det.status()
+    finally:
+        det.set_precision("fp32")
+    again = det.detect(tp, ts, tq).cpu().numpy()
+    det.status()
+    np.testing.assert_array_equal(again, l32.cpu().numpy())
