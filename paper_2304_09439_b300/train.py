@@ -211,8 +211,15 @@ def main():
             tr.commit()
             for prec in ("fp32", "bf16", "fp8"):
                 det.set_precision(prec)
-                row[f"{os.path.basename(path)}:{prec}"] = metrics(
-                    evaluate(det, name, data, dev, cache), data["targets"])
+                pred = evaluate(det, name, data, dev, cache)
+                row[f"{os.path.basename(path)}:{prec}"] = metrics(pred, data["targets"])
+                if prec == "fp32":
+                    # pairs within 5 cm of contact (true depth > -0.05) and the rest
+                    near = data["targets"][:, 7] > -0.05
+                    for tag, m in (("near", near), ("far", ~near)):
+                        if m.any():
+                            row[f"{os.path.basename(path)}:fp32:{tag}"] = metrics(
+                                pred[m], data["targets"][m])
             det.set_precision("fp32")
             tl = lib if name == lib_name else cache.setdefault(name, make_library(name))
             row[f"{os.path.basename(path)}:aabb"] = metrics(aabb_overlap(tl, data),
