@@ -59,13 +59,16 @@ static_assert(E_IMG_BYTES % 16 == 0, "image must be a whole number of 16-byte ch
 // NSLOT pair slots.  Each slot: raw crop rows (f32, 2 KB) and one 32 KB
 // operand region that holds, in turn, the X tile (4 KB), H1 (16 KB) and H2
 // (32 KB): each is dead once the MMA that reads it has completed, which the
-// epilogue that writes the next one has already waited for.
+// epilogue that writes the next one has already waited for.  The operand
+// regions of all slots are contiguous, so the H2 tiles of slots s and s + 1
+// form one [256 points x 128] operand: layer 3 of a slot pair is one N = 256
+// MMA chain (W3 read once for two pairs).
 constexpr int NSLOT = 4;
-constexpr int E_SLOT0 = (E_IMG_BYTES + 1023) / 1024 * 1024;
-constexpr int S_STG = 0;                  // [128] float4                    2 KB
-constexpr int S_OPD = S_STG + ROWS * 16;  // X [128x16] / H1 [128x64] / H2 [128x128] bf16
-constexpr int SLOT_BYTES = S_OPD + 128 * 128 * 2;
-constexpr int E_CTRL = E_SLOT0 + NSLOT * SLOT_BYTES;
+constexpr int E_STG0 = (E_IMG_BYTES + 1023) / 1024 * 1024;  // [NSLOT][128] float4
+constexpr int E_OPD0 = E_STG0 + NSLOT * ROWS * 16;           // [NSLOT][128 x 128] bf16
+constexpr int STG_BYTES = ROWS * 16, OPD_BYTES = 128 * 128 * 2;
+constexpr int E_CTRL = E_OPD0 + NSLOT * OPD_BYTES;
+static_assert(E_OPD0 % 1024 == 0, "operand regions must stay 1 KB aligned");
 // control block: mbarriers (8 B each), tmem slot, abort flag, counts [slot][4 warps]
 constexpr int NBAR = 9 * NSLOT + 2;
 constexpr int C_BAR = 0, C_TMEM = 8 * NBAR, C_ABORT = C_TMEM + 4, C_CNT = C_ABORT + 4;
@@ -209,7 +212,7 @@ __global__ void __launch_bounds__(E_THREADS, 1)
       const int p = lo + blockIdx.x + i * gridDim.x;
       if (lane == 0) {
         mbar_expect_tx(BAR(B_FULLX + s), ROWS * 16);
-        bulk_g2s(smem_u32(smem + E_SLOT0 + s * SLOT_BYTES + S_STG), xyz + (size_t)p * ROWS,
+        bulk_g2s(smem_u32(smem + E_STG0 + s * STG_BYTES), xyz + (size_t)p * ROWS,
                  ROWS * 16, BAR(B_FULLX + s));
       }
       ++issued[s];
@@ -218,6 +221,7 @@ __global__ void __launch_bounds__(E_THREADS, 1)
     bool ok = mbar_wait_warp(BAR(B_W), 0, abort, WAIT_CYCLES);
     tc_fence_after();
     const uint32_t id64 = idesc_bf16(128, 64), id128 = idesc_bf16(128, 128);
+    const uint32_t id256 = idesc_bf16(128, 256);
     for (int r = 0; ok && NSLOT * r < my_pairs; ++r) {
       const uint32_t ph = r & 1;
       const int ns = min(NSLOT, my_pairs - NSLOT * r);  // slots in use this round
@@ -227,7 +231,7 @@ __global__ void __launch_bounds__(E_THREADS, 1)
         tc_fence_after();
         const int i = NSLOT * r + s;
         if (i + NSLOT < my_pairs) load_pair(i + NSLOT);  // staging rows of slot s are free
-        const uint32_t sX = smem_u32(smem + E_SLOT0 + s * SLOT_BYTES + S_OPD);
+        const uint32_t sX = smem_u32(smem + E_OPD0 + s * OPD_BYTES);
         if (elect_one()) {
           mma_bf16(tbase + s * SLOT_COLS, sdesc(sX, 128, 256), sdesc(sW1, 128, 256), id64, 0);
           mma_commit(BAR(B_D1 + s));
@@ -238,7 +242,7 @@ __global__ void __launch_bounds__(E_THREADS, 1)
       for (int s = 0; s < ns && ok; ++s) {
         if (!(ok = mbar_wait_warp(BAR(B_H1RDY + s), ph, abort, WAIT_CYCLES))) break;
         tc_fence_after();
-        const uint32_t sH = smem_u32(smem + E_SLOT0 + s * SLOT_BYTES + S_OPD);
+        const uint32_t sH = smem_u32(smem + E_OPD0 + s * OPD_BYTES);
         if (elect_one()) {
 #pragma unroll
           for (int kk = 0; kk < 4; ++kk)
@@ -248,33 +252,32 @@ __global__ void __launch_bounds__(E_THREADS, 1)
         }
         __syncwarp();
       }
-      // layer 3, half 0 (channels 0..127), transposed: D3^T = W3img[0:128] . H2^T
-      for (int s = 0; s < ns && ok; ++s) {
-        if (!(ok = mbar_wait_warp(BAR(B_H2RDY + s), ph, abort, WAIT_CYCLES))) break;
-        tc_fence_after();
-        const uint32_t sH = smem_u32(smem + E_SLOT0 + s * SLOT_BYTES + S_OPD);
-        if (elect_one()) {
+      // layer 3, transposed: D3^T = W3img[half] . H2^T, two slots per chain
+      // (N = 256: slot s's points in its columns, slot s + 1's in the next
+      // 128); half 0 (channels 0..127) after both slots' H2, half 1
+      // (channels 128..255) once both have pooled half 0.  A last odd slot
+      // runs alone with N = 128.
+      for (int half = 0; half < 2 && ok; ++half) {
+        const int bwait = half ? B_E3A : B_H2RDY, bdone = half ? B_D3B : B_D3A;
+        const uint32_t sW = sW3 + 32768 * half;
+        for (int s = 0; s < ns && ok; s += 2) {
+          const bool two = s + 1 < ns;
+          ok = mbar_wait_warp(BAR(bwait + s), ph, abort, WAIT_CYCLES);
+          if (two) ok = ok && mbar_wait_warp(BAR(bwait + s + 1), ph, abort, WAIT_CYCLES);
+          if (!ok) break;
+          tc_fence_after();
+          const uint32_t sH = smem_u32(smem + E_OPD0 + s * OPD_BYTES);
+          if (elect_one()) {
+            const uint32_t idn = two ? id256 : id128;
 #pragma unroll
-          for (int kk = 0; kk < 8; ++kk)
-            mma_bf16(tbase + s * SLOT_COLS, sdesc(sW3 + 256 * kk, 128, 2048),
-                     sdesc(sH + 256 * kk, 128, 2048), id128, kk > 0);
-          mma_commit(BAR(B_D3A + s));
+            for (int kk = 0; kk < 8; ++kk)
+              mma_bf16(tbase + s * SLOT_COLS, sdesc(sW + 256 * kk, 128, 2048),
+                       sdesc(sH + 256 * kk, 128, 2048), idn, kk > 0);
+            mma_commit(BAR(bdone + s));
+            if (two) mma_commit(BAR(bdone + s + 1));
+          }
+          __syncwarp();
         }
-        __syncwarp();
-      }
-      // layer 3, half 1 (channels 128..255), once half 0 has been pooled
-      for (int s = 0; s < ns && ok; ++s) {
-        if (!(ok = mbar_wait_warp(BAR(B_E3A + s), ph, abort, WAIT_CYCLES))) break;
-        tc_fence_after();
-        const uint32_t sH = smem_u32(smem + E_SLOT0 + s * SLOT_BYTES + S_OPD);
-        if (elect_one()) {
-#pragma unroll
-          for (int kk = 0; kk < 8; ++kk)
-            mma_bf16(tbase + s * SLOT_COLS, sdesc(sW3 + 32768 + 256 * kk, 128, 2048),
-                     sdesc(sH + 256 * kk, 128, 2048), id128, kk > 0);
-          mma_commit(BAR(B_D3B + s));
-        }
-        __syncwarp();
       }
     }
     if (__any_sync(0xffffffffu, *abort) && elect_one()) {
@@ -288,8 +291,8 @@ __global__ void __launch_bounds__(E_THREADS, 1)
   } else {
     // ------------------------------------------------ epilogue warpgroup of slot s
     const int s = warp >> 2, row = tid & 127, wq = warp & 3;
-    unsigned char* slot = smem + E_SLOT0 + s * SLOT_BYTES;
-    unsigned char* opd = slot + S_OPD;
+    unsigned char* stg = smem + E_STG0 + s * STG_BYTES;
+    unsigned char* opd = smem + E_OPD0 + s * OPD_BYTES;
     const uint32_t tslot = tbase + s * SLOT_COLS + ((uint32_t)(32 * wq) << 16);
     int* cnt_s = s_cnt + 4 * s;
     bool ok = mbar_wait_or_abort(BAR(B_W), 0, abort, WAIT_CYCLES);
@@ -301,7 +304,7 @@ __global__ void __launch_bounds__(E_THREADS, 1)
       // crop rows -> bf16 hi/lo X tile
       if (!(ok = mbar_wait_or_abort(BAR(B_FULLX + s), ph, abort, WAIT_CYCLES))) break;
       {
-        const float4 q = reinterpret_cast<const float4*>(slot + S_STG)[row];
+        const float4 q = reinterpret_cast<const float4*>(stg)[row];
         const unsigned m = __ballot_sync(0xffffffffu, q.w > 0.5f);
         if (lane == 0) cnt_s[wq] = __popc(m);
         const __nv_bfloat16 xh = __float2bfloat16_rn(q.x), yh = __float2bfloat16_rn(q.y),
