@@ -75,7 +75,7 @@ int ensure_capacity(locc_handle* h, int n_pairs, cudaStream_t stream) {
       cudaMalloc(&h->d_cnt, P * 2 * sizeof(int32_t)) != cudaSuccess ||
       cudaMalloc(&h->d_centre, P * sizeof(float4)) != cudaSuccess ||
       cudaMalloc(&h->d_feat, P * 512 * sizeof(float)) != cudaSuccess ||
-      cudaMalloc(&h->d_defer, (1 + 2 * P) * sizeof(int)) != cudaSuccess ||
+      cudaMalloc(&h->d_defer, (2 + 2 * P) * sizeof(int)) != cudaSuccess ||
       cudaMalloc(&h->d_feat_tc, (P + 127) / 128 * 128 * 512 * 2) != cudaSuccess) {
     cudaGetLastError();
     free_scratch(h);

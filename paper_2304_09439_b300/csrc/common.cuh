@@ -147,8 +147,9 @@ namespace locc {
 // n_dev (nullable): device count of pairs actually present (<= n_pairs), read
 // by the kernels so that a fixed launch serves a count produced on the device.
 // grid_cap (crop): at most this many resident CTAs per SM (0 = occupancy limit).
-// defer (crop): device int [1 + 2 * (pairs of one launch)], scratch for the
-// objects left to the exact fallback kernel (defer[0] = their count).
+// defer (crop): device int [2 + 2 * (pairs of one launch)], scratch: defer[0]
+// counts the objects left to the exact fallback kernel, defer[1] hands out
+// objects to the crop warps, defer[2..] lists the deferred objects.
 // mode: LOCC_CROP_LOCAL (nearest-first within the ball) or LOCC_CROP_GLOBAL
 // (the first KMAX samples of each shape, same canonical frame).
 cudaError_t launch_crop(const DevLibrary& lib, const PairInputs& in, const PairRange& rg,

@@ -307,7 +307,7 @@ __device__ __forceinline__ void write_crop(const unsigned long long* buf, int cn
   }
 }
 
-__device__ __forceinline__ void crop_pair(const DevLibrary& lib, const PairInputs& in, int p, int warp,
+__device__ __forceinline__ void crop_pair(const DevLibrary& lib, const PairInputs& in, int p, int obj,
                                           int lane, float r, float4* __restrict__ xyz_out,
                                           int32_t* __restrict__ idx_out,
                                           int32_t* __restrict__ cnt_out,
@@ -316,32 +316,32 @@ __device__ __forceinline__ void crop_pair(const DevLibrary& lib, const PairInput
                                           unsigned long long* ebuf, float* rsh, int* defer,
                                           int defer_cap) {
   int a, b, sa, sb;
-  const bool ok = load_pair(in, lib.n_shapes, p, &a, &b, &sa, &sb, (warp == 0 && lane == 0) ? err : nullptr);
+  const bool ok = load_pair(in, lib.n_shapes, p, &a, &b, &sa, &sb, (obj == 0 && lane == 0) ? err : nullptr);
   if (!ok) {
-    float4* xo = xyz_out + ((size_t)p * 2 + warp) * KMAX;
-    int32_t* io = idx_out ? idx_out + ((size_t)p * 2 + warp) * KMAX : nullptr;
+    float4* xo = xyz_out + ((size_t)p * 2 + obj) * KMAX;
+    int32_t* io = idx_out ? idx_out + ((size_t)p * 2 + obj) * KMAX : nullptr;
     const float nan = __int_as_float(0x7fc00000);
     xo[lane] = xo[lane + 32] = make_float4(0.f, 0.f, 0.f, 0.f);
     if (io) io[lane] = io[lane + 32] = -1;
-    if (lane == 0) cnt_out[2 * p + warp] = 0;
-    if (warp == 0 && lane == 0 && centre_out) centre_out[p] = make_float4(nan, nan, nan, nan);
+    if (lane == 0) cnt_out[2 * p + obj] = 0;
+    if (obj == 0 && lane == 0 && centre_out) centre_out[p] = make_float4(nan, nan, nan, nan);
     return;
   }
   Frame f;
   pair_frame(in.poses + 7 * (size_t)a, in.poses + 7 * (size_t)b, lib.aabb[2 * sa],
              lib.aabb[2 * sa + 1], lib.aabb[2 * sb], lib.aabb[2 * sb + 1], f);
-  if (warp == 0 && lane == 0 && centre_out) centre_out[p] = make_float4(f.c[0], f.c[1], f.c[2], 0.f);
+  if (obj == 0 && lane == 0 && centre_out) centre_out[p] = make_float4(f.c[0], f.c[1], f.c[2], 0.f);
 
   // B's canonical coordinates need R_rel at the very end: park it in shared
   // memory instead of keeping nine registers live through the selection
-  if (warp == 1 && lane == 0) {
+  if (obj == 1 && lane == 0) {
 #pragma unroll
     for (int i = 0; i < 9; ++i) rsh[i] = f.rrel[i];
   }
-  const int shape = warp == 0 ? sa : sb;
-  const float cx = warp == 0 ? f.c[0] : f.cb[0];
-  const float cy = warp == 0 ? f.c[1] : f.cb[1];
-  const float cz = warp == 0 ? f.c[2] : f.cb[2];
+  const int shape = obj == 0 ? sa : sb;
+  const float cx = obj == 0 ? f.c[0] : f.cb[0];
+  const float cy = obj == 0 ? f.c[1] : f.cb[1];
+  const float cz = obj == 0 ? f.c[2] : f.cb[2];
   const float r2 = fmul(r, r);
   const float r2_cull = r2 * 1.001f + 1e-30f;  // conservative block test
   const float4* pts = lib.points + (size_t)shape * lib.n_pad;
@@ -431,15 +431,15 @@ __device__ __forceinline__ void crop_pair(const DevLibrary& lib, const PairInput
     // crop_fallback_kernel redoes this object with an exact streaming sort
     if (lane == 0) {
       const int slot = atomicAdd(defer, 1);
-      if (slot < defer_cap) defer[1 + slot] = 2 * p + warp;
+      if (slot < defer_cap) defer[2 + slot] = 2 * p + obj;
     }
     return;
   }
   __syncwarp();
-  write_crop(buf, cnt, pts, cx, cy, cz, warp == 1 ? rsh : nullptr,
-             xyz_out + ((size_t)p * 2 + warp) * KMAX,
-             idx_out ? idx_out + ((size_t)p * 2 + warp) * KMAX : nullptr, lane);
-  if (lane == 0) cnt_out[2 * p + warp] = cnt;
+  write_crop(buf, cnt, pts, cx, cy, cz, obj == 1 ? rsh : nullptr,
+             xyz_out + ((size_t)p * 2 + obj) * KMAX,
+             idx_out ? idx_out + ((size_t)p * 2 + obj) * KMAX : nullptr, lane);
+  if (lane == 0) cnt_out[2 * p + obj] = cnt;
   __syncwarp();
 }
 
@@ -520,13 +520,26 @@ __global__ void __launch_bounds__(64, 16) crop_kernel(DevLibrary lib, PairInputs
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int lo, hi;
   range_bounds(rg, &lo, &hi);
-  for (int p = lo + blockIdx.x; p < hi; p += gridDim.x) {
-    crop_pair(lib, in, p, warp, lane, r, xyz_out, idx_out, cnt_out, centre_out, err, cand[warp],
-              hist[warp], ebuf[warp], rsh[warp], defer, defer_cap);
+  // Objects (2 per pair, o = 2 (p - lo) + object) are handed out one at a
+  // time: the first of every warp statically, the rest from a counter
+  // (defer[1], zeroed before the launch).  Per-object costs are heavy-tailed
+  // (culled blocks and in-ball points vary with the overlap), so a static
+  // split leaves most warps idle while the unluckiest finish; with the
+  // counter all warps stop within about one object of each other.  The next
+  // index is fetched while the current object runs.
+  const int n_obj = 2 * (hi - lo);
+  const int first = 2 * (int)gridDim.x;
+  int o = 2 * (int)blockIdx.x + warp;
+  while (o < n_obj) {
+    int nxt = 0;
+    if (lane == 0) nxt = first + atomicAdd(&defer[1], 1);
+    crop_pair(lib, in, lo + (o >> 1), o & 1, lane, r, xyz_out, idx_out, cnt_out, centre_out, err,
+              cand[warp], hist[warp], ebuf[warp], rsh[warp], defer, defer_cap);
+    o = __shfl_sync(FULL, nxt, 0);
   }
 }
 
-// One warp per deferred object (defer[0] = count, defer[1 + i] = 2 p + object).
+// One warp per deferred object (defer[0] = count, defer[2 + i] = 2 p + object).
 __global__ void __launch_bounds__(64) crop_fallback_kernel(DevLibrary lib, PairInputs in, float r,
                                                            float4* __restrict__ xyz_out,
                                                            int32_t* __restrict__ idx_out,
@@ -537,7 +550,7 @@ __global__ void __launch_bounds__(64) crop_fallback_kernel(DevLibrary lib, PairI
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int n = min(defer[0], defer_cap);
   for (int e = 2 * blockIdx.x + warp; e < n; e += 2 * gridDim.x) {
-    const int code = defer[1 + e];
+    const int code = defer[2 + e];
     fallback_object(lib, in, code >> 1, code & 1, lane, r, xyz_out, idx_out, cnt_out, cand[warp]);
   }
 }
@@ -615,7 +628,7 @@ cudaError_t launch_crop(const DevLibrary& lib, const PairInputs& in, const PairR
   const int span = (in.n_pairs + rg.n_chunks - 1) / rg.n_chunks + 1;
   const int grid = std::max(1, std::min(span, n_sm * cap));
   const int defer_cap = 2 * (span - 1);  // both objects of every pair of one chunk
-  cudaError_t e = cudaMemsetAsync(defer, 0, sizeof(int), stream);
+  cudaError_t e = cudaMemsetAsync(defer, 0, 2 * sizeof(int), stream);  // count, object counter
   if (e != cudaSuccess) return e;
   crop_kernel<<<grid, 64, 0, stream>>>(lib, in, rg, r, xyz, idx, cnt, centre, err, defer,
                                        defer_cap);

@@ -25,7 +25,7 @@ constexpr size_t kXyzBytes = (size_t)kMaxPairs * locc::ROWS * sizeof(float4);
 constexpr size_t kFeatBytes = (size_t)kMaxPairs * 512 * sizeof(float);
 constexpr size_t kCentreBytes = (size_t)kMaxPairs * sizeof(float4);
 constexpr size_t kCntBytes = (size_t)kMaxPairs * 2 * sizeof(int32_t);
-constexpr size_t kDeferBytes = (1 + (size_t)kMaxPairs * 2) * sizeof(int32_t);
+constexpr size_t kDeferBytes = (2 + (size_t)kMaxPairs * 2) * sizeof(int32_t);
 constexpr size_t kScratchBytes = kXyzBytes + kFeatBytes + kCentreBytes + kCntBytes + kDeferBytes;
 
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];

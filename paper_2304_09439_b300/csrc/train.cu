@@ -405,7 +405,7 @@ int locc_trainer_create(locc_handle* h, int32_t max_batch, const locc_train_conf
   bool ok = cudaMalloc(&t->params, NP * 4) == cudaSuccess && cudaMalloc(&t->grad, NP * 4) == cudaSuccess &&
             cudaMalloc(&t->m, NP * 4) == cudaSuccess && cudaMalloc(&t->v, NP * 4) == cudaSuccess &&
             cudaMalloc(&t->xyz, M * 16) == cudaSuccess && cudaMalloc(&t->cnt, P * 8) == cudaSuccess &&
-            cudaMalloc(&t->defer, (1 + 2 * P) * sizeof(int)) == cudaSuccess &&
+            cudaMalloc(&t->defer, (2 + 2 * P) * sizeof(int)) == cudaSuccess &&
             cudaMalloc(&t->centre, P * 16) == cudaSuccess && cudaMalloc(&t->X, M * 16) == cudaSuccess &&
             cudaMalloc(&t->T, P * 32) == cudaSuccess && cudaMalloc(&t->H1, M * 64 * 4) == cudaSuccess &&
             cudaMalloc(&t->H2, M * 128 * 4) == cudaSuccess &&
