@@ -50,10 +50,22 @@ using namespace tc;
 constexpr long long WAIT_CYCLES = 2000000000LL;  // ~1 s at 2 GHz
 
 // ----------------------------------------------------------------- encoder
+// The biases of layers 1 and 2 are added by the MMAs themselves (the
+// epilogues then only apply ReLU, round and store, which more than halves
+// their instruction count): layer 1 through two constant-one columns of the X
+// tile against b1 (hi, lo) in W1's spare K columns; layer 2 through one extra
+// K = 16 step, issued first so that it also initialises the accumulator: a
+// tile of ones (columns 0, 1) against a tile holding b2 (hi, lo) in its K
+// columns 0, 1.  The bias tile stores only the first core matrix of each
+// 8-row group (K columns 0..7, SBO 128); its second core matrix (K 8..15)
+// reads the ones tile through LBO = 2048, finite values that meet the ones
+// tile's zero columns.
 constexpr int E_W1 = 0;                       // [64 x 16]   2 KB
 constexpr int E_W2 = E_W1 + 64 * 16 * 2;      // [128 x 64] 16 KB
 constexpr int E_W3 = E_W2 + 128 * 64 * 2;     // [256 x 128] 64 KB
-constexpr int E_BIAS = E_W3 + 256 * 128 * 2;  // b1 64, b2 128, b3 256 (f32)
+constexpr int E_B2T = E_W3 + 256 * 128 * 2;   // [128 x 8] b2 (hi, lo), 2 KB
+constexpr int E_ONE = E_B2T + 128 * 8 * 2;    // [128 x 16] ones in columns 0, 1, 4 KB
+constexpr int E_BIAS = E_ONE + 128 * 16 * 2;  // b1 64, b2 128, b3 256 (f32)
 constexpr int E_IMG_BYTES = E_BIAS + (64 + 128 + 256) * 4;
 static_assert(E_IMG_BYTES % 16 == 0, "image must be a whole number of 16-byte chunks");
 // NSLOT pair slots.  Each slot: raw crop rows (f32, 2 KB) and one 32 KB
@@ -83,23 +95,22 @@ constexpr int B_FULLX = 0, B_XRDY = NSLOT, B_H1RDY = 2 * NSLOT, B_H2RDY = 3 * NS
               B_E3A = 4 * NSLOT, B_D1 = 5 * NSLOT, B_D2 = 6 * NSLOT, B_D3A = 7 * NSLOT,
               B_D3B = 8 * NSLOT, B_W = 9 * NSLOT, B_DRAIN = 9 * NSLOT + 1;
 
-// Epilogue of layers 1 and 2: TMEM row -> relu(x + b) -> bf16 row of the next
-// A operand (K = NCOL).
+// Epilogue of layers 1 and 2: TMEM row (bias already accumulated) -> relu ->
+// bf16 row of the next A operand (K = NCOL).
 template <int NCOL>
-__device__ __forceinline__ void enc_epi_rows(uint32_t taddr, const float* b, unsigned char* dst,
-                                             int row) {
+__device__ __forceinline__ void enc_epi_rows(uint32_t taddr, unsigned char* dst, int row) {
   float v[32];
-#pragma unroll
+#pragma unroll 1
   for (int h = 0; h < NCOL / 32; ++h) {
     tmem_ld32(taddr + 32 * h, v);
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
       uint4 w;
       const int j = 8 * c, o = 32 * h + j;
-      w.x = pack_relu_bf16(v[j + 0] + b[o + 0], v[j + 1] + b[o + 1]);
-      w.y = pack_relu_bf16(v[j + 2] + b[o + 2], v[j + 3] + b[o + 3]);
-      w.z = pack_relu_bf16(v[j + 4] + b[o + 4], v[j + 5] + b[o + 5]);
-      w.w = pack_relu_bf16(v[j + 6] + b[o + 6], v[j + 7] + b[o + 7]);
+      w.x = pack_relu_bf16(v[j + 0], v[j + 1]);
+      w.y = pack_relu_bf16(v[j + 2], v[j + 3]);
+      w.z = pack_relu_bf16(v[j + 4], v[j + 5]);
+      w.w = pack_relu_bf16(v[j + 6], v[j + 7]);
       *reinterpret_cast<uint4*>(dst + kmajor_off(row, o, NCOL)) = w;
     }
   }
@@ -189,15 +200,14 @@ __global__ void __launch_bounds__(E_THREADS, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tbase = *tmem_slot;
-  const float* b1 = reinterpret_cast<const float*>(smem + E_BIAS);
-  const float* b2 = b1 + 64;
-  const float* b3 = b2 + 128;
+  const float* b3 = reinterpret_cast<const float*>(smem + E_BIAS) + 64 + 128;
 
   if (warp == MMA_WARP) {
     // ------------------------------------------ MMA issuer + TMA producer warp
     // (warp-uniform control flow; copies by lane 0, MMAs by an elected lane)
     const uint32_t sW1 = smem_u32(smem + E_W1), sW2 = smem_u32(smem + E_W2);
     const uint32_t sW3 = smem_u32(smem + E_W3);
+    const uint32_t sB2T = smem_u32(smem + E_B2T), sOne = smem_u32(smem + E_ONE);
     // resident weights, in bulk copies of at most 32 KB
     if (lane == 0) {
       mbar_expect_tx(BAR(B_W), E_IMG_BYTES);
@@ -238,16 +248,17 @@ __global__ void __launch_bounds__(E_THREADS, 1)
         }
         __syncwarp();
       }
-      // layer 2: D2[128 x 128] = H1[128 x 64] . W2img^T
+      // layer 2: D2[128 x 128] = ones . b2img^T + H1[128 x 64] . W2img^T
       for (int s = 0; s < ns && ok; ++s) {
         if (!(ok = mbar_wait_warp(BAR(B_H1RDY + s), ph, abort, WAIT_CYCLES))) break;
         tc_fence_after();
         const uint32_t sH = smem_u32(smem + E_OPD0 + s * OPD_BYTES);
         if (elect_one()) {
+          mma_bf16(tbase + s * SLOT_COLS, sdesc(sOne, 128, 256), sdesc(sB2T, 2048, 128), id128, 0);
 #pragma unroll
           for (int kk = 0; kk < 4; ++kk)
             mma_bf16(tbase + s * SLOT_COLS, sdesc(sH + 256 * kk, 128, 1024),
-                     sdesc(sW2 + 256 * kk, 128, 1024), id128, kk > 0);
+                     sdesc(sW2 + 256 * kk, 128, 1024), id128, 1);
           mma_commit(BAR(B_D2 + s));
         }
         __syncwarp();
@@ -315,8 +326,9 @@ __global__ void __launch_bounds__(E_THREADS, 1)
         c0.y = pack_bf16(fz, q.x - fx);
         c0.z = pack_bf16(q.y - fy, q.z - fz);
         c0.w = pack_bf16(fx, fy);
-        c1.x = pack_bf16(fz, 0.f);
-        c1.y = c1.z = c1.w = 0u;
+        c1.x = pack_bf16(fz, 1.f);  // K columns 9, 10: ones against b1 (hi, lo)
+        c1.y = pack_bf16(1.f, 0.f);
+        c1.z = c1.w = 0u;
         *reinterpret_cast<uint4*>(opd + kmajor_off(row, 0, 16)) = c0;
         *reinterpret_cast<uint4*>(opd + kmajor_off(row, 8, 16)) = c1;
       }
@@ -326,14 +338,14 @@ __global__ void __launch_bounds__(E_THREADS, 1)
       // layer 1 epilogue -> H1 (over X: MMA1 has completed)
       if (!(ok = mbar_wait_or_abort(BAR(B_D1 + s), ph, abort, WAIT_CYCLES))) break;
       tc_fence_after();
-      enc_epi_rows<64>(tslot, b1, opd, row);
+      enc_epi_rows<64>(tslot, opd, row);
       fence_async_smem();
       tc_fence_before();
       mbar_arrive(BAR(B_H1RDY + s));
       // layer 2 epilogue -> H2 (over H1: MMA2 has completed)
       if (!(ok = mbar_wait_or_abort(BAR(B_D2 + s), ph, abort, WAIT_CYCLES))) break;
       tc_fence_after();
-      enc_epi_rows<128>(tslot, b2, opd, row);
+      enc_epi_rows<128>(tslot, opd, row);
       fence_async_smem();
       tc_fence_before();
       mbar_arrive(BAR(B_H2RDY + s));
@@ -731,13 +743,24 @@ int upload_tc_params(locc_handle* h, const std::vector<float>& params) {
   const size_t total = enc_bytes + H_IMG_BYTES;
   std::vector<unsigned char> img(total, 0);
   unsigned char* e = img.data();
-  // layer 1 B operand: row c = [W_hi(3), W_hi(3), W_lo(3), 0 x 7]
+  // bias (hi, lo): two bf16 values whose float32 sum is b to ~2^-17 relative
+  auto bias_split = [&](int l, int c, int part) -> float {
+    const float b = params[offb[l] + c];
+    const float hi = bf16_value(bf16_bits(b));
+    return part == 0 ? hi : b - hi;
+  };
+  // layer 1 B operand: row c = [W_hi(3), W_hi(3), W_lo(3), b1_hi, b1_lo, 0 x 5]
   put_tile(e + E_W1, 64, 16, [&](int c, int k) -> float {
+    if (k == 9 || k == 10) return bias_split(0, c, k - 9);
     if (k >= 9) return 0.f;
     const float w = W(0, c, k % 3);
     const float hi = bf16_value(bf16_bits(w));
     return k < 6 ? hi : w - hi;
   });
+  // layer 2 bias tile (first core matrix of each row group: K columns 0..7)
+  // and the ones tile it is multiplied with
+  put_tile(e + E_B2T, 128, 8, [&](int c, int k) { return k < 2 ? bias_split(1, c, k) : 0.f; });
+  put_tile(e + E_ONE, 128, 16, [&](int, int k) { return k < 2 ? 1.f : 0.f; });
   put_tile(e + E_W2, 128, 64, [&](int c, int k) { return W(1, c, k); });
   put_tile(e + E_W3, 256, 128, [&](int c, int k) { return W(2, c, k); });
   std::memcpy(e + E_BIAS, &params[offb[0]], 64 * 4);
