@@ -8,11 +8,12 @@
 //
 // encoder_tc_kernel (persistent, one CTA of 544 threads per SM, warp
 // specialised, NSLOT = 4 pairs in flight per CTA):
-//   * warp 16 (one elected lane) copies the bf16 images of W1, W2, W3 (82 KB)
-//     and the biases into shared memory once (cp.async.bulk), then streams the
-//     128 crop rows of each pair into its slot's staging buffer (bulk copies
-//     on an mbarrier) and issues every tcgen05.mma; warps 4s..4s+3 are the
-//     epilogue warpgroup of slot s (one thread per TMEM lane / crop row);
+//   * warp 16 copies the bf16 weight images (90 KB) into shared memory once
+//     (cp.async.bulk) and issues every tcgen05.mma (one elected lane);
+//     warps 4s..4s+3 are the epilogue warpgroup of slot s (one thread per
+//     TMEM lane / crop row), and one of its lanes streams the 128 crop rows
+//     of the slot's pairs into its staging buffer (bulk copies on an
+//     mbarrier);
 //   * each slot owns 128 TMEM columns and one 32 KB shared operand region that
 //     holds X (layer-1 A operand), then H1, then H2 as the pair moves through
 //     the layers, so four pairs overlap: while one slot's epilogue converts a
@@ -21,13 +22,13 @@
 //   * layer 1 packs K = 16: coordinates and weights are split into bf16 hi/lo
 //     parts, x.W ~ x_hi W_hi + x_lo W_hi + x_hi W_lo (9 of the 16 columns);
 //   * layers 1 and 2: D[128 x N] in TMEM, thread r owns row r (point r); the
-//     epilogue adds the bias, applies ReLU and writes the bf16 row as the next
-//     layer's A operand;
+//     MMAs accumulate the bias as well, the epilogue applies ReLU and writes
+//     the bf16 row as the next layer's A operand;
 //   * layer 3 is computed transposed, D^T = W3 . H2^T (M = 128 channels per
 //     half, N = 128 points) in two halves that reuse the slot's 128 columns:
 //     thread r owns channel r, so the max-pool over the valid points of each
-//     object is a register reduction over TMEM columns; the second half is
-//     issued once the first has been pooled.
+//     object is a reduction over TMEM columns (tcgen05.ld.red max); the
+//     second half is issued once the first has been pooled.
 // head_tc_kernel (persistent over tiles of 128 pairs): layer 1 streams W_h1 in
 // K-chunks of 64 through shared memory, layers 2 and 3 likewise; activations
 // stay on chip (TMEM -> bf16 in shared memory); the epilogue maps outputs to
@@ -126,12 +127,11 @@ __device__ __forceinline__ void enc_pool(uint32_t taddr, int cntA, int cntB, flo
     const int cnt = q < 2 ? cntA : cntB;
     const int c0 = 32 * (q & 1);  // first point slot of this chunk within its object
     if (c0 < cnt) {
-      tmem_ld32(taddr + 32 * q, v);
       float m = -INFINITY;
       if (c0 + 32 <= cnt) {
-#pragma unroll
-        for (int jj = 0; jj < 32; ++jj) m = fmaxf(m, v[jj]);
+        m = tmem_ldmax32(taddr + 32 * q);  // whole chunk valid: max in the load
       } else {
+        tmem_ld32(taddr + 32 * q, v);
 #pragma unroll
         for (int jj = 0; jj < 32; ++jj) m = fmaxf(m, (c0 + jj < cnt) ? v[jj] : -INFINITY);
       }
@@ -203,8 +203,8 @@ __global__ void __launch_bounds__(E_THREADS, 1)
   const float* b3 = reinterpret_cast<const float*>(smem + E_BIAS) + 64 + 128;
 
   if (warp == MMA_WARP) {
-    // ------------------------------------------ MMA issuer + TMA producer warp
-    // (warp-uniform control flow; copies by lane 0, MMAs by an elected lane)
+    // ------------------------------------------------------------ MMA issuer warp
+    // (warp-uniform control flow; weight copies by lane 0, MMAs by an elected lane)
     const uint32_t sW1 = smem_u32(smem + E_W1), sW2 = smem_u32(smem + E_W2);
     const uint32_t sW3 = smem_u32(smem + E_W3);
     const uint32_t sB2T = smem_u32(smem + E_B2T), sOne = smem_u32(smem + E_ONE);
@@ -216,18 +216,6 @@ __global__ void __launch_bounds__(E_THREADS, 1)
         bulk_g2s(smem_u32(smem + off), img + off, bytes, BAR(B_W));
       }
     }
-    int issued[NSLOT] = {};
-    auto load_pair = [&](int i) {
-      const int s = i % NSLOT;
-      const int p = lo + blockIdx.x + i * gridDim.x;
-      if (lane == 0) {
-        mbar_expect_tx(BAR(B_FULLX + s), ROWS * 16);
-        bulk_g2s(smem_u32(smem + E_STG0 + s * STG_BYTES), xyz + (size_t)p * ROWS,
-                 ROWS * 16, BAR(B_FULLX + s));
-      }
-      ++issued[s];
-    };
-    for (int i = 0; i < NSLOT && i < my_pairs; ++i) load_pair(i);
     bool ok = mbar_wait_warp(BAR(B_W), 0, abort, WAIT_CYCLES);
     tc_fence_after();
     const uint32_t id64 = idesc_bf16(128, 64), id128 = idesc_bf16(128, 128);
@@ -235,12 +223,10 @@ __global__ void __launch_bounds__(E_THREADS, 1)
     for (int r = 0; ok && NSLOT * r < my_pairs; ++r) {
       const uint32_t ph = r & 1;
       const int ns = min(NSLOT, my_pairs - NSLOT * r);  // slots in use this round
-      // layer 1: D1[128 x 64] = X[128 x 16] . W1img^T
+      // layer 1: D1[128 x 64] = X[128 x 16] . W1img^T (+ b1 via the ones columns)
       for (int s = 0; s < ns && ok; ++s) {
         if (!(ok = mbar_wait_warp(BAR(B_XRDY + s), ph, abort, WAIT_CYCLES))) break;
         tc_fence_after();
-        const int i = NSLOT * r + s;
-        if (i + NSLOT < my_pairs) load_pair(i + NSLOT);  // staging rows of slot s are free
         const uint32_t sX = smem_u32(smem + E_OPD0 + s * OPD_BYTES);
         if (elect_one()) {
           mma_bf16(tbase + s * SLOT_COLS, sdesc(sX, 128, 256), sdesc(sW1, 128, 256), id64, 0);
@@ -292,11 +278,9 @@ __global__ void __launch_bounds__(E_THREADS, 1)
       }
     }
     if (__any_sync(0xffffffffu, *abort) && elect_one()) {
-      // drain: wait (bounded) for every MMA and bulk copy this warp issued
+      // drain: wait (bounded) for every MMA this warp issued
       mma_commit(BAR(B_DRAIN));
       mbar_wait(BAR(B_DRAIN), 0, WAIT_CYCLES);
-      for (int s = 0; s < NSLOT; ++s)
-        if (issued[s] > 0) mbar_wait(BAR(B_FULLX + s), (issued[s] - 1) & 1, WAIT_CYCLES);
     }
     __syncwarp();
   } else {
@@ -306,38 +290,55 @@ __global__ void __launch_bounds__(E_THREADS, 1)
     unsigned char* opd = smem + E_OPD0 + s * OPD_BYTES;
     const uint32_t tslot = tbase + s * SLOT_COLS + ((uint32_t)(32 * wq) << 16);
     int* cnt_s = s_cnt + 4 * s;
+    // crop rows of the slot's pair jn -> bf16 hi/lo X tile (over the previous
+    // pair's H2, dead once its layer 3 has completed), crop counts, XRDY
+    auto build_x = [&](int jn) {
+      if (!mbar_wait_or_abort(BAR(B_FULLX + s), jn & 1, abort, WAIT_CYCLES)) return false;
+      const float4 q = reinterpret_cast<const float4*>(stg)[row];
+      const unsigned m = __ballot_sync(0xffffffffu, q.w > 0.5f);
+      if (lane == 0) cnt_s[wq] = __popc(m);
+      const __nv_bfloat16 xh = __float2bfloat16_rn(q.x), yh = __float2bfloat16_rn(q.y),
+                          zh = __float2bfloat16_rn(q.z);
+      const float fx = __bfloat162float(xh), fy = __bfloat162float(yh), fz = __bfloat162float(zh);
+      uint4 c0, c1;
+      c0.x = pack_bf16(fx, fy);
+      c0.y = pack_bf16(fz, q.x - fx);
+      c0.z = pack_bf16(q.y - fy, q.z - fz);
+      c0.w = pack_bf16(fx, fy);
+      c1.x = pack_bf16(fz, 1.f);  // K columns 9, 10: ones against b1 (hi, lo)
+      c1.y = pack_bf16(1.f, 0.f);
+      c1.z = c1.w = 0u;
+      *reinterpret_cast<uint4*>(opd + kmajor_off(row, 0, 16)) = c0;
+      *reinterpret_cast<uint4*>(opd + kmajor_off(row, 8, 16)) = c1;
+      fence_async_smem();
+      tc_fence_before();  // also orders this thread's earlier TMEM reads before XRDY
+      mbar_arrive(BAR(B_XRDY + s));
+      return true;
+    };
+    // The slot's crop rows arrive by bulk copy into its staging buffer, issued
+    // by one lane of the warpgroup: pair 0 at the start, pair j + 1 once
+    // layer 1 of pair j has completed (all of X_j, hence every read of the
+    // staging rows, is done).  Keeps the copies off the MMA warp's path.
+    const bool copier = wq == 0 && lane == 0;
+    int n_loads = 0;
+    auto load_rows = [&](int jn) {
+      const int pn = lo + blockIdx.x + (NSLOT * jn + s) * gridDim.x;
+      mbar_expect_tx(BAR(B_FULLX + s), ROWS * 16);
+      bulk_g2s(smem_u32(stg), xyz + (size_t)pn * ROWS, ROWS * 16, BAR(B_FULLX + s));
+      ++n_loads;
+    };
+    if (copier && s < my_pairs) load_rows(0);
     bool ok = mbar_wait_or_abort(BAR(B_W), 0, abort, WAIT_CYCLES);
+    if (ok && s < my_pairs) ok = build_x(0);
     for (int j = 0; ok; ++j) {
       const int i = NSLOT * j + s;
       if (i >= my_pairs) break;
       const int p = lo + blockIdx.x + i * gridDim.x;
       const uint32_t ph = j & 1;
-      // crop rows -> bf16 hi/lo X tile
-      if (!(ok = mbar_wait_or_abort(BAR(B_FULLX + s), ph, abort, WAIT_CYCLES))) break;
-      {
-        const float4 q = reinterpret_cast<const float4*>(stg)[row];
-        const unsigned m = __ballot_sync(0xffffffffu, q.w > 0.5f);
-        if (lane == 0) cnt_s[wq] = __popc(m);
-        const __nv_bfloat16 xh = __float2bfloat16_rn(q.x), yh = __float2bfloat16_rn(q.y),
-                            zh = __float2bfloat16_rn(q.z);
-        const float fx = __bfloat162float(xh), fy = __bfloat162float(yh), fz = __bfloat162float(zh);
-        uint4 c0, c1;
-        c0.x = pack_bf16(fx, fy);
-        c0.y = pack_bf16(fz, q.x - fx);
-        c0.z = pack_bf16(q.y - fy, q.z - fz);
-        c0.w = pack_bf16(fx, fy);
-        c1.x = pack_bf16(fz, 1.f);  // K columns 9, 10: ones against b1 (hi, lo)
-        c1.y = pack_bf16(1.f, 0.f);
-        c1.z = c1.w = 0u;
-        *reinterpret_cast<uint4*>(opd + kmajor_off(row, 0, 16)) = c0;
-        *reinterpret_cast<uint4*>(opd + kmajor_off(row, 8, 16)) = c1;
-      }
-      fence_async_smem();
-      tc_fence_before();
-      mbar_arrive(BAR(B_XRDY + s));
       // layer 1 epilogue -> H1 (over X: MMA1 has completed)
       if (!(ok = mbar_wait_or_abort(BAR(B_D1 + s), ph, abort, WAIT_CYCLES))) break;
       tc_fence_after();
+      if (copier && i + NSLOT < my_pairs) load_rows(j + 1);
       enc_epi_rows<64>(tslot, opd, row);
       fence_async_smem();
       tc_fence_before();
@@ -352,7 +353,9 @@ __global__ void __launch_bounds__(E_THREADS, 1)
       // layer 3 epilogues: masked max over the valid points of each object
       if (!(ok = mbar_wait_or_abort(BAR(B_D3A + s), ph, abort, WAIT_CYCLES))) break;
       tc_fence_after();
-      // crop counts written by other threads of this warpgroup
+      // crop counts written by other threads of this warpgroup (the next
+      // pair's counts overwrite them only after every thread has passed
+      // E3A below, which layer 3's second half waits for)
       asm volatile("bar.sync %0, 128;" ::"r"(1 + s) : "memory");
       const int cntA = cnt_s[0] + cnt_s[1], cntB = cnt_s[2] + cnt_s[3];
       float mA, mB;
@@ -367,6 +370,9 @@ __global__ void __launch_bounds__(E_THREADS, 1)
       if (!(ok = mbar_wait_or_abort(BAR(B_D3B + s), ph, abort, WAIT_CYCLES))) break;
       tc_fence_after();
       enc_pool(tslot, cntA, cntB, &mA, &mB);
+      // the next pair's X first (the slot's TMEM columns and H2 are free now),
+      // so that its layer 1 does not wait for these feature stores
+      if (i + NSLOT < my_pairs) ok = build_x(j + 1);
       {
         const float bias = b3[128 + row];
         put_feat(feat, ftile, p, p - lo, 128 + row, cntA > 0 ? fmaxf(mA + bias, 0.f) : 0.f);
@@ -374,6 +380,8 @@ __global__ void __launch_bounds__(E_THREADS, 1)
       }
       tc_fence_before();
     }
+    // on an abort: wait (bounded) for this lane's copy still in flight
+    if (copier && n_loads > 0 && *abort) mbar_wait(BAR(B_FULLX + s), (n_loads - 1) & 1, WAIT_CYCLES);
   }
   __syncthreads();
   if (tid == 0 && *abort) atomicOr(err, 2);

@@ -225,6 +225,28 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// Max over 32 consecutive TMEM columns of this thread's lane (32x32b shape):
+// tcgen05.ld.red returns the loaded values (unused here) and their maximum
+// in one instruction (sm_103a), which replaces 32 register max operations.
+__device__ __forceinline__ float tmem_ldmax32(uint32_t taddr) {
+  uint32_t r[32];
+  float m;
+  asm volatile(
+      "tcgen05.ld.red.sync.aligned.32x32b.x32.max.f32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, %32, [%33];\n\t"
+      "tcgen05.wait::ld.sync.aligned;\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]), "=f"(m)
+      : "r"(taddr)
+      : "memory");
+  (void)r;
+  return m;
+}
+
 // Byte offset of element (r, k) in a no-swizzle K-major bf16 tile with K
 // columns (lbo = 128, sbo = K * 16).
 __host__ __device__ constexpr uint32_t kmajor_off(int r, int k, int K) {
