@@ -15,7 +15,10 @@
 // and one saturating cvt:  next = cvt_relu(D alpha_c + beta_c) with
 // alpha_c = w_c / s_c, beta_c = b_c / s_c.  e4m3 is a floating-point format
 // (2^14.8 of range), so a loose bound costs little precision.  The
-// coefficients are computed on the host in float64 at create time.
+// coefficients are computed on the host in float64 at create time.  Layer 1
+// (bf16 hi/lo) has 1 / s_c folded into W1 and its bias b1 / s_c accumulated
+// by the MMA through two constant-one columns of X, so its epilogue is the
+// cvt alone.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -47,7 +50,7 @@ __global__ void quant_e4m3_kernel(const float* __restrict__ W, const float* __re
 }
 
 // ------------------------------------------------------------- encoder
-constexpr int F_W1 = 0;                        // [64 x 16] bf16 (hi/lo)   2 KB
+constexpr int F_W1 = 0;                        // [64 x 16] bf16 (hi/lo, b1)  2 KB
 constexpr int F_W2 = F_W1 + 64 * 16 * 2;       // [128 x 64] e4m3          8 KB
 constexpr int F_W3 = F_W2 + 128 * 64;          // [256 x 128] e4m3        32 KB
 constexpr int F_EP = F_W3 + 256 * 128;         // a1 c1 [64], a2 c2 [128], w3 b3 finv [256] (f32)
@@ -91,8 +94,26 @@ __device__ __forceinline__ void epi_e4m3_32(const float (&v)[32], const float* a
   }
 }
 
+// relu(D) for 32 TMEM columns (scale and bias already in D) -> 32 e4m3
+// bytes at row `row`, columns [k0, k0 + 32) of a K-wide tile.
+template <int K>
+__device__ __forceinline__ void epi_e4m3_relu_32(const float (&v)[32], unsigned char* dst, int row,
+                                                 int k0) {
+#pragma unroll
+  for (int c = 0; c < 2; ++c) {
+    const float* t = v + 16 * c;
+    uint4 w;
+    w.x = pack_e4m3x4_relu(t[0], t[1], t[2], t[3]);
+    w.y = pack_e4m3x4_relu(t[4], t[5], t[6], t[7]);
+    w.z = pack_e4m3x4_relu(t[8], t[9], t[10], t[11]);
+    w.w = pack_e4m3x4_relu(t[12], t[13], t[14], t[15]);
+    *reinterpret_cast<uint4*>(dst + kmajor_off8(row, k0 + 16 * c, K)) = w;
+  }
+}
+
 // Masked max over the valid points of each object (thread = channel);
-// columns [0, 64) are A's points, [64, 128) B's.
+// columns [0, 64) are A's points, [64, 128) B's.  Whole valid 32-column
+// chunks are loads with max reduction (tcgen05.ld.red).
 __device__ __forceinline__ void pool8(uint32_t taddr, int cntA, int cntB, float* mA, float* mB) {
   float v[32];
   float a = -INFINITY, b = -INFINITY;
@@ -101,12 +122,11 @@ __device__ __forceinline__ void pool8(uint32_t taddr, int cntA, int cntB, float*
     const int cnt = q < 2 ? cntA : cntB;
     const int q0 = 32 * (q & 1);
     if (q0 < cnt) {
-      tmem_ld32(taddr + 32 * q, v);
       float m = -INFINITY;
       if (q0 + 32 <= cnt) {
-#pragma unroll
-        for (int jj = 0; jj < 32; ++jj) m = fmaxf(m, v[jj]);
+        m = tmem_ldmax32(taddr + 32 * q);
       } else {
+        tmem_ld32(taddr + 32 * q, v);
 #pragma unroll
         for (int jj = 0; jj < 32; ++jj) m = fmaxf(m, (q0 + jj < cnt) ? v[jj] : -INFINITY);
       }
@@ -173,17 +193,16 @@ __global__ void __launch_bounds__(F_THREADS, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tbase = *tmem_slot;
-  const float* a1 = reinterpret_cast<const float*>(smem + F_EP);
-  const float* c1 = a1 + 64;
-  const float* a2 = c1 + 64;
+  // (a1, c1 stay in the image for reference; layer 1 has them folded into W1)
+  const float* a2 = reinterpret_cast<const float*>(smem + F_EP) + 128;
   const float* c2 = a2 + 128;
   const float* w3 = c2 + 128;
   const float* b3 = w3 + 256;
   const float* fin = b3 + 256;
 
   if (warp == MMA_WARP) {
-    // MMA issuer + TMA producer warp: warp-uniform control flow, copies by
-    // lane 0, MMAs by an elected lane
+    // MMA issuer warp: warp-uniform control flow, weight copies by lane 0,
+    // MMAs by an elected lane
     const uint32_t sW1 = smem_u32(smem + F_W1), sW2 = smem_u32(smem + F_W2);
     const uint32_t sW3 = smem_u32(smem + F_W3);
     if (lane == 0) {
@@ -191,18 +210,6 @@ __global__ void __launch_bounds__(F_THREADS, 1)
       for (int off = 0; off < F_IMG_BYTES; off += 32768)
         bulk_g2s(smem_u32(smem + off), img + off, min(32768, F_IMG_BYTES - off), BAR(B_W));
     }
-    int issued[NSLOT] = {};
-    auto load_pair = [&](int i) {
-      const int s = i % NSLOT;
-      const int p = lo + blockIdx.x + i * gridDim.x;
-      if (lane == 0) {
-        mbar_expect_tx(BAR(B_FULLX + s), ROWS * 16);
-        bulk_g2s(smem_u32(smem + F_SLOT0 + s * F_SLOT_BYTES + FS_STG), xyz + (size_t)p * ROWS,
-                 ROWS * 16, BAR(B_FULLX + s));
-      }
-      ++issued[s];
-    };
-    for (int i = 0; i < NSLOT && i < my_pairs; ++i) load_pair(i);
     bool ok = mbar_wait_warp(BAR(B_W), 0, abort, WAIT_CYCLES);
     tc_fence_after();
     const uint32_t id64 = idesc_bf16(128, 64), id128 = idesc_e4m3(128, 128);
@@ -212,8 +219,6 @@ __global__ void __launch_bounds__(F_THREADS, 1)
       for (int s = 0; s < ns && ok; ++s) {
         if (!(ok = mbar_wait_warp(BAR(B_XRDY + s), ph, abort, WAIT_CYCLES))) break;
         tc_fence_after();
-        const int i = NSLOT * r + s;
-        if (i + NSLOT < my_pairs) load_pair(i + NSLOT);
         const uint32_t sX = smem_u32(smem + F_SLOT0 + s * F_SLOT_BYTES + FS_OPD);
         if (elect_one()) {
           mma_bf16(tbase + s * SLOT_COLS, sdesc(sX, 128, 256), sdesc(sW1, 128, 256), id64, 0);
@@ -264,8 +269,6 @@ __global__ void __launch_bounds__(F_THREADS, 1)
     if (__any_sync(0xffffffffu, *abort) && elect_one()) {
       mma_commit(BAR(B_DRAIN));
       mbar_wait(BAR(B_DRAIN), 0, WAIT_CYCLES);
-      for (int s = 0; s < NSLOT; ++s)
-        if (issued[s] > 0) mbar_wait(BAR(B_FULLX + s), (issued[s] - 1) & 1, WAIT_CYCLES);
     }
     __syncwarp();
   } else {
@@ -274,42 +277,60 @@ __global__ void __launch_bounds__(F_THREADS, 1)
     unsigned char* opd = slot + FS_OPD;
     const uint32_t tslot = tbase + s * SLOT_COLS + ((uint32_t)(32 * wq) << 16);
     int* cnt_s = s_cnt + 4 * s;
+    // crop rows of the slot's pair jn -> bf16 hi/lo X tile (over the previous
+    // pair's H2, dead once its layer 3 has completed), crop counts, XRDY
+    auto build_x = [&](int jn) {
+      if (!mbar_wait_or_abort(BAR(B_FULLX + s), jn & 1, abort, WAIT_CYCLES)) return false;
+      const float4 q = reinterpret_cast<const float4*>(slot + FS_STG)[row];
+      const unsigned m = __ballot_sync(0xffffffffu, q.w > 0.5f);
+      if (lane == 0) cnt_s[wq] = __popc(m);
+      const float fx = __bfloat162float(__float2bfloat16_rn(q.x));
+      const float fy = __bfloat162float(__float2bfloat16_rn(q.y));
+      const float fz = __bfloat162float(__float2bfloat16_rn(q.z));
+      uint4 c0, cc1;
+      c0.x = pack_bf16(fx, fy);
+      c0.y = pack_bf16(fz, q.x - fx);
+      c0.z = pack_bf16(q.y - fy, q.z - fz);
+      c0.w = pack_bf16(fx, fy);
+      cc1.x = pack_bf16(fz, 1.f);  // K columns 9, 10: ones against b1 / s1 (hi, lo)
+      cc1.y = pack_bf16(1.f, 0.f);
+      cc1.z = cc1.w = 0u;
+      *reinterpret_cast<uint4*>(opd + kmajor_off(row, 0, 16)) = c0;
+      *reinterpret_cast<uint4*>(opd + kmajor_off(row, 8, 16)) = cc1;
+      fence_async_smem();
+      tc_fence_before();  // also orders this thread's earlier TMEM reads before XRDY
+      mbar_arrive(BAR(B_XRDY + s));
+      return true;
+    };
+    // the slot's crop rows by bulk copy, issued by one lane of the
+    // warpgroup: pair 0 at the start, pair j + 1 once layer 1 of pair j has
+    // completed (every read of the staging rows is done by then)
+    const bool copier = wq == 0 && lane == 0;
+    int n_loads = 0;
+    auto load_rows = [&](int jn) {
+      const int pn = lo + blockIdx.x + (NSLOT * jn + s) * gridDim.x;
+      mbar_expect_tx(BAR(B_FULLX + s), ROWS * 16);
+      bulk_g2s(smem_u32(slot + FS_STG), xyz + (size_t)pn * ROWS, ROWS * 16, BAR(B_FULLX + s));
+      ++n_loads;
+    };
+    if (copier && s < my_pairs) load_rows(0);
     bool ok = mbar_wait_or_abort(BAR(B_W), 0, abort, WAIT_CYCLES);
+    if (ok && s < my_pairs) ok = build_x(0);
     for (int j = 0; ok; ++j) {
       const int i = NSLOT * j + s;
       if (i >= my_pairs) break;
       const int p = lo + blockIdx.x + i * gridDim.x;
       const uint32_t ph = j & 1;
-      if (!(ok = mbar_wait_or_abort(BAR(B_FULLX + s), ph, abort, WAIT_CYCLES))) break;
-      {
-        const float4 q = reinterpret_cast<const float4*>(slot + FS_STG)[row];
-        const unsigned m = __ballot_sync(0xffffffffu, q.w > 0.5f);
-        if (lane == 0) cnt_s[wq] = __popc(m);
-        const float fx = __bfloat162float(__float2bfloat16_rn(q.x));
-        const float fy = __bfloat162float(__float2bfloat16_rn(q.y));
-        const float fz = __bfloat162float(__float2bfloat16_rn(q.z));
-        uint4 c0, cc1;
-        c0.x = pack_bf16(fx, fy);
-        c0.y = pack_bf16(fz, q.x - fx);
-        c0.z = pack_bf16(q.y - fy, q.z - fz);
-        c0.w = pack_bf16(fx, fy);
-        cc1.x = pack_bf16(fz, 0.f);
-        cc1.y = cc1.z = cc1.w = 0u;
-        *reinterpret_cast<uint4*>(opd + kmajor_off(row, 0, 16)) = c0;
-        *reinterpret_cast<uint4*>(opd + kmajor_off(row, 8, 16)) = cc1;
-      }
-      fence_async_smem();
-      tc_fence_before();
-      mbar_arrive(BAR(B_XRDY + s));
-      // layer 1 epilogue -> e4m3 H1 (static per-channel scale), over X
+      // layer 1 epilogue -> e4m3 H1 (scale and bias already in D1), over X
       if (!(ok = mbar_wait_or_abort(BAR(B_D1 + s), ph, abort, WAIT_CYCLES))) break;
       tc_fence_after();
+      if (copier && i + NSLOT < my_pairs) load_rows(j + 1);
       {
         float v[32];
-#pragma unroll
+#pragma unroll 1
         for (int h = 0; h < 2; ++h) {
           tmem_ld32(tslot + 32 * h, v);
-          epi_e4m3_32<64>(v, a1 + 32 * h, c1 + 32 * h, opd, row, 32 * h);
+          epi_e4m3_relu_32<64>(v, opd, row, 32 * h);
         }
       }
       fence_async_smem();
@@ -347,6 +368,8 @@ __global__ void __launch_bounds__(F_THREADS, 1)
       if (!(ok = mbar_wait_or_abort(BAR(B_D3B + s), ph, abort, WAIT_CYCLES))) break;
       tc_fence_after();
       pool8(tslot, cntA, cntB, &mA, &mB);
+      // the next pair's X first (the slot's TMEM columns and H2 are free now)
+      if (i + NSLOT < my_pairs) ok = build_x(j + 1);
       {
         const float sc = w3[128 + row], bias = b3[128 + row], fi = fin[128 + row];
         put_feat8(feat, ftile, p, p - lo, 128 + row, cntA > 0 ? fmaxf(fmaf(mA, sc, bias), 0.f) : 0.f,
@@ -356,6 +379,8 @@ __global__ void __launch_bounds__(F_THREADS, 1)
       }
       tc_fence_before();
     }
+    // on an abort: wait (bounded) for this lane's copy still in flight
+    if (copier && n_loads > 0 && *abort) mbar_wait(BAR(B_FULLX + s), (n_loads - 1) & 1, WAIT_CYCLES);
   }
   __syncthreads();
   if (tid == 0 && *abort) atomicOr(err, 2);
@@ -729,13 +754,16 @@ int upload_fp8_params(locc_handle* h, const std::vector<float>& params) {
   const size_t total = enc_bytes + G_IMG_BYTES;
   std::vector<unsigned char> img(total, 0);
   unsigned char* e = img.data();
+  // layer 1 B operand, scaled by 1 / s1: row c = [W_hi(3), W_hi(3), W_lo(3),
+  // (b1 / s1)_hi, (b1 / s1)_lo, 0 x 5]
   for (int c = 0; c < 64; ++c)
     for (int k = 0; k < 16; ++k) {
       float val = 0.f;
-      if (k < 9) {
-        const float w = P[off[0] + (size_t)c * 3 + (k % 3)];
+      if (k < 9 || k == 9 || k == 10) {
+        const float w = k < 9 ? (float)(P[off[0] + (size_t)c * 3 + (k % 3)] / s1[c])
+                              : (float)(P[offb[0] + c] / s1[c]);
         const float hi = bf16_value_h(bf16_bits_h(w));
-        val = k < 6 ? hi : w - hi;
+        val = (k < 6 || k == 9) ? hi : w - hi;
       }
       const uint16_t b = bf16_bits_h(val);
       std::memcpy(e + F_W1 + kmajor_off(c, k, 16), &b, 2);
