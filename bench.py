@@ -50,13 +50,12 @@ FLOP_HEAD = 2 * (512 * 256 + 256 * 256 + 256 * 8)          # per pair
 WORKLOAD = "uneven_scenes_8192env_poisson8_64shapes"
 # DRAM bytes (read + write) per pair of the encoder kernel from one ncu capture
 # of the bench's scene 1 (154,924 pairs; profiles/kernels_bf16_fp8_uneven8192.md):
-# scaled by the pairs of a launch to give the per-launch traffic (the BF16
-# encoder from the capture after its last change, the rest from the one before).
-ENC_DRAM_BYTES_PER_PAIR = {"bf16": (317.427968e6 + 128.645376e6) / 154924,
-                           "fp8": (317.391104e6 + 63.572480e6) / 154924}
+# scaled by the pairs of a launch to give the per-launch traffic.
+ENC_DRAM_BYTES_PER_PAIR = {"bf16": (317.429504e6 + 128.481792e6) / 154924,
+                           "fp8": (317.402880e6 + 63.598080e6) / 154924}
 # the same for the head kernel (same capture)
-HEAD_DRAM_BYTES_PER_PAIR = {"bf16": (164.734464e6 + 4.893440e6) / 154924,
-                            "fp8": (85.178368e6 + 2.168832e6) / 154924}
+HEAD_DRAM_BYTES_PER_PAIR = {"bf16": (164.733184e6 + 4.888064e6) / 154924,
+                            "fp8": (85.161216e6 + 2.122496e6) / 154924}
 WEIGHTS = os.path.join(ROOT, "paper_2304_09439_b300", "weights", "locc_trained.bin")
 
 
