@@ -307,41 +307,15 @@ __device__ __forceinline__ void write_crop(const unsigned long long* buf, int cn
   }
 }
 
-__device__ __forceinline__ void crop_pair(const DevLibrary& lib, const PairInputs& in, int p, int obj,
-                                          int lane, float r, float4* __restrict__ xyz_out,
-                                          int32_t* __restrict__ idx_out,
-                                          int32_t* __restrict__ cnt_out,
-                                          float4* __restrict__ centre_out, int* __restrict__ err,
-                                          unsigned long long* buf, int* hist,
-                                          unsigned long long* ebuf, float* rsh, int* defer,
-                                          int defer_cap) {
-  int a, b, sa, sb;
-  const bool ok = load_pair(in, lib.n_shapes, p, &a, &b, &sa, &sb, (obj == 0 && lane == 0) ? err : nullptr);
-  if (!ok) {
-    float4* xo = xyz_out + ((size_t)p * 2 + obj) * KMAX;
-    int32_t* io = idx_out ? idx_out + ((size_t)p * 2 + obj) * KMAX : nullptr;
-    const float nan = __int_as_float(0x7fc00000);
-    xo[lane] = xo[lane + 32] = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (io) io[lane] = io[lane + 32] = -1;
-    if (lane == 0) cnt_out[2 * p + obj] = 0;
-    if (obj == 0 && lane == 0 && centre_out) centre_out[p] = make_float4(nan, nan, nan, nan);
-    return;
-  }
-  Frame f;
-  pair_frame(in.poses + 7 * (size_t)a, in.poses + 7 * (size_t)b, lib.aabb[2 * sa],
-             lib.aabb[2 * sa + 1], lib.aabb[2 * sb], lib.aabb[2 * sb + 1], f);
-  if (obj == 0 && lane == 0 && centre_out) centre_out[p] = make_float4(f.c[0], f.c[1], f.c[2], 0.f);
-
-  // B's canonical coordinates need R_rel at the very end: park it in shared
-  // memory instead of keeping nine registers live through the selection
-  if (obj == 1 && lane == 0) {
-#pragma unroll
-    for (int i = 0; i < 9; ++i) rsh[i] = f.rrel[i];
-  }
-  const int shape = obj == 0 ? sa : sb;
-  const float cx = obj == 0 ? f.c[0] : f.cb[0];
-  const float cy = obj == 0 ? f.c[1] : f.cb[1];
-  const float cz = obj == 0 ? f.c[2] : f.cb[2];
+// Crop of one object of pair p (obj 0 = A, 1 = B) about the crop centre
+// (cx, cy, cz) in its body frame; R (shared memory) = R_rel for B, null for A.
+__device__ __forceinline__ void crop_object(const DevLibrary& lib, int p, int obj, int shape,
+                                            float cx, float cy, float cz, const float* R, int lane,
+                                            float r, float4* __restrict__ xyz_out,
+                                            int32_t* __restrict__ idx_out,
+                                            int32_t* __restrict__ cnt_out,
+                                            unsigned long long* buf, int* hist,
+                                            unsigned long long* ebuf, int* defer, int defer_cap) {
   const float r2 = fmul(r, r);
   const float r2_cull = r2 * 1.001f + 1e-30f;  // conservative block test
   const float4* pts = lib.points + (size_t)shape * lib.n_pad;
@@ -387,10 +361,14 @@ __device__ __forceinline__ void crop_pair(const DevLibrary& lib, const PairInput
         const float4 q = qu[u];
         const float s = point_d2(q, cx, cy, cz);
         const bool in = s <= r2;
-        n_in += __popc(__ballot_sync(FULL, in));
-        bool take = in && d2_bin(s, inv_w) < bcut;
-        unsigned tm = __ballot_sync(FULL, take);
+        const unsigned im = __ballot_sync(FULL, in);
+        n_in += __popc(im);
+        // the bins matter only once the list has overflowed (bcut < NBINS,
+        // warp-uniform): until then every in-ball key is taken
+        unsigned tm = im;
+        if (bcut < NBINS) tm = __ballot_sync(FULL, in && d2_bin(s, inv_w) < bcut);
         if (tm == 0) continue;
+        bool take = (tm >> lane) & 1u;
         if (n + __popc(tm) > CAND_CAP) {
           int below;
           bin_histogram(buf, n, inv_w, hist, lane);
@@ -436,11 +414,64 @@ __device__ __forceinline__ void crop_pair(const DevLibrary& lib, const PairInput
     return;
   }
   __syncwarp();
-  write_crop(buf, cnt, pts, cx, cy, cz, obj == 1 ? rsh : nullptr,
+  write_crop(buf, cnt, pts, cx, cy, cz, R,
              xyz_out + ((size_t)p * 2 + obj) * KMAX,
              idx_out ? idx_out + ((size_t)p * 2 + obj) * KMAX : nullptr, lane);
   if (lane == 0) cnt_out[2 * p + obj] = cnt;
   __syncwarp();
+}
+
+// Both objects of pair p, one after the other on one warp: the pair's frame
+// (two rotations, the relative pose, the crop centre in both body frames) is
+// computed once.  R_rel and both centres wait in shared memory, so that they
+// hold no registers through the selections.
+__device__ __forceinline__ void crop_pair(const DevLibrary& lib, const PairInputs& in, int p, int lane,
+                                          float r, float4* __restrict__ xyz_out,
+                                          int32_t* __restrict__ idx_out,
+                                          int32_t* __restrict__ cnt_out,
+                                          float4* __restrict__ centre_out, int* __restrict__ err,
+                                          unsigned long long* buf, int* hist,
+                                          unsigned long long* ebuf, float* rsh, int* defer,
+                                          int defer_cap) {
+  int a, b, sa, sb;
+  const bool ok = load_pair(in, lib.n_shapes, p, &a, &b, &sa, &sb, lane == 0 ? err : nullptr);
+  if (!ok) {
+    const float nan = __int_as_float(0x7fc00000);
+#pragma unroll
+    for (int obj = 0; obj < 2; ++obj) {
+      float4* xo = xyz_out + ((size_t)p * 2 + obj) * KMAX;
+      int32_t* io = idx_out ? idx_out + ((size_t)p * 2 + obj) * KMAX : nullptr;
+      xo[lane] = xo[lane + 32] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (io) io[lane] = io[lane + 32] = -1;
+      if (lane == 0) cnt_out[2 * p + obj] = 0;
+    }
+    if (lane == 0 && centre_out) centre_out[p] = make_float4(nan, nan, nan, nan);
+    return;
+  }
+  {
+    Frame f;
+    pair_frame(in.poses + 7 * (size_t)a, in.poses + 7 * (size_t)b, lib.aabb[2 * sa],
+               lib.aabb[2 * sa + 1], lib.aabb[2 * sb], lib.aabb[2 * sb + 1], f);
+    if (lane == 0) {
+      if (centre_out) centre_out[p] = make_float4(f.c[0], f.c[1], f.c[2], 0.f);
+#pragma unroll
+      for (int i = 0; i < 9; ++i) rsh[i] = f.rrel[i];
+      rsh[9] = f.c[0];
+      rsh[10] = f.c[1];
+      rsh[11] = f.c[2];
+      rsh[12] = f.cb[0];
+      rsh[13] = f.cb[1];
+      rsh[14] = f.cb[2];
+    }
+  }
+  __syncwarp();
+  // one call site: the selection code exists once in the binary
+#pragma unroll 1
+  for (int obj = 0; obj < 2; ++obj) {
+    const float* c = rsh + 9 + 3 * obj;
+    crop_object(lib, p, obj, obj ? sb : sa, c[0], c[1], c[2], obj ? rsh : nullptr, lane, r,
+                xyz_out, idx_out, cnt_out, buf, hist, ebuf, defer, defer_cap);
+  }
 }
 
 // Exact fallback for the objects crop_kernel deferred: the classic streaming
@@ -516,26 +547,25 @@ __global__ void __launch_bounds__(64, 16) crop_kernel(DevLibrary lib, PairInputs
   __shared__ unsigned long long cand[2][CAND_CAP];
   __shared__ unsigned long long ebuf[2][EBUF];
   __shared__ int hist[2][NBINS];
-  __shared__ float rsh[2][12];
+  __shared__ float rsh[2][16];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int lo, hi;
   range_bounds(rg, &lo, &hi);
-  // Objects (2 per pair, o = 2 (p - lo) + object) are handed out one at a
-  // time: the first of every warp statically, the rest from a counter
-  // (defer[1], zeroed before the launch).  Per-object costs are heavy-tailed
-  // (culled blocks and in-ball points vary with the overlap), so a static
-  // split leaves most warps idle while the unluckiest finish; with the
-  // counter all warps stop within about one object of each other.  The next
-  // index is fetched while the current object runs.
-  const int n_obj = 2 * (hi - lo);
+  // Pairs are handed out one at a time: the first of every warp statically,
+  // the rest from a counter (defer[1], zeroed before the launch).  Per-pair
+  // costs are heavy-tailed (culled blocks and in-ball points vary with the
+  // overlap), so a static split leaves most warps idle while the unluckiest
+  // finish; with the counter all warps stop within about one pair of each
+  // other.  The next index is fetched while the current pair runs.
+  const int n_pairs = hi - lo;
   const int first = 2 * (int)gridDim.x;
-  int o = 2 * (int)blockIdx.x + warp;
-  while (o < n_obj) {
+  int pr = 2 * (int)blockIdx.x + warp;
+  while (pr < n_pairs) {
     int nxt = 0;
     if (lane == 0) nxt = first + atomicAdd(&defer[1], 1);
-    crop_pair(lib, in, lo + (o >> 1), o & 1, lane, r, xyz_out, idx_out, cnt_out, centre_out, err,
-              cand[warp], hist[warp], ebuf[warp], rsh[warp], defer, defer_cap);
-    o = __shfl_sync(FULL, nxt, 0);
+    crop_pair(lib, in, lo + pr, lane, r, xyz_out, idx_out, cnt_out, centre_out, err, cand[warp],
+              hist[warp], ebuf[warp], rsh[warp], defer, defer_cap);
+    pr = __shfl_sync(FULL, nxt, 0);
   }
 }
 
