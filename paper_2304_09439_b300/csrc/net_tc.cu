@@ -100,14 +100,14 @@ constexpr int B_FULLX = 0, B_XRDY = NSLOT, B_H1RDY = 2 * NSLOT, B_H2RDY = 3 * NS
 // bf16 row of the next A operand (K = NCOL).
 template <int NCOL>
 __device__ __forceinline__ void enc_epi_rows(uint32_t taddr, unsigned char* dst, int row) {
-  float v[32];
+  float v[64];
 #pragma unroll 1
-  for (int h = 0; h < NCOL / 32; ++h) {
-    tmem_ld32(taddr + 32 * h, v);
+  for (int h = 0; h < NCOL / 64; ++h) {
+    tmem_ld32x2(taddr + 64 * h, v);  // 64 columns, two loads in flight
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
+    for (int c = 0; c < 8; ++c) {
       uint4 w;
-      const int j = 8 * c, o = 32 * h + j;
+      const int j = 8 * c, o = 64 * h + j;
       w.x = pack_relu_bf16(v[j + 0], v[j + 1]);
       w.y = pack_relu_bf16(v[j + 2], v[j + 3]);
       w.z = pack_relu_bf16(v[j + 4], v[j + 5]);
