@@ -216,26 +216,32 @@ __global__ void __launch_bounds__(F_THREADS, 1)
     for (int r = 0; ok && NSLOT * r < my_pairs; ++r) {
       const uint32_t ph = r & 1;
       const int ns = min(NSLOT, my_pairs - NSLOT * r);
-      for (int s = 0; s < ns && ok; ++s) {
-        if (!(ok = mbar_wait_warp(BAR(B_XRDY + s), ph, abort, WAIT_CYCLES))) break;
-        tc_fence_after();
-        const uint32_t sX = smem_u32(smem + F_SLOT0 + s * F_SLOT_BYTES + FS_OPD);
-        if (elect_one()) {
-          mma_bf16(tbase + s * SLOT_COLS, sdesc(sX, 128, 256), sdesc(sW1, 128, 256), id64, 0);
-          mma_commit(BAR(B_D1 + s));
-        }
-        __syncwarp();
-      }
-      for (int s = 0; s < ns && ok; ++s) {
-        if (!(ok = mbar_wait_warp(BAR(B_H1RDY + s), ph, abort, WAIT_CYCLES))) break;
-        tc_fence_after();
-        const uint32_t sH = smem_u32(smem + F_SLOT0 + s * F_SLOT_BYTES + FS_OPD);
-        if (elect_one()) {
+      // layers 1 and 2 in the order L1 0, L1 1, L1 2, L2 0, L1 3, L2 1, L2 2,
+      // L2 3 (nibble t of kOrder: slot | layer << 2): slot 0's layer 2 goes
+      // out while slot 3 is still building its X, instead of waiting behind it
+      constexpr uint32_t kOrder = 0x76534210u;
 #pragma unroll
-          for (int kk = 0; kk < 2; ++kk)
-            mma_e4m3(tbase + s * SLOT_COLS, sdesc(sH + 256 * kk, 128, 512),
-                     sdesc(sW2 + 256 * kk, 128, 512), id128, kk > 0);
-          mma_commit(BAR(B_D2 + s));
+      for (int t = 0; t < 8; ++t) {
+        const int e = (int)((kOrder >> (4 * t)) & 0xfu), s = e & 3;
+        if (!ok || s >= ns) continue;
+        const uint32_t sO = smem_u32(smem + F_SLOT0 + s * F_SLOT_BYTES + FS_OPD);
+        if ((e >> 2) == 0) {
+          if (!(ok = mbar_wait_warp(BAR(B_XRDY + s), ph, abort, WAIT_CYCLES))) break;
+          tc_fence_after();
+          if (elect_one()) {
+            mma_bf16(tbase + s * SLOT_COLS, sdesc(sO, 128, 256), sdesc(sW1, 128, 256), id64, 0);
+            mma_commit(BAR(B_D1 + s));
+          }
+        } else {
+          if (!(ok = mbar_wait_warp(BAR(B_H1RDY + s), ph, abort, WAIT_CYCLES))) break;
+          tc_fence_after();
+          if (elect_one()) {
+#pragma unroll
+            for (int kk = 0; kk < 2; ++kk)
+              mma_e4m3(tbase + s * SLOT_COLS, sdesc(sO + 256 * kk, 128, 512),
+                       sdesc(sW2 + 256 * kk, 128, 512), id128, kk > 0);
+            mma_commit(BAR(B_D2 + s));
+          }
         }
         __syncwarp();
       }
