@@ -223,8 +223,19 @@ int locc_autotune(locc_handle *h, const float *poses, const int32_t *obj_shape,
                   void *stream);
 
 /* Wait for `stream`, then report and clear the device error flag:
- * 0 or LOCC_ERR_BAD_INDEX. */
+ * 0, LOCC_ERR_TIMEOUT (a bounded device wait ran out) or LOCC_ERR_BAD_INDEX. */
 int locc_status(locc_handle *h, void *stream);
+
+/* Test entry for the failure path of the tensor-core kernels, which the paper
+ * does not have: launches one CTA on `stream` that allocates TMEM and waits
+ * on an mbarrier that nothing completes, bounded by max_cycles SM cycles
+ * (1 <= max_cycles <= 2e9, else LOCC_ERR_INVALID_ARG).  The wait runs out;
+ * the CTA raises the timeout bit of the handle's device error flag,
+ * releases its TMEM and returns -- the path every bounded wait of the
+ * encoder and head kernels takes.  The next locc_status reports
+ * LOCC_ERR_TIMEOUT and clears the flag; the CUDA context stays usable.
+ * Nothing traps or faults. */
+int locc_selftest_wait_timeout(locc_handle *h, int64_t max_cycles, void *stream);
 
 /* Allocation-free detection, for callers that may not allocate device memory
  * while they run: a simulator whose own pool allocator owns all of HBM after

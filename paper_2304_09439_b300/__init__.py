@@ -123,8 +123,16 @@ class Detector:
         return ms[:n]
 
     def status(self, stream=None) -> None:
-        """Wait for the stream; raise if a kernel flagged a bad index."""
+        """Wait for the stream; raise if a kernel flagged a bad index or a
+        bounded device wait ran out."""
         abi.check(self._lib.locc_status(self._h, abi.stream_ptr(stream)))
+
+    def selftest_wait_timeout(self, max_cycles: int = 1_000_000, stream=None) -> None:
+        """Test hook: one CTA waits (bounded) on an mbarrier nothing completes
+        and takes the kernels' timeout path; the next ``status`` raises
+        ``LoccError`` with code -4 (TIMEOUT)."""
+        abi.check(self._lib.locc_selftest_wait_timeout(self._h, int(max_cycles),
+                                                       abi.stream_ptr(stream)))
 
     # -- the path -----------------------------------------------------------
     def detect(self, poses, obj_shape, pairs, out=None, stream=None):

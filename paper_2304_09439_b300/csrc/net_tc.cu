@@ -743,6 +743,38 @@ void put_tile(unsigned char* dst, int rows, int K, F val) {
 
 }  // namespace
 
+// One CTA waits, bounded, on an mbarrier nothing completes (the test entry
+// locc_selftest_wait_timeout): same primitives and same abort path as the
+// encoder and head kernels -- bounded wait, error bit 2, TMEM released.
+__global__ void __launch_bounds__(128) wait_timeout_kernel(long long max_cycles, int* err) {
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ uint32_t tslot;
+  __shared__ int abort_flag;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  volatile int* abort = &abort_flag;
+  if (tid == 0) {
+    mbar_init(smem_u32(&bar), 1);
+    *abort = 0;
+    fence_mbar_init();
+  }
+  if (warp == 0) {
+    tmem_alloc(smem_u32(&tslot), 32);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tbase = tslot;
+  const bool ok = mbar_wait_or_abort(smem_u32(&bar), 0, abort, max_cycles);
+  tc_fence_before();
+  __syncthreads();
+  if (tid == 0 && (!ok || *abort)) atomicOr(err, 2);
+  if (warp == 0) {
+    tc_fence_after();
+    tmem_dealloc(tbase, 32);
+  }
+}
+
 int upload_tc_params(locc_handle* h, const std::vector<float>& params) {
   // flat parameter offsets (W then b per layer)
   size_t off[6], offb[6], o = 0;
@@ -844,3 +876,20 @@ int run_network_tc(locc_handle* h, const float4* xyz, const PairRange& rg, const
 }
 
 }  // namespace locc
+
+extern "C" int locc_selftest_wait_timeout(locc_handle* h, int64_t max_cycles, void* stream) {
+  if (!h) {
+    locc::set_error("handle is NULL");
+    return LOCC_ERR_INVALID_ARG;
+  }
+  if (max_cycles < 1 || max_cycles > 2000000000LL) {
+    locc::set_error("max_cycles must be in [1, 2e9]");
+    return LOCC_ERR_INVALID_ARG;
+  }
+  locc::wait_timeout_kernel<<<1, 128, 0, (cudaStream_t)stream>>>((long long)max_cycles, h->d_err);
+  if (cudaGetLastError() != cudaSuccess) {
+    locc::set_error("wait_timeout_kernel launch failed");
+    return LOCC_ERR_CUDA;
+  }
+  return LOCC_OK;
+}
