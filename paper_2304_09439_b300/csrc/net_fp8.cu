@@ -304,9 +304,13 @@ __global__ void __launch_bounds__(F_THREADS, 1)
       *reinterpret_cast<uint4*>(opd + kmajor_off(row, 0, 16)) = c0;
       *reinterpret_cast<uint4*>(opd + kmajor_off(row, 8, 16)) = cc1;
       fence_async_smem();
-      tc_fence_before();  // also orders this thread's earlier TMEM reads before XRDY
-      mbar_arrive(BAR(B_XRDY + s));
       return true;
+    };
+    // X of the pair is in place and this thread's TMEM reads of the slot are
+    // done: the slot's layer 1 may run
+    auto x_ready = [&]() {
+      tc_fence_before();
+      mbar_arrive(BAR(B_XRDY + s));
     };
     // the slot's crop rows by bulk copy, issued by one lane of the
     // warpgroup: pair 0 at the start, pair j + 1 once layer 1 of pair j has
@@ -321,7 +325,10 @@ __global__ void __launch_bounds__(F_THREADS, 1)
     };
     if (copier && s < my_pairs) load_rows(0);
     bool ok = mbar_wait_or_abort(BAR(B_W), 0, abort, WAIT_CYCLES);
-    if (ok && s < my_pairs) ok = build_x(0);
+    if (ok && s < my_pairs) {
+      ok = build_x(0);
+      if (ok) x_ready();
+    }
     for (int j = 0; ok; ++j) {
       const int i = NSLOT * j + s;
       if (i >= my_pairs) break;
@@ -373,9 +380,12 @@ __global__ void __launch_bounds__(F_THREADS, 1)
       }
       if (!(ok = mbar_wait_or_abort(BAR(B_D3B + s), ph, abort, WAIT_CYCLES))) break;
       tc_fence_after();
+      // the next pair's X (H2 is dead once layer 3 has completed), the second
+      // pooling, then XRDY (the slot's TMEM columns are free only after it)
+      const bool nx = i + NSLOT < my_pairs;
+      if (nx) ok = build_x(j + 1);
       pool8(tslot, cntA, cntB, &mA, &mB);
-      // the next pair's X first (the slot's TMEM columns and H2 are free now)
-      if (i + NSLOT < my_pairs) ok = build_x(j + 1);
+      if (nx && ok) x_ready();
       {
         const float sc = w3[128 + row], bias = b3[128 + row], fi = fin[128 + row];
         put_feat8(feat, ftile, p, p - lo, 128 + row, cntA > 0 ? fmaxf(fmaf(mA, sc, bias), 0.f) : 0.f,

@@ -319,9 +319,13 @@ __global__ void __launch_bounds__(E_THREADS, 1)
       *reinterpret_cast<uint4*>(opd + kmajor_off(row, 0, 16)) = c0;
       *reinterpret_cast<uint4*>(opd + kmajor_off(row, 8, 16)) = c1;
       fence_async_smem();
-      tc_fence_before();  // also orders this thread's earlier TMEM reads before XRDY
-      mbar_arrive(BAR(B_XRDY + s));
       return true;
+    };
+    // X of the pair is in place and this thread's TMEM reads of the slot are
+    // done: the slot's layer 1 may run
+    auto x_ready = [&]() {
+      tc_fence_before();
+      mbar_arrive(BAR(B_XRDY + s));
     };
     // The slot's crop rows arrive by bulk copy into its staging buffer, issued
     // by one lane of the warpgroup: pair 0 at the start, pair j + 1 once
@@ -337,7 +341,10 @@ __global__ void __launch_bounds__(E_THREADS, 1)
     };
     if (copier && s < my_pairs) load_rows(0);
     bool ok = mbar_wait_or_abort(BAR(B_W), 0, abort, WAIT_CYCLES);
-    if (ok && s < my_pairs) ok = build_x(0);
+    if (ok && s < my_pairs) {
+      ok = build_x(0);
+      if (ok) x_ready();
+    }
     for (int j = 0; ok; ++j) {
       const int i = NSLOT * j + s;
       if (i >= my_pairs) break;
@@ -377,10 +384,14 @@ __global__ void __launch_bounds__(E_THREADS, 1)
       }
       if (!(ok = mbar_wait_or_abort(BAR(B_D3B + s), ph, abort, WAIT_CYCLES))) break;
       tc_fence_after();
+      // the next pair's X first (H2 is dead once layer 3 has completed), then
+      // the second pooling, then XRDY (the slot's TMEM columns are free only
+      // after that pooling), then the feature stores: layer 1 of the next pair
+      // waits for neither the X build nor the stores
+      const bool nx = i + NSLOT < my_pairs;
+      if (nx) ok = build_x(j + 1);
       enc_pool(tslot, cntA, cntB, &mA, &mB);
-      // the next pair's X first (the slot's TMEM columns and H2 are free now),
-      // so that its layer 1 does not wait for these feature stores
-      if (i + NSLOT < my_pairs) ok = build_x(j + 1);
+      if (nx && ok) x_ready();
       {
         const float bias = b3[128 + row];
         put_feat(feat, ftile, p, p - lo, 128 + row, cntA > 0 ? fmaxf(mA + bias, 0.f) : 0.f);
