@@ -51,11 +51,11 @@ WORKLOAD = "uneven_scenes_8192env_poisson8_64shapes"
 # DRAM bytes (read + write) per pair of the encoder kernel from one ncu capture
 # of the bench's scene 1 (154,924 pairs; profiles/kernels_bf16_fp8_uneven8192.md):
 # scaled by the pairs of a launch to give the per-launch traffic.
-ENC_DRAM_BYTES_PER_PAIR = {"bf16": (317.429504e6 + 128.481792e6) / 154924,
-                           "fp8": (317.402880e6 + 63.598080e6) / 154924}
+ENC_DRAM_BYTES_PER_PAIR = {"bf16": (317.458944e6 + 128.572416e6) / 154924,
+                           "fp8": (317.409792e6 + 63.491072e6) / 154924}
 # the same for the head kernel (same capture)
-HEAD_DRAM_BYTES_PER_PAIR = {"bf16": (164.733184e6 + 4.888064e6) / 154924,
-                            "fp8": (85.161216e6 + 2.122496e6) / 154924}
+HEAD_DRAM_BYTES_PER_PAIR = {"bf16": (164.736000e6 + 4.787200e6) / 154924,
+                            "fp8": (85.161728e6 + 2.337280e6) / 154924}
 WEIGHTS = os.path.join(ROOT, "paper_2304_09439_b300", "weights", "locc_trained.bin")
 
 
