@@ -10,7 +10,8 @@
 // first, ties to the lower sample index, expressed in the canonical crop frame
 // (A's body axes, origin at the centre).
 //
-// Design (one CTA of two warps per pair, warp 0 = object A, warp 1 = B):
+// Design (CTAs of two warps; each warp takes whole pairs from a device
+// counter and crops object A, then object B):
 //   * every float32 operation of the selection uses an explicit round-to-
 //     nearest intrinsic in a fixed order, so index sets are reproducible bit
 //     for bit on any IEEE-754 machine that performs the same operations;
