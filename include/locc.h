@@ -88,10 +88,14 @@ typedef struct {
  * crop selection are float32 in every mode.
  *   LOCC_FP32: float32 CUDA-core products (the plain path);
  *   LOCC_BF16: bf16 operands on the tensor cores, float32 accumulation;
+ *              the biases of encoder layers 1 and 2 enter the accumulation
+ *              as bf16 hi + lo pairs (exact to about 2^-17 relative);
  *   LOCC_FP8:  e4m3 operands on the tensor cores, float32 accumulation;
  *              per-output-channel weight scales, and static per-channel
  *              activation scales (bounds that follow from the crop radius and
- *              the weights) folded into the next layer's weights. */
+ *              the weights) folded into the next layer's weights; encoder
+ *              layer 1 stays bf16 (hi/lo split), with its scale and bias
+ *              folded in the same way. */
 typedef enum { LOCC_FP32 = 0, LOCC_BF16 = 1, LOCC_FP8 = 2 } locc_precision;
 
 /* Create a detector on the current CUDA device.
