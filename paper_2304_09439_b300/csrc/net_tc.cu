@@ -443,10 +443,10 @@ __device__ __forceinline__ void head_epi_32(uint32_t taddr, const float* b, unsi
   for (int c = 0; c < 4; ++c) {
     uint4 w;
     const int j = 8 * c;
-    w.x = pack_bf16(fmaxf(v[j + 0] + b[j + 0], 0.f), fmaxf(v[j + 1] + b[j + 1], 0.f));
-    w.y = pack_bf16(fmaxf(v[j + 2] + b[j + 2], 0.f), fmaxf(v[j + 3] + b[j + 3], 0.f));
-    w.z = pack_bf16(fmaxf(v[j + 4] + b[j + 4], 0.f), fmaxf(v[j + 5] + b[j + 5], 0.f));
-    w.w = pack_bf16(fmaxf(v[j + 6] + b[j + 6], 0.f), fmaxf(v[j + 7] + b[j + 7], 0.f));
+    w.x = pack_relu_bf16(v[j + 0] + b[j + 0], v[j + 1] + b[j + 1]);
+    w.y = pack_relu_bf16(v[j + 2] + b[j + 2], v[j + 3] + b[j + 3]);
+    w.z = pack_relu_bf16(v[j + 4] + b[j + 4], v[j + 5] + b[j + 5]);
+    w.w = pack_relu_bf16(v[j + 6] + b[j + 6], v[j + 7] + b[j + 7]);
     *reinterpret_cast<uint4*>(G + kmajor_off(row, k0 + j, 256)) = w;
   }
 }
@@ -463,10 +463,10 @@ __device__ __forceinline__ void head_epi_256(uint32_t taddr, const float* b, uns
     for (int c = 0; c < 4; ++c) {
       uint4 w;
       const int j = 8 * c, o = 32 * h + j;
-      w.x = pack_bf16(fmaxf(v[j + 0] + b[o + 0], 0.f), fmaxf(v[j + 1] + b[o + 1], 0.f));
-      w.y = pack_bf16(fmaxf(v[j + 2] + b[o + 2], 0.f), fmaxf(v[j + 3] + b[o + 3], 0.f));
-      w.z = pack_bf16(fmaxf(v[j + 4] + b[o + 4], 0.f), fmaxf(v[j + 5] + b[o + 5], 0.f));
-      w.w = pack_bf16(fmaxf(v[j + 6] + b[o + 6], 0.f), fmaxf(v[j + 7] + b[o + 7], 0.f));
+      w.x = pack_relu_bf16(v[j + 0] + b[o + 0], v[j + 1] + b[o + 1]);
+      w.y = pack_relu_bf16(v[j + 2] + b[o + 2], v[j + 3] + b[o + 3]);
+      w.z = pack_relu_bf16(v[j + 4] + b[o + 4], v[j + 5] + b[o + 5]);
+      w.w = pack_relu_bf16(v[j + 6] + b[o + 6], v[j + 7] + b[o + 7]);
       *reinterpret_cast<uint4*>(G + kmajor_off(row, k0 + o, 256)) = w;
     }
   }

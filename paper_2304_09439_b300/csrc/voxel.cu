@@ -472,10 +472,10 @@ __device__ __forceinline__ void epi64(uint32_t taddr, const float* b, unsigned c
     for (int c = 0; c < 4; ++c) {
       const int j = 8 * c, o = c0 + 32 * h + j;
       uint4 w;
-      w.x = pack_bf16(fmaxf(v[j + 0] + b[o + 0], 0.f), fmaxf(v[j + 1] + b[o + 1], 0.f));
-      w.y = pack_bf16(fmaxf(v[j + 2] + b[o + 2], 0.f), fmaxf(v[j + 3] + b[o + 3], 0.f));
-      w.z = pack_bf16(fmaxf(v[j + 4] + b[o + 4], 0.f), fmaxf(v[j + 5] + b[o + 5], 0.f));
-      w.w = pack_bf16(fmaxf(v[j + 6] + b[o + 6], 0.f), fmaxf(v[j + 7] + b[o + 7], 0.f));
+      w.x = pack_relu_bf16(v[j + 0] + b[o + 0], v[j + 1] + b[o + 1]);
+      w.y = pack_relu_bf16(v[j + 2] + b[o + 2], v[j + 3] + b[o + 3]);
+      w.z = pack_relu_bf16(v[j + 4] + b[o + 4], v[j + 5] + b[o + 5]);
+      w.w = pack_relu_bf16(v[j + 6] + b[o + 6], v[j + 7] + b[o + 7]);
       *reinterpret_cast<uint4*>(dst + kmajor_off(row, o, 128)) = w;
     }
   }
