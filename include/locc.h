@@ -302,6 +302,18 @@ int locc_trainer_grad(locc_trainer *t, float *grad_out, void *stream);
 int locc_trainer_params(locc_trainer *t, float *params_out, void *stream);
 int locc_trainer_set_params(locc_trainer *t, const float *params, void *stream);
 
+/* Optimizer state for training checkpoints (the paper has no counterpart):
+ * copy out / restore Adam's first and second moments (device float32
+ * [LOCC_N_PARAMS] each, same layout as the parameters) and the number of
+ * Adam steps taken (the bias-correction exponent).  Together with the
+ * parameters this is everything a resumed run needs to continue exactly where
+ * the checkpoint was taken.  Asynchronous on `stream` except for the step
+ * count, which is host state (step >= 0, else LOCC_ERR_INVALID_ARG). */
+int locc_trainer_get_state(locc_trainer *t, float *m_out, float *v_out, int64_t *step_out,
+                           void *stream);
+int locc_trainer_set_state(locc_trainer *t, const float *m, const float *v, int64_t step,
+                           void *stream);
+
 /* Install the trainer's parameters as the handle's inference weights (all
  * precisions); blocking. */
 int locc_trainer_commit(locc_trainer *t);

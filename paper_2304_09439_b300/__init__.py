@@ -456,6 +456,26 @@ class Trainer:
         _need(p, torch.float32, "params", self.det.device)
         abi.check(self._lib.locc_trainer_set_params(self._t, abi.ptr(p), abi.stream_ptr(stream)))
 
+    def state(self, stream=None):
+        """Adam state for a checkpoint: (m, v) device tensors and the step count."""
+        import torch
+        m = torch.empty(weights.N_PARAMS, dtype=torch.float32, device=f"cuda:{self.det.device}")
+        v = torch.empty_like(m)
+        step = ctypes.c_int64(0)
+        abi.check(self._lib.locc_trainer_get_state(self._t, abi.ptr(m), abi.ptr(v),
+                                                   ctypes.byref(step), abi.stream_ptr(stream)))
+        return m, v, int(step.value)
+
+    def set_state(self, m, v, step: int, stream=None) -> None:
+        """Restore Adam's moments and step count (from ``state``)."""
+        import torch
+        _need(m, torch.float32, "m", self.det.device)
+        _need(v, torch.float32, "v", self.det.device)
+        if m.numel() != weights.N_PARAMS or v.numel() != weights.N_PARAMS:
+            raise ValueError(f"m and v need {weights.N_PARAMS} values")
+        abi.check(self._lib.locc_trainer_set_state(self._t, abi.ptr(m), abi.ptr(v), int(step),
+                                                   abi.stream_ptr(stream)))
+
     def set_lr(self, lr: float) -> None:
         """Learning rate of the following steps."""
         abi.check(self._lib.locc_trainer_set_lr(self._t, float(lr)))

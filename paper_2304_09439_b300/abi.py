@@ -34,7 +34,7 @@ EXPORTS = ["locc_create", "locc_set_precision", "locc_detect", "locc_detect_host
            "locc_voxel_set_precision",
            "locc_voxel_destroy", "locc_sim_step", "locc_sphere_contacts", "locc_set_crop_mode",
            "locc_gjk_create", "locc_gjk_detect", "locc_gjk_status", "locc_gjk_destroy",
-           "locc_selftest_wait_timeout"]
+           "locc_selftest_wait_timeout", "locc_trainer_get_state", "locc_trainer_set_state"]
 VOID_EXPORTS = ("locc_destroy", "locc_last_error", "locc_trainer_destroy", "locc_server_destroy",
                 "locc_voxel_destroy", "locc_gjk_destroy")
 NOALLOC_MAX_PAIRS = 1024
@@ -124,6 +124,8 @@ def load(build_if_needed: bool = True) -> ctypes.CDLL:
         lib.locc_stage_times.argtypes = [P, P, ctypes.c_int]
         lib.locc_status.argtypes = [P, P]
         lib.locc_selftest_wait_timeout.argtypes = [P, ctypes.c_int64, P]
+        lib.locc_trainer_get_state.argtypes = [P, P, P, ctypes.POINTER(ctypes.c_int64), P]
+        lib.locc_trainer_set_state.argtypes = [P, P, P, ctypes.c_int64, P]
         lib.locc_trainer_create.argtypes = [P, I, ctypes.POINTER(TrainConfig), ctypes.POINTER(P)]
         lib.locc_train_step.argtypes = [P, P, P, I, P, I, P, P, P, I, P]
         lib.locc_trainer_grad.argtypes = [P, P, P]

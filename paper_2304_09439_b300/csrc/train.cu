@@ -545,6 +545,26 @@ int locc_trainer_set_params(locc_trainer* t, const float* params, void* stream) 
   return LOCC_OK;
 }
 
+int locc_trainer_get_state(locc_trainer* t, float* m_out, float* v_out, int64_t* step_out,
+                           void* stream) {
+  if (!t || !m_out || !v_out || !step_out) return tfail(LOCC_ERR_INVALID_ARG, "bad argument");
+  const cudaStream_t s = (cudaStream_t)stream;
+  TCU(cudaMemcpyAsync(m_out, t->m, (size_t)LOCC_N_PARAMS * 4, cudaMemcpyDeviceToDevice, s));
+  TCU(cudaMemcpyAsync(v_out, t->v, (size_t)LOCC_N_PARAMS * 4, cudaMemcpyDeviceToDevice, s));
+  *step_out = (int64_t)t->step;
+  return LOCC_OK;
+}
+
+int locc_trainer_set_state(locc_trainer* t, const float* m, const float* v, int64_t step,
+                           void* stream) {
+  if (!t || !m || !v || step < 0) return tfail(LOCC_ERR_INVALID_ARG, "bad argument");
+  const cudaStream_t s = (cudaStream_t)stream;
+  TCU(cudaMemcpyAsync(t->m, m, (size_t)LOCC_N_PARAMS * 4, cudaMemcpyDeviceToDevice, s));
+  TCU(cudaMemcpyAsync(t->v, v, (size_t)LOCC_N_PARAMS * 4, cudaMemcpyDeviceToDevice, s));
+  t->step = (long long)step;
+  return LOCC_OK;
+}
+
 int locc_trainer_commit(locc_trainer* t) {
   if (!t) return tfail(LOCC_ERR_INVALID_ARG, "trainer is NULL");
   std::vector<float> flat(LOCC_N_PARAMS);

@@ -174,6 +174,10 @@ def main():
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--out", default=None)
     ap.add_argument("--report", default=None)
+    ap.add_argument("--checkpoint", default=None,
+                    help="write a training checkpoint (parameters, Adam state, step, sampler "
+                         "state, best-so-far) here at every validation and at the end")
+    ap.add_argument("--resume", default=None, help="continue from a checkpoint of this run")
     ap.add_argument("--crop-mode", default="local", choices=["local", "global"],
                     help="local crops (the method) or global crops (the ablation without "
                          "locality)")
@@ -231,7 +235,6 @@ def main():
         tr.commit()
         return metrics(_run(det, val, dev), val["targets"])
 
-    run_eval(0)
     P = len(train["pairs"])
     d_poses = torch.from_numpy(train["poses"]).to(dev)
     d_shape = torch.from_numpy(train["obj_shape"]).to(dev)
@@ -240,8 +243,13 @@ def main():
     loss = torch.zeros(1, dtype=torch.float32, device=dev)
     hist = []
     best = (-1.0, 0, None)
+    first = 1
+    if args.resume:
+        first, best, hist = load_checkpoint(args.resume, tr, rng, report, dev)
+    else:
+        run_eval(0)
     t0 = time.time()
-    for step in range(1, args.steps + 1):
+    for step in range(first, args.steps + 1):
         tr.set_lr(tr_lr(args, step))
         idx = rng.integers(0, P, B)
         objs = np.stack([2 * idx, 2 * idx + 1], 1).ravel()
@@ -260,6 +268,8 @@ def main():
             score = v["f1"] - 1e-3 * v["depth_mae"]
             if score > best[0]:
                 best = (score, step, tr.params().clone())
+            if args.checkpoint:
+                save_checkpoint(args.checkpoint, tr, step, rng, best, hist, report)
         if step % args.eval_every == 0 or step == args.steps:
             print(f"step {step} loss {hist[-1][1]:.4f} lr {tr_lr(args, step):.2e} "
                   f"{time.time() - t0:.0f} s", flush=True)
@@ -278,6 +288,44 @@ def main():
             json.dump(report, f, indent=1)
     tr.close()
     det.close()
+
+
+def save_checkpoint(path, tr, step, rng, best, hist, report):
+    """Everything a resumed run needs, written atomically: parameters, Adam
+    moments and step count, the last finished step, the batch sampler's state,
+    the best-so-far parameters and the history kept for the report."""
+    m, v, adam_step = tr.state()
+    js = lambda o: np.frombuffer(json.dumps(o).encode(), np.uint8)
+    state = dict(params=tr.params().cpu().numpy(), m=m.cpu().numpy(), v=v.cpu().numpy(),
+                 adam_step=np.int64(adam_step), step=np.int64(step),
+                 rng=js(rng.bit_generator.state), best_score=np.float64(best[0]),
+                 best_step=np.int64(best[1]),
+                 best_params=(best[2].cpu().numpy() if best[2] is not None
+                              else np.zeros(0, np.float32)),
+                 hist=np.array(hist, np.float64).reshape(-1, 2),
+                 report=js({"val": report["val"], "evals": report["evals"]}))
+    tmp = path + ".tmp"
+    with open(tmp, "wb") as f:
+        np.savez(f, **state)
+    os.replace(tmp, path)
+
+
+def load_checkpoint(path, tr, rng, report, dev):
+    """Restore a checkpoint written by save_checkpoint into the trainer, the
+    sampler and the report; returns (first step to run, best, history)."""
+    import torch
+    ck = np.load(path)
+    tr.set_params(torch.from_numpy(ck["params"]).to(dev))
+    tr.set_state(torch.from_numpy(ck["m"]).to(dev), torch.from_numpy(ck["v"]).to(dev),
+                 int(ck["adam_step"]))
+    rng.bit_generator.state = json.loads(bytes(ck["rng"]).decode())
+    saved = json.loads(bytes(ck["report"]).decode())
+    report["val"], report["evals"] = saved["val"], saved["evals"]
+    bp = ck["best_params"]
+    best = (float(ck["best_score"]), int(ck["best_step"]),
+            torch.from_numpy(bp).to(dev) if bp.size else None)
+    hist = [(int(a), float(b)) for a, b in ck["hist"]]
+    return int(ck["step"]) + 1, best, hist
 
 
 def tr_lr(args, step):
