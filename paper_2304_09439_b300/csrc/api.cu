@@ -10,8 +10,19 @@
 #include <numeric>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "common.cuh"
 #include "handle.cuh"
+
+namespace {
+// NVTX range for the duration of a scope: host-side markers of the entry
+// points and stages for timeline profilers (no cost without a tool attached).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+};
+}  // namespace
 
 namespace {
 
@@ -179,13 +190,16 @@ int run_path(locc_handle* h, const PairInputs& in, int n_cap, const int* n_dev, 
   if (C == 1) {
     const PairRange rg = whole_range(n_cap, n_dev);
     if (prof) CUDA_TRY(cudaEventRecord(h->ev_c0[0], s));
-    CUDA_TRY(launch_crop(lib, in, rg, h->radius, h->d_xyz, nullptr, h->d_cnt, h->d_centre, h->d_err,
-                         h->d_defer,
-                         h->n_sm, h->crop_cap, s, h->crop_mode));
+    {
+      NvtxRange r("crop");
+      CUDA_TRY(launch_crop(lib, in, rg, h->radius, h->d_xyz, nullptr, h->d_cnt, h->d_centre,
+                           h->d_err, h->d_defer, h->n_sm, h->crop_cap, s, h->crop_mode));
+    }
     if (prof) {
       CUDA_TRY(cudaEventRecord(h->ev_c1[0], s));
       CUDA_TRY(cudaEventRecord(h->ev_e0[0], s));
     }
+    NvtxRange r_net("network");
     const int st = run_network(h, h->d_xyz, rg, &in, h->d_centre, out, nullptr, nullptr, s,
                                prof ? h->ev_e1[0] : nullptr);
     if (st) return st;
@@ -342,6 +356,7 @@ int locc_reserve(locc_handle* h, int32_t max_pairs, int32_t max_envs) {
 int locc_step(locc_handle* h, const float* poses, const int32_t* obj_shape, int32_t n_obj,
               const int32_t* env_offsets, int32_t n_env, int32_t* pairs_out, int32_t* n_pairs_out,
               int32_t max_pairs, float* out, void* stream) {
+  NvtxRange nvtx_range("locc_step");
   if (!h) return fail(LOCC_ERR_INVALID_ARG, "handle is NULL");
   if (n_env < 0 || max_pairs < 0 || n_obj < 0) return fail(LOCC_ERR_INVALID_ARG, "negative size");
   if (!n_pairs_out) return fail(LOCC_ERR_INVALID_ARG, "n_pairs_out is NULL");
@@ -476,6 +491,7 @@ int locc_autotune(locc_handle* h, const float* poses, const int32_t* obj_shape, 
 int locc_step_host(locc_handle* h, const float* poses, const int32_t* obj_shape, int32_t n_obj,
                    const int32_t* env_offsets, int32_t n_env, int32_t* pairs_out,
                    int32_t* n_pairs_out, int32_t max_pairs, float* out, void* stream) {
+  NvtxRange nvtx_range("locc_step_host");
   if (!h) return fail(LOCC_ERR_INVALID_ARG, "handle is NULL");
   if (n_env < 0 || max_pairs < 0 || n_obj < 0) return fail(LOCC_ERR_INVALID_ARG, "negative size");
   if (!n_pairs_out || (n_env > 0 && (!poses || !obj_shape || !env_offsets)) ||
@@ -533,6 +549,7 @@ int locc_step_host(locc_handle* h, const float* poses, const int32_t* obj_shape,
 int locc_crop(locc_handle* h, const float* poses, const int32_t* obj_shape, int32_t n_obj,
               const int32_t* pairs, int32_t n_pairs, float* xyz_out, int32_t* idx_out,
               int32_t* cnt_out, float* centre_out, void* stream) {
+  NvtxRange nvtx_range("locc_crop");
   if (!h) return fail(LOCC_ERR_INVALID_ARG, "handle is NULL");
   if (n_pairs < 0 || n_obj < 0) return fail(LOCC_ERR_INVALID_ARG, "negative size");
   if (n_pairs == 0) return LOCC_OK;
@@ -550,6 +567,7 @@ int locc_crop(locc_handle* h, const float* poses, const int32_t* obj_shape, int3
 
 int locc_network(locc_handle* h, const float* xyz, int32_t n_pairs, float* y_out,
                  float* feat_out, void* stream) {
+  NvtxRange nvtx_range("locc_network");
   if (!h) return fail(LOCC_ERR_INVALID_ARG, "handle is NULL");
   if (n_pairs < 0) return fail(LOCC_ERR_INVALID_ARG, "negative size");
   if (n_pairs == 0) return LOCC_OK;
@@ -563,6 +581,7 @@ int locc_network(locc_handle* h, const float* xyz, int32_t n_pairs, float* y_out
 
 int locc_detect(locc_handle* h, const float* poses, const int32_t* obj_shape, int32_t n_obj,
                 const int32_t* pairs, int32_t n_pairs, float* out, void* stream) {
+  NvtxRange nvtx_range("locc_detect");
   if (!h) return fail(LOCC_ERR_INVALID_ARG, "handle is NULL");
   if (n_pairs < 0 || n_obj < 0) return fail(LOCC_ERR_INVALID_ARG, "negative size");
   if (n_pairs == 0) return LOCC_OK;
@@ -628,6 +647,7 @@ int locc_detect_host(locc_handle* h, const float* poses, const int32_t* obj_shap
 int locc_broadphase(locc_handle* h, const float* poses, const int32_t* obj_shape,
                     const int32_t* env_offsets, int32_t n_env, int32_t* pairs_out,
                     int32_t* n_pairs_out, int32_t max_pairs, void* stream) {
+  NvtxRange nvtx_range("locc_broadphase");
   if (!h) return fail(LOCC_ERR_INVALID_ARG, "handle is NULL");
   if (n_env < 0 || max_pairs < 0) return fail(LOCC_ERR_INVALID_ARG, "negative size");
   if (!n_pairs_out) return fail(LOCC_ERR_INVALID_ARG, "n_pairs_out is NULL");
