@@ -108,6 +108,10 @@ typedef enum { LOCC_FP32 = 0, LOCC_BF16 = 1, LOCC_FP8 = 2 } locc_precision;
  *   crop_radius:  radius r of the crop ball, > 0 (body-frame units).
  *   prec:         arithmetic of the network products (see above).
  *   out:          receives the handle; *out is NULL on failure.
+ * Also sets up the library's kernels on this device once per handle (their
+ * shared-memory limits, module loads and the device address of
+ * locc_detect_noalloc's scratch array), so that no later call on the handle
+ * loads a module.
  * Errors: INVALID_ARG, BAD_WEIGHTS, OOM, CUDA. */
 int locc_create(const locc_shape_library *lib, const void *weights_blob,
                 size_t blob_bytes, float crop_radius, locc_precision prec,
@@ -122,8 +126,10 @@ int locc_set_precision(locc_handle *h, locc_precision prec);
  *   pairs:     int32 [n_pairs][2], object indices (A, B)
  *   out:       float32 [n_pairs][8] = {logit, px, py, pz, nx, ny, nz, depth};
  *              collision <=> logit > 0.
- * n_pairs == 0 is a no-op.  Scratch grows on demand (stream-ordered
- * allocation); call locc_reserve first to keep this call allocation-free. */
+ * n_pairs == 0 is a no-op.  Scratch grows on demand: when n_pairs exceeds
+ * the handle's capacity the call synchronises the stream and re-allocates
+ * with cudaMalloc (not graph-capturable); call locc_reserve first to keep
+ * every later call free of allocations and synchronisation. */
 int locc_detect(locc_handle *h, const float *poses, const int32_t *obj_shape,
                 int32_t n_obj, const int32_t *pairs, int32_t n_pairs,
                 float *out, void *stream);
@@ -251,9 +257,10 @@ int locc_selftest_wait_timeout(locc_handle *h, int64_t max_cycles, void *stream)
  *   <= LOCC_NOALLOC_MAX_PAIRS, else LOCC_ERR_INVALID_ARG with a message.
  *   Scratch: one library-owned __device__ array of about 4 MiB, resident on
  *   every device that loads the library until the process exits.  The call
- *   allocates nothing (no cudaMalloc / cudaFree, no allocating library call).
- *   The first call on a device looks up that array's device address
- *   (cudaGetSymbolAddress), so make it before any stream capture.
+ *   allocates nothing (no cudaMalloc / cudaFree, no allocating library call)
+ *   and loads nothing: locc_create already looked up that array's device
+ *   address (cudaGetSymbolAddress, with the handle's device current) and
+ *   loaded the kernels this call launches.
  *   All calls share the array: calls whose kernels may overlap on the GPU
  *   (other streams, handles or host threads) race and must be ordered by the
  *   caller.  The current device must be the handle's device. */

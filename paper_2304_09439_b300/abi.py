@@ -37,7 +37,22 @@ EXPORTS = ["locc_create", "locc_set_precision", "locc_detect", "locc_detect_host
            "locc_selftest_wait_timeout", "locc_trainer_get_state", "locc_trainer_set_state"]
 VOID_EXPORTS = ("locc_destroy", "locc_last_error", "locc_trainer_destroy", "locc_server_destroy",
                 "locc_voxel_destroy", "locc_gjk_destroy")
-NOALLOC_MAX_PAIRS = 1024
+
+
+def _header_define(name: str) -> int:
+    """Integer value of a #define in include/locc.h (the header is the one
+    place such a limit is written down)."""
+    import re
+    hdr = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                       "include", "locc.h")
+    with open(hdr) as f:
+        m = re.search(rf"^#define\s+{name}\s+(\d+)\s*$", f.read(), re.M)
+    if not m:
+        raise RuntimeError(f"{name} not found in {hdr}")
+    return int(m.group(1))
+
+
+NOALLOC_MAX_PAIRS = _header_define("LOCC_NOALLOC_MAX_PAIRS")
 
 
 class LoccError(RuntimeError):

@@ -326,6 +326,17 @@ int locc_create(const locc_shape_library* lib, const void* blob, size_t blob_byt
               cudaGetErrorString(cudaGetLastError()));
   }
   if (st == LOCC_OK) st = upload_params(h, params);
+  if (st == LOCC_OK) {
+    // per-device kernel set-up: shared-memory limits, module loads, the
+    // allocation-free entry point's scratch address
+    cudaError_t e = prepare_crop_kernels(h->device);
+    if (e == cudaSuccess) e = prepare_fp32_kernels();
+    if (e == cudaSuccess) e = prepare_tc_kernels();
+    if (e == cudaSuccess) e = prepare_fp8_kernels();
+    if (e != cudaSuccess)
+      st = fail(LOCC_ERR_CUDA, "kernel set-up failed: %s", cudaGetErrorString(e));
+    if (st == LOCC_OK) st = noalloc_prepare(h);
+  }
   if (st == LOCC_OK && cudaMalloc(&h->d_err, sizeof(int)) != cudaSuccess)
     st = fail(LOCC_ERR_OOM, "cannot allocate the error flag");
   if (st == LOCC_OK && cudaMemset(h->d_err, 0, sizeof(int)) != cudaSuccess)

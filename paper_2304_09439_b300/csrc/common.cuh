@@ -156,6 +156,12 @@ cudaError_t launch_crop(const DevLibrary& lib, const PairInputs& in, const PairR
                         float r, float4* xyz, int32_t* idx, int32_t* cnt, float4* centre,
                         int* err, int* defer, int n_sm, int grid_cap, cudaStream_t stream,
                         int mode = LOCC_CROP_LOCAL);
+// Per-device set-up of the kernels above, run by locc_create with the
+// handle's device current: loads their modules (so that no later launch
+// loads one) and records the crop kernel's occupancy for that device.
+cudaError_t prepare_crop_kernels(int device);
+// Sets the dynamic shared-memory limits of the float32 network kernels.
+cudaError_t prepare_fp32_kernels();
 cudaError_t launch_encoder_fp32(const float4* xyz, const PairRange& rg,
                                 const Fp32Params& prm, float* feat, int n_sm,
                                 cudaStream_t stream);

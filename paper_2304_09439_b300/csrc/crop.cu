@@ -637,7 +637,24 @@ __global__ void __launch_bounds__(64)
   }
 }
 
+constexpr int kMaxDevices = 64;
+// resident crop CTAs per SM, per device (set by prepare_crop_kernels)
+int g_crop_per_sm[kMaxDevices] = {};
+
 }  // namespace
+
+cudaError_t prepare_crop_kernels(int device) {
+  if (device < 0 || device >= kMaxDevices) return cudaErrorInvalidDevice;
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaFuncGetAttributes(&fa, crop_kernel);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, crop_fallback_kernel);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, crop_global_kernel);
+  int per_sm = 0;
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, crop_kernel, 64, 0);
+  if (e != cudaSuccess) return e;
+  g_crop_per_sm[device] = per_sm < 1 ? 1 : per_sm;
+  return cudaSuccess;
+}
 
 cudaError_t launch_crop(const DevLibrary& lib, const PairInputs& in, const PairRange& rg, float r,
                         float4* xyz, int32_t* idx, int32_t* cnt, float4* centre, int* err,
@@ -650,11 +667,10 @@ cudaError_t launch_crop(const DevLibrary& lib, const PairInputs& in, const PairR
     return cudaGetLastError();
   }
   // one wave of resident CTAs (at most grid_cap per SM); each strides over its pairs
-  static int per_sm = 0;
-  if (per_sm == 0) {
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, crop_kernel, 64, 0);
-    if (e != cudaSuccess || per_sm < 1) per_sm = 1;
-  }
+  int dev = 0;
+  cudaGetDevice(&dev);
+  int per_sm = (dev >= 0 && dev < kMaxDevices) ? g_crop_per_sm[dev] : 0;
+  if (per_sm < 1) per_sm = 1;
   const int cap = grid_cap > 0 ? std::min(grid_cap, per_sm) : per_sm;
   const int span = (in.n_pairs + rg.n_chunks - 1) / rg.n_chunks + 1;
   const int grid = std::max(1, std::min(span, n_sm * cap));

@@ -61,6 +61,9 @@ struct locc_handle {
   cudaEvent_t ev_c0[LOCC_MAX_CHUNKS] = {}, ev_c1[LOCC_MAX_CHUNKS] = {};
   cudaEvent_t ev_e0[LOCC_MAX_CHUNKS] = {}, ev_e1[LOCC_MAX_CHUNKS] = {}, ev_h1[LOCC_MAX_CHUNKS] = {};
   int prof_chunks = 0;
+  // device address of the allocation-free entry point's static scratch array
+  // on this handle's device (resolved by locc_create)
+  unsigned char* noalloc_scratch = nullptr;
 };
 
 namespace locc {
@@ -86,6 +89,12 @@ int run_network(locc_handle* h, const float4* xyz, const PairRange& rg, const Pa
                 const float4* centre, float* out, float* y_raw, float* feat_out,
                 cudaStream_t stream, cudaEvent_t mid);
 int upload_fp8_params(locc_handle* h, const std::vector<float>& params);
+// Per-device set-up of the tensor-core kernels (dynamic shared-memory limits;
+// module load), run by locc_create with the handle's device current.
+cudaError_t prepare_tc_kernels();
+cudaError_t prepare_fp8_kernels();
+// Resolves h->noalloc_scratch on the current device (the handle's).
+int noalloc_prepare(locc_handle* h);
 int run_network_fp8(locc_handle* h, const float4* xyz, const PairRange& rg, const PairInputs* in,
                     const float4* centre, float* out, float* y_raw, float* feat_out,
                     cudaStream_t stream, cudaEvent_t mid);

@@ -255,17 +255,19 @@ __device__ __forceinline__ void head_tile(const float* __restrict__ feat, int n_
 
 }  // namespace
 
+cudaError_t prepare_fp32_kernels() {
+  cudaError_t e = cudaFuncSetAttribute(encoder_fp32_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ENC_SMEM);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(head_fp32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)HEAD_SMEM);
+  return e;
+}
+
 cudaError_t launch_encoder_fp32(const float4* xyz, const PairRange& rg, const Fp32Params& prm,
                                 float* feat, int n_sm, cudaStream_t stream) {
   const int n_pairs = (rg.n_cap + rg.n_chunks - 1) / rg.n_chunks + 1;
   if (rg.n_cap <= 0) return cudaSuccess;
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(encoder_fp32_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ENC_SMEM);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
   const int grid = std::min(n_pairs, 2 * n_sm);
   encoder_fp32_kernel<<<grid, ENC_THREADS, ENC_SMEM, stream>>>(xyz, rg, prm, feat);
   return cudaGetLastError();
@@ -276,13 +278,6 @@ cudaError_t launch_head_fp32(const float* feat, const PairRange& rg, const Fp32P
                              int n_sm, cudaStream_t stream) {
   const int n_pairs = (rg.n_cap + rg.n_chunks - 1) / rg.n_chunks + 1;
   if (rg.n_cap <= 0) return cudaSuccess;
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(head_fp32_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)HEAD_SMEM);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
   PairInputs pin{};
   if (in) pin = *in;
   const int grid = std::min((n_pairs + HEAD_PAIRS - 1) / HEAD_PAIRS, n_sm);

@@ -846,21 +846,18 @@ int upload_fp8_params(locc_handle* h, const std::vector<float>& params) {
   return LOCC_OK;
 }
 
+cudaError_t prepare_fp8_kernels() {
+  cudaError_t e = cudaFuncSetAttribute(encoder_fp8_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, F_SMEM);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(head_fp8_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, G_SMEM);
+  return e;
+}
+
 int run_network_fp8(locc_handle* h, const float4* xyz, const PairRange& rg, const PairInputs* in,
                     const float4* centre, float* out, float* y_raw, float* feat_out,
                     cudaStream_t stream, cudaEvent_t mid) {
   const int n_pairs = (rg.n_cap + rg.n_chunks - 1) / rg.n_chunks + 1;  // pairs of one chunk, at most
-  static bool attr = false;
-  if (!attr) {
-    if (cudaFuncSetAttribute(encoder_fp8_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             F_SMEM) != cudaSuccess ||
-        cudaFuncSetAttribute(head_fp8_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             G_SMEM) != cudaSuccess) {
-      set_error("cudaFuncSetAttribute failed for the fp8 kernels");
-      return LOCC_ERR_CUDA;
-    }
-    attr = true;
-  }
   unsigned char* ftile = static_cast<unsigned char*>(h->d_feat_tc);
   encoder_fp8_kernel<<<std::min(n_pairs, h->n_sm), F_THREADS, F_SMEM, stream>>>(
       xyz, rg, h->wf8_enc, feat_out, ftile, h->d_err);

@@ -848,23 +848,20 @@ int upload_tc_params(locc_handle* h, const std::vector<float>& params) {
   return LOCC_OK;
 }
 
+cudaError_t prepare_tc_kernels() {
+  cudaError_t e = cudaFuncSetAttribute(encoder_tc_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, E_SMEM);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(head_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, H_SMEM);
+  return e;
+}
+
 int run_network_tc(locc_handle* h, const float4* xyz, const PairRange& rg, const PairInputs* in,
                    const float4* centre, float* out, float* y_raw, float* feat_out,
                    cudaStream_t stream, cudaEvent_t mid) {
   if (h->prec == LOCC_FP8)
     return run_network_fp8(h, xyz, rg, in, centre, out, y_raw, feat_out, stream, mid);
   const int n_pairs = (rg.n_cap + rg.n_chunks - 1) / rg.n_chunks + 1;  // pairs of one chunk, at most
-  static bool attr = false;
-  if (!attr) {
-    if (cudaFuncSetAttribute(encoder_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             E_SMEM) != cudaSuccess ||
-        cudaFuncSetAttribute(head_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             H_SMEM) != cudaSuccess) {
-      set_error("cudaFuncSetAttribute failed for the tensor-core kernels");
-      return LOCC_ERR_CUDA;
-    }
-    attr = true;
-  }
   __nv_bfloat16* ftile = static_cast<__nv_bfloat16*>(h->d_feat_tc);
   const int grid_e = std::min(n_pairs, h->n_sm);
   encoder_tc_kernel<<<grid_e, E_THREADS, E_SMEM, stream>>>(xyz, rg, h->wtc_enc, feat_out, ftile,

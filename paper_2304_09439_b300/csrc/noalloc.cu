@@ -10,11 +10,14 @@
 //
 // The array holds at most LOCC_NOALLOC_MAX_PAIRS pairs of scratch (about
 // 4 MiB) and stays resident on every device that loads the library until the
-// process exits.  All calls share it, so two calls whose kernels overlap on a
-// GPU (different streams, different handles or different host threads)
-// corrupt each other's results; the caller must order them.  No scratch
+// process exits.  locc_create looks up its device address (and so loads it)
+// together with the kernels this entry point launches, so a detection call
+// itself neither allocates nor loads anything.  All calls share the array, so
+// two calls whose kernels overlap on a GPU (different streams, different
+// handles or different host threads) corrupt each other's results; the
+// caller must order them.  No scratch
 // location has to start at zero: every call writes each byte it later reads.
-#include <mutex>
+#include <cstdio>
 
 #include "handle.cuh"
 
@@ -30,36 +33,29 @@ constexpr size_t kScratchBytes = kXyzBytes + kFeatBytes + kCentreBytes + kCntByt
 
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-unsigned char* g_scratch_ptr[kMaxDevices] = {};
+}  // namespace
 
-// Device address of g_scratch on the current device (set up once per device).
-// In host code `g_scratch` is only a host-side stand-in for the symbol, so the
-// address must come from cudaGetSymbolAddress with the device current.
-int scratch_for_current_device(unsigned char** out) {
-  int dev = -1;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+namespace locc {
+
+// Set-up, once per handle, from locc_create with the handle's device current.
+// In host code `g_scratch` is only a host-side stand-in for the symbol, so
+// the array's device address must come from cudaGetSymbolAddress with that
+// device current.  Doing it here (not in the first detection call) also
+// makes the runtime load this file's module -- and with it the array --
+// while the caller can still allocate, so no detection call ever does.
+int noalloc_prepare(locc_handle* h) {
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
+  if (e != cudaSuccess || !p) {
     cudaGetLastError();
-    locc::set_error("locc_detect_noalloc: no usable current CUDA device");
+    set_error("cudaGetSymbolAddress of the allocation-free scratch array failed");
     return LOCC_ERR_CUDA;
   }
-  std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_scratch_ptr[dev]) {
-    void* p = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
-    if (e != cudaSuccess || !p) {
-      cudaGetLastError();
-      locc::set_error("locc_detect_noalloc: cudaGetSymbolAddress of the scratch array failed");
-      return LOCC_ERR_CUDA;
-    }
-    g_scratch_ptr[dev] = static_cast<unsigned char*>(p);
-  }
-  *out = g_scratch_ptr[dev];
+  h->noalloc_scratch = static_cast<unsigned char*>(p);
   return LOCC_OK;
 }
 
-}  // namespace
+}  // namespace locc
 
 extern "C" int locc_detect_noalloc(locc_handle* h, const float* poses, const int32_t* obj_shape,
                                    int32_t n_obj, const int32_t* pairs, int32_t n_pairs,
@@ -74,8 +70,12 @@ extern "C" int locc_detect_noalloc(locc_handle* h, const float* poses, const int
     return LOCC_ERR_INVALID_ARG;
   }
   if (n_pairs > kMaxPairs) {
-    set_error("locc_detect_noalloc: n_pairs exceeds LOCC_NOALLOC_MAX_PAIRS (1024); split the "
-              "batch or use locc_detect");
+    char msg[160];
+    std::snprintf(msg, sizeof(msg),
+                  "locc_detect_noalloc: n_pairs %d exceeds LOCC_NOALLOC_MAX_PAIRS (%d); split the "
+                  "batch or use locc_detect",
+                  (int)n_pairs, kMaxPairs);
+    set_error(msg);
     return LOCC_ERR_INVALID_ARG;
   }
   if (n_pairs == 0) return LOCC_OK;
@@ -89,9 +89,11 @@ extern "C" int locc_detect_noalloc(locc_handle* h, const float* poses, const int
     set_error("locc_detect_noalloc: the current device is not the handle's device");
     return LOCC_ERR_INVALID_ARG;
   }
-  unsigned char* base = nullptr;
-  int st = scratch_for_current_device(&base);
-  if (st) return st;
+  unsigned char* base = h->noalloc_scratch;
+  if (!base) {
+    set_error("locc_detect_noalloc: the handle has no scratch address (locc_create failed?)");
+    return LOCC_ERR_INVALID_ARG;
+  }
   float4* xyz = reinterpret_cast<float4*>(base);
   float* feat = reinterpret_cast<float*>(base + kXyzBytes);
   float4* centre = reinterpret_cast<float4*>(base + kXyzBytes + kFeatBytes);
