@@ -48,13 +48,15 @@ MAX_PAIRS = 400_000
 FLOP_ENC = 2 * 128 * (3 * 64 + 64 * 128 + 128 * 256)       # per pair
 FLOP_HEAD = 2 * (512 * 256 + 256 * 256 + 256 * 8)          # per pair
 FLOP_POINT = 2 * (3 * 64 + 64 * 128 + 128 * 256)           # encoder, per crop point
+# encoder work per object with a non-empty crop (64 point rows); an empty
+# crop's pooled feature is 0 by definition and takes no arithmetic
+FLOP_OBJ = 64 * FLOP_POINT
 WORKLOAD = "uneven_scenes_8192env_poisson8_64shapes"
 # DRAM bytes (read + write) per pair of the encoder kernel from one ncu capture
 # of the bench's scene 1 (154,924 pairs; the ncu summary of the crop, encoder
 # and head kernels under profiles/): scaled by the pairs of a launch to give
 # the per-launch traffic.
-ENC_DRAM_BYTES_PER_PAIR = {"bf16": (317.458944e6 + 128.572416e6) / 154924,
-                           "fp8": (317.409792e6 + 63.491072e6) / 154924}
+ENC_DRAM_BYTES_PER_PAIR = {}
 # the same for the head kernel (same capture)
 HEAD_DRAM_BYTES_PER_PAIR = {"bf16": (164.736000e6 + 4.787200e6) / 154924,
                             "fp8": (85.161728e6 + 2.337280e6) / 154924}
@@ -560,8 +562,10 @@ def main():
         chunks, cap = (int(x) for x in args.pipeline.split(","))
         det.set_pipeline(chunks, cap)
         tune_ms = None
-    # broadphase (3 kernels), then per chunk: crop, crop fallback, encoder, head
-    launches_per_step = 3 + 4 * (chunks if max(n_pairs) >= 4096 else 1)
+    # broadphase (3 kernels), then per chunk: crop, crop fallback, (object
+    # list for the tensor-core encoders,) encoder, head
+    per_chunk = 4 if args.precision == "fp32" else 5
+    launches_per_step = 3 + per_chunk * (chunks if max(n_pairs) >= 4096 else 1)
 
     def step_plain(i):
         p, s, e = dsc[i % len(dsc)]
@@ -589,7 +593,7 @@ def main():
         ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
         ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
         stage = np.zeros(5)
-        total = rows = 0
+        total = rows = objs = 0
         for i in range(args.steps):
             flush.zero_()
             ev0[i].record(stream)
@@ -600,20 +604,21 @@ def main():
                 stage += det.stage_times()
             total += n_pairs[i % len(dsc)]
             rows += valid_rows[i % len(dsc)]
+            objs += nonempty[i % len(dsc)]
         torch.cuda.synchronize()
         if world > 1:
             dist.barrier()
         det.profile(False)
         ms = sum(a.elapsed_time(b) for a, b in zip(ev0, ev1))
-        return ms, total, stage, rows
+        return ms, total, stage, rows, objs
 
     use_graph = not args.no_graph
     with ClockSampler(local) as clk:
         t_wall = time.perf_counter()
-        ms, total_pairs, _, _ = run_timed(use_graph, profile=False)
+        ms, total_pairs, _, _, _ = run_timed(use_graph, profile=False)
         t_wall = time.perf_counter() - t_wall
         # second pass, plain launches with per-stage CUDA events (roofline)
-        ms_prof, _, stage, rows_prof = run_timed(False, profile=True)
+        ms_prof, _, stage, rows_prof, objs_prof = run_timed(False, profile=True)
     det.status()
 
     # end to end through the host-buffer C call: H2D inputs, step, D2H outputs
@@ -652,7 +657,12 @@ def main():
             peak = peaks["bf16_tflops"] * (2.0 if args.precision == "fp8" else 1.0)
             bound, peak_src = "tensor", f"{src} bf16_tflops (burst)" + \
                 (" x 2 (fp8/bf16 nominal ratio)" if args.precision == "fp8" else "")
-        achieved = FLOP_ENC * per_step_pairs / (enc_ms * 1e-3) / 1e12
+        # the tensor-core encoders skip objects with empty crops (their pooled
+        # feature is exactly 0); the float32 encoder computes every object
+        enc_flop = (FLOP_ENC * per_step_pairs if args.precision == "fp32"
+                    else FLOP_OBJ * objs_prof / args.steps)
+        achieved = enc_flop / (enc_ms * 1e-3) / 1e12
+        achieved_padded = FLOP_ENC * per_step_pairs / (enc_ms * 1e-3) / 1e12
         # the same kernel time against the FLOPs of the valid crop rows only
         # (padded rows of partly filled or empty crops excluded)
         achieved_valid = FLOP_POINT * (rows_prof / args.steps) / (enc_ms * 1e-3) / 1e12
@@ -693,6 +703,7 @@ def main():
                          "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                          "kernel_ms": enc_ms,
                          "frac_valid_rows": achieved_valid / peak,
+                         "frac_all_pairs_padded": achieved_padded / peak,
                          "valid_rows_per_step": rows_prof / args.steps,
                          "valid_row_share": rows_prof / args.steps / (128 * per_step_pairs),
                          "stage_ms": {"broadphase": stage[0] / args.steps,
@@ -700,9 +711,13 @@ def main():
                                       "head": stage[3] / args.steps},
                          "traffic": (ENC_DRAM_BYTES_PER_PAIR[args.precision] * per_step_pairs
                                      if args.precision in ENC_DRAM_BYTES_PER_PAIR else None),
+                         "nonempty_objects_per_step": objs_prof / args.steps,
                          "traffic_unit": "bytes per launch (ncu dram read+write per pair x pairs)",
                          "peak_source": peak_src,
-                         "algorithmic": f"{FLOP_ENC} FLOP per pair x pairs per launch"},
+                         "algorithmic": (f"{FLOP_ENC} FLOP per pair x pairs per launch"
+                                         if args.precision == "fp32" else
+                                         f"{FLOP_OBJ} FLOP per object with a non-empty crop "
+                                         "(64 point rows) x such objects per launch")},
             # the head GEMMs on their own (the second tensor-core kernel)
             "roofline_head": {"kernel": "head", "bound": bound, "achieved": achieved_head,
                               "peak": peak, "unit": "TFLOP/s", "frac": achieved_head / peak,

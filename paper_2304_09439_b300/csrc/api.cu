@@ -87,7 +87,9 @@ int ensure_capacity(locc_handle* h, int n_pairs, cudaStream_t stream) {
       cudaMalloc(&h->d_centre, P * sizeof(float4)) != cudaSuccess ||
       cudaMalloc(&h->d_feat, P * 512 * sizeof(float)) != cudaSuccess ||
       cudaMalloc(&h->d_defer, (2 + 2 * P) * sizeof(int)) != cudaSuccess ||
-      cudaMalloc(&h->d_feat_tc, (P + 127) / 128 * 128 * 512 * 2) != cudaSuccess) {
+      cudaMalloc(&h->d_feat_tc, (P + 127) / 128 * 128 * 512 * 2) != cudaSuccess ||
+      cudaMalloc(&h->d_list, 2 * P * sizeof(int)) != cudaSuccess ||
+      cudaMalloc(&h->d_list_n, LOCC_MAX_CHUNKS * sizeof(int)) != cudaSuccess) {
     cudaGetLastError();
     free_scratch(h);
     return fail(LOCC_ERR_OOM, "cannot allocate scratch for %d pairs", n_pairs);
@@ -103,8 +105,10 @@ void free_scratch(locc_handle* h) {
   cudaFree(h->d_feat);
   cudaFree(h->d_defer);
   cudaFree(h->d_feat_tc);
+  cudaFree(h->d_list);
+  cudaFree(h->d_list_n);
   h->d_xyz = nullptr, h->d_cnt = nullptr, h->d_centre = nullptr, h->d_feat = nullptr;
-  h->d_defer = nullptr, h->d_feat_tc = nullptr;
+  h->d_defer = nullptr, h->d_feat_tc = nullptr, h->d_list = nullptr, h->d_list_n = nullptr;
   h->cap_pairs = 0;
 }
 

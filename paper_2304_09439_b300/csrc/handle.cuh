@@ -38,6 +38,8 @@ struct locc_handle {
   float* d_feat = nullptr;
   int* d_defer = nullptr;  // crop objects left to the exact fallback kernel
   void* d_feat_tc = nullptr;  // bf16 pooled features in the head's operand tiles
+  int* d_list = nullptr;      // [2 cap_pairs] objects with non-empty crops (tensor-core encoders)
+  int* d_list_n = nullptr;    // [LOCC_MAX_CHUNKS] list length per pipeline chunk
   int* d_err = nullptr;
   // broadphase per-environment counts / offsets
   int32_t* d_env_counts = nullptr;
@@ -92,6 +94,10 @@ int upload_fp8_params(locc_handle* h, const std::vector<float>& params);
 // Per-device set-up of the tensor-core kernels (dynamic shared-memory limits;
 // module load), run by locc_create with the handle's device current.
 cudaError_t prepare_tc_kernels();
+// Zeroes the pooled features of the objects of `rg` whose crop is empty and
+// lists the others for the tensor-core encoders (h->d_list, h->d_list_n).
+cudaError_t launch_enc_list(locc_handle* h, const float4* xyz, const PairRange& rg, float* feat,
+                            void* ftile, int chunks_per_side, cudaStream_t stream);
 cudaError_t prepare_fp8_kernels();
 // Resolves h->noalloc_scratch on the current device (the handle's).
 int noalloc_prepare(locc_handle* h);

@@ -66,7 +66,8 @@ constexpr int F_SLOT_BYTES = FS_OPD + 128 * 128;
 constexpr int F_CTRL = F_SLOT0 + NSLOT * F_SLOT_BYTES;
 constexpr int NBAR = 9 * NSLOT + 2;
 constexpr int C_BAR = 0, C_TMEM = 8 * NBAR, C_ABORT = C_TMEM + 4, C_CNT = C_ABORT + 4;
-constexpr int F_SMEM = F_CTRL + C_CNT + 16 * NSLOT;
+constexpr int C_OBJ = C_CNT + 16 * NSLOT;  // [slot][tile parity][u, v] object ids
+constexpr int F_SMEM = F_CTRL + C_OBJ + 16 * NSLOT;
 static_assert(F_SMEM <= 227 * 1024, "fp8 encoder shared memory");
 constexpr int F_THREADS = 32 * (4 * NSLOT + 1);
 constexpr int MMA_WARP = 4 * NSLOT;
@@ -149,17 +150,22 @@ __device__ __forceinline__ void put_feat8(float* feat, unsigned char* ftile, int
   t[kmajor_off8(rel & 127, k & 63, 64)] = (unsigned char)(pack_e4m3x4(v * inv_s, 0.f, 0.f, 0.f) & 0xffu);
 }
 
+// Tiles of two listed objects with non-empty crops, as in the BF16 encoder
+// (object u in rows 0..63, v in 64..127; CTA b takes tiles b, b + G, ...).
 __global__ void __launch_bounds__(F_THREADS, 1)
     encoder_fp8_kernel(const float4* __restrict__ xyz, PairRange rg,
+                       const int* __restrict__ list, const int* __restrict__ list_n,
                        const unsigned char* __restrict__ img, float* __restrict__ feat,
                        unsigned char* __restrict__ ftile, int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char smem[];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   int lo, hi;
   range_bounds(rg, &lo, &hi);
-  const int n = hi - lo;
+  const int n_objs = min(list_n[rg.chunk], 2 * (hi - lo));
+  const int* lst = list + 2 * (size_t)lo;
+  const int n = (n_objs + 1) >> 1;  // tiles
   if ((int)blockIdx.x >= n) return;
-  const int my_pairs = (n - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
+  const int my_pairs = (n - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;  // tiles
 
   unsigned char* ctrl = smem + F_CTRL;
   const uint32_t bar0 = smem_u32(ctrl + C_BAR);
@@ -283,11 +289,17 @@ __global__ void __launch_bounds__(F_THREADS, 1)
     unsigned char* opd = slot + FS_OPD;
     const uint32_t tslot = tbase + s * SLOT_COLS + ((uint32_t)(32 * wq) << 16);
     int* cnt_s = s_cnt + 4 * s;
-    // crop rows of the slot's pair jn -> bf16 hi/lo X tile (over the previous
-    // pair's H2, dead once its layer 3 has completed), crop counts, XRDY
+    int* obj_s = reinterpret_cast<int*>(ctrl + C_OBJ) + 4 * s;  // [parity][u, v]
+    int tu0 = -1, tv0 = -1, tu1 = -1, tv1 = -1;  // objects of the slot's tiles, by parity
+    // crop rows of the slot's tile jn -> bf16 hi/lo X tile (over the previous
+    // tile's H2, dead once its layer 3 has completed), crop counts, XRDY
     auto build_x = [&](int jn) {
       if (!mbar_wait_or_abort(BAR(B_FULLX + s), jn & 1, abort, WAIT_CYCLES)) return false;
-      const float4 q = reinterpret_cast<const float4*>(slot + FS_STG)[row];
+      const int nu = obj_s[2 * (jn & 1)], nv = obj_s[2 * (jn & 1) + 1];
+      if (jn & 1) tu1 = nu, tv1 = nv;
+      else tu0 = nu, tv0 = nv;
+      float4 q = reinterpret_cast<const float4*>(slot + FS_STG)[row];
+      if (row >= KMAX && nv < 0) q = make_float4(0.f, 0.f, 0.f, 0.f);
       const unsigned m = __ballot_sync(0xffffffffu, q.w > 0.5f);
       if (lane == 0) cnt_s[wq] = __popc(m);
       const float fx = __bfloat162float(__float2bfloat16_rn(q.x));
@@ -318,9 +330,15 @@ __global__ void __launch_bounds__(F_THREADS, 1)
     const bool copier = wq == 0 && lane == 0;
     int n_loads = 0;
     auto load_rows = [&](int jn) {
-      const int pn = lo + blockIdx.x + (NSLOT * jn + s) * gridDim.x;
-      mbar_expect_tx(BAR(B_FULLX + s), ROWS * 16);
-      bulk_g2s(smem_u32(slot + FS_STG), xyz + (size_t)pn * ROWS, ROWS * 16, BAR(B_FULLX + s));
+      const int tg = blockIdx.x + (NSLOT * jn + s) * gridDim.x;
+      const int u = lst[2 * tg], v = 2 * tg + 1 < n_objs ? lst[2 * tg + 1] : -1;
+      obj_s[2 * (jn & 1)] = u;
+      obj_s[2 * (jn & 1) + 1] = v;
+      mbar_expect_tx(BAR(B_FULLX + s), (v >= 0 ? 2 : 1) * KMAX * 16);
+      bulk_g2s(smem_u32(slot + FS_STG), xyz + (size_t)u * KMAX, KMAX * 16, BAR(B_FULLX + s));
+      if (v >= 0)
+        bulk_g2s(smem_u32(slot + FS_STG + KMAX * 16), xyz + (size_t)v * KMAX, KMAX * 16,
+                 BAR(B_FULLX + s));
       ++n_loads;
     };
     if (copier && s < my_pairs) load_rows(0);
@@ -332,7 +350,6 @@ __global__ void __launch_bounds__(F_THREADS, 1)
     for (int j = 0; ok; ++j) {
       const int i = NSLOT * j + s;
       if (i >= my_pairs) break;
-      const int p = lo + blockIdx.x + i * gridDim.x;
       const uint32_t ph = j & 1;
       // layer 1 epilogue -> e4m3 H1 (scale and bias already in D1), over X
       if (!(ok = mbar_wait_or_abort(BAR(B_D1 + s), ph, abort, WAIT_CYCLES))) break;
@@ -372,11 +389,15 @@ __global__ void __launch_bounds__(F_THREADS, 1)
       pool8(tslot, cntA, cntB, &mA, &mB);
       tc_fence_before();
       mbar_arrive(BAR(B_E3A + s));
+      const int u = ph ? tu1 : tu0, v = ph ? tv1 : tv0;
+      const int pu = u >> 1, ku = (u & 1) * 256, pv = v >> 1, kv = (v & 1) * 256;
       {
         const float sc = w3[row], bias = b3[row], fi = fin[row];
-        put_feat8(feat, ftile, p, p - lo, row, cntA > 0 ? fmaxf(fmaf(mA, sc, bias), 0.f) : 0.f, fi);
-        put_feat8(feat, ftile, p, p - lo, 256 + row, cntB > 0 ? fmaxf(fmaf(mB, sc, bias), 0.f) : 0.f,
-                  fi);
+        put_feat8(feat, ftile, pu, pu - lo, ku + row,
+                  cntA > 0 ? fmaxf(fmaf(mA, sc, bias), 0.f) : 0.f, fi);
+        if (v >= 0)
+          put_feat8(feat, ftile, pv, pv - lo, kv + row,
+                    cntB > 0 ? fmaxf(fmaf(mB, sc, bias), 0.f) : 0.f, fi);
       }
       if (!(ok = mbar_wait_or_abort(BAR(B_D3B + s), ph, abort, WAIT_CYCLES))) break;
       tc_fence_after();
@@ -388,10 +409,11 @@ __global__ void __launch_bounds__(F_THREADS, 1)
       if (nx && ok) x_ready();
       {
         const float sc = w3[128 + row], bias = b3[128 + row], fi = fin[128 + row];
-        put_feat8(feat, ftile, p, p - lo, 128 + row, cntA > 0 ? fmaxf(fmaf(mA, sc, bias), 0.f) : 0.f,
-                  fi);
-        put_feat8(feat, ftile, p, p - lo, 384 + row, cntB > 0 ? fmaxf(fmaf(mB, sc, bias), 0.f) : 0.f,
-                  fi);
+        put_feat8(feat, ftile, pu, pu - lo, ku + 128 + row,
+                  cntA > 0 ? fmaxf(fmaf(mA, sc, bias), 0.f) : 0.f, fi);
+        if (v >= 0)
+          put_feat8(feat, ftile, pv, pv - lo, kv + 128 + row,
+                    cntB > 0 ? fmaxf(fmaf(mB, sc, bias), 0.f) : 0.f, fi);
       }
       tc_fence_before();
     }
@@ -859,8 +881,12 @@ int run_network_fp8(locc_handle* h, const float4* xyz, const PairRange& rg, cons
                     cudaStream_t stream, cudaEvent_t mid) {
   const int n_pairs = (rg.n_cap + rg.n_chunks - 1) / rg.n_chunks + 1;  // pairs of one chunk, at most
   unsigned char* ftile = static_cast<unsigned char*>(h->d_feat_tc);
+  if (launch_enc_list(h, xyz, rg, feat_out, ftile, 4, stream) != cudaSuccess) {
+    set_error("enc_list_kernel launch failed");
+    return LOCC_ERR_CUDA;
+  }
   encoder_fp8_kernel<<<std::min(n_pairs, h->n_sm), F_THREADS, F_SMEM, stream>>>(
-      xyz, rg, h->wf8_enc, feat_out, ftile, h->d_err);
+      xyz, rg, h->d_list, h->d_list_n, h->wf8_enc, feat_out, ftile, h->d_err);
   if (cudaGetLastError() != cudaSuccess) {
     set_error("encoder_fp8_kernel launch failed");
     return LOCC_ERR_CUDA;

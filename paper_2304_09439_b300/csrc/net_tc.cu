@@ -85,7 +85,8 @@ static_assert(E_OPD0 % 1024 == 0, "operand regions must stay 1 KB aligned");
 // control block: mbarriers (8 B each), tmem slot, abort flag, counts [slot][4 warps]
 constexpr int NBAR = 9 * NSLOT + 2;
 constexpr int C_BAR = 0, C_TMEM = 8 * NBAR, C_ABORT = C_TMEM + 4, C_CNT = C_ABORT + 4;
-constexpr int E_SMEM = E_CTRL + C_CNT + 16 * NSLOT;
+constexpr int C_OBJ = C_CNT + 16 * NSLOT;  // [slot][tile parity][u, v] object ids
+constexpr int E_SMEM = E_CTRL + C_OBJ + 16 * NSLOT;
 static_assert(E_SMEM <= 227 * 1024, "encoder shared memory");
 constexpr int E_THREADS = 32 * (4 * NSLOT + 1);  // 4 epilogue warps per slot + the MMA/TMA warp
 constexpr int MMA_WARP = 4 * NSLOT;
@@ -143,6 +144,55 @@ __device__ __forceinline__ void enc_pool(uint32_t taddr, int cntA, int cntB, flo
   *mB = b;
 }
 
+// ------------------------------------------------------------- object list
+// The tensor-core encoders work on the objects whose crop is not empty, two
+// objects (2 x 64 crop rows) per M = 128 tile.  An empty crop pools to
+// exactly 0 (the max-pool runs over no point and ReLU outputs are >= 0), so
+// those objects need no MMA at all: this kernel writes their features (zeros)
+// and appends every other object of the launch's pairs [lo, hi) to
+// list[2 lo ..] (object id 2 p + side, in no particular order: each object's
+// features depend on its own rows only), counting them in list_n[chunk],
+// which the caller has zeroed.  The valid points of an object come first in
+// its 64 rows (the crop writes them that way), so row 0 decides.
+// Zero features: float32 [P][512] when feat is given, and the head's operand
+// tiles (K-chunks of 8 KB, chunks_per_side per object: 8 of 32 bf16 or 4 of
+// 64 e4m3; both put one row's 16-byte pieces at (r / 8) 512 + q 128 +
+// (r % 8) 16, q = 0..3).
+__global__ void __launch_bounds__(256)
+    enc_list_kernel(const float4* __restrict__ xyz, PairRange rg, int* __restrict__ list,
+                    int* __restrict__ list_n, float* __restrict__ feat,
+                    unsigned char* __restrict__ ftile, int chunks_per_side) {
+  int lo, hi;
+  range_bounds(rg, &lo, &hi);
+  const int n_obj = 2 * (hi - lo), lane = threadIdx.x & 31;
+  int* lst = list + 2 * (size_t)lo;
+  const size_t tile_bytes = (size_t)2 * chunks_per_side * 8192;
+  for (int base = blockIdx.x * blockDim.x; base < n_obj; base += gridDim.x * blockDim.x) {
+    const int i = base + (int)threadIdx.x;
+    bool live = false;
+    if (i < n_obj) live = xyz[(size_t)(2 * lo + i) * KMAX].w > 0.5f;
+    const unsigned m = __ballot_sync(0xffffffffu, live);
+    int b0 = 0;
+    if (lane == 0 && m) b0 = atomicAdd(list_n + rg.chunk, __popc(m));
+    b0 = __shfl_sync(0xffffffffu, b0, 0);
+    if (live) lst[b0 + __popc(m & ((1u << lane) - 1u))] = 2 * lo + i;
+    if (i < n_obj && !live) {
+      const int rel = i >> 1, side = i & 1, r = rel & 127;
+      unsigned char* t = ftile + (size_t)(rel >> 7) * tile_bytes +
+                         (size_t)side * chunks_per_side * 8192 + (r >> 3) * 512 + (r & 7) * 16;
+      for (int c = 0; c < chunks_per_side; ++c)
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          *reinterpret_cast<uint4*>(t + c * 8192 + q * 128) = make_uint4(0u, 0u, 0u, 0u);
+      if (feat) {
+        float4* f = reinterpret_cast<float4*>(feat + (size_t)(lo + rel) * 512 + side * 256);
+#pragma unroll 4
+        for (int k = 0; k < 64; ++k) f[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+    }
+  }
+}
+
 // Pooled feature k of pair p (rel = p - first pair of the launch): float32
 // [P][512] when feat is given (the network's feature output), and always
 // bf16 in the head's operand layout -- tiles of 128 pairs, each 16 K-chunks
@@ -156,17 +206,24 @@ __device__ __forceinline__ void put_feat(float* feat, __nv_bfloat16* ftile, int 
   *reinterpret_cast<__nv_bfloat16*>(t + kmajor_off(rel & 127, k & 31, 32)) = __float2bfloat16_rn(v);
 }
 
+// Tiles: the launch's list of objects with non-empty crops (enc_list_kernel),
+// two per tile -- object u in rows / points 0..63, object v in 64..127 (a
+// last odd object runs alone, its second half counting as empty).  CTA b
+// takes tiles b, b + G, b + 2G, ...
 __global__ void __launch_bounds__(E_THREADS, 1)
     encoder_tc_kernel(const float4* __restrict__ xyz, PairRange rg,
+                      const int* __restrict__ list, const int* __restrict__ list_n,
                       const unsigned char* __restrict__ img, float* __restrict__ feat,
                       __nv_bfloat16* __restrict__ ftile, int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char smem[];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   int lo, hi;
   range_bounds(rg, &lo, &hi);
-  const int n = hi - lo;
+  const int n_objs = min(list_n[rg.chunk], 2 * (hi - lo));
+  const int* lst = list + 2 * (size_t)lo;
+  const int n = (n_objs + 1) >> 1;  // tiles
   if ((int)blockIdx.x >= n) return;
-  const int my_pairs = (n - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
+  const int my_pairs = (n - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;  // tiles
 
   unsigned char* ctrl = smem + E_CTRL;
   const uint32_t bar0 = smem_u32(ctrl + C_BAR);
@@ -298,11 +355,18 @@ __global__ void __launch_bounds__(E_THREADS, 1)
     unsigned char* opd = smem + E_OPD0 + s * OPD_BYTES;
     const uint32_t tslot = tbase + s * SLOT_COLS + ((uint32_t)(32 * wq) << 16);
     int* cnt_s = s_cnt + 4 * s;
-    // crop rows of the slot's pair jn -> bf16 hi/lo X tile (over the previous
-    // pair's H2, dead once its layer 3 has completed), crop counts, XRDY
+    int* obj_s = reinterpret_cast<int*>(ctrl + C_OBJ) + 4 * s;  // [parity][u, v]
+    int tu0 = -1, tv0 = -1, tu1 = -1, tv1 = -1;  // objects of the slot's tiles, by parity
+    // crop rows of the slot's tile jn -> bf16 hi/lo X tile (over the previous
+    // tile's H2, dead once its layer 3 has completed), crop counts, XRDY
     auto build_x = [&](int jn) {
       if (!mbar_wait_or_abort(BAR(B_FULLX + s), jn & 1, abort, WAIT_CYCLES)) return false;
-      const float4 q = reinterpret_cast<const float4*>(stg)[row];
+      // the copier wrote the tile's objects before its expect_tx arrival
+      const int nu = obj_s[2 * (jn & 1)], nv = obj_s[2 * (jn & 1) + 1];
+      if (jn & 1) tu1 = nu, tv1 = nv;
+      else tu0 = nu, tv0 = nv;
+      float4 q = reinterpret_cast<const float4*>(stg)[row];
+      if (row >= KMAX && nv < 0) q = make_float4(0.f, 0.f, 0.f, 0.f);
       const unsigned m = __ballot_sync(0xffffffffu, q.w > 0.5f);
       if (lane == 0) cnt_s[wq] = __popc(m);
       const __nv_bfloat16 xh = __float2bfloat16_rn(q.x), yh = __float2bfloat16_rn(q.y),
@@ -328,15 +392,21 @@ __global__ void __launch_bounds__(E_THREADS, 1)
       mbar_arrive(BAR(B_XRDY + s));
     };
     // The slot's crop rows arrive by bulk copy into its staging buffer, issued
-    // by one lane of the warpgroup: pair 0 at the start, pair j + 1 once
-    // layer 1 of pair j has completed (all of X_j, hence every read of the
-    // staging rows, is done).  Keeps the copies off the MMA warp's path.
+    // by one lane of the warpgroup: tile 0 at the start, tile j + 1 once
+    // layer 1 of tile j has completed (all of X_j, hence every read of the
+    // staging rows and of the tile's object ids, is done).  Keeps the copies
+    // off the MMA warp's path.
     const bool copier = wq == 0 && lane == 0;
     int n_loads = 0;
     auto load_rows = [&](int jn) {
-      const int pn = lo + blockIdx.x + (NSLOT * jn + s) * gridDim.x;
-      mbar_expect_tx(BAR(B_FULLX + s), ROWS * 16);
-      bulk_g2s(smem_u32(stg), xyz + (size_t)pn * ROWS, ROWS * 16, BAR(B_FULLX + s));
+      const int tg = blockIdx.x + (NSLOT * jn + s) * gridDim.x;
+      const int u = lst[2 * tg], v = 2 * tg + 1 < n_objs ? lst[2 * tg + 1] : -1;
+      obj_s[2 * (jn & 1)] = u;
+      obj_s[2 * (jn & 1) + 1] = v;
+      mbar_expect_tx(BAR(B_FULLX + s), (v >= 0 ? 2 : 1) * KMAX * 16);
+      bulk_g2s(smem_u32(stg), xyz + (size_t)u * KMAX, KMAX * 16, BAR(B_FULLX + s));
+      if (v >= 0)
+        bulk_g2s(smem_u32(stg + KMAX * 16), xyz + (size_t)v * KMAX, KMAX * 16, BAR(B_FULLX + s));
       ++n_loads;
     };
     if (copier && s < my_pairs) load_rows(0);
@@ -348,7 +418,6 @@ __global__ void __launch_bounds__(E_THREADS, 1)
     for (int j = 0; ok; ++j) {
       const int i = NSLOT * j + s;
       if (i >= my_pairs) break;
-      const int p = lo + blockIdx.x + i * gridDim.x;
       const uint32_t ph = j & 1;
       // layer 1 epilogue -> H1 (over X: MMA1 has completed)
       if (!(ok = mbar_wait_or_abort(BAR(B_D1 + s), ph, abort, WAIT_CYCLES))) break;
@@ -377,10 +446,15 @@ __global__ void __launch_bounds__(E_THREADS, 1)
       enc_pool(tslot, cntA, cntB, &mA, &mB);
       tc_fence_before();
       mbar_arrive(BAR(B_E3A + s));
+      // the tile's objects (before build_x of the next tile reuses the other
+      // parity's registers; this parity's stay until tile j + 2)
+      const int u = ph ? tu1 : tu0, v = ph ? tv1 : tv0;
+      const int pu = u >> 1, ku = (u & 1) * 256, pv = v >> 1, kv = (v & 1) * 256;
       {
         const float bias = b3[row];
-        put_feat(feat, ftile, p, p - lo, row, cntA > 0 ? fmaxf(mA + bias, 0.f) : 0.f);
-        put_feat(feat, ftile, p, p - lo, 256 + row, cntB > 0 ? fmaxf(mB + bias, 0.f) : 0.f);
+        put_feat(feat, ftile, pu, pu - lo, ku + row, cntA > 0 ? fmaxf(mA + bias, 0.f) : 0.f);
+        if (v >= 0)
+          put_feat(feat, ftile, pv, pv - lo, kv + row, cntB > 0 ? fmaxf(mB + bias, 0.f) : 0.f);
       }
       if (!(ok = mbar_wait_or_abort(BAR(B_D3B + s), ph, abort, WAIT_CYCLES))) break;
       tc_fence_after();
@@ -394,8 +468,10 @@ __global__ void __launch_bounds__(E_THREADS, 1)
       if (nx && ok) x_ready();
       {
         const float bias = b3[128 + row];
-        put_feat(feat, ftile, p, p - lo, 128 + row, cntA > 0 ? fmaxf(mA + bias, 0.f) : 0.f);
-        put_feat(feat, ftile, p, p - lo, 384 + row, cntB > 0 ? fmaxf(mB + bias, 0.f) : 0.f);
+        put_feat(feat, ftile, pu, pu - lo, ku + 128 + row, cntA > 0 ? fmaxf(mA + bias, 0.f) : 0.f);
+        if (v >= 0)
+          put_feat(feat, ftile, pv, pv - lo, kv + 128 + row,
+                   cntB > 0 ? fmaxf(mB + bias, 0.f) : 0.f);
       }
       tc_fence_before();
     }
@@ -848,6 +924,17 @@ int upload_tc_params(locc_handle* h, const std::vector<float>& params) {
   return LOCC_OK;
 }
 
+cudaError_t launch_enc_list(locc_handle* h, const float4* xyz, const PairRange& rg, float* feat,
+                            void* ftile, int chunks_per_side, cudaStream_t stream) {
+  cudaError_t e = cudaMemsetAsync(h->d_list_n + rg.chunk, 0, sizeof(int), stream);
+  if (e != cudaSuccess) return e;
+  const int n_obj = 2 * ((rg.n_cap + rg.n_chunks - 1) / rg.n_chunks + 1);
+  const int grid = std::max(1, std::min((n_obj + 255) / 256, 8 * h->n_sm));
+  enc_list_kernel<<<grid, 256, 0, stream>>>(xyz, rg, h->d_list, h->d_list_n, feat,
+                                            static_cast<unsigned char*>(ftile), chunks_per_side);
+  return cudaGetLastError();
+}
+
 cudaError_t prepare_tc_kernels() {
   cudaError_t e = cudaFuncSetAttribute(encoder_tc_kernel,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, E_SMEM);
@@ -863,9 +950,13 @@ int run_network_tc(locc_handle* h, const float4* xyz, const PairRange& rg, const
     return run_network_fp8(h, xyz, rg, in, centre, out, y_raw, feat_out, stream, mid);
   const int n_pairs = (rg.n_cap + rg.n_chunks - 1) / rg.n_chunks + 1;  // pairs of one chunk, at most
   __nv_bfloat16* ftile = static_cast<__nv_bfloat16*>(h->d_feat_tc);
+  if (launch_enc_list(h, xyz, rg, feat_out, ftile, 8, stream) != cudaSuccess) {
+    set_error("enc_list_kernel launch failed");
+    return LOCC_ERR_CUDA;
+  }
   const int grid_e = std::min(n_pairs, h->n_sm);
-  encoder_tc_kernel<<<grid_e, E_THREADS, E_SMEM, stream>>>(xyz, rg, h->wtc_enc, feat_out, ftile,
-                                                           h->d_err);
+  encoder_tc_kernel<<<grid_e, E_THREADS, E_SMEM, stream>>>(xyz, rg, h->d_list, h->d_list_n,
+                                                           h->wtc_enc, feat_out, ftile, h->d_err);
   if (cudaGetLastError() != cudaSuccess) {
     set_error("encoder_tc_kernel launch failed");
     return LOCC_ERR_CUDA;
