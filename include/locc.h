@@ -275,13 +275,17 @@ int locc_detect_noalloc(locc_handle *h, const float *poses,
  * backward kernels (float32): binary cross-entropy on the collision logit plus
  * alpha * mean(f^2) on the pooled embedding (Sec. III-A loss, alpha = 0.5),
  * regression terms on the contact point, normal and depth (collisions only for
- * point and normal; Huber loss on depth), Adam with bias correction (Sec. IV-A
- * and the hyper-parameter table: lr 1e-3, beta1 0.9, beta2 0.999, eps 1e-8). */
+ * point and normal; Huber loss on depth), w_len (|n| - 1)^2 on the length of
+ * the raw normal output of every pair (this library's term: the epilogue
+ * normalises n, and a short raw n would amplify the rounding of the BF16 /
+ * FP8 paths), Adam with bias correction (Sec. IV-A and the hyper-parameter
+ * table: lr 1e-3, beta1 0.9, beta2 0.999, eps 1e-8). */
 typedef struct locc_trainer locc_trainer;
 typedef struct {
   float lr, beta1, beta2, eps;       /* Adam */
   float w_pt, w_n, w_d, huber_beta;  /* regression weights, Huber width */
   float alpha;                       /* embedding regulariser */
+  float w_len;                       /* raw-normal length term (0 = off) */
 } locc_train_config;
 
 /* Trainer for the handle's network; parameters start from the handle's

@@ -171,7 +171,7 @@ def network(params: np.ndarray, xyz: np.ndarray, cnt: np.ndarray,
     return y, f
 
 
-DEFAULT_LOSS_HP = (1.0, 1.0, 1.0, 0.01, 0.5)  # w_pt, w_n, w_d, huber beta, alpha
+DEFAULT_LOSS_HP = (1.0, 1.0, 1.0, 0.01, 0.5, 0.0)  # w_pt, w_n, w_d, huber beta, alpha, w_len
 
 
 def loss_grad(params: np.ndarray, xyz: np.ndarray, cnt: np.ndarray,
@@ -182,7 +182,8 @@ def loss_grad(params: np.ndarray, xyz: np.ndarray, cnt: np.ndarray,
     xyz = _c(xyz, np.float32)
     cnt = _c(cnt, np.int32)
     tgt = _c(tgt, np.float64)
-    hp = _c(hp, np.float64)
+    hp = _c(tuple(hp) + (0.0,) * (6 - len(hp)), np.float64)  # w_len defaults to 0
+    assert hp.size == 6
     g = np.empty(N_PARAMS, np.float64)
     L = lib.orb_loss_grad(_ptr(params), _ptr(xyz), _ptr(cnt), _ptr(tgt),
                           cnt.shape[0], kmax, _ptr(hp), _ptr(g))

@@ -481,13 +481,16 @@ int orb_network(const double *params, const float *xyz, const int32_t *cnt,
 /* Loss of one pair on raw canonical outputs y and pooled f:
  *   BCE(sigmoid(y0), lab)
  *   + lab * (w_pt |y[1:4] - pt|^2 + w_n (1 - cos(y[4:7], n)))
+ *   + w_len * (|y[4:7]| - 1)^2       (every pair; this library's term: keeps
+ *                                     the raw normal away from zero length)
  *   + w_d * huber_beta(y7 - depth)
  *   + alpha * mean(f^2).
- * tgt = {lab, pt.xyz, n.xyz, depth} in the canonical frame.
+ * tgt = {lab, pt.xyz, n.xyz, depth} in the canonical frame;
+ * hp = {w_pt, w_n, w_d, beta, alpha, w_len}.
  * Writes dL/dy [8] and dL/df [512]; returns the loss. */
 static double orb_pair_loss(const double *y, const double *f, const double *tgt,
                             const double *hp, double *dy, double *df) {
-  double w_pt = hp[0], w_n = hp[1], w_d = hp[2], beta = hp[3], alpha = hp[4];
+  double w_pt = hp[0], w_n = hp[1], w_d = hp[2], beta = hp[3], alpha = hp[4], w_len = hp[5];
   double lab = tgt[0];
   double z = y[0];
   /* BCE with logits: max(z,0) - z*lab + log(1 + exp(-|z|)) */
@@ -510,6 +513,13 @@ static double orb_pair_loss(const double *y, const double *f, const double *tgt,
       /* d cos / d n = t/(|n||t|) - cos * n / |n|^2 */
       for (int i = 0; i < 3; ++i)
         dy[4 + i] = -lab * w_n * (tgt[4 + i] / (nn * tn) - cs * y[4 + i] / (nn * nn));
+    }
+  }
+  if (w_len > 0) {
+    double nl = sqrt(y[4] * y[4] + y[5] * y[5] + y[6] * y[6]);
+    if (nl > 1e-12) {
+      L += w_len * (nl - 1.0) * (nl - 1.0);
+      for (int i = 0; i < 3; ++i) dy[4 + i] += w_len * 2.0 * (nl - 1.0) * y[4 + i] / nl;
     }
   }
   double e = y[7] - tgt[7];
@@ -583,7 +593,7 @@ static void orb_encode_backward(const double *P, const float *xyz, int cnt,
 }
 
 /* Mean loss over n_pairs given crops and canonical targets tgt [P][8]
- * ({label, point, normal, depth}); hp = {w_pt, w_n, w_d, beta, alpha}.
+ * ({label, point, normal, depth}); hp = {w_pt, w_n, w_d, beta, alpha, w_len}.
  * Accumulates the gradient of the mean loss into grad (zeroed here). */
 double orb_loss_grad(const double *params, const float *xyz, const int32_t *cnt,
                      const double *tgt, int n_pairs, int kmax, const double *hp,

@@ -400,11 +400,11 @@ class Trainer:
     """Owns one ``locc_trainer`` (GPU training of a Detector's network)."""
 
     def __init__(self, det: "Detector", max_batch: int, lr=1e-3, beta1=0.9, beta2=0.999,
-                 eps=1e-8, w_pt=1.0, w_n=1.0, w_d=1.0, huber_beta=0.01, alpha=0.5):
+                 eps=1e-8, w_pt=1.0, w_n=1.0, w_d=1.0, huber_beta=0.01, alpha=0.5, w_len=0.0):
         self._lib = abi.load()
         self.det = det
         self.max_batch = int(max_batch)
-        cfg = abi.TrainConfig(lr, beta1, beta2, eps, w_pt, w_n, w_d, huber_beta, alpha)
+        cfg = abi.TrainConfig(lr, beta1, beta2, eps, w_pt, w_n, w_d, huber_beta, alpha, w_len)
         self._t = ctypes.c_void_p()
         abi.check(self._lib.locc_trainer_create(det._h, self.max_batch, ctypes.byref(cfg),
                                                 ctypes.byref(self._t)))

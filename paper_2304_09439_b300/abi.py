@@ -63,7 +63,8 @@ class LoccError(RuntimeError):
 
 class TrainConfig(ctypes.Structure):
     _fields_ = [(n, ctypes.c_float) for n in
-                ("lr", "beta1", "beta2", "eps", "w_pt", "w_n", "w_d", "huber_beta", "alpha")]
+                ("lr", "beta1", "beta2", "eps", "w_pt", "w_n", "w_d", "huber_beta", "alpha",
+                 "w_len")]
 
 
 class ServerConfig(ctypes.Structure):

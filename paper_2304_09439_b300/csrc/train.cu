@@ -272,6 +272,17 @@ __global__ void loss_kernel(const float* __restrict__ Y, const float* __restrict
           g[4 + i] = -lab * cfg.w_n * (t[4 + i] / (nn * tn) - cs * y[4 + i] / (nn * nn));
       }
     }
+    // length of the raw normal (every pair): w_len (|n| - 1)^2 keeps the
+    // vector that the epilogue normalises away from zero, where rounding of
+    // the reduced-precision paths would be amplified
+    if (cfg.w_len > 0.f) {
+      const float nn = sqrtf(y[4] * y[4] + y[5] * y[5] + y[6] * y[6]);
+      if (nn > 1e-12f) {
+        const float d = nn - 1.f;
+        L += cfg.w_len * d * d;
+        for (int i = 0; i < 3; ++i) g[4 + i] += cfg.w_len * 2.f * d * y[4 + i] / nn;
+      }
+    }
     const float e = y[7] - t[7];
     if (fabsf(e) < cfg.huber_beta) {
       L += cfg.w_d * 0.5f * e * e / cfg.huber_beta;

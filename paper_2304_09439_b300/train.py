@@ -172,6 +172,8 @@ def main():
     ap.add_argument("--eval-every", type=int, default=5000)
     ap.add_argument("--val-every", type=int, default=1000)
     ap.add_argument("--seed", type=int, default=1)
+    ap.add_argument("--w-len", type=float, default=0.0,
+                    help="weight of the raw-normal length term (|n| - 1)^2 on every pair")
     ap.add_argument("--out", default=None)
     ap.add_argument("--report", default=None)
     ap.add_argument("--checkpoint", default=None,
@@ -199,7 +201,7 @@ def main():
     tests = [(p,) + load_dataset(p) for p in args.test]
     det = Detector(lib.points, lib.aabb, synth.xavier_weights(args.seed), RADIUS, "fp32")
     det.set_crop_mode(args.crop_mode)
-    tr = Trainer(det, args.batch, lr=args.lr)
+    tr = Trainer(det, args.batch, lr=args.lr, w_len=args.w_len)
     cache = {"train_lib": lib_name, "crop_mode": args.crop_mode, "blob": lambda: weights.pack(
         weights.from_flat(tr.params().cpu().numpy()))}
 

@@ -19,7 +19,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 R = 0.25
-HP = (1.0, 1.0, 1.0, 0.01, 0.5)
+HP = (1.0, 1.0, 1.0, 0.01, 0.5, 0.3)  # w_pt, w_n, w_d, huber beta, alpha, w_len
 
 
 def _dev():
@@ -94,7 +94,8 @@ def test_gradient_matches_oracle(augment):
                        None if Q is None else Q.astype(np.float64))
     L_ref, g_ref = oracle.loss_grad(params, xyz.astype(np.float32), ref["cnt"], tgt_c, HP)
     with Detector(lib.points, lib.aabb, layers, R, "fp32") as det:
-        tr = Trainer(det, 64, w_pt=HP[0], w_n=HP[1], w_d=HP[2], huber_beta=HP[3], alpha=HP[4])
+        tr = Trainer(det, 64, w_pt=HP[0], w_n=HP[1], w_d=HP[2], huber_beta=HP[3], alpha=HP[4],
+                     w_len=HP[5])
         loss = tr.step(_t(poses, dev), _t(osh, dev), _t(pairs, dev), _t(tgt, dev),
                        None if Q is None else _t(Q.reshape(-1, 9), dev), update=False)
         g = tr.grad().cpu().numpy().astype(np.float64)

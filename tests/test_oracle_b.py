@@ -215,7 +215,8 @@ def test_epilogue_maps_canonical_outputs_to_world(tiny_lib):
         np.testing.assert_allclose(r["out"][p, 7], -0.02)
 
 
-def test_backward_matches_finite_differences():
+@pytest.mark.parametrize("w_len", [0.0, 0.3])
+def test_backward_matches_finite_differences(w_len):
     rng = np.random.default_rng(5)
     W = synth.xavier_weights(7, bias_scale=0.2)
     params = oracle.flatten_params(W)
@@ -228,7 +229,7 @@ def test_backward_matches_finite_differences():
     n = rng.normal(size=(P, 3))
     tgt[:, 4:7] = n / np.linalg.norm(n, axis=1, keepdims=True)
     tgt[:, 7] = rng.normal(0, 0.05, P)
-    hp = (1.0, 1.0, 1.0, 0.5, 0.5)  # wide huber so the depth term is smooth
+    hp = (1.0, 1.0, 1.0, 0.5, 0.5, w_len)  # wide huber so the depth term is smooth
     L, g = oracle.loss_grad(params, xyz, cnt, tgt, hp)
     # probe parameters with a large gradient in every layer
     offs = np.cumsum([0] + [i * o + o for i, o in oracle.LAYER_DIMS])

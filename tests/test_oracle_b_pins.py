@@ -272,6 +272,24 @@ def test_loss_value_weights_and_huber_branch_edge():
     assert _loss(y, tgt, hp=hp) == pytest.approx(want, rel=1e-10)
 
 
+def test_loss_value_raw_normal_length_term():
+    # w_len (|n| - 1)^2 on every pair: raw normal (3, 4, 0) has length 5 ->
+    # 0.25 * 16 = 4; label 0 (the term does not depend on the label), logit
+    # 0: log 2; depth exact; the normal's direction plays no part (cos term
+    # off for label 0)
+    y = [0.0, 0.0, 0.0, 0.0, 3.0, 4.0, 0.0, 0.0]
+    tgt = [0, 0.0, 0.0, 0.0, 1.0, 0.0, 0.0, 0.0]
+    hp = (1.0, 1.0, 1.0, 0.01, 0.0, 0.25)
+    assert _loss(y, tgt, hp=hp) == pytest.approx(math.log(2.0) + 4.0, rel=1e-12)
+    # unit length: no contribution; length 0.5 with label 1 and the target
+    # along n: log(1 + e^{-2}) + 0.25 * 0.25
+    y = [2.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.5, 0.0]
+    tgt = [1, 0.0, 0.0, 0.0, 0.0, 0.0, 1.0, 0.0]
+    assert _loss(y, tgt, hp=hp) == pytest.approx(math.log1p(math.exp(-2.0)) + 0.0625, rel=1e-12)
+    y[6] = 1.0
+    assert _loss(y, tgt, hp=hp) == pytest.approx(math.log1p(math.exp(-2.0)), rel=1e-12)
+
+
 def test_loss_is_mean_over_pairs():
     y = [0.0, 0.0, 0.0, 0.0, 1.0, 0.0, 0.0, 0.0]
     xyz = np.zeros((2, 2, KMAX, 3), np.float32)
