@@ -566,6 +566,8 @@ def main():
     # list for the tensor-core encoders,) encoder, head
     per_chunk = 4 if args.precision == "fp32" else 5
     launches_per_step = 3 + per_chunk * (chunks if max(n_pairs) >= 4096 else 1)
+    if chunks == 0:  # fused crop + encoder, fallback crop, deferred-object encoder, head
+        launches_per_step = 3 + 4
 
     def step_plain(i):
         p, s, e = dsc[i % len(dsc)]

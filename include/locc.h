@@ -220,12 +220,20 @@ int locc_stage_times(locc_handle *h, float *ms_out, int n);
  * cap) so they fit beside a network CTA.  Defaults: 1 chunk, no cap.  Results
  * do not depend on these settings. */
 int locc_set_pipeline(locc_handle *h, int32_t n_chunks, int32_t crop_ctas_per_sm);
+/*   n_chunks == 0 selects instead the fused launch of the BF16 path: one
+ *   persistent kernel in which crop warps on the CUDA cores hand each
+ *   object's crop rows through shared memory to the tensor-core encoder of
+ *   the same SM (crop_ctas_per_sm is then the number of crop warps per CTA,
+ *   6 or 8); used for BF16 with local crops, the other modes run separate
+ *   kernels. */
 
 /* Autotuner: times locc_step (reps repetitions after one warm-up) for each
  * pipelining setting in {1, 2, 4, 8} chunks x {no cap, 8, 6, 4} crop CTAs per
- * SM on the given step inputs (as locc_step), keeps the fastest and writes it
- * to best_out[2] = {n_chunks, crop_ctas_per_sm} and its mean step time in ms
- * to *best_ms_out (either may be NULL).  Blocking. */
+ * SM, and for BF16 with local crops the fused launch with 6 or 8 crop warps
+ * per CTA, on the given step inputs (as locc_step), keeps the fastest and
+ * writes it to best_out[2] = {n_chunks, crop_ctas_per_sm} (n_chunks 0: the
+ * fused launch, see locc_set_pipeline) and its mean step time in ms to
+ * *best_ms_out (either may be NULL).  Blocking. */
 int locc_autotune(locc_handle *h, const float *poses, const int32_t *obj_shape,
                   int32_t n_obj, const int32_t *env_offsets, int32_t n_env,
                   int32_t *pairs_out, int32_t *n_pairs_out, int32_t max_pairs,

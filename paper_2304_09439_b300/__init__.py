@@ -92,7 +92,9 @@ class Detector:
     def autotune(self, poses, obj_shape, env_offsets, max_pairs: int, reps: int = 3,
                  pairs_out=None, n_pairs_out=None, out=None, stream=None):
         """Pick the fastest pipelining setting for these step inputs; returns
-        ((n_chunks, crop_ctas_per_sm), ms per step)."""
+        ((n_chunks, crop_ctas_per_sm), ms per step).  n_chunks 0 is the fused
+        crop + encoder launch (BF16), crop_ctas_per_sm then its crop warps per
+        CTA."""
         import numpy as np
         import torch
         dev = poses.device

@@ -87,7 +87,7 @@ int ensure_capacity(locc_handle* h, int n_pairs, cudaStream_t stream) {
       cudaMalloc(&h->d_centre, P * sizeof(float4)) != cudaSuccess ||
       cudaMalloc(&h->d_feat, P * 512 * sizeof(float)) != cudaSuccess ||
       cudaMalloc(&h->d_defer, (2 + 2 * P) * sizeof(int)) != cudaSuccess ||
-      cudaMalloc(&h->d_feat_tc, (P + 127) / 128 * 128 * 512 * 2) != cudaSuccess ||
+      cudaMalloc(&h->d_feat_tc, (P + 127) / 128 * 128 * 512 * 2 * 2) != cudaSuccess ||
       cudaMalloc(&h->d_list, 2 * P * sizeof(int)) != cudaSuccess ||
       cudaMalloc(&h->d_list_n, LOCC_MAX_CHUNKS * sizeof(int)) != cudaSuccess) {
     cudaGetLastError();
@@ -191,6 +191,34 @@ int run_path(locc_handle* h, const PairInputs& in, int n_cap, const int* n_dev, 
   const bool prof = h->profiling;
   const DevLibrary lib = dev_library(h);
   h->prof_chunks = C;
+  if (h->fused_warps > 0 && h->prec == LOCC_BF16 && h->crop_mode == LOCC_CROP_LOCAL) {
+    // one launch crops and encodes; the rare deferred objects follow (exact
+    // fallback crop, then the list-driven encoder), then the head
+    h->prof_chunks = 1;
+    const PairRange rg = whole_range(n_cap, n_dev);
+    const int defer_cap = 2 * n_cap;
+    if (prof) CUDA_TRY(cudaEventRecord(h->ev_c0[0], s));
+    {
+      NvtxRange r("crop+encoder");
+      CUDA_TRY(launch_fused(lib, in, rg, h->radius, h->d_cnt, h->d_centre, h->d_err, h->d_defer,
+                            defer_cap, h->wtc_enc, static_cast<__nv_bfloat16*>(h->d_feat_tc),
+                            h->n_sm, h->fused_warps, s));
+    }
+    if (prof) {
+      CUDA_TRY(cudaEventRecord(h->ev_c1[0], s));
+      CUDA_TRY(cudaEventRecord(h->ev_e0[0], s));
+    }
+    CUDA_TRY(launch_crop_fallback(lib, in, h->radius, h->d_xyz, h->d_cnt, h->d_defer, defer_cap,
+                                  h->n_sm, s));
+    int st = launch_encoder_list(h, h->d_xyz, rg, h->d_defer + 2, h->d_defer, 2, s);
+    if (st) return st;
+    if (prof) CUDA_TRY(cudaEventRecord(h->ev_e1[0], s));
+    NvtxRange r_net("head");
+    st = launch_head_tc(h, rg, &in, h->d_centre, out, nullptr, s);
+    if (st) return st;
+    if (prof) CUDA_TRY(cudaEventRecord(h->ev_h1[0], s));
+    return LOCC_OK;
+  }
   if (C == 1) {
     const PairRange rg = whole_range(n_cap, n_dev);
     if (prof) CUDA_TRY(cudaEventRecord(h->ev_c0[0], s));
@@ -337,6 +365,7 @@ int locc_create(const locc_shape_library* lib, const void* blob, size_t blob_byt
     if (e == cudaSuccess) e = prepare_fp32_kernels();
     if (e == cudaSuccess) e = prepare_tc_kernels();
     if (e == cudaSuccess) e = prepare_fp8_kernels();
+    if (e == cudaSuccess) e = prepare_fused_kernels();
     if (e != cudaSuccess)
       st = fail(LOCC_ERR_CUDA, "kernel set-up failed: %s", cudaGetErrorString(e));
     if (st == LOCC_OK) st = noalloc_prepare(h);
@@ -445,11 +474,20 @@ int locc_set_crop_mode(locc_handle* h, int32_t mode) {
 
 int locc_set_pipeline(locc_handle* h, int32_t n_chunks, int32_t crop_ctas_per_sm) {
   if (!h) return fail(LOCC_ERR_INVALID_ARG, "handle is NULL");
+  if (n_chunks == 0) {
+    if (crop_ctas_per_sm != 6 && crop_ctas_per_sm != 8)
+      return fail(LOCC_ERR_INVALID_ARG, "the fused launch takes 6 or 8 crop warps per CTA");
+    h->n_chunks = 1;
+    h->crop_cap = 0;
+    h->fused_warps = crop_ctas_per_sm;
+    return LOCC_OK;
+  }
   if (n_chunks < 1 || n_chunks > LOCC_MAX_CHUNKS || crop_ctas_per_sm < 0)
-    return fail(LOCC_ERR_INVALID_ARG, "n_chunks must be 1..%d, crop_ctas_per_sm >= 0",
+    return fail(LOCC_ERR_INVALID_ARG, "n_chunks must be 0..%d, crop_ctas_per_sm >= 0",
                 LOCC_MAX_CHUNKS);
   h->n_chunks = n_chunks;
   h->crop_cap = crop_ctas_per_sm;
+  h->fused_warps = 0;
   return LOCC_OK;
 }
 
@@ -459,7 +497,9 @@ int locc_autotune(locc_handle* h, const float* poses, const int32_t* obj_shape, 
                   int32_t* best_out, float* best_ms_out, void* stream) {
   if (!h || reps < 1) return fail(LOCC_ERR_INVALID_ARG, "bad argument");
   cudaStream_t s = (cudaStream_t)stream;
-  static const int kChunks[] = {1, 2, 4, 8};
+  // {0, w}: fused crop + encoder launch with w crop warps per CTA (BF16,
+  // local crops); {c, cap}: separate kernels in c chunks, cap crop CTAs per SM
+  static const int kChunks[] = {0, 1, 2, 4, 8};
   static const int kCaps[] = {0, 8, 6, 4};
   cudaEvent_t e0, e1;
   CUDA_TRY(cudaEventCreate(&e0));
@@ -467,12 +507,16 @@ int locc_autotune(locc_handle* h, const float* poses, const int32_t* obj_shape, 
   const bool prof = h->profiling;
   h->profiling = false;
   float best = 1e30f;
-  int bc = h->n_chunks, bp = h->crop_cap, st = LOCC_OK;
+  int bc = h->fused_warps ? 0 : h->n_chunks, bp = h->fused_warps ? h->fused_warps : h->crop_cap;
+  int st = LOCC_OK;
+  const bool can_fuse = h->prec == LOCC_BF16 && h->crop_mode == LOCC_CROP_LOCAL;
   for (int c : kChunks) {
     for (int cap : kCaps) {
       if (c == 1 && cap != 0) continue;
-      h->n_chunks = c;
-      h->crop_cap = cap;
+      if (c == 0 && (!can_fuse || (cap != 8 && cap != 6))) continue;
+      h->n_chunks = c == 0 ? 1 : c;
+      h->crop_cap = c == 0 ? 0 : cap;
+      h->fused_warps = c == 0 ? cap : 0;
       st = locc_step(h, poses, obj_shape, n_obj, env_offsets, n_env, pairs_out, n_pairs_out,
                      max_pairs, out, stream);  // warm-up
       if (st) break;
@@ -495,8 +539,9 @@ int locc_autotune(locc_handle* h, const float* poses, const int32_t* obj_shape, 
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   h->profiling = prof;
-  h->n_chunks = bc;
-  h->crop_cap = bp;
+  h->n_chunks = bc == 0 ? 1 : bc;
+  h->crop_cap = bc == 0 ? 0 : bp;
+  h->fused_warps = bc == 0 ? bp : 0;
   if (st) return st;
   if (best_out) best_out[0] = bc, best_out[1] = bp;
   if (best_ms_out) *best_ms_out = best;

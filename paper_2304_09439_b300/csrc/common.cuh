@@ -160,6 +160,12 @@ cudaError_t launch_crop(const DevLibrary& lib, const PairInputs& in, const PairR
 // handle's device current: loads their modules (so that no later launch
 // loads one) and records the crop kernel's occupancy for that device.
 cudaError_t prepare_crop_kernels(int device);
+// Exact crop of the objects listed in defer (defer[0] = count, defer[2 + i] =
+// 2 p + object) into xyz / cnt; a fixed grid that reads the count on the
+// device (does nothing when no object was deferred).
+cudaError_t launch_crop_fallback(const DevLibrary& lib, const PairInputs& in, float r, float4* xyz,
+                                 int32_t* cnt, int* defer, int defer_cap, int n_sm,
+                                 cudaStream_t stream);
 // Sets the dynamic shared-memory limits of the float32 network kernels.
 cudaError_t prepare_fp32_kernels();
 cudaError_t launch_encoder_fp32(const float4* xyz, const PairRange& rg,

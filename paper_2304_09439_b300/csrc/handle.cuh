@@ -37,7 +37,7 @@ struct locc_handle {
   float4* d_centre = nullptr;
   float* d_feat = nullptr;
   int* d_defer = nullptr;  // crop objects left to the exact fallback kernel
-  void* d_feat_tc = nullptr;  // bf16 pooled features in the head's operand tiles
+  void* d_feat_tc = nullptr;  // pooled features in the head's operand tiles (bf16 hi/lo or e4m3)
   int* d_list = nullptr;      // [2 cap_pairs] objects with non-empty crops (tensor-core encoders)
   int* d_list_n = nullptr;    // [LOCC_MAX_CHUNKS] list length per pipeline chunk
   int* d_err = nullptr;
@@ -53,6 +53,9 @@ struct locc_handle {
   // that they fit beside a network CTA
   int n_chunks = 1;
   int crop_cap = 0;
+  // BF16: crop gather and encoder in one fused launch with this many crop
+  // warps per CTA (0 = separate kernels)
+  int fused_warps = 0;
   cudaStream_t aux = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   cudaEvent_t ev_crop[LOCC_MAX_CHUNKS] = {};
@@ -97,8 +100,21 @@ cudaError_t prepare_tc_kernels();
 // Zeroes the pooled features of the objects of `rg` whose crop is empty and
 // lists the others for the tensor-core encoders (h->d_list, h->d_list_n).
 cudaError_t launch_enc_list(locc_handle* h, const float4* xyz, const PairRange& rg, float* feat,
-                            void* ftile, int chunks_per_side, cudaStream_t stream);
+                            void* ftile, int e4m3, cudaStream_t stream);
 cudaError_t prepare_fp8_kernels();
+// BF16 head over the pairs of rg from the pooled features in h->d_feat_tc.
+int launch_head_tc(locc_handle* h, const PairRange& rg, const PairInputs* in, const float4* centre,
+                   float* out, float* y_raw, cudaStream_t stream);
+// BF16 encoder over a device list of objects (2 p + side; list_n[rg.chunk]
+// entries at list + 2 lo) on `grid` CTAs, rows from xyz.
+int launch_encoder_list(locc_handle* h, const float4* xyz, const PairRange& rg, const int* list,
+                        const int* list_n, int grid, cudaStream_t stream);
+// Fused crop + BF16 encoder (fused.cu), crop_warps 6 or 8 per CTA.
+cudaError_t prepare_fused_kernels();
+cudaError_t launch_fused(const DevLibrary& lib, const PairInputs& in, const PairRange& rg, float r,
+                         int32_t* cnt, float4* centre, int* err, int* defer, int defer_cap,
+                         const unsigned char* img, __nv_bfloat16* ftile, int n_sm, int crop_warps,
+                         cudaStream_t s);
 // Resolves h->noalloc_scratch on the current device (the handle's).
 int noalloc_prepare(locc_handle* h);
 int run_network_fp8(locc_handle* h, const float4* xyz, const PairRange& rg, const PairInputs* in,

@@ -881,7 +881,7 @@ int run_network_fp8(locc_handle* h, const float4* xyz, const PairRange& rg, cons
                     cudaStream_t stream, cudaEvent_t mid) {
   const int n_pairs = (rg.n_cap + rg.n_chunks - 1) / rg.n_chunks + 1;  // pairs of one chunk, at most
   unsigned char* ftile = static_cast<unsigned char*>(h->d_feat_tc);
-  if (launch_enc_list(h, xyz, rg, feat_out, ftile, 4, stream) != cudaSuccess) {
+  if (launch_enc_list(h, xyz, rg, feat_out, ftile, 1, stream) != cudaSuccess) {
     set_error("enc_list_kernel launch failed");
     return LOCC_ERR_CUDA;
   }

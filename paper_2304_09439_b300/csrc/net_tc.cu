@@ -40,35 +40,15 @@
 #include <cstring>
 #include <vector>
 
+#include "enc_tc.cuh"
 #include "handle.cuh"
-#include "tc_ptx.cuh"
 
 namespace locc {
 namespace {
 
 using namespace tc;
 
-constexpr long long WAIT_CYCLES = 2000000000LL;  // ~1 s at 2 GHz
-
 // ----------------------------------------------------------------- encoder
-// The biases of layers 1 and 2 are added by the MMAs themselves (the
-// epilogues then only apply ReLU, round and store, which more than halves
-// their instruction count): layer 1 through two constant-one columns of the X
-// tile against b1 (hi, lo) in W1's spare K columns; layer 2 through one extra
-// K = 16 step, issued first so that it also initialises the accumulator: a
-// tile of ones (columns 0, 1) against a tile holding b2 (hi, lo) in its K
-// columns 0, 1.  The bias tile stores only the first core matrix of each
-// 8-row group (K columns 0..7, SBO 128); its second core matrix (K 8..15)
-// reads the ones tile through LBO = 2048, finite values that meet the ones
-// tile's zero columns.
-constexpr int E_W1 = 0;                       // [64 x 16]   2 KB
-constexpr int E_W2 = E_W1 + 64 * 16 * 2;      // [128 x 64] 16 KB
-constexpr int E_W3 = E_W2 + 128 * 64 * 2;     // [256 x 128] 64 KB
-constexpr int E_B2T = E_W3 + 256 * 128 * 2;   // [128 x 8] b2 (hi, lo), 2 KB
-constexpr int E_ONE = E_B2T + 128 * 8 * 2;    // [128 x 16] ones in columns 0, 1, 4 KB
-constexpr int E_BIAS = E_ONE + 128 * 16 * 2;  // b1 64, b2 128, b3 256 (f32)
-constexpr int E_IMG_BYTES = E_BIAS + (64 + 128 + 256) * 4;
-static_assert(E_IMG_BYTES % 16 == 0, "image must be a whole number of 16-byte chunks");
 // NSLOT pair slots.  Each slot: raw crop rows (f32, 2 KB) and one 32 KB
 // operand region that holds, in turn, the X tile (4 KB), H1 (16 KB) and H2
 // (32 KB): each is dead once the MMA that reads it has completed, which the
@@ -97,53 +77,6 @@ constexpr int B_FULLX = 0, B_XRDY = NSLOT, B_H1RDY = 2 * NSLOT, B_H2RDY = 3 * NS
               B_E3A = 4 * NSLOT, B_D1 = 5 * NSLOT, B_D2 = 6 * NSLOT, B_D3A = 7 * NSLOT,
               B_D3B = 8 * NSLOT, B_W = 9 * NSLOT, B_DRAIN = 9 * NSLOT + 1;
 
-// Epilogue of layers 1 and 2: TMEM row (bias already accumulated) -> relu ->
-// bf16 row of the next A operand (K = NCOL).
-template <int NCOL>
-__device__ __forceinline__ void enc_epi_rows(uint32_t taddr, unsigned char* dst, int row) {
-  float v[64];
-#pragma unroll 1
-  for (int h = 0; h < NCOL / 64; ++h) {
-    tmem_ld32x2(taddr + 64 * h, v);  // 64 columns, two loads in flight
-#pragma unroll
-    for (int c = 0; c < 8; ++c) {
-      uint4 w;
-      const int j = 8 * c, o = 64 * h + j;
-      w.x = pack_relu_bf16(v[j + 0], v[j + 1]);
-      w.y = pack_relu_bf16(v[j + 2], v[j + 3]);
-      w.z = pack_relu_bf16(v[j + 4], v[j + 5]);
-      w.w = pack_relu_bf16(v[j + 6], v[j + 7]);
-      *reinterpret_cast<uint4*>(dst + kmajor_off(row, o, NCOL)) = w;
-    }
-  }
-}
-
-// Masked max over the valid points of each object of one layer-3 half
-// (thread = channel): TMEM columns [0, 64) are A's points, [64, 128) B's.
-__device__ __forceinline__ void enc_pool(uint32_t taddr, int cntA, int cntB, float* mA, float* mB) {
-  float v[32];
-  float a = -INFINITY, b = -INFINITY;
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const int cnt = q < 2 ? cntA : cntB;
-    const int c0 = 32 * (q & 1);  // first point slot of this chunk within its object
-    if (c0 < cnt) {
-      float m = -INFINITY;
-      if (c0 + 32 <= cnt) {
-        m = tmem_ldmax32(taddr + 32 * q);  // whole chunk valid: max in the load
-      } else {
-        tmem_ld32(taddr + 32 * q, v);
-#pragma unroll
-        for (int jj = 0; jj < 32; ++jj) m = fmaxf(m, (c0 + jj < cnt) ? v[jj] : -INFINITY);
-      }
-      if (q < 2) a = fmaxf(a, m);
-      else b = fmaxf(b, m);
-    }
-  }
-  *mA = a;
-  *mB = b;
-}
-
 // ------------------------------------------------------------- object list
 // The tensor-core encoders work on the objects whose crop is not empty, two
 // objects (2 x 64 crop rows) per M = 128 tile.  An empty crop pools to
@@ -155,18 +88,17 @@ __device__ __forceinline__ void enc_pool(uint32_t taddr, int cntA, int cntB, flo
 // which the caller has zeroed.  The valid points of an object come first in
 // its 64 rows (the crop writes them that way), so row 0 decides.
 // Zero features: float32 [P][512] when feat is given, and the head's operand
-// tiles (K-chunks of 8 KB, chunks_per_side per object: 8 of 32 bf16 or 4 of
-// 64 e4m3; both put one row's 16-byte pieces at (r / 8) 512 + q 128 +
-// (r % 8) 16, q = 0..3).
+// tiles: bf16 (e4m3 == 0) as hi / lo K = 16 chunks (feat_piece_off), or
+// e4m3 (e4m3 == 1) as 4 K-chunks of 64 per object, one row's 16-byte pieces
+// at (r / 8) 512 + q 128 + (r % 8) 16, q = 0..3.
 __global__ void __launch_bounds__(256)
     enc_list_kernel(const float4* __restrict__ xyz, PairRange rg, int* __restrict__ list,
                     int* __restrict__ list_n, float* __restrict__ feat,
-                    unsigned char* __restrict__ ftile, int chunks_per_side) {
+                    unsigned char* __restrict__ ftile, int e4m3) {
   int lo, hi;
   range_bounds(rg, &lo, &hi);
   const int n_obj = 2 * (hi - lo), lane = threadIdx.x & 31;
   int* lst = list + 2 * (size_t)lo;
-  const size_t tile_bytes = (size_t)2 * chunks_per_side * 8192;
   for (int base = blockIdx.x * blockDim.x; base < n_obj; base += gridDim.x * blockDim.x) {
     const int i = base + (int)threadIdx.x;
     bool live = false;
@@ -178,12 +110,18 @@ __global__ void __launch_bounds__(256)
     if (live) lst[b0 + __popc(m & ((1u << lane) - 1u))] = 2 * lo + i;
     if (i < n_obj && !live) {
       const int rel = i >> 1, side = i & 1, r = rel & 127;
-      unsigned char* t = ftile + (size_t)(rel >> 7) * tile_bytes +
-                         (size_t)side * chunks_per_side * 8192 + (r >> 3) * 512 + (r & 7) * 16;
-      for (int c = 0; c < chunks_per_side; ++c)
+      if (e4m3) {
+        unsigned char* t = ftile + (size_t)(rel >> 7) * (128 * 512) + (size_t)side * 4 * 8192 +
+                           (r >> 3) * 512 + (r & 7) * 16;
+        for (int c = 0; c < 4; ++c)
 #pragma unroll
-        for (int q = 0; q < 4; ++q)
-          *reinterpret_cast<uint4*>(t + c * 8192 + q * 128) = make_uint4(0u, 0u, 0u, 0u);
+          for (int q = 0; q < 4; ++q)
+            *reinterpret_cast<uint4*>(t + c * 8192 + q * 128) = make_uint4(0u, 0u, 0u, 0u);
+      } else {
+        unsigned char* t = ftile + (size_t)(rel >> 7) * FT_TILE;
+        for (int q = 0; q < 64; ++q)
+          *reinterpret_cast<uint4*>(t + feat_piece_off(r, side, q)) = make_uint4(0u, 0u, 0u, 0u);
+      }
       if (feat) {
         float4* f = reinterpret_cast<float4*>(feat + (size_t)(lo + rel) * 512 + side * 256);
 #pragma unroll 4
@@ -191,19 +129,6 @@ __global__ void __launch_bounds__(256)
       }
     }
   }
-}
-
-// Pooled feature k of pair p (rel = p - first pair of the launch): float32
-// [P][512] when feat is given (the network's feature output), and always
-// bf16 in the head's operand layout -- tiles of 128 pairs, each 16 K-chunks
-// of 32 features in the K-major core-matrix layout (8 KB per chunk) -- so that
-// the head loads A chunks with bulk copies.
-__device__ __forceinline__ void put_feat(float* feat, __nv_bfloat16* ftile, int p, int rel, int k,
-                                         float v) {
-  if (feat) feat[(size_t)p * 512 + k] = v;
-  unsigned char* t = reinterpret_cast<unsigned char*>(ftile) + (size_t)(rel >> 7) * (128 * 512 * 2) +
-                     (size_t)(k >> 5) * (128 * 32 * 2);
-  *reinterpret_cast<__nv_bfloat16*>(t + kmajor_off(rel & 127, k & 31, 32)) = __float2bfloat16_rn(v);
 }
 
 // Tiles: the launch's list of objects with non-empty crops (enc_list_kernel),
@@ -369,19 +294,7 @@ __global__ void __launch_bounds__(E_THREADS, 1)
       if (row >= KMAX && nv < 0) q = make_float4(0.f, 0.f, 0.f, 0.f);
       const unsigned m = __ballot_sync(0xffffffffu, q.w > 0.5f);
       if (lane == 0) cnt_s[wq] = __popc(m);
-      const __nv_bfloat16 xh = __float2bfloat16_rn(q.x), yh = __float2bfloat16_rn(q.y),
-                          zh = __float2bfloat16_rn(q.z);
-      const float fx = __bfloat162float(xh), fy = __bfloat162float(yh), fz = __bfloat162float(zh);
-      uint4 c0, c1;
-      c0.x = pack_bf16(fx, fy);
-      c0.y = pack_bf16(fz, q.x - fx);
-      c0.z = pack_bf16(q.y - fy, q.z - fz);
-      c0.w = pack_bf16(fx, fy);
-      c1.x = pack_bf16(fz, 1.f);  // K columns 9, 10: ones against b1 (hi, lo)
-      c1.y = pack_bf16(1.f, 0.f);
-      c1.z = c1.w = 0u;
-      *reinterpret_cast<uint4*>(opd + kmajor_off(row, 0, 16)) = c0;
-      *reinterpret_cast<uint4*>(opd + kmajor_off(row, 8, 16)) = c1;
+      x_tile_row(q, opd, row);
       fence_async_smem();
       return true;
     };
@@ -487,16 +400,25 @@ __global__ void __launch_bounds__(E_THREADS, 1)
 }
 
 // -------------------------------------------------------------------- head
-constexpr int HT = 128;                                   // pairs per tile
-constexpr int H_W3 = 0;                                    // [16 x 256] 8 KB
-constexpr int H_BIAS = H_W3 + 16 * 256 * 2;                // hb1 256, hb2 256, hb3 16
+// Layer 1 and layer 3 run in split precision: the features arrive as bf16
+// hi / lo pairs (FT_*), W_h1 and W_h3 are stored as bf16 hi / lo pairs, and
+// D = A_hi W_hi + A_lo W_hi + A_hi W_lo (layer 3: G W_hi + G W_lo); the
+// dropped A_lo W_lo term is ~2^-16 relative.  Layer 2 keeps plain bf16.
+constexpr int HT = 128;                                    // pairs per tile
+constexpr int H_W3 = 0;                                    // [16 x 256] hi 8 KB, lo 8 KB
+constexpr int H_W3LO = 16 * 256 * 2;
+constexpr int H_BIAS = H_W3 + 2 * 16 * 256 * 2;            // hb1 256, hb2 256, hb3 16
 constexpr int H_RES_BYTES = H_BIAS + (256 + 256 + 16) * 4; // resident part of the image
-constexpr int HK = 32;                                     // K of one streamed chunk
-constexpr int H_CHUNK = 256 * HK * 2;                      // bytes of one B chunk [256 x 32]
-constexpr int H_ACHUNK = 128 * HK * 2;                     // bytes of one A (feature) chunk
+constexpr int HK1 = FT_K;                                  // K of one layer-1 chunk (hi + lo)
+constexpr int HK2 = 32;                                    // K of one layer-2 chunk
+constexpr int H_CHUNK = 16384;                             // one B chunk: [256 x 16] hi + lo,
+                                                           // or [256 x 32]
+constexpr int H_BSUB = 256 * HK1 * 2;                      // offset of the lo B tile
+constexpr int H_ACHUNK = FT_CHUNK;                         // one A chunk: [128 x 16] hi + lo
+static_assert(2 * H_BSUB == H_CHUNK && 256 * HK2 * 2 == H_CHUNK, "chunk sizes");
 constexpr int H_NST = 6;                                   // operand stages
-constexpr int H_L1C = 512 / HK, H_NCH = H_L1C + 256 / HK;  // chunks per tile: 16 + 8
-constexpr int H_A0 = (H_RES_BYTES + 1023) / 1024 * 1024;   // A stages [128 x 32] 8 KB each
+constexpr int H_L1C = 512 / HK1, H_NCH = H_L1C + 256 / HK2;  // chunks per tile: 32 + 8
+constexpr int H_A0 = (H_RES_BYTES + 127) / 128 * 128;      // A stages 8 KB each
 constexpr int H_B0 = H_A0 + H_NST * H_ACHUNK;              // B stages [256 x 32] 16 KB each
 constexpr int H_G = H_B0 + H_NST * H_CHUNK;                // G [128 x 256] 64 KB
 constexpr int H_CTRL = H_G + 128 * 256 * 2;                // mbarriers, TMEM address, abort
@@ -632,7 +554,7 @@ __global__ void __launch_bounds__(H_THREADS, 1)
       if (c < H_L1C) {
         mbar_expect_tx(bf, H_ACHUNK + H_CHUNK);
         bulk_g2s(smem_u32(smem + H_A0 + st * H_ACHUNK),
-                 reinterpret_cast<const unsigned char*>(ftile) + (size_t)tile * (128 * 512 * 2) +
+                 reinterpret_cast<const unsigned char*>(ftile) + (size_t)tile * FT_TILE +
                      (size_t)c * H_ACHUNK,
                  H_ACHUNK, bf);
         bulk_g2s(smem_u32(smem + H_B0 + st * H_CHUNK), img + H_IMG_W1 + (size_t)c * H_CHUNK,
@@ -656,6 +578,10 @@ __global__ void __launch_bounds__(H_THREADS, 1)
         for (int kk = 0; kk < 16; ++kk)
           mma_bf16(tbase + 256, sdesc(sG + 256 * kk, 128, 4096), sdesc(sW3 + 256 * kk, 128, 4096),
                    idesc_bf16(128, 16), kk > 0);
+#pragma unroll
+        for (int kk = 0; kk < 16; ++kk)
+          mma_bf16(tbase + 256, sdesc(sG + 256 * kk, 128, 4096),
+                   sdesc(sW3 + H_W3LO + 256 * kk, 128, 4096), idesc_bf16(128, 16), 1u);
         mma_commit(B_L3);
       }
       __syncwarp();
@@ -696,15 +622,29 @@ __global__ void __launch_bounds__(H_THREADS, 1)
       const uint32_t sB1 = smem_u32(smem + H_B0 + st1 * H_CHUNK);
       const uint32_t sA0 = l1 ? smem_u32(smem + H_A0 + st0 * H_ACHUNK) : sG + 512 * j;
       const uint32_t sA1 = l1 ? smem_u32(smem + H_A0 + st1 * H_ACHUNK) : sG + 512 * (j + 1);
-      const uint32_t dcol = l1 ? 0u : 256u, sbo = l1 ? 512u : 4096u;
+      // (layer 2: chunk j of G is K columns [32 j, 32 j + 32), 512 bytes per K = 32 step)
       const uint32_t acc0 = (l1 ? c : j) > 0 ? 1u : 0u;
+      const uint32_t id = idesc_bf16(128, 256);
       if (elect_one()) {
-        mma_bf16(tbase + dcol, sdesc(sA0, 128, sbo), sdesc(sB0, 128, 512), idesc_bf16(128, 256), acc0);
-        mma_bf16(tbase + dcol, sdesc(sA0 + 256, 128, sbo), sdesc(sB0 + 256, 128, 512), idesc_bf16(128, 256), 1u);
-        mma_commit(B_DONE + 8 * st0);
-        mma_bf16(tbase + dcol, sdesc(sA1, 128, sbo), sdesc(sB1, 128, 512), idesc_bf16(128, 256), 1u);
-        mma_bf16(tbase + dcol, sdesc(sA1 + 256, 128, sbo), sdesc(sB1 + 256, 128, 512), idesc_bf16(128, 256), 1u);
-        mma_commit(B_DONE + 8 * st1);
+        if (l1) {
+          // [128 x 16] A and [256 x 16] B tiles (sbo 256): A_hi B_hi, A_lo B_hi, A_hi B_lo
+          mma_bf16(tbase, sdesc(sA0, 128, 256), sdesc(sB0, 128, 256), id, acc0);
+          mma_bf16(tbase, sdesc(sA0 + FT_SUB, 128, 256), sdesc(sB0, 128, 256), id, 1u);
+          mma_bf16(tbase, sdesc(sA0, 128, 256), sdesc(sB0 + H_BSUB, 128, 256), id, 1u);
+          mma_commit(B_DONE + 8 * st0);
+          mma_bf16(tbase, sdesc(sA1, 128, 256), sdesc(sB1, 128, 256), id, 1u);
+          mma_bf16(tbase, sdesc(sA1 + FT_SUB, 128, 256), sdesc(sB1, 128, 256), id, 1u);
+          mma_bf16(tbase, sdesc(sA1, 128, 256), sdesc(sB1 + H_BSUB, 128, 256), id, 1u);
+          mma_commit(B_DONE + 8 * st1);
+        } else {
+          // G (K = 256, sbo 4096) against [256 x 32] B chunks (sbo 512), two K = 16 steps each
+          mma_bf16(tbase + 256, sdesc(sA0, 128, 4096), sdesc(sB0, 128, 512), id, acc0);
+          mma_bf16(tbase + 256, sdesc(sA0 + 256, 128, 4096), sdesc(sB0 + 256, 128, 512), id, 1u);
+          mma_commit(B_DONE + 8 * st0);
+          mma_bf16(tbase + 256, sdesc(sA1, 128, 4096), sdesc(sB1, 128, 512), id, 1u);
+          mma_bf16(tbase + 256, sdesc(sA1 + 256, 128, 4096), sdesc(sB1 + 256, 128, 512), id, 1u);
+          mma_commit(B_DONE + 8 * st1);
+        }
         if (c + 1 == H_L1C - 1) mma_commit(B_L1D);
         if (c + 1 == H_NCH - 1) mma_commit(B_L2D);
       }
@@ -902,16 +842,24 @@ int upload_tc_params(locc_handle* h, const std::vector<float>& params) {
   std::memcpy(e + E_BIAS + 64 * 4, &params[offb[1]], 128 * 4);
   std::memcpy(e + E_BIAS + 192 * 4, &params[offb[2]], 256 * 4);
   unsigned char* hd = img.data() + enc_bytes;
+  auto hi_of = [&](float w) { return bf16_value(bf16_bits(w)); };
   put_tile(hd + H_W3, 16, 256, [&](int c, int k) { return c < 8 ? W(5, c, k) : 0.f; });
+  put_tile(hd + H_W3LO, 16, 256,
+           [&](int c, int k) { return c < 8 ? W(5, c, k) - hi_of(W(5, c, k)) : 0.f; });
   std::memcpy(hd + H_BIAS, &params[offb[3]], 256 * 4);
   std::memcpy(hd + H_BIAS + 256 * 4, &params[offb[4]], 256 * 4);
   std::memcpy(hd + H_BIAS + 512 * 4, &params[offb[5]], 8 * 4);
-  for (int kc = 0; kc < H_L1C; ++kc)
-    put_tile(hd + H_IMG_W1 + (size_t)kc * H_CHUNK, 256, HK,
-             [&](int c, int k) { return W(3, c, HK * kc + k); });
+  for (int kc = 0; kc < H_L1C; ++kc) {
+    put_tile(hd + H_IMG_W1 + (size_t)kc * H_CHUNK, 256, HK1,
+             [&](int c, int k) { return W(3, c, HK1 * kc + k); });
+    put_tile(hd + H_IMG_W1 + (size_t)kc * H_CHUNK + H_BSUB, 256, HK1, [&](int c, int k) {
+      const float w = W(3, c, HK1 * kc + k);
+      return w - hi_of(w);
+    });
+  }
   for (int kc = 0; kc < H_NCH - H_L1C; ++kc)
-    put_tile(hd + H_IMG_W2 + (size_t)kc * H_CHUNK, 256, HK,
-             [&](int c, int k) { return W(4, c, HK * kc + k); });
+    put_tile(hd + H_IMG_W2 + (size_t)kc * H_CHUNK, 256, HK2,
+             [&](int c, int k) { return W(4, c, HK2 * kc + k); });
   if (cudaMalloc(&h->d_wtc, total) != cudaSuccess ||
       cudaMemcpy(h->d_wtc, img.data(), total, cudaMemcpyHostToDevice) != cudaSuccess) {
     cudaGetLastError();
@@ -925,13 +873,13 @@ int upload_tc_params(locc_handle* h, const std::vector<float>& params) {
 }
 
 cudaError_t launch_enc_list(locc_handle* h, const float4* xyz, const PairRange& rg, float* feat,
-                            void* ftile, int chunks_per_side, cudaStream_t stream) {
+                            void* ftile, int e4m3, cudaStream_t stream) {
   cudaError_t e = cudaMemsetAsync(h->d_list_n + rg.chunk, 0, sizeof(int), stream);
   if (e != cudaSuccess) return e;
   const int n_obj = 2 * ((rg.n_cap + rg.n_chunks - 1) / rg.n_chunks + 1);
   const int grid = std::max(1, std::min((n_obj + 255) / 256, 8 * h->n_sm));
   enc_list_kernel<<<grid, 256, 0, stream>>>(xyz, rg, h->d_list, h->d_list_n, feat,
-                                            static_cast<unsigned char*>(ftile), chunks_per_side);
+                                            static_cast<unsigned char*>(ftile), e4m3);
   return cudaGetLastError();
 }
 
@@ -950,7 +898,7 @@ int run_network_tc(locc_handle* h, const float4* xyz, const PairRange& rg, const
     return run_network_fp8(h, xyz, rg, in, centre, out, y_raw, feat_out, stream, mid);
   const int n_pairs = (rg.n_cap + rg.n_chunks - 1) / rg.n_chunks + 1;  // pairs of one chunk, at most
   __nv_bfloat16* ftile = static_cast<__nv_bfloat16*>(h->d_feat_tc);
-  if (launch_enc_list(h, xyz, rg, feat_out, ftile, 8, stream) != cudaSuccess) {
+  if (launch_enc_list(h, xyz, rg, feat_out, ftile, 0, stream) != cudaSuccess) {
     set_error("enc_list_kernel launch failed");
     return LOCC_ERR_CUDA;
   }
@@ -962,13 +910,32 @@ int run_network_tc(locc_handle* h, const float4* xyz, const PairRange& rg, const
     return LOCC_ERR_CUDA;
   }
   if (mid && cudaEventRecord(mid, stream) != cudaSuccess) return LOCC_ERR_CUDA;
+  return launch_head_tc(h, rg, in, centre, out, y_raw, stream);
+}
+
+int launch_head_tc(locc_handle* h, const PairRange& rg, const PairInputs* in, const float4* centre,
+                   float* out, float* y_raw, cudaStream_t stream) {
+  const int n_pairs = (rg.n_cap + rg.n_chunks - 1) / rg.n_chunks + 1;  // pairs of one chunk, at most
   PairInputs pin{};
   if (in) pin = *in;
   const int grid_h = std::min((n_pairs + HT - 1) / HT, h->n_sm);
-  head_tc_kernel<<<grid_h, H_THREADS, H_SMEM, stream>>>(ftile, rg, h->wtc_head, pin, in != nullptr,
-                                                        centre, out, y_raw, h->d_err);
+  head_tc_kernel<<<grid_h, H_THREADS, H_SMEM, stream>>>(static_cast<__nv_bfloat16*>(h->d_feat_tc),
+                                                        rg, h->wtc_head, pin, in != nullptr, centre,
+                                                        out, y_raw, h->d_err);
   if (cudaGetLastError() != cudaSuccess) {
     set_error("head_tc_kernel launch failed");
+    return LOCC_ERR_CUDA;
+  }
+  return LOCC_OK;
+}
+
+int launch_encoder_list(locc_handle* h, const float4* xyz, const PairRange& rg, const int* list,
+                        const int* list_n, int grid, cudaStream_t stream) {
+  encoder_tc_kernel<<<grid, E_THREADS, E_SMEM, stream>>>(
+      xyz, rg, list, list_n, h->wtc_enc, nullptr, static_cast<__nv_bfloat16*>(h->d_feat_tc),
+      h->d_err);
+  if (cudaGetLastError() != cudaSuccess) {
+    set_error("encoder_tc_kernel launch failed");
     return LOCC_ERR_CUDA;
   }
   return LOCC_OK;
