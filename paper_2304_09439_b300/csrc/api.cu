@@ -156,7 +156,7 @@ DevLibrary dev_library(const locc_handle* h) {
 // Network on the crops in h->d_xyz (or `xyz`): feat -> y / out.
 int run_network(locc_handle* h, const float4* xyz, const PairRange& rg, const PairInputs* in,
                 const float4* centre, float* out, float* y_raw, float* feat_out,
-                cudaStream_t stream, cudaEvent_t mid) {
+                cudaStream_t stream, cudaEvent_t mid, int list_mode) {
   float* feat = feat_out ? feat_out : h->d_feat;
   switch (h->prec) {
     case LOCC_FP32:
@@ -165,7 +165,7 @@ int run_network(locc_handle* h, const float4* xyz, const PairRange& rg, const Pa
       CUDA_TRY(launch_head_fp32(feat, rg, h->fp32, in, centre, out, y_raw, h->n_sm, stream));
       return LOCC_OK;
     default:
-      return run_network_tc(h, xyz, rg, in, centre, out, y_raw, feat_out, stream, mid);
+      return run_network_tc(h, xyz, rg, in, centre, out, y_raw, feat_out, stream, mid, list_mode);
   }
 }
 
@@ -219,13 +219,21 @@ int run_path(locc_handle* h, const PairInputs& in, int n_cap, const int* n_dev, 
     if (prof) CUDA_TRY(cudaEventRecord(h->ev_h1[0], s));
     return LOCC_OK;
   }
+  // the tensor-core encoders take the list of objects with non-empty crops:
+  // local crops list them as they go, global crops through the list kernel.
+  // The heads zero the rows of empty objects from the crop counts.
+  const bool list_in_crop = h->prec != LOCC_FP32 && h->crop_mode == LOCC_CROP_LOCAL;
+  int* list = list_in_crop ? h->d_list : nullptr;
+  int* list_n = list_in_crop ? h->d_list_n : nullptr;
+  const int list_mode = list_in_crop ? LIST_FROM_CROP : LIST_FROM_ROWS;
   if (C == 1) {
     const PairRange rg = whole_range(n_cap, n_dev);
     if (prof) CUDA_TRY(cudaEventRecord(h->ev_c0[0], s));
     {
       NvtxRange r("crop");
       CUDA_TRY(launch_crop(lib, in, rg, h->radius, h->d_xyz, nullptr, h->d_cnt, h->d_centre,
-                           h->d_err, h->d_defer, h->n_sm, h->crop_cap, s, h->crop_mode));
+                           h->d_err, h->d_defer, h->n_sm, h->crop_cap, s, h->crop_mode, list,
+                           list_n));
     }
     if (prof) {
       CUDA_TRY(cudaEventRecord(h->ev_c1[0], s));
@@ -233,7 +241,7 @@ int run_path(locc_handle* h, const PairInputs& in, int n_cap, const int* n_dev, 
     }
     NvtxRange r_net("network");
     const int st = run_network(h, h->d_xyz, rg, &in, h->d_centre, out, nullptr, nullptr, s,
-                               prof ? h->ev_e1[0] : nullptr);
+                               prof ? h->ev_e1[0] : nullptr, list_mode);
     if (st) return st;
     if (prof) CUDA_TRY(cudaEventRecord(h->ev_h1[0], s));
     return LOCC_OK;
@@ -246,14 +254,13 @@ int run_path(locc_handle* h, const PairInputs& in, int n_cap, const int* n_dev, 
     const PairRange rg{n_cap, n_dev, i, C};
     if (prof) CUDA_TRY(cudaEventRecord(h->ev_c0[i], s));
     CUDA_TRY(launch_crop(lib, in, rg, h->radius, h->d_xyz, nullptr, h->d_cnt, h->d_centre, h->d_err,
-                         h->d_defer,
-                         h->n_sm, h->crop_cap, s, h->crop_mode));
+                         h->d_defer, h->n_sm, h->crop_cap, s, h->crop_mode, list, list_n));
     if (prof) CUDA_TRY(cudaEventRecord(h->ev_c1[i], s));
     CUDA_TRY(cudaEventRecord(h->ev_crop[i], s));
     CUDA_TRY(cudaStreamWaitEvent(h->aux, h->ev_crop[i], 0));
     if (prof) CUDA_TRY(cudaEventRecord(h->ev_e0[i], h->aux));
     st = run_network(h, h->d_xyz, rg, &in, h->d_centre, out, nullptr, nullptr, h->aux,
-                     prof ? h->ev_e1[i] : nullptr);
+                     prof ? h->ev_e1[i] : nullptr, list_mode);
     if (st) return st;
     if (prof) CUDA_TRY(cudaEventRecord(h->ev_h1[i], h->aux));
   }
@@ -636,7 +643,8 @@ int locc_network(locc_handle* h, const float* xyz, int32_t n_pairs, float* y_out
   int st = ensure_capacity(h, n_pairs, s);
   if (st) return st;
   return run_network(h, reinterpret_cast<const float4*>(xyz), whole_range(n_pairs, nullptr),
-                     nullptr, nullptr, nullptr, y_out, feat_out, s, nullptr);
+                     nullptr, nullptr, nullptr, y_out, feat_out, s, nullptr,
+                     LIST_AND_COUNTS_FROM_ROWS);
 }
 
 int locc_detect(locc_handle* h, const float* poses, const int32_t* obj_shape, int32_t n_obj,

@@ -67,6 +67,41 @@ __device__ __forceinline__ void range_bounds(const PairRange& r, int* lo, int* h
   *hi = (int)(((long long)n * (r.chunk + 1)) / r.n_chunks);
 }
 
+// Pooled-feature operand tiles of the tensor-core heads, per 128 pairs:
+// BF16: 32 K-chunks of 16 features, each a [128 x 16] bf16 hi tile and a lo
+// tile FT_SUB bytes further (K-major, no swizzle); FP8: 8 K-chunks of 64
+// e4m3 features of 8 KB each.
+constexpr int FT_K = 16;                         // features per BF16 chunk
+constexpr int FT_SUB = 128 * FT_K * 2;           // one [128 x 16] bf16 tile
+constexpr int FT_CHUNK = 2 * FT_SUB;             // hi + lo
+constexpr int FT_TILE = (512 / FT_K) * FT_CHUNK; // BF16 tile of 128 pairs
+constexpr int FT8_TILE = 128 * 512;              // e4m3 tile of 128 pairs
+
+// Zero pooled feature of object `side` of pair row rel (relative to the
+// launch's first pair), written by one warp: an empty crop pools to exactly
+// 0.  BF16: 64 pieces of 16 bytes (chunk side 16 + i / 4, hi / lo tile, K
+// columns 0..7 / 8..15), two per lane; FP8: 16 pieces (chunk side 4 + i / 4,
+// a row's 64 bytes as four pieces 128 bytes apart), lanes 0..15.
+__device__ __forceinline__ void zero_feat_warp(unsigned char* ftile, int rel, int side, int lane,
+                                               bool e4m3) {
+  const int r = rel & 127;
+  const uint4 z = make_uint4(0u, 0u, 0u, 0u);
+  if (e4m3) {
+    if (lane < 16)
+      *reinterpret_cast<uint4*>(ftile + (size_t)(rel >> 7) * FT8_TILE +
+                                (size_t)(side * 4 + (lane >> 2)) * 8192 + (r >> 3) * 512 +
+                                (lane & 3) * 128 + (r & 7) * 16) = z;
+    return;
+  }
+  unsigned char* t = ftile + (size_t)(rel >> 7) * FT_TILE + (r >> 3) * 256 + (r & 7) * 16;
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int i = lane + 32 * h;
+    *reinterpret_cast<uint4*>(t + (size_t)(side * 16 + (i >> 2)) * FT_CHUNK +
+                              ((i >> 1) & 1) * FT_SUB + (i & 1) * 128) = z;
+  }
+}
+
 // Float32 parameters for the CUDA-core kernels: per layer W^T [in][out]
 // followed by b [out].
 struct Fp32Params {
@@ -152,10 +187,14 @@ namespace locc {
 // objects to the crop warps, defer[2..] lists the deferred objects.
 // mode: LOCC_CROP_LOCAL (nearest-first within the ball) or LOCC_CROP_GLOBAL
 // (the first KMAX samples of each shape, same canonical frame).
+// list / list_n (local mode, nullable): the object list of the tensor-core
+// encoders -- every object with a non-empty crop (2 p + side) is appended to
+// list + 2 lo (lo = the chunk's first pair), counted in list_n[chunk] (zeroed
+// here before the crop).
 cudaError_t launch_crop(const DevLibrary& lib, const PairInputs& in, const PairRange& rg,
                         float r, float4* xyz, int32_t* idx, int32_t* cnt, float4* centre,
                         int* err, int* defer, int n_sm, int grid_cap, cudaStream_t stream,
-                        int mode = LOCC_CROP_LOCAL);
+                        int mode = LOCC_CROP_LOCAL, int* list = nullptr, int* list_n = nullptr);
 // Per-device set-up of the kernels above, run by locc_create with the
 // handle's device current: loads their modules (so that no later launch
 // loads one) and records the crop kernel's occupancy for that device.

@@ -44,7 +44,8 @@ namespace {
 
 // Crop of one object of pair p (obj 0 = A, 1 = B) about the crop centre
 // (cx, cy, cz) in its body frame; R (shared memory) = R_rel for B, null for A.
-__device__ __forceinline__ void crop_object(const DevLibrary& lib, int p, int obj, int shape,
+// Returns the count, -1 when the object was deferred.
+__device__ __forceinline__ int crop_object(const DevLibrary& lib, int p, int obj, int shape,
                                             float cx, float cy, float cz, const float* R, int lane,
                                             float r, float4* __restrict__ xyz_out,
                                             int32_t* __restrict__ idx_out,
@@ -53,26 +54,38 @@ __device__ __forceinline__ void crop_object(const DevLibrary& lib, int p, int ob
                                             unsigned long long* ebuf, int* defer, int defer_cap) {
   const int cnt = select_object(lib, p, obj, shape, cx, cy, cz, lane, r, buf, hist, ebuf, defer,
                                 defer_cap);
-  if (cnt < 0) return;
+  if (cnt < 0) return -1;
   write_crop(buf, cnt, lib.points + (size_t)shape * lib.n_pad, cx, cy, cz, R,
              xyz_out + ((size_t)p * 2 + obj) * KMAX,
              idx_out ? idx_out + ((size_t)p * 2 + obj) * KMAX : nullptr, lane);
   if (lane == 0) cnt_out[2 * p + obj] = cnt;
   __syncwarp();
+  return cnt;
+}
+
+// Object list of the tensor-core encoders (list[0, *list_n) = 2 p + side of
+// the objects with non-empty crops, any order): one atomic per call.
+__device__ __forceinline__ void list_objects(int* list, int* list_n, int p, bool a, bool b) {
+  const int k = (int)a + (int)b;
+  if (k == 0) return;
+  const int base = atomicAdd(list_n, k);
+  if (a) list[base] = 2 * p;
+  if (b) list[base + (int)a] = 2 * p + 1;
 }
 
 // Both objects of pair p, one after the other on one warp: the pair's frame
 // (two rotations, the relative pose, the crop centre in both body frames) is
 // computed once.  R_rel and both centres wait in shared memory, so that they
 // hold no registers through the selections.
-__device__ __forceinline__ void crop_pair(const DevLibrary& lib, const PairInputs& in, int p, int lane,
+__device__ __forceinline__ void crop_pair(const DevLibrary& lib, const PairInputs& in, int p,
+                                          int lane,
                                           float r, float4* __restrict__ xyz_out,
                                           int32_t* __restrict__ idx_out,
                                           int32_t* __restrict__ cnt_out,
                                           float4* __restrict__ centre_out, int* __restrict__ err,
                                           unsigned long long* buf, int* hist,
                                           unsigned long long* ebuf, float* rsh, int* defer,
-                                          int defer_cap) {
+                                          int defer_cap, int* list, int* list_n) {
   int a, b, sa, sb;
   const bool ok = load_pair(in, lib.n_shapes, p, &a, &b, &sa, &sb, lane == 0 ? err : nullptr);
   if (!ok) {
@@ -106,12 +119,18 @@ __device__ __forceinline__ void crop_pair(const DevLibrary& lib, const PairInput
   }
   __syncwarp();
   // one call site: the selection code exists once in the binary
+  int c0 = 0, c1 = 0;
 #pragma unroll 1
   for (int obj = 0; obj < 2; ++obj) {
     const float* c = rsh + 9 + 3 * obj;
-    crop_object(lib, p, obj, obj ? sb : sa, c[0], c[1], c[2], obj ? rsh : nullptr, lane, r,
-                xyz_out, idx_out, cnt_out, buf, hist, ebuf, defer, defer_cap);
+    const int cnt = crop_object(lib, p, obj, obj ? sb : sa, c[0], c[1], c[2], obj ? rsh : nullptr,
+                                lane, r, xyz_out, idx_out, cnt_out, buf, hist, ebuf, defer,
+                                defer_cap);
+    if (obj) c1 = cnt;
+    else c0 = cnt;
   }
+  // deferred objects (-1) are listed by the fallback kernel
+  if (list && lane == 0) list_objects(list, list_n, p, c0 > 0, c1 > 0);
 }
 
 // Exact fallback for the objects crop_kernel deferred: the classic streaming
@@ -122,7 +141,7 @@ __device__ __forceinline__ void fallback_object(const DevLibrary& lib, const Pai
                                                 float4* __restrict__ xyz_out,
                                                 int32_t* __restrict__ idx_out,
                                                 int32_t* __restrict__ cnt_out,
-                                                unsigned long long* buf) {
+                                                unsigned long long* buf, int* list, int* list_n) {
   int a, b, sa, sb;
   if (!load_pair(in, lib.n_shapes, p, &a, &b, &sa, &sb, nullptr)) return;
   Frame f;
@@ -174,6 +193,7 @@ __device__ __forceinline__ void fallback_object(const DevLibrary& lib, const Pai
              xyz_out + ((size_t)p * 2 + obj) * KMAX,
              idx_out ? idx_out + ((size_t)p * 2 + obj) * KMAX : nullptr, lane);
   if (lane == 0) cnt_out[2 * p + obj] = cnt;
+  if (list && lane == 0 && cnt > 0) list[atomicAdd(list_n, 1)] = 2 * p + obj;
   __syncwarp();
 }
 
@@ -183,7 +203,8 @@ __global__ void __launch_bounds__(64, 16) crop_kernel(DevLibrary lib, PairInputs
                                                       int32_t* __restrict__ cnt_out,
                                                       float4* __restrict__ centre_out,
                                                       int* __restrict__ err, int* __restrict__ defer,
-                                                      int defer_cap) {
+                                                      int defer_cap, int* __restrict__ list,
+                                                      int* __restrict__ list_n) {
   __shared__ unsigned long long cand[2][CAND_CAP];
   __shared__ unsigned long long ebuf[2][EBUF];
   __shared__ int hist[2][NBINS];
@@ -199,29 +220,38 @@ __global__ void __launch_bounds__(64, 16) crop_kernel(DevLibrary lib, PairInputs
   // other.  The next index is fetched while the current pair runs.
   const int n_pairs = hi - lo;
   const int first = 2 * (int)gridDim.x;
+  int* lbase = list ? list + 2 * (size_t)lo : nullptr;  // this chunk's part of the list
+  int* lcnt = list ? list_n + rg.chunk : nullptr;
   int pr = 2 * (int)blockIdx.x + warp;
   while (pr < n_pairs) {
     int nxt = 0;
     if (lane == 0) nxt = first + atomicAdd(&defer[1], 1);
     crop_pair(lib, in, lo + pr, lane, r, xyz_out, idx_out, cnt_out, centre_out, err, cand[warp],
-              hist[warp], ebuf[warp], rsh[warp], defer, defer_cap);
+              hist[warp], ebuf[warp], rsh[warp], defer, defer_cap, lbase, lcnt);
     pr = __shfl_sync(FULL, nxt, 0);
   }
 }
 
 // One warp per deferred object (defer[0] = count, defer[2 + i] = 2 p + object).
 __global__ void __launch_bounds__(64) crop_fallback_kernel(DevLibrary lib, PairInputs in, float r,
+                                                           PairRange rg,
                                                            float4* __restrict__ xyz_out,
                                                            int32_t* __restrict__ idx_out,
                                                            int32_t* __restrict__ cnt_out,
                                                            const int* __restrict__ defer,
-                                                           int defer_cap) {
+                                                           int defer_cap, int* __restrict__ list,
+                                                           int* __restrict__ list_n) {
   __shared__ unsigned long long cand[2][CAND_CAP];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int n = min(defer[0], defer_cap);
+  int lo, hi;
+  range_bounds(rg, &lo, &hi);
+  int* lbase = list ? list + 2 * (size_t)lo : nullptr;
+  int* lcnt = list ? list_n + rg.chunk : nullptr;
   for (int e = 2 * blockIdx.x + warp; e < n; e += 2 * gridDim.x) {
     const int code = defer[2 + e];
-    fallback_object(lib, in, code >> 1, code & 1, lane, r, xyz_out, idx_out, cnt_out, cand[warp]);
+    fallback_object(lib, in, code >> 1, code & 1, lane, r, xyz_out, idx_out, cnt_out, cand[warp],
+                    lbase, lcnt);
   }
 }
 
@@ -298,13 +328,15 @@ cudaError_t prepare_crop_kernels(int device) {
 cudaError_t launch_crop_fallback(const DevLibrary& lib, const PairInputs& in, float r, float4* xyz,
                                  int32_t* cnt, int* defer, int defer_cap, int n_sm,
                                  cudaStream_t stream) {
-  crop_fallback_kernel<<<n_sm, 64, 0, stream>>>(lib, in, r, xyz, nullptr, cnt, defer, defer_cap);
+  crop_fallback_kernel<<<n_sm, 64, 0, stream>>>(lib, in, r, whole_range(0, nullptr), xyz, nullptr,
+                                                 cnt, defer, defer_cap, nullptr, nullptr);
   return cudaGetLastError();
 }
 
 cudaError_t launch_crop(const DevLibrary& lib, const PairInputs& in, const PairRange& rg, float r,
                         float4* xyz, int32_t* idx, int32_t* cnt, float4* centre, int* err,
-                        int* defer, int n_sm, int grid_cap, cudaStream_t stream, int mode) {
+                        int* defer, int n_sm, int grid_cap, cudaStream_t stream, int mode,
+                        int* list, int* list_n) {
   if (in.n_pairs <= 0) return cudaSuccess;
   if (mode == LOCC_CROP_GLOBAL) {
     const int span = (in.n_pairs + rg.n_chunks - 1) / rg.n_chunks + 1;
@@ -322,12 +354,14 @@ cudaError_t launch_crop(const DevLibrary& lib, const PairInputs& in, const PairR
   const int grid = std::max(1, std::min(span, n_sm * cap));
   const int defer_cap = 2 * (span - 1);  // both objects of every pair of one chunk
   cudaError_t e = cudaMemsetAsync(defer, 0, 2 * sizeof(int), stream);  // count, object counter
+  if (e == cudaSuccess && list) e = cudaMemsetAsync(list_n + rg.chunk, 0, sizeof(int), stream);
   if (e != cudaSuccess) return e;
   crop_kernel<<<grid, 64, 0, stream>>>(lib, in, rg, r, xyz, idx, cnt, centre, err, defer,
-                                       defer_cap);
+                                       defer_cap, list, list_n);
   // a fixed grid that reads the count on the device (graph-capturable); it
   // finds nothing to do unless some object was deferred
-  crop_fallback_kernel<<<n_sm, 64, 0, stream>>>(lib, in, r, xyz, idx, cnt, defer, defer_cap);
+  crop_fallback_kernel<<<n_sm, 64, 0, stream>>>(lib, in, r, rg, xyz, idx, cnt, defer, defer_cap,
+                                                list, list_n);
   return cudaGetLastError();
 }
 

@@ -101,15 +101,12 @@ __device__ __forceinline__ void enc_pool(uint32_t taddr, int cntA, int cntB, flo
   *mB = b;
 }
 
-// Pooled features in the BF16 head's A-operand layout: tiles of 128 pairs,
-// each 32 K-chunks of 16 features; a chunk holds the bf16 value (hi) as a
-// K-major no-swizzle [128 x 16] tile and the bf16 rounding of the remainder
-// (lo, f - hi) as a second tile FT_SUB bytes further.  The head multiplies
-// both with its weights, so the features enter it to about 2^-16 relative.
-constexpr int FT_K = 16;                        // features per chunk
-constexpr int FT_SUB = 128 * FT_K * 2;          // one [128 x 16] bf16 tile
-constexpr int FT_CHUNK = 2 * FT_SUB;            // hi + lo
-constexpr int FT_TILE = (512 / FT_K) * FT_CHUNK; // one tile of 128 pairs
+// Pooled features in the BF16 head's A-operand layout (FT_* in common.cuh):
+// tiles of 128 pairs, each 32 K-chunks of 16 features; a chunk holds the
+// bf16 value (hi) as a K-major no-swizzle [128 x 16] tile and the bf16
+// rounding of the remainder (lo, f - hi) as a second tile FT_SUB bytes
+// further.  The head multiplies both with its weights, so the features enter
+// it to about 2^-16 relative.
 
 // Pooled feature k of pair p (rel = p - first pair of the launch): float32
 // [P][512] when feat is given, and always the hi / lo pair in the head's
@@ -122,14 +119,6 @@ __device__ __forceinline__ void put_feat(float* feat, __nv_bfloat16* ftile, int 
   const __nv_bfloat16 hi = __float2bfloat16_rn(v);
   *reinterpret_cast<__nv_bfloat16*>(t) = hi;
   *reinterpret_cast<__nv_bfloat16*>(t + FT_SUB) = __float2bfloat16_rn(v - __bfloat162float(hi));
-}
-
-// Byte offset (from the tile base) of 16-byte piece i (0..63) of the pooled
-// feature of object `side` of row r: chunk side * 16 + i / 4, then the hi /
-// lo tile, then K columns 0..7 / 8..15 of the row.
-__device__ __forceinline__ size_t feat_piece_off(int r, int side, int i) {
-  return (size_t)(side * 16 + (i >> 2)) * FT_CHUNK + ((i >> 1) & 1) * FT_SUB + (r >> 3) * 256 +
-         (i & 1) * 128 + (r & 7) * 16;
 }
 
 }  // namespace

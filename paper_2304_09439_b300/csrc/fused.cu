@@ -79,15 +79,6 @@ struct Fused {
 
 enum { TK_GOT = 0, TK_END = 1, TK_ABORT = 2 };
 
-// Zero pooled feature of object `side` of pair rel (relative to the launch's
-// first pair) in the head's hi / lo operand tiles: 32 lanes x 2 x 16 bytes.
-__device__ __forceinline__ void zero_feat_tile(__nv_bfloat16* ftile, int rel, int side, int lane) {
-  unsigned char* t = reinterpret_cast<unsigned char*>(ftile) + (size_t)(rel >> 7) * FT_TILE;
-  *reinterpret_cast<uint4*>(t + feat_piece_off(rel & 127, side, lane)) = make_uint4(0u, 0u, 0u, 0u);
-  *reinterpret_cast<uint4*>(t + feat_piece_off(rel & 127, side, lane + 32)) =
-      make_uint4(0u, 0u, 0u, 0u);
-}
-
 template <int FC>
 __global__ void __launch_bounds__(Fused<FC>::THREADS, 1)
     fused_crop_encoder_kernel(DevLibrary lib, PairInputs in, PairRange rg, float radius,
@@ -167,8 +158,8 @@ __global__ void __launch_bounds__(Fused<FC>::THREADS, 1)
       if (!load_pair(in, lib.n_shapes, p, &a, &b, &sa, &sb, lane == 0 ? err : nullptr)) {
         // invalid indices: zero features, count 0, NaN centre (the head
         // writes the NaN row)
-        zero_feat_tile(ftile, p - lo, 0, lane);
-        zero_feat_tile(ftile, p - lo, 1, lane);
+        zero_feat_warp(reinterpret_cast<unsigned char*>(ftile), p - lo, 0, lane, false);
+        zero_feat_warp(reinterpret_cast<unsigned char*>(ftile), p - lo, 1, lane, false);
         if (lane == 0) {
           const float nan = __int_as_float(0x7fc00000);
           cnt_out[2 * p] = cnt_out[2 * p + 1] = 0;
@@ -198,8 +189,8 @@ __global__ void __launch_bounds__(Fused<FC>::THREADS, 1)
                                       hist, ebuf, defer, defer_cap);
         if (cnt < 0) continue;  // deferred: fallback crop + list-driven encoder
         if (lane == 0) cnt_out[2 * p + obj] = cnt;
-        if (cnt == 0) {
-          zero_feat_tile(ftile, p - lo, obj, lane);
+        if (cnt == 0) {  // the pooled feature is exactly 0
+          zero_feat_warp(reinterpret_cast<unsigned char*>(ftile), p - lo, obj, lane, false);
           continue;
         }
         int t = 0;

@@ -92,7 +92,7 @@ int run_path(locc_handle* h, const PairInputs& in, int n_cap, const int* n_dev, 
 // between the encoder and the head.
 int run_network(locc_handle* h, const float4* xyz, const PairRange& rg, const PairInputs* in,
                 const float4* centre, float* out, float* y_raw, float* feat_out,
-                cudaStream_t stream, cudaEvent_t mid);
+                cudaStream_t stream, cudaEvent_t mid, int list_mode);
 int upload_fp8_params(locc_handle* h, const std::vector<float>& params);
 // Per-device set-up of the tensor-core kernels (dynamic shared-memory limits;
 // module load), run by locc_create with the handle's device current.
@@ -100,7 +100,12 @@ cudaError_t prepare_tc_kernels();
 // Zeroes the pooled features of the objects of `rg` whose crop is empty and
 // lists the others for the tensor-core encoders (h->d_list, h->d_list_n).
 cudaError_t launch_enc_list(locc_handle* h, const float4* xyz, const PairRange& rg, float* feat,
-                            void* ftile, int e4m3, cudaStream_t stream);
+                            bool counts, void* ftile, int e4m3, cudaStream_t stream);
+// Who builds the tensor-core encoders' object list: the crop kernel, or the
+// list kernel from the crop rows (which, for crops given by the caller, also
+// writes 0 / 1 crop counts).  The heads zero the feature rows of the objects
+// whose count is 0.
+enum { LIST_FROM_CROP = 0, LIST_FROM_ROWS = 1, LIST_AND_COUNTS_FROM_ROWS = 2 };
 cudaError_t prepare_fp8_kernels();
 // BF16 head over the pairs of rg from the pooled features in h->d_feat_tc.
 int launch_head_tc(locc_handle* h, const PairRange& rg, const PairInputs* in, const float4* centre,
@@ -119,8 +124,8 @@ cudaError_t launch_fused(const DevLibrary& lib, const PairInputs& in, const Pair
 int noalloc_prepare(locc_handle* h);
 int run_network_fp8(locc_handle* h, const float4* xyz, const PairRange& rg, const PairInputs* in,
                     const float4* centre, float* out, float* y_raw, float* feat_out,
-                    cudaStream_t stream, cudaEvent_t mid);
+                    cudaStream_t stream, cudaEvent_t mid, int list_mode);
 int run_network_tc(locc_handle* h, const float4* xyz, const PairRange& rg, const PairInputs* in,
                    const float4* centre, float* out, float* y_raw, float* feat_out,
-                   cudaStream_t stream, cudaEvent_t mid);
+                   cudaStream_t stream, cudaEvent_t mid, int list_mode);
 }  // namespace locc

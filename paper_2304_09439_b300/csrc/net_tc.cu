@@ -81,20 +81,21 @@ constexpr int B_FULLX = 0, B_XRDY = NSLOT, B_H1RDY = 2 * NSLOT, B_H2RDY = 3 * NS
 // The tensor-core encoders work on the objects whose crop is not empty, two
 // objects (2 x 64 crop rows) per M = 128 tile.  An empty crop pools to
 // exactly 0 (the max-pool runs over no point and ReLU outputs are >= 0), so
-// those objects need no MMA at all: this kernel writes their features (zeros)
-// and appends every other object of the launch's pairs [lo, hi) to
-// list[2 lo ..] (object id 2 p + side, in no particular order: each object's
-// features depend on its own rows only), counting them in list_n[chunk],
-// which the caller has zeroed.  The valid points of an object come first in
-// its 64 rows (the crop writes them that way), so row 0 decides.
-// Zero features: float32 [P][512] when feat is given, and the head's operand
-// tiles: bf16 (e4m3 == 0) as hi / lo K = 16 chunks (feat_piece_off), or
-// e4m3 (e4m3 == 1) as 4 K-chunks of 64 per object, one row's 16-byte pieces
-// at (r / 8) 512 + q 128 + (r % 8) 16, q = 0..3.
+// those objects need no MMA; their pooled features (zeros) are written by the
+// crop kernel, or here (ftile).  The crop kernel lists the objects as it goes;
+// for crops given by the caller (or global crops) this kernel lists the
+// objects of the launch's pairs [lo, hi) with a valid row 0 (the valid
+// points of an object come first in its 64 rows) into list[2 lo ..] (object
+// id 2 p + side, in no particular order: each object's features depend on its
+// own rows only), counted in list_n[chunk], which the caller has zeroed.
+// cnt_out (nullable): 1 / 0 per object (non-empty or not); feat (nullable):
+// float32 zero features of the empty objects; ftile (nullable): their zero
+// features in the head's operand tiles (bf16 hi / lo, or e4m3), one warp per
+// empty object (zero_feat_warp).
 __global__ void __launch_bounds__(256)
     enc_list_kernel(const float4* __restrict__ xyz, PairRange rg, int* __restrict__ list,
-                    int* __restrict__ list_n, float* __restrict__ feat,
-                    unsigned char* __restrict__ ftile, int e4m3) {
+                    int* __restrict__ list_n, int32_t* __restrict__ cnt_out,
+                    float* __restrict__ feat, unsigned char* __restrict__ ftile, int e4m3) {
   int lo, hi;
   range_bounds(rg, &lo, &hi);
   const int n_obj = 2 * (hi - lo), lane = threadIdx.x & 31;
@@ -108,25 +109,19 @@ __global__ void __launch_bounds__(256)
     if (lane == 0 && m) b0 = atomicAdd(list_n + rg.chunk, __popc(m));
     b0 = __shfl_sync(0xffffffffu, b0, 0);
     if (live) lst[b0 + __popc(m & ((1u << lane) - 1u))] = 2 * lo + i;
-    if (i < n_obj && !live) {
-      const int rel = i >> 1, side = i & 1, r = rel & 127;
-      if (e4m3) {
-        unsigned char* t = ftile + (size_t)(rel >> 7) * (128 * 512) + (size_t)side * 4 * 8192 +
-                           (r >> 3) * 512 + (r & 7) * 16;
-        for (int c = 0; c < 4; ++c)
-#pragma unroll
-          for (int q = 0; q < 4; ++q)
-            *reinterpret_cast<uint4*>(t + c * 8192 + q * 128) = make_uint4(0u, 0u, 0u, 0u);
-      } else {
-        unsigned char* t = ftile + (size_t)(rel >> 7) * FT_TILE;
-        for (int q = 0; q < 64; ++q)
-          *reinterpret_cast<uint4*>(t + feat_piece_off(r, side, q)) = make_uint4(0u, 0u, 0u, 0u);
+    if (i < n_obj && cnt_out) cnt_out[2 * lo + i] = live ? 1 : 0;
+    if (ftile) {
+      unsigned em = __ballot_sync(0xffffffffu, i < n_obj && !live);
+      while (em) {
+        const int j = base + (int)(threadIdx.x & ~31u) + __ffs(em) - 1;
+        em &= em - 1;
+        zero_feat_warp(ftile, j >> 1, j & 1, lane, e4m3 != 0);
       }
-      if (feat) {
-        float4* f = reinterpret_cast<float4*>(feat + (size_t)(lo + rel) * 512 + side * 256);
+    }
+    if (i < n_obj && !live && feat) {
+      float4* f = reinterpret_cast<float4*>(feat + (size_t)(lo + (i >> 1)) * 512 + (i & 1) * 256);
 #pragma unroll 4
-        for (int k = 0; k < 64; ++k) f[k] = make_float4(0.f, 0.f, 0.f, 0.f);
-      }
+      for (int k = 0; k < 64; ++k) f[k] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
   }
 }
@@ -422,7 +417,7 @@ constexpr int H_A0 = (H_RES_BYTES + 127) / 128 * 128;      // A stages 8 KB each
 constexpr int H_B0 = H_A0 + H_NST * H_ACHUNK;              // B stages [256 x 32] 16 KB each
 constexpr int H_G = H_B0 + H_NST * H_CHUNK;                // G [128 x 256] 64 KB
 constexpr int H_CTRL = H_G + 128 * 256 * 2;                // mbarriers, TMEM address, abort
-constexpr int H_SMEM = H_CTRL + 256;
+constexpr int H_SMEM = H_CTRL + 320;
 // global image: [resident][W_h1 chunks x 16][W_h2 chunks x 8]
 constexpr int H_IMG_W1 = (H_RES_BYTES + 127) / 128 * 128;
 constexpr int H_IMG_W2 = H_IMG_W1 + H_L1C * H_CHUNK;
@@ -491,13 +486,13 @@ __device__ __forceinline__ void head_epi_256(uint32_t taddr, const float* b, uns
 //   full[s] / done[s]: one per chunk in stage s; L1D, L2D, L3: one per tile;
 //   GC0-GC3: one per tile (G chunk k holds layer 1); EPI: two per tile (G
 //   holds layer 2; outputs have left TMEM).
-constexpr int H_THREADS = 320;  // 8 epilogue warps, the copy warp, the MMA warp
-constexpr int H_COPY = 256, H_MMA_WARP = 9;
+constexpr int H_THREADS = 352;  // 8 epilogue warps, the copy warp, the MMA warp, the zeroer
+constexpr int H_COPY = 256, H_MMA_WARP = 9, H_ZERO_WARP = 10;
 __global__ void __launch_bounds__(H_THREADS, 1)
     head_tc_kernel(const __nv_bfloat16* __restrict__ ftile, PairRange rg,
                    const unsigned char* __restrict__ img, PairInputs in, int have_in,
-                   const float4* __restrict__ centre, float* __restrict__ out,
-                   float* __restrict__ y_raw, int* __restrict__ err) {
+                   const float4* __restrict__ centre, const int32_t* __restrict__ cnt,
+                   float* __restrict__ out, float* __restrict__ y_raw, int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char smem[];
   const int tid = threadIdx.x, warp = tid >> 5;
   int lo, n;
@@ -512,11 +507,14 @@ __global__ void __launch_bounds__(H_THREADS, 1)
   const uint32_t B_FULL = bar0, B_DONE = bar0 + 48;
   const uint32_t B_L3 = bar0 + 96, B_EPI = bar0 + 104, B_RES = bar0 + 112, B_DRAIN = bar0 + 120;
   const uint32_t B_L1D = bar0 + 128, B_L2D = bar0 + 136, B_GC = bar0 + 144;
+  // [32, 38): stage s ready for the MMAs (rows of empty objects zeroed)
+  const uint32_t B_READY = bar0 + 256;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + H_CTRL + 192);
   volatile int* abort = reinterpret_cast<volatile int*>(smem + H_CTRL + 196);
   int* s_issued = reinterpret_cast<int*>(smem + H_CTRL + 200);
   if (tid == 0) {
     for (int i = 0; i < 22; ++i) mbar_init(bar0 + 8 * i, (i == 13 || i >= 18) ? 256 : 1);
+    for (int i = 0; i < H_NST; ++i) mbar_init(B_READY + 8 * i, 32);
     *abort = 0;
     *s_issued = 0;
     fence_mbar_init();
@@ -613,8 +611,8 @@ __global__ void __launch_bounds__(H_THREADS, 1)
         if (j == 0 && t > 0) ok = mbar_wait_warp(B_EPI, (2 * t - 1) & 1, abort, WAIT_CYCLES);
         ok = ok && mbar_wait_warp(B_GC + 8 * (j >> 1), t & 1, abort, WAIT_CYCLES);
       }
-      ok = ok && mbar_wait_warp(B_FULL + 8 * st0, (g / H_NST) & 1, abort, WAIT_CYCLES);
-      ok = ok && mbar_wait_warp(B_FULL + 8 * st1, ((g + 1) / H_NST) & 1, abort, WAIT_CYCLES);
+      ok = ok && mbar_wait_warp(B_READY + 8 * st0, (g / H_NST) & 1, abort, WAIT_CYCLES);
+      ok = ok && mbar_wait_warp(B_READY + 8 * st1, ((g + 1) / H_NST) & 1, abort, WAIT_CYCLES);
       if (!ok) break;
       tc_fence_after();
       // descriptors from warp-uniform values; one elected lane issues
@@ -654,6 +652,54 @@ __global__ void __launch_bounds__(H_THREADS, 1)
     if (ok && l3 >= 0) {
       ok = mbar_wait_warp(B_EPI, (2 * l3) & 1, abort, WAIT_CYCLES);
       if (ok) layer3();
+    }
+    if (!ok) *abort = 1;
+  } else if (warp == H_ZERO_WARP) {
+    // ---------------------------------------------------------- zeroer warp
+    // An object with an empty crop has a pooled feature of exactly 0, which
+    // nothing writes to the feature tiles: once two layer-1 chunks have
+    // landed (the MMA warp takes them in pairs), this warp zeroes in shared
+    // memory the rows whose object on the chunks' side (chunks [0, 16): A,
+    // [16, 32): B) has crop count 0, then hands both stages to the MMA warp.
+    const int lane = tid & 31;
+    uint32_t mA = 0, mB = 0;  // this lane's rows (4 lane .. 4 lane + 3) with an empty A / B
+    for (int g = 0; g < n_chunks && ok; g += 2) {
+      const int st0 = g % H_NST, st1 = (g + 1) % H_NST, c = g % H_NCH, t = g / H_NCH;
+      if (c == 0) {
+        mA = mB = 0;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int pr = lo + ((int)blockIdx.x + t * (int)gridDim.x) * HT + 4 * lane + i;
+          if (pr < n) {
+            mA |= (cnt[2 * (size_t)pr] == 0 ? 1u : 0u) << i;
+            mB |= (cnt[2 * (size_t)pr + 1] == 0 ? 1u : 0u) << i;
+          }
+        }
+      }
+      ok = mbar_wait_warp(B_FULL + 8 * st0, (g / H_NST) & 1, abort, WAIT_CYCLES);
+      ok = ok && mbar_wait_warp(B_FULL + 8 * st1, ((g + 1) / H_NST) & 1, abort, WAIT_CYCLES);
+      if (!ok) break;
+      const uint32_t m = c < H_L1C / 2 ? mA : (c < H_L1C ? mB : 0u);
+      if (m) {
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+          unsigned char* a = smem + H_A0 + (k ? st1 : st0) * H_ACHUNK;
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            if (!((m >> i) & 1u)) continue;
+            const int r = 4 * lane + i;
+            unsigned char* p = a + (r >> 3) * 256 + (r & 7) * 16;  // K 0..7 of row r
+            const uint4 zz = make_uint4(0u, 0u, 0u, 0u);
+            *reinterpret_cast<uint4*>(p) = zz;
+            *reinterpret_cast<uint4*>(p + 128) = zz;           // K 8..15
+            *reinterpret_cast<uint4*>(p + FT_SUB) = zz;        // lo tile
+            *reinterpret_cast<uint4*>(p + FT_SUB + 128) = zz;
+          }
+        }
+        fence_async_smem();
+      }
+      mbar_arrive(B_READY + 8 * st0);
+      mbar_arrive(B_READY + 8 * st1);
     }
     if (!ok) *abort = 1;
   }
@@ -873,12 +919,13 @@ int upload_tc_params(locc_handle* h, const std::vector<float>& params) {
 }
 
 cudaError_t launch_enc_list(locc_handle* h, const float4* xyz, const PairRange& rg, float* feat,
-                            void* ftile, int e4m3, cudaStream_t stream) {
+                            bool counts, void* ftile, int e4m3, cudaStream_t stream) {
   cudaError_t e = cudaMemsetAsync(h->d_list_n + rg.chunk, 0, sizeof(int), stream);
   if (e != cudaSuccess) return e;
   const int n_obj = 2 * ((rg.n_cap + rg.n_chunks - 1) / rg.n_chunks + 1);
   const int grid = std::max(1, std::min((n_obj + 255) / 256, 8 * h->n_sm));
-  enc_list_kernel<<<grid, 256, 0, stream>>>(xyz, rg, h->d_list, h->d_list_n, feat,
+  enc_list_kernel<<<grid, 256, 0, stream>>>(xyz, rg, h->d_list, h->d_list_n,
+                                            counts ? h->d_cnt : nullptr, feat,
                                             static_cast<unsigned char*>(ftile), e4m3);
   return cudaGetLastError();
 }
@@ -893,12 +940,14 @@ cudaError_t prepare_tc_kernels() {
 
 int run_network_tc(locc_handle* h, const float4* xyz, const PairRange& rg, const PairInputs* in,
                    const float4* centre, float* out, float* y_raw, float* feat_out,
-                   cudaStream_t stream, cudaEvent_t mid) {
+                   cudaStream_t stream, cudaEvent_t mid, int list_mode) {
   if (h->prec == LOCC_FP8)
-    return run_network_fp8(h, xyz, rg, in, centre, out, y_raw, feat_out, stream, mid);
+    return run_network_fp8(h, xyz, rg, in, centre, out, y_raw, feat_out, stream, mid, list_mode);
   const int n_pairs = (rg.n_cap + rg.n_chunks - 1) / rg.n_chunks + 1;  // pairs of one chunk, at most
   __nv_bfloat16* ftile = static_cast<__nv_bfloat16*>(h->d_feat_tc);
-  if (launch_enc_list(h, xyz, rg, feat_out, ftile, 0, stream) != cudaSuccess) {
+  if (list_mode != LIST_FROM_CROP &&
+      launch_enc_list(h, xyz, rg, feat_out, list_mode == LIST_AND_COUNTS_FROM_ROWS, nullptr, 0,
+                      stream) != cudaSuccess) {
     set_error("enc_list_kernel launch failed");
     return LOCC_ERR_CUDA;
   }
@@ -921,7 +970,7 @@ int launch_head_tc(locc_handle* h, const PairRange& rg, const PairInputs* in, co
   const int grid_h = std::min((n_pairs + HT - 1) / HT, h->n_sm);
   head_tc_kernel<<<grid_h, H_THREADS, H_SMEM, stream>>>(static_cast<__nv_bfloat16*>(h->d_feat_tc),
                                                         rg, h->wtc_head, pin, in != nullptr, centre,
-                                                        out, y_raw, h->d_err);
+                                                        h->d_cnt, out, y_raw, h->d_err);
   if (cudaGetLastError() != cudaSuccess) {
     set_error("head_tc_kernel launch failed");
     return LOCC_ERR_CUDA;
