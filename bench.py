@@ -47,6 +47,9 @@ RADIUS = 0.25
 MAX_PAIRS = 400_000
 FLOP_ENC = 2 * 128 * (3 * 64 + 64 * 128 + 128 * 256)       # per pair
 FLOP_HEAD = 2 * (512 * 256 + 256 * 256 + 256 * 8)          # per pair
+# MMA work the BF16 head executes per pair: layer 1 in split precision (three
+# products per K step), layer 2 plain, layer 3 two products into 16 columns
+FLOP_HEAD_EXEC_BF16 = 2 * (3 * 512 * 256 + 256 * 256 + 2 * 256 * 16)
 FLOP_POINT = 2 * (3 * 64 + 64 * 128 + 128 * 256)           # encoder, per crop point
 # encoder work per object with a non-empty crop (64 point rows); an empty
 # crop's pooled feature is 0 by definition and takes no arithmetic
@@ -562,10 +565,9 @@ def main():
         chunks, cap = (int(x) for x in args.pipeline.split(","))
         det.set_pipeline(chunks, cap)
         tune_ms = None
-    # broadphase (3 kernels), then per chunk: crop, crop fallback, (object
-    # list for the tensor-core encoders,) encoder, head
-    per_chunk = 4 if args.precision == "fp32" else 5
-    launches_per_step = 3 + per_chunk * (chunks if max(n_pairs) >= 4096 else 1)
+    # broadphase (3 kernels), then per chunk: crop (which also lists the
+    # objects with non-empty crops), crop fallback, encoder, head
+    launches_per_step = 3 + 4 * (chunks if max(n_pairs) >= 4096 else 1)
     if chunks == 0:  # fused crop + encoder, fallback crop, deferred-object encoder, head
         launches_per_step = 3 + 4
 
@@ -728,7 +730,10 @@ def main():
                               "traffic_unit": "bytes per launch (ncu dram read+write per pair x "
                                               "pairs)",
                               "peak_source": peak_src,
-                              "algorithmic": f"{FLOP_HEAD} FLOP per pair x pairs per launch"},
+                              "algorithmic": f"{FLOP_HEAD} FLOP per pair x pairs per launch",
+                              "executed_mma_frac": (FLOP_HEAD_EXEC_BF16 * per_step_pairs /
+                                                    (head_ms * 1e-3) / 1e12 / peak
+                                                    if args.precision == "bf16" else None)},
             "e2e": {"value": e2e_pairs_all / e2e_max, "unit": "pairs/s",
                     "h2d_bytes_per_step": h2d // args.steps, "d2h_bytes_per_step": d2h // args.steps},
             "gpu_launches": launches_per_step * args.steps,

@@ -221,7 +221,7 @@ int run_path(locc_handle* h, const PairInputs& in, int n_cap, const int* n_dev, 
   }
   // the tensor-core encoders take the list of objects with non-empty crops:
   // local crops list them as they go, global crops through the list kernel.
-  // The heads zero the rows of empty objects from the crop counts.
+  // The encoders zero the empty objects' features from the crop counts.
   const bool list_in_crop = h->prec != LOCC_FP32 && h->crop_mode == LOCC_CROP_LOCAL;
   int* list = list_in_crop ? h->d_list : nullptr;
   int* list_n = list_in_crop ? h->d_list_n : nullptr;

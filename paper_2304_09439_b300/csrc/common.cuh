@@ -102,6 +102,26 @@ __device__ __forceinline__ void zero_feat_warp(unsigned char* ftile, int rel, in
   }
 }
 
+// One warp zeroes the pooled features of the objects with crop count 0 among
+// its CTA's slice of the launch's objects [2 lo, 2 hi): every CTA of the
+// grid takes a contiguous, 32-aligned slice, so that all objects are covered
+// whatever the number of CTAs that have encoder tiles.
+__device__ __forceinline__ void zero_empty_objects(const int32_t* cnt, unsigned char* ftile, int lo,
+                                                   int hi, int lane, bool e4m3) {
+  const int n_obj = 2 * (hi - lo);
+  const int per = ((n_obj + (int)gridDim.x - 1) / (int)gridDim.x + 31) & ~31;
+  const int o0 = (int)blockIdx.x * per, o1 = min(o0 + per, n_obj);
+  for (int b = o0; b < o1; b += 32) {
+    const int i = b + lane;
+    unsigned em = __ballot_sync(0xffffffffu, i < o1 && cnt[2 * (size_t)lo + i] == 0);
+    while (em) {
+      const int j = b + __ffs(em) - 1;
+      em &= em - 1;
+      zero_feat_warp(ftile, j >> 1, j & 1, lane, e4m3);
+    }
+  }
+}
+
 // Float32 parameters for the CUDA-core kernels: per layer W^T [in][out]
 // followed by b [out].
 struct Fp32Params {

@@ -103,8 +103,8 @@ cudaError_t launch_enc_list(locc_handle* h, const float4* xyz, const PairRange& 
                             bool counts, void* ftile, int e4m3, cudaStream_t stream);
 // Who builds the tensor-core encoders' object list: the crop kernel, or the
 // list kernel from the crop rows (which, for crops given by the caller, also
-// writes 0 / 1 crop counts).  The heads zero the feature rows of the objects
-// whose count is 0.
+// writes 0 / 1 crop counts).  A warp of each encoder CTA zeroes the pooled
+// features of the objects whose count is 0.
 enum { LIST_FROM_CROP = 0, LIST_FROM_ROWS = 1, LIST_AND_COUNTS_FROM_ROWS = 2 };
 cudaError_t prepare_fp8_kernels();
 // BF16 head over the pairs of rg from the pooled features in h->d_feat_tc.

@@ -69,8 +69,10 @@ constexpr int C_BAR = 0, C_TMEM = 8 * NBAR, C_ABORT = C_TMEM + 4, C_CNT = C_ABOR
 constexpr int C_OBJ = C_CNT + 16 * NSLOT;  // [slot][tile parity][u, v] object ids
 constexpr int F_SMEM = F_CTRL + C_OBJ + 16 * NSLOT;
 static_assert(F_SMEM <= 227 * 1024, "fp8 encoder shared memory");
-constexpr int F_THREADS = 32 * (4 * NSLOT + 1);
+constexpr int F_THREADS = 32 * (4 * NSLOT + 2);
 constexpr int MMA_WARP = 4 * NSLOT;
+// zeroes the pooled features of the empty objects (zero_empty_objects)
+constexpr int ZERO_WARP = 4 * NSLOT + 1;
 constexpr int SLOT_COLS = 512 / NSLOT;
 constexpr int B_FULLX = 0, B_XRDY = NSLOT, B_H1RDY = 2 * NSLOT, B_H2RDY = 3 * NSLOT,
               B_E3A = 4 * NSLOT, B_D1 = 5 * NSLOT, B_D2 = 6 * NSLOT, B_D3A = 7 * NSLOT,
@@ -155,6 +157,7 @@ __device__ __forceinline__ void put_feat8(float* feat, unsigned char* ftile, int
 __global__ void __launch_bounds__(F_THREADS, 1)
     encoder_fp8_kernel(const float4* __restrict__ xyz, PairRange rg,
                        const int* __restrict__ list, const int* __restrict__ list_n,
+                       const int32_t* __restrict__ cnt,
                        const unsigned char* __restrict__ img, float* __restrict__ feat,
                        unsigned char* __restrict__ ftile, int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char smem[];
@@ -164,7 +167,10 @@ __global__ void __launch_bounds__(F_THREADS, 1)
   const int n_objs = min(list_n[rg.chunk], 2 * (hi - lo));
   const int* lst = list + 2 * (size_t)lo;
   const int n = (n_objs + 1) >> 1;  // tiles
-  if ((int)blockIdx.x >= n) return;
+  if ((int)blockIdx.x >= n) {  // no tile here: only this CTA's share of the zero features
+    if (warp == ZERO_WARP && cnt) zero_empty_objects(cnt, ftile, lo, hi, lane, true);
+    return;
+  }
   const int my_pairs = (n - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;  // tiles
 
   unsigned char* ctrl = smem + F_CTRL;
@@ -283,6 +289,9 @@ __global__ void __launch_bounds__(F_THREADS, 1)
       mbar_wait(BAR(B_DRAIN), 0, WAIT_CYCLES);
     }
     __syncwarp();
+  } else if (warp == ZERO_WARP) {
+    // the empty objects' pooled features (exactly 0, e4m3) for the head
+    if (cnt) zero_empty_objects(cnt, ftile, lo, hi, lane, true);
   } else {
     const int s = warp >> 2, row = tid & 127, wq = warp & 3;
     unsigned char* slot = smem + F_SLOT0 + s * F_SLOT_BYTES;
@@ -446,9 +455,9 @@ constexpr int G_A0 = (G_RES_BYTES + 1023) / 1024 * 1024;  // A stages [128 x 64]
 constexpr int G_B0 = G_A0 + G_NST * G_ACHUNK;              // B stages [256 x 64] e4m3
 constexpr int G_G = G_B0 + G_NST * G_CHUNK;                // G [128 x 256] e4m3, 32 KB
 constexpr int G_CTRL = G_G + 128 * 256;                    // mbarriers, TMEM address, abort
-constexpr int G_SMEM = G_CTRL + 320;
-constexpr int G_THREADS = 352;  // 8 epilogue warps, the copy warp, the MMA warp, the zeroer
-constexpr int G_COPY = 256, G_MMA_WARP = 9, G_ZERO_WARP = 10;
+constexpr int G_SMEM = G_CTRL + 256;
+constexpr int G_THREADS = 320;  // 8 epilogue warps, the copy warp, the MMA warp
+constexpr int G_COPY = 256, G_MMA_WARP = 9;
 static_assert(G_RES_BYTES % 16 == 0 && G_IMG_W1 % 16 == 0, "bulk copies need 16-byte chunks");
 static_assert(G_SMEM <= 227 * 1024, "fp8 head shared memory");
 
@@ -474,8 +483,8 @@ __device__ __forceinline__ void head_epi_fp8(uint32_t taddr, const float* alpha,
 __global__ void __launch_bounds__(G_THREADS, 1)
     head_fp8_kernel(const unsigned char* __restrict__ ftile, PairRange rg,
                     const unsigned char* __restrict__ img, PairInputs in, int have_in,
-                    const float4* __restrict__ centre, const int32_t* __restrict__ cnt,
-                    float* __restrict__ out, float* __restrict__ y_raw, int* __restrict__ err) {
+                    const float4* __restrict__ centre, float* __restrict__ out,
+                    float* __restrict__ y_raw, int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char smem[];
   const int tid = threadIdx.x, warp = tid >> 5;
   int lo, n;
@@ -491,14 +500,11 @@ __global__ void __launch_bounds__(G_THREADS, 1)
   const uint32_t B_FULL = bar0, B_DONE = bar0 + 48;
   const uint32_t B_L3 = bar0 + 96, B_EPI = bar0 + 104, B_RES = bar0 + 112, B_DRAIN = bar0 + 120;
   const uint32_t B_L1D = bar0 + 128, B_L2D = bar0 + 136, B_GC = bar0 + 144;
-  // [32, 38): stage s ready for the MMAs (rows of empty objects zeroed)
-  const uint32_t B_READY = bar0 + 256;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + G_CTRL + 192);
   volatile int* abort = reinterpret_cast<volatile int*>(smem + G_CTRL + 196);
   int* s_issued = reinterpret_cast<int*>(smem + G_CTRL + 200);
   if (tid == 0) {
     for (int i = 0; i < 22; ++i) mbar_init(bar0 + 8 * i, (i == 13 || i >= 18) ? 256 : 1);
-    for (int i = 0; i < G_NST; ++i) mbar_init(B_READY + 8 * i, 32);
     *abort = 0;
     *s_issued = 0;
     fence_mbar_init();
@@ -593,8 +599,8 @@ __global__ void __launch_bounds__(G_THREADS, 1)
         ok = ok && mbar_wait_warp(B_GC + 8 * j, t & 1, abort, WAIT_CYCLES);
         ok = ok && mbar_wait_warp(B_GC + 8 * (j + 1), t & 1, abort, WAIT_CYCLES);
       }
-      ok = ok && mbar_wait_warp(B_READY + 8 * st0, (g / G_NST) & 1, abort, WAIT_CYCLES);
-      ok = ok && mbar_wait_warp(B_READY + 8 * st1, ((g + 1) / G_NST) & 1, abort, WAIT_CYCLES);
+      ok = ok && mbar_wait_warp(B_FULL + 8 * st0, (g / G_NST) & 1, abort, WAIT_CYCLES);
+      ok = ok && mbar_wait_warp(B_FULL + 8 * st1, ((g + 1) / G_NST) & 1, abort, WAIT_CYCLES);
       if (!ok) break;
       tc_fence_after();
       // descriptors from warp-uniform values; one elected lane issues
@@ -620,50 +626,6 @@ __global__ void __launch_bounds__(G_THREADS, 1)
     if (ok && l3 >= 0) {
       ok = mbar_wait_warp(B_EPI, (2 * l3) & 1, abort, WAIT_CYCLES);
       if (ok) layer3();
-    }
-    if (!ok) *abort = 1;
-  } else if (warp == G_ZERO_WARP) {
-    // ---------------------------------------------------------- zeroer warp
-    // As in the BF16 head: rows of objects with an empty crop are zeroed in
-    // each landed pair of layer-1 chunks (chunks [0, 4): A, [4, 8): B; e4m3
-    // K = 64, a row's 64 bytes as four 16-byte pieces 128 bytes apart).
-    const int lane = tid & 31;
-    uint32_t mA = 0, mB = 0;  // this lane's rows (4 lane .. 4 lane + 3) with an empty A / B
-    for (int g = 0; g < n_chunks && ok; g += 2) {
-      const int st0 = g % G_NST, st1 = (g + 1) % G_NST, c = g % G_NCH, t = g / G_NCH;
-      if (c == 0) {
-        mA = mB = 0;
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          const int pr = lo + ((int)blockIdx.x + t * (int)gridDim.x) * HT + 4 * lane + i;
-          if (pr < n) {
-            mA |= (cnt[2 * (size_t)pr] == 0 ? 1u : 0u) << i;
-            mB |= (cnt[2 * (size_t)pr + 1] == 0 ? 1u : 0u) << i;
-          }
-        }
-      }
-      ok = mbar_wait_warp(B_FULL + 8 * st0, (g / G_NST) & 1, abort, WAIT_CYCLES);
-      ok = ok && mbar_wait_warp(B_FULL + 8 * st1, ((g + 1) / G_NST) & 1, abort, WAIT_CYCLES);
-      if (!ok) break;
-      const uint32_t m = c < G_L1C / 2 ? mA : (c < G_L1C ? mB : 0u);
-      if (m) {
-#pragma unroll
-        for (int k = 0; k < 2; ++k) {
-          unsigned char* a = smem + G_A0 + (k ? st1 : st0) * G_ACHUNK;
-#pragma unroll
-          for (int i = 0; i < 4; ++i) {
-            if (!((m >> i) & 1u)) continue;
-            const int r = 4 * lane + i;
-            unsigned char* p = a + (r >> 3) * 512 + (r & 7) * 16;
-#pragma unroll
-            for (int q = 0; q < 4; ++q)
-              *reinterpret_cast<uint4*>(p + 128 * q) = make_uint4(0u, 0u, 0u, 0u);
-          }
-        }
-        fence_async_smem();
-      }
-      mbar_arrive(B_READY + 8 * st0);
-      mbar_arrive(B_READY + 8 * st1);
     }
     if (!ok) *abort = 1;
   }
@@ -935,7 +897,7 @@ int run_network_fp8(locc_handle* h, const float4* xyz, const PairRange& rg, cons
     return LOCC_ERR_CUDA;
   }
   encoder_fp8_kernel<<<std::min(n_pairs, h->n_sm), F_THREADS, F_SMEM, stream>>>(
-      xyz, rg, h->d_list, h->d_list_n, h->wf8_enc, feat_out, ftile, h->d_err);
+      xyz, rg, h->d_list, h->d_list_n, h->d_cnt, h->wf8_enc, feat_out, ftile, h->d_err);
   if (cudaGetLastError() != cudaSuccess) {
     set_error("encoder_fp8_kernel launch failed");
     return LOCC_ERR_CUDA;
@@ -944,7 +906,7 @@ int run_network_fp8(locc_handle* h, const float4* xyz, const PairRange& rg, cons
   PairInputs pin{};
   if (in) pin = *in;
   head_fp8_kernel<<<std::min((n_pairs + HT - 1) / HT, h->n_sm), G_THREADS, G_SMEM, stream>>>(
-      ftile, rg, h->wf8_head, pin, in != nullptr, centre, h->d_cnt, out, y_raw, h->d_err);
+      ftile, rg, h->wf8_head, pin, in != nullptr, centre, out, y_raw, h->d_err);
   if (cudaGetLastError() != cudaSuccess) {
     set_error("head_fp8_kernel launch failed");
     return LOCC_ERR_CUDA;

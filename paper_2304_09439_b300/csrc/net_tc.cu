@@ -68,8 +68,10 @@ constexpr int C_BAR = 0, C_TMEM = 8 * NBAR, C_ABORT = C_TMEM + 4, C_CNT = C_ABOR
 constexpr int C_OBJ = C_CNT + 16 * NSLOT;  // [slot][tile parity][u, v] object ids
 constexpr int E_SMEM = E_CTRL + C_OBJ + 16 * NSLOT;
 static_assert(E_SMEM <= 227 * 1024, "encoder shared memory");
-constexpr int E_THREADS = 32 * (4 * NSLOT + 1);  // 4 epilogue warps per slot + the MMA/TMA warp
+constexpr int E_THREADS = 32 * (4 * NSLOT + 2);  // 4 epilogue warps per slot + the MMA/TMA warp
 constexpr int MMA_WARP = 4 * NSLOT;
+// zeroes the pooled features of the empty objects (zero_empty_objects)
+constexpr int ZERO_WARP = 4 * NSLOT + 1;
 constexpr int SLOT_COLS = 512 / NSLOT;  // TMEM columns per slot: D1 [0,64), D2 / D3a / D3b [0,128)
 
 // barrier indices (per slot s: index + s)
@@ -133,6 +135,7 @@ __global__ void __launch_bounds__(256)
 __global__ void __launch_bounds__(E_THREADS, 1)
     encoder_tc_kernel(const float4* __restrict__ xyz, PairRange rg,
                       const int* __restrict__ list, const int* __restrict__ list_n,
+                      const int32_t* __restrict__ cnt,
                       const unsigned char* __restrict__ img, float* __restrict__ feat,
                       __nv_bfloat16* __restrict__ ftile, int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char smem[];
@@ -142,7 +145,10 @@ __global__ void __launch_bounds__(E_THREADS, 1)
   const int n_objs = min(list_n[rg.chunk], 2 * (hi - lo));
   const int* lst = list + 2 * (size_t)lo;
   const int n = (n_objs + 1) >> 1;  // tiles
-  if ((int)blockIdx.x >= n) return;
+  if ((int)blockIdx.x >= n) {  // no tile here: only this CTA's share of the zero features
+    if (warp == ZERO_WARP && cnt) zero_empty_objects(cnt, reinterpret_cast<unsigned char*>(ftile), lo, hi, lane, false);
+    return;
+  }
   const int my_pairs = (n - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;  // tiles
 
   unsigned char* ctrl = smem + E_CTRL;
@@ -268,6 +274,9 @@ __global__ void __launch_bounds__(E_THREADS, 1)
       mbar_wait(BAR(B_DRAIN), 0, WAIT_CYCLES);
     }
     __syncwarp();
+  } else if (warp == ZERO_WARP) {
+    // the empty objects' pooled features (exactly 0) for the head
+    if (cnt) zero_empty_objects(cnt, reinterpret_cast<unsigned char*>(ftile), lo, hi, lane, false);
   } else {
     // ------------------------------------------------ epilogue warpgroup of slot s
     const int s = warp >> 2, row = tid & 127, wq = warp & 3;
@@ -417,7 +426,7 @@ constexpr int H_A0 = (H_RES_BYTES + 127) / 128 * 128;      // A stages 8 KB each
 constexpr int H_B0 = H_A0 + H_NST * H_ACHUNK;              // B stages [256 x 32] 16 KB each
 constexpr int H_G = H_B0 + H_NST * H_CHUNK;                // G [128 x 256] 64 KB
 constexpr int H_CTRL = H_G + 128 * 256 * 2;                // mbarriers, TMEM address, abort
-constexpr int H_SMEM = H_CTRL + 320;
+constexpr int H_SMEM = H_CTRL + 256;
 // global image: [resident][W_h1 chunks x 16][W_h2 chunks x 8]
 constexpr int H_IMG_W1 = (H_RES_BYTES + 127) / 128 * 128;
 constexpr int H_IMG_W2 = H_IMG_W1 + H_L1C * H_CHUNK;
@@ -486,13 +495,13 @@ __device__ __forceinline__ void head_epi_256(uint32_t taddr, const float* b, uns
 //   full[s] / done[s]: one per chunk in stage s; L1D, L2D, L3: one per tile;
 //   GC0-GC3: one per tile (G chunk k holds layer 1); EPI: two per tile (G
 //   holds layer 2; outputs have left TMEM).
-constexpr int H_THREADS = 352;  // 8 epilogue warps, the copy warp, the MMA warp, the zeroer
-constexpr int H_COPY = 256, H_MMA_WARP = 9, H_ZERO_WARP = 10;
+constexpr int H_THREADS = 320;  // 8 epilogue warps, the copy warp, the MMA warp
+constexpr int H_COPY = 256, H_MMA_WARP = 9;
 __global__ void __launch_bounds__(H_THREADS, 1)
     head_tc_kernel(const __nv_bfloat16* __restrict__ ftile, PairRange rg,
                    const unsigned char* __restrict__ img, PairInputs in, int have_in,
-                   const float4* __restrict__ centre, const int32_t* __restrict__ cnt,
-                   float* __restrict__ out, float* __restrict__ y_raw, int* __restrict__ err) {
+                   const float4* __restrict__ centre, float* __restrict__ out,
+                   float* __restrict__ y_raw, int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char smem[];
   const int tid = threadIdx.x, warp = tid >> 5;
   int lo, n;
@@ -507,14 +516,11 @@ __global__ void __launch_bounds__(H_THREADS, 1)
   const uint32_t B_FULL = bar0, B_DONE = bar0 + 48;
   const uint32_t B_L3 = bar0 + 96, B_EPI = bar0 + 104, B_RES = bar0 + 112, B_DRAIN = bar0 + 120;
   const uint32_t B_L1D = bar0 + 128, B_L2D = bar0 + 136, B_GC = bar0 + 144;
-  // [32, 38): stage s ready for the MMAs (rows of empty objects zeroed)
-  const uint32_t B_READY = bar0 + 256;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + H_CTRL + 192);
   volatile int* abort = reinterpret_cast<volatile int*>(smem + H_CTRL + 196);
   int* s_issued = reinterpret_cast<int*>(smem + H_CTRL + 200);
   if (tid == 0) {
     for (int i = 0; i < 22; ++i) mbar_init(bar0 + 8 * i, (i == 13 || i >= 18) ? 256 : 1);
-    for (int i = 0; i < H_NST; ++i) mbar_init(B_READY + 8 * i, 32);
     *abort = 0;
     *s_issued = 0;
     fence_mbar_init();
@@ -611,8 +617,8 @@ __global__ void __launch_bounds__(H_THREADS, 1)
         if (j == 0 && t > 0) ok = mbar_wait_warp(B_EPI, (2 * t - 1) & 1, abort, WAIT_CYCLES);
         ok = ok && mbar_wait_warp(B_GC + 8 * (j >> 1), t & 1, abort, WAIT_CYCLES);
       }
-      ok = ok && mbar_wait_warp(B_READY + 8 * st0, (g / H_NST) & 1, abort, WAIT_CYCLES);
-      ok = ok && mbar_wait_warp(B_READY + 8 * st1, ((g + 1) / H_NST) & 1, abort, WAIT_CYCLES);
+      ok = ok && mbar_wait_warp(B_FULL + 8 * st0, (g / H_NST) & 1, abort, WAIT_CYCLES);
+      ok = ok && mbar_wait_warp(B_FULL + 8 * st1, ((g + 1) / H_NST) & 1, abort, WAIT_CYCLES);
       if (!ok) break;
       tc_fence_after();
       // descriptors from warp-uniform values; one elected lane issues
@@ -652,54 +658,6 @@ __global__ void __launch_bounds__(H_THREADS, 1)
     if (ok && l3 >= 0) {
       ok = mbar_wait_warp(B_EPI, (2 * l3) & 1, abort, WAIT_CYCLES);
       if (ok) layer3();
-    }
-    if (!ok) *abort = 1;
-  } else if (warp == H_ZERO_WARP) {
-    // ---------------------------------------------------------- zeroer warp
-    // An object with an empty crop has a pooled feature of exactly 0, which
-    // nothing writes to the feature tiles: once two layer-1 chunks have
-    // landed (the MMA warp takes them in pairs), this warp zeroes in shared
-    // memory the rows whose object on the chunks' side (chunks [0, 16): A,
-    // [16, 32): B) has crop count 0, then hands both stages to the MMA warp.
-    const int lane = tid & 31;
-    uint32_t mA = 0, mB = 0;  // this lane's rows (4 lane .. 4 lane + 3) with an empty A / B
-    for (int g = 0; g < n_chunks && ok; g += 2) {
-      const int st0 = g % H_NST, st1 = (g + 1) % H_NST, c = g % H_NCH, t = g / H_NCH;
-      if (c == 0) {
-        mA = mB = 0;
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          const int pr = lo + ((int)blockIdx.x + t * (int)gridDim.x) * HT + 4 * lane + i;
-          if (pr < n) {
-            mA |= (cnt[2 * (size_t)pr] == 0 ? 1u : 0u) << i;
-            mB |= (cnt[2 * (size_t)pr + 1] == 0 ? 1u : 0u) << i;
-          }
-        }
-      }
-      ok = mbar_wait_warp(B_FULL + 8 * st0, (g / H_NST) & 1, abort, WAIT_CYCLES);
-      ok = ok && mbar_wait_warp(B_FULL + 8 * st1, ((g + 1) / H_NST) & 1, abort, WAIT_CYCLES);
-      if (!ok) break;
-      const uint32_t m = c < H_L1C / 2 ? mA : (c < H_L1C ? mB : 0u);
-      if (m) {
-#pragma unroll
-        for (int k = 0; k < 2; ++k) {
-          unsigned char* a = smem + H_A0 + (k ? st1 : st0) * H_ACHUNK;
-#pragma unroll
-          for (int i = 0; i < 4; ++i) {
-            if (!((m >> i) & 1u)) continue;
-            const int r = 4 * lane + i;
-            unsigned char* p = a + (r >> 3) * 256 + (r & 7) * 16;  // K 0..7 of row r
-            const uint4 zz = make_uint4(0u, 0u, 0u, 0u);
-            *reinterpret_cast<uint4*>(p) = zz;
-            *reinterpret_cast<uint4*>(p + 128) = zz;           // K 8..15
-            *reinterpret_cast<uint4*>(p + FT_SUB) = zz;        // lo tile
-            *reinterpret_cast<uint4*>(p + FT_SUB + 128) = zz;
-          }
-        }
-        fence_async_smem();
-      }
-      mbar_arrive(B_READY + 8 * st0);
-      mbar_arrive(B_READY + 8 * st1);
     }
     if (!ok) *abort = 1;
   }
@@ -953,7 +911,8 @@ int run_network_tc(locc_handle* h, const float4* xyz, const PairRange& rg, const
   }
   const int grid_e = std::min(n_pairs, h->n_sm);
   encoder_tc_kernel<<<grid_e, E_THREADS, E_SMEM, stream>>>(xyz, rg, h->d_list, h->d_list_n,
-                                                           h->wtc_enc, feat_out, ftile, h->d_err);
+                                                           h->d_cnt, h->wtc_enc, feat_out, ftile,
+                                                           h->d_err);
   if (cudaGetLastError() != cudaSuccess) {
     set_error("encoder_tc_kernel launch failed");
     return LOCC_ERR_CUDA;
@@ -970,7 +929,7 @@ int launch_head_tc(locc_handle* h, const PairRange& rg, const PairInputs* in, co
   const int grid_h = std::min((n_pairs + HT - 1) / HT, h->n_sm);
   head_tc_kernel<<<grid_h, H_THREADS, H_SMEM, stream>>>(static_cast<__nv_bfloat16*>(h->d_feat_tc),
                                                         rg, h->wtc_head, pin, in != nullptr, centre,
-                                                        h->d_cnt, out, y_raw, h->d_err);
+                                                        out, y_raw, h->d_err);
   if (cudaGetLastError() != cudaSuccess) {
     set_error("head_tc_kernel launch failed");
     return LOCC_ERR_CUDA;
@@ -981,8 +940,8 @@ int launch_head_tc(locc_handle* h, const PairRange& rg, const PairInputs* in, co
 int launch_encoder_list(locc_handle* h, const float4* xyz, const PairRange& rg, const int* list,
                         const int* list_n, int grid, cudaStream_t stream) {
   encoder_tc_kernel<<<grid, E_THREADS, E_SMEM, stream>>>(
-      xyz, rg, list, list_n, h->wtc_enc, nullptr, static_cast<__nv_bfloat16*>(h->d_feat_tc),
-      h->d_err);
+      xyz, rg, list, list_n, nullptr, h->wtc_enc, nullptr,
+      static_cast<__nv_bfloat16*>(h->d_feat_tc), h->d_err);
   if (cudaGetLastError() != cudaSuccess) {
     set_error("encoder_tc_kernel launch failed");
     return LOCC_ERR_CUDA;
