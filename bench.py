@@ -56,13 +56,15 @@ FLOP_POINT = 2 * (3 * 64 + 64 * 128 + 128 * 256)           # encoder, per crop p
 FLOP_OBJ = 64 * FLOP_POINT
 WORKLOAD = "uneven_scenes_8192env_poisson8_64shapes"
 # DRAM bytes (read + write) per pair of the encoder kernel from one ncu capture
-# of the bench's scene 1 (154,924 pairs; the ncu summary of the crop, encoder
-# and head kernels under profiles/): scaled by the pairs of a launch to give
-# the per-launch traffic.
-ENC_DRAM_BYTES_PER_PAIR = {}
+# of the bench's scene at 4096 environments (76,965 pairs; the ncu summary of
+# the crop, encoder and head kernels under profiles/): scaled by the pairs of a
+# launch to give the per-launch traffic (both kernels' traffic grows in
+# proportion to the pairs).
+ENC_DRAM_BYTES_PER_PAIR = {"bf16": (205.417216e6 + 194.258944e6) / 76965,
+                           "fp8": (110.662912e6 + 25.118720e6) / 76965}
 # the same for the head kernel (same capture)
-HEAD_DRAM_BYTES_PER_PAIR = {"bf16": (164.736000e6 + 4.787200e6) / 154924,
-                            "fp8": (85.161728e6 + 2.337280e6) / 154924}
+HEAD_DRAM_BYTES_PER_PAIR = {"bf16": (160.763904e6 + 3.801600e6) / 76965,
+                            "fp8": (42.317824e6 + 0.0) / 76965}
 WEIGHTS = os.path.join(ROOT, "paper_2304_09439_b300", "weights", "locc_trained.bin")
 
 
@@ -145,9 +147,9 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def make_inputs(rank: int, n_sets: int):
+def make_inputs(rank: int, n_sets: int, n_env: int = N_ENV):
     lib = synth.make_library(N_SHAPES, LIB_SEED)
-    scenes = [synth.uneven_scene(N_ENV, N_SHAPES, seed=sd) for sd in rank_scene_seeds(rank, n_sets)]
+    scenes = [synth.uneven_scene(n_env, N_SHAPES, seed=sd) for sd in rank_scene_seeds(rank, n_sets)]
     return lib, scenes
 
 
@@ -505,6 +507,8 @@ def main():
     ap.add_argument("--serve-max-active", type=int, default=256,
                     help="requests admitted at once (sharing the launches)")
     ap.add_argument("--no-voxel", action="store_true", help="skip the voxel-latent variant leg")
+    ap.add_argument("--n-env", type=int, default=N_ENV,
+                    help="environments per scene (smaller scenes for profiler captures)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -525,10 +529,10 @@ def main():
     if world > 1:
         dist.init_process_group("nccl", device_id=dev)
 
-    lib, scenes = make_inputs(rank, args.sets)
+    lib, scenes = make_inputs(rank, args.sets, args.n_env)
     layers = trained_layers()
     det = Detector(lib.points, lib.aabb, layers, RADIUS, args.precision)
-    det.reserve(MAX_PAIRS, N_ENV)
+    det.reserve(MAX_PAIRS, args.n_env)
     dsc = []
     for poses, osh, env in scenes:
         dsc.append((torch.from_numpy(poses).to(dev), torch.from_numpy(osh).to(dev),
@@ -690,7 +694,9 @@ def main():
             "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": args.precision if args.precision != "fp8" else "e4m3",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n_env": N_ENV, "n_shapes": N_SHAPES,
+            "config": {"workload": (WORKLOAD if args.n_env == N_ENV else
+                                    f"uneven_scenes_{args.n_env}env_poisson8_64shapes"),
+                       "n_env": args.n_env, "n_shapes": N_SHAPES,
                        "pairs_per_step": per_step_pairs, "crop_radius": RADIUS,
                        "points_per_shape": 2048, "crop_points": 64, "precision": args.precision,
                        "l2": "flushed between steps (256 MiB write)",
