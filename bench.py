@@ -414,6 +414,61 @@ def oracle_configs(stream, reps: int = 20):
 FLOP_VOX = 2 * (2 * (23 * 128 + 2 * 128 * 128) + 3 * 128 * 128 + 128)  # predictor, per pair
 
 
+def train_leg(lib, dsc, scene_pairs, stream, flush, steps, warmup, batches=(1024, 8192),
+              precisions=("fp32", "bf16")):
+    """Training throughput: full Adam steps (crop, forward, loss, backward,
+    update) of the trainer on broadphase pairs of the bench scenes with
+    random labels, targets and augmentation rotations (values do not change
+    the work), in both trainer precisions.  L2 flushed between steps."""
+    import torch
+    from scipy.spatial.transform import Rotation
+    from paper_2304_09439_b300 import Detector, Trainer
+    rng = np.random.default_rng(11)
+    out = {"what": "training step (crop + forward + loss + backward + Adam) on broadphase "
+                   "pairs of the bench scenes", "weights_start": "trained", "batches": {}}
+    with Detector(lib.points, lib.aabb, trained_layers(), RADIUS, "fp32") as det:
+        for B in batches:
+            p, s, _ = dsc[0]
+            pairs = scene_pairs[0][:B].contiguous()
+            tgt = np.zeros((B, 8), np.float32)
+            tgt[:, 0] = rng.integers(0, 2, B)
+            tgt[:, 1:4] = rng.normal(0, 1, (B, 3))
+            nv = rng.normal(size=(B, 3))
+            tgt[:, 4:7] = nv / np.linalg.norm(nv, axis=1, keepdims=True)
+            tgt[:, 7] = rng.normal(0, 0.03, B)
+            tt = torch.from_numpy(tgt).to(p.device)
+            rot = torch.from_numpy(Rotation.random(B, random_state=5).as_matrix()
+                                   .reshape(B, 9).astype(np.float32)).to(p.device)
+            row = {}
+            for prec in precisions:
+                tr = Trainer(det, B, precision=prec, w_len=2.0)
+                loss = torch.zeros(1, dtype=torch.float32, device=p.device)
+                for _ in range(warmup):
+                    flush.zero_()
+                    tr.step(p, s, pairs, tt, rot, update=True, loss_out=loss, stream=stream)
+                torch.cuda.synchronize()
+                ms = 0.0
+                n = max(3, steps // (4 if prec == "fp32" else 1))
+                for _ in range(n):
+                    flush.zero_()
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    tr.step(p, s, pairs, tt, rot, update=True, loss_out=loss, stream=stream)
+                    e1.record(stream)
+                    e1.synchronize()
+                    ms += e0.elapsed_time(e1)
+                det.status()
+                if not np.isfinite(loss.item()):
+                    raise RuntimeError(f"training loss not finite ({prec}, batch {B})")
+                tr.close()
+                row[prec] = {"pairs_per_s": B * n / (ms * 1e-3), "ms_per_step": ms / n,
+                             "steps": n}
+            if "bf16" in row and "fp32" in row:
+                row["bf16_over_fp32"] = row["bf16"]["pairs_per_s"] / row["fp32"]["pairs_per_s"]
+            out["batches"][str(B)] = row
+    return out
+
+
 def voxel_leg(lib, dsc, scene_pairs, stream, flush, steps, warmup, peaks):
     """The voxel-latent variant (the paper's own design) on the same scenes:
     latents of the 64-shape library, then per step the cell selection,
@@ -507,6 +562,12 @@ def main():
     ap.add_argument("--serve-max-active", type=int, default=256,
                     help="requests admitted at once (sharing the launches)")
     ap.add_argument("--no-voxel", action="store_true", help="skip the voxel-latent variant leg")
+    ap.add_argument("--no-train", action="store_true", help="skip the training-throughput leg")
+    ap.add_argument("--train-only", action="store_true",
+                    help="run only the training leg and print its JSON (profiler captures)")
+    ap.add_argument("--train-batches", default="1024,8192",
+                    help="comma-separated training batch sizes of the training leg")
+    ap.add_argument("--train-precisions", default="fp32,bf16")
     ap.add_argument("--n-env", type=int, default=N_ENV,
                     help="environments per scene (smaller scenes for profiler captures)")
     args = ap.parse_args()
@@ -561,6 +622,13 @@ def main():
         valid_rows.append(int(cnt.sum().item()))
         nonempty.append(int((cnt > 0).sum().item()))
 
+    if args.train_only:
+        training = train_leg(lib, dsc, scene_pairs, stream, flush, args.steps, args.warmup,
+                             tuple(int(b) for b in args.train_batches.split(",")),
+                             tuple(args.train_precisions.split(",")))
+        print(json.dumps({"training": training}), flush=True)
+        det.close()
+        return
     # pipelining: autotuned on the first scene, or given
     if args.pipeline == "auto":
         (chunks, cap), tune_ms = det.autotune(*dsc[0], MAX_PAIRS, reps=3, pairs_out=pairs_buf,
@@ -684,6 +752,11 @@ def main():
         voxel = None
         if not args.no_voxel:
             voxel = voxel_leg(lib, dsc, scene_pairs, stream, flush, args.steps, args.warmup, peaks)
+        training = None
+        if not args.no_train and world == 1:
+            training = train_leg(lib, dsc, scene_pairs, stream, flush, args.steps, args.warmup,
+                                 tuple(int(b) for b in args.train_batches.split(",")),
+                                 tuple(args.train_precisions.split(",")))
         serving = None
         if args.serve_seconds > 0:
             serving = serving_leg(det, args.serve_seconds, args.serve_rate,
@@ -752,6 +825,7 @@ def main():
                        "hyper-parameter table); quoted as context, not a target",
             "serving": serving,
             "voxel_path": voxel,
+            "training": training,
             "wall_s_timed": t_wall,
         }
         print(json.dumps(line), flush=True)

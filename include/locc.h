@@ -341,6 +341,15 @@ int locc_trainer_commit(locc_trainer *t);
  * takes effect at the next locc_train_step.  lr >= 0 and finite, else
  * LOCC_ERR_INVALID_ARG. */
 int locc_trainer_set_lr(locc_trainer *t, float lr);
+/* Arithmetic of the following steps (host-side; default LOCC_FP32):
+ *   LOCC_FP32: float32 CUDA-core products (gradients to float32 rounding);
+ *   LOCC_BF16: the dense products of forward and backward on the tensor
+ *     cores with bf16 operands and float32 accumulation; parameters, Adam
+ *     moments, activations and gradients stay float32.  Layer 3's backward
+ *     is computed sparsely (its gradient is non-zero only at each channel's
+ *     argmax row, Sec. III-A max-pooling) in float32.
+ * Other values: LOCC_ERR_INVALID_ARG. */
+int locc_trainer_set_precision(locc_trainer *t, int32_t precision);
 void locc_trainer_destroy(locc_trainer *t);
 
 /* ---------------------------------------------------------------- serving

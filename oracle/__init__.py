@@ -69,8 +69,10 @@ def _load():
         lib.orb_run_global.restype = I
         lib.orb_network.argtypes = [P, P, P, I, I, P, P]
         lib.orb_network.restype = I
-        lib.orb_loss_grad.argtypes = [P, P, P, P, I, I, P, P]
+        lib.orb_loss_grad.argtypes = [P, P, P, P, I, I, P, I, P]
         lib.orb_loss_grad.restype = ctypes.c_double
+        lib.orb_bf16.argtypes = [ctypes.c_double]
+        lib.orb_bf16.restype = ctypes.c_double
         lib.orb_n_params.restype = I
         lib.ora_contact_batch.argtypes = [P, P, P, P, P, P, I, P, P, P, I, I,
                                           P, I]
@@ -175,8 +177,14 @@ DEFAULT_LOSS_HP = (1.0, 1.0, 1.0, 0.01, 0.5, 0.0)  # w_pt, w_n, w_d, huber beta,
 
 
 def loss_grad(params: np.ndarray, xyz: np.ndarray, cnt: np.ndarray,
-              tgt: np.ndarray, hp=DEFAULT_LOSS_HP, kmax: int = KMAX):
-    """Mean training loss over the pairs and its gradient (flat float64)."""
+              tgt: np.ndarray, hp=DEFAULT_LOSS_HP, kmax: int = KMAX, operands: str = "exact"):
+    """Mean training loss over the pairs and its gradient (flat float64).
+
+    operands="bf16" rounds both operands of the matrix-product layers to
+    bfloat16 before their float64 products (the arithmetic of a bf16
+    tensor-core trainer; which products, in oracle_b.c's header)."""
+    if operands not in ("exact", "bf16"):
+        raise ValueError(f"operands must be 'exact' or 'bf16', not {operands!r}")
     lib = _load()
     params = _c(params, np.float64)
     xyz = _c(xyz, np.float32)
@@ -186,8 +194,15 @@ def loss_grad(params: np.ndarray, xyz: np.ndarray, cnt: np.ndarray,
     assert hp.size == 6
     g = np.empty(N_PARAMS, np.float64)
     L = lib.orb_loss_grad(_ptr(params), _ptr(xyz), _ptr(cnt), _ptr(tgt),
-                          cnt.shape[0], kmax, _ptr(hp), _ptr(g))
+                          cnt.shape[0], kmax, _ptr(hp), int(operands == "bf16"), _ptr(g))
     return float(L), g
+
+
+def round_bf16(x) -> np.ndarray:
+    """The oracle's bfloat16 rounding (orb_bf16) of each value, as float64."""
+    lib = _load()
+    a = np.asarray(x, np.float64)
+    return np.array([lib.orb_bf16(float(v)) for v in a.ravel()], np.float64).reshape(a.shape)
 
 
 def broadphase(aabb, poses, obj_shape, env_offsets) -> np.ndarray:

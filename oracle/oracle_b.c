@@ -33,6 +33,19 @@
  * written below (this file must be compiled with -ffp-contract=off and without
  * -ffast-math), so that crop index sets are reproducible bit for bit.  Steps
  * 5-7 run in float64 with the float32 parameters widened.
+ *
+ * Operand mode "bf16" of the loss and gradient (orb_loss_grad, bf16 != 0):
+ * the same float64 arithmetic, except that both operands of every product
+ * that a bf16 tensor-core trainer runs as a matrix multiply are first rounded
+ * to bfloat16 (orb_bf16: to float32, then to 8 significant bits, ties to
+ * even).  Those products: layers 2 and 3 of the encoder and layers 1 and 2 of
+ * the head in the forward pass, and in the backward pass the weight
+ * gradients and the input gradients of those head layers and of encoder layer
+ * 2.  Everything else stays unrounded: encoder layer 1, the head's output
+ * layer, the loss, layer 3's backward (sparse: only argmax rows), biases.
+ * The max-pool's argmax is then decided on the same rounded operands as in
+ * such a trainer, which leaves only the float32-versus-float64 accumulation
+ * between the two.
  */
 #include <math.h>
 #include <pthread.h>
@@ -244,13 +257,45 @@ static void orb_relu(double *v, int n) {
     if (v[i] < 0.0) v[i] = 0.0;
 }
 
+/* bfloat16 rounding of a value held in float32: 8 significant bits (the
+ * implicit one and 7 stored), round to nearest, ties to even.  Zero, inf and
+ * NaN pass through; values below the normal range are not met here. */
+double orb_bf16(double v) {
+  const float f = (float)v;
+  if (f == 0.0f || !isfinite(f)) return (double)f;
+  int e;
+  const double m = frexp((double)f, &e); /* f = m 2^e, 0.5 <= |m| < 1 */
+  return ldexp(nearbyint(ldexp(m, 8)), e - 8);
+}
+
+/* dst[i] = orb_bf16(src[i]) when bf16, else a copy. */
+static void orb_operand(const double *src, int n, int bf16, double *dst) {
+  for (int i = 0; i < n; ++i) dst[i] = bf16 ? orb_bf16(src[i]) : src[i];
+}
+
+/* Per-object encoder forward of point k: h1 (layer 1, unrounded), h2
+ * (layer 2 on bf16 operands in bf16 mode; Pr holds the rounded weights) and
+ * h3 (layer 3 likewise), each after its ReLU. */
+static void orb_encode_point(const double *P, const double *Pr, int bf16, const double x[3],
+                             double h1[64], double h2[128], double h3[256]) {
+  int offW[6], offb[6];
+  orb_layer_offsets(offW, offb);
+  double t1[64], t2[128];
+  orb_affine(P + offW[0], P + offb[0], x, 3, 64, h1);
+  orb_relu(h1, 64);
+  orb_operand(h1, 64, bf16, t1);
+  orb_affine(Pr + offW[1], P + offb[1], t1, 64, 128, h2);
+  orb_relu(h2, 128);
+  orb_operand(h2, 128, bf16, t2);
+  orb_affine(Pr + offW[2], P + offb[2], t2, 128, 256, h3);
+  orb_relu(h3, 256);
+}
+
 /* Per-object encoder of up to kmax points; writes pooled [256] and, if
  * argmax != NULL, the index of the point that realises each channel's max
  * (ties to the lower point slot; -1 when the crop is empty). */
-static void orb_encode(const double *P, const float *xyz, int cnt,
-                       double *pooled, int *argmax) {
-  int offW[6], offb[6];
-  orb_layer_offsets(offW, offb);
+static void orb_encode_mode(const double *P, const double *Pr, int bf16, const float *xyz,
+                            int cnt, double *pooled, int *argmax) {
   for (int c = 0; c < ORB_FEAT; ++c) {
     pooled[c] = 0.0;
     if (argmax) argmax[c] = -1;
@@ -258,12 +303,7 @@ static void orb_encode(const double *P, const float *xyz, int cnt,
   double x[3], h1[64], h2[128], h3[256];
   for (int k = 0; k < cnt; ++k) {
     for (int a = 0; a < 3; ++a) x[a] = (double)xyz[3 * k + a];
-    orb_affine(P + offW[0], P + offb[0], x, 3, 64, h1);
-    orb_relu(h1, 64);
-    orb_affine(P + offW[1], P + offb[1], h1, 64, 128, h2);
-    orb_relu(h2, 128);
-    orb_affine(P + offW[2], P + offb[2], h2, 128, 256, h3);
-    orb_relu(h3, 256);
+    orb_encode_point(P, Pr, bf16, x, h1, h2, h3);
     for (int c = 0; c < ORB_FEAT; ++c) {
       if (k == 0 || h3[c] > pooled[c]) {
         pooled[c] = h3[c];
@@ -271,6 +311,10 @@ static void orb_encode(const double *P, const float *xyz, int cnt,
       }
     }
   }
+}
+
+static void orb_encode(const double *P, const float *xyz, int cnt, double *pooled, int *argmax) {
+  orb_encode_mode(P, P, 0, xyz, cnt, pooled, argmax);
 }
 
 /* Head on f = [f_A, f_B] (512) -> raw outputs y[8] (canonical frame). */
@@ -281,6 +325,22 @@ static void orb_head(const double *P, const double *f, double *g1, double *g2,
   orb_affine(P + offW[3], P + offb[3], f, 512, 256, g1);
   orb_relu(g1, 256);
   orb_affine(P + offW[4], P + offb[4], g1, 256, 256, g2);
+  orb_relu(g2, 256);
+  orb_affine(P + offW[5], P + offb[5], g2, 256, 8, y);
+}
+
+/* The head in either operand mode: g1 = relu(W4 f + b4), g2 = relu(W5 g1 + b5)
+ * with bf16 operands in bf16 mode, y = W6 g2 + b6 unrounded. */
+static void orb_head_mode(const double *P, const double *Pr, int bf16, const double *f,
+                          double *g1, double *g2, double *y) {
+  int offW[6], offb[6];
+  orb_layer_offsets(offW, offb);
+  double fr[512], g1r[256];
+  orb_operand(f, 512, bf16, fr);
+  orb_affine(Pr + offW[3], P + offb[3], fr, 512, 256, g1);
+  orb_relu(g1, 256);
+  orb_operand(g1, 256, bf16, g1r);
+  orb_affine(Pr + offW[4], P + offb[4], g1r, 256, 256, g2);
   orb_relu(g2, 256);
   orb_affine(P + offW[5], P + offb[5], g2, 256, 8, y);
 }
@@ -540,15 +600,15 @@ static double orb_pair_loss(const double *y, const double *f, const double *tgt,
 /* Backward through the encoder of one object: dpool [256] -> grads.  The
  * gradient of the max-pool goes to the point that realises each channel's
  * max (ties to the lower slot); ReLU passes gradient where its output > 0. */
-static void orb_encode_backward(const double *P, const float *xyz, int cnt,
-                                const double *dpool, double *G) {
+static void orb_encode_backward(const double *P, const double *Pr, int bf16, const float *xyz,
+                                int cnt, const double *dpool, double *G) {
   int offW[6], offb[6];
   orb_layer_offsets(offW, offb);
   if (cnt <= 0) return;
   double pooled[256];
   int am[256];
-  orb_encode(P, xyz, cnt, pooled, am);
-  double x[3], h1[64], h2[128], h3[256], d3[256], d2[128], d1[64];
+  orb_encode_mode(P, Pr, bf16, xyz, cnt, pooled, am);
+  double x[3], h1[64], h2[128], h3[256], d3[256], d2[128], d1[64], h1r[64], d2r[128];
   for (int k = 0; k < cnt; ++k) {
     int any = 0;
     for (int c = 0; c < 256; ++c) {
@@ -560,11 +620,7 @@ static void orb_encode_backward(const double *P, const float *xyz, int cnt,
     }
     if (!any) continue;
     for (int a = 0; a < 3; ++a) x[a] = (double)xyz[3 * k + a];
-    orb_affine(P + offW[0], P + offb[0], x, 3, 64, h1);
-    orb_relu(h1, 64);
-    orb_affine(P + offW[1], P + offb[1], h1, 64, 128, h2);
-    orb_relu(h2, 128);
-    orb_affine(P + offW[2], P + offb[2], h2, 128, 256, h3);
+    orb_encode_point(P, Pr, bf16, x, h1, h2, h3);
     /* layer 3: d3 already masked by h3 > 0 via pooled > 0 */
     for (int o = 0; o < 256; ++o) {
       if (d3[o] == 0.0) continue;
@@ -576,13 +632,16 @@ static void orb_encode_backward(const double *P, const float *xyz, int cnt,
       for (int o = 0; o < 256; ++o) s += P[offW[2] + o * 128 + i] * d3[o];
       d2[i] = h2[i] > 0.0 ? s : 0.0;
     }
+    /* layer 2 (a matrix product in bf16 mode: d2 and h1 rounded) */
+    orb_operand(d2, 128, bf16, d2r);
+    orb_operand(h1, 64, bf16, h1r);
     for (int o = 0; o < 128; ++o) {
       G[offb[1] + o] += d2[o];
-      for (int i = 0; i < 64; ++i) G[offW[1] + o * 64 + i] += d2[o] * h1[i];
+      for (int i = 0; i < 64; ++i) G[offW[1] + o * 64 + i] += d2r[o] * h1r[i];
     }
     for (int i = 0; i < 64; ++i) {
       double s = 0.0;
-      for (int o = 0; o < 128; ++o) s += P[offW[1] + o * 64 + i] * d2[o];
+      for (int o = 0; o < 128; ++o) s += Pr[offW[1] + o * 64 + i] * d2r[o];
       d1[i] = h1[i] > 0.0 ? s : 0.0;
     }
     for (int o = 0; o < 64; ++o) {
@@ -597,19 +656,27 @@ static void orb_encode_backward(const double *P, const float *xyz, int cnt,
  * Accumulates the gradient of the mean loss into grad (zeroed here). */
 double orb_loss_grad(const double *params, const float *xyz, const int32_t *cnt,
                      const double *tgt, int n_pairs, int kmax, const double *hp,
-                     double *grad) {
+                     int bf16, double *grad) {
   int offW[6], offb[6];
   orb_layer_offsets(offW, offb);
   int np = orb_n_params();
   memset(grad, 0, sizeof(double) * (size_t)np);
+  /* Pr: the weights of the matrix-product layers rounded in bf16 mode */
+  double *Pr = (double *)malloc(sizeof(double) * (size_t)np);
+  if (!Pr) return NAN;
+  memcpy(Pr, params, sizeof(double) * (size_t)np);
+  if (bf16)
+    for (int l = 1; l <= 4; ++l)
+      for (int i = offW[l]; i < offb[l]; ++i) Pr[i] = orb_bf16(params[i]);
   double total = 0.0;
   double f[512], g1[256], g2[256], y[8], dy[8], df[512], dg2[256], dg1[256];
+  double fr[512], g1r[256], dg2r[256], dg1r[256];
   for (int p = 0; p < n_pairs; ++p) {
     const float *x = xyz + (size_t)p * 6 * kmax;
     int ca = cnt[2 * p], cb = cnt[2 * p + 1];
-    orb_encode(params, x, ca, f, NULL);
-    orb_encode(params, x + 3 * kmax, cb, f + 256, NULL);
-    orb_head(params, f, g1, g2, y);
+    orb_encode_mode(params, Pr, bf16, x, ca, f, NULL);
+    orb_encode_mode(params, Pr, bf16, x + 3 * kmax, cb, f + 256, NULL);
+    orb_head_mode(params, Pr, bf16, f, g1, g2, y);
     total += orb_pair_loss(y, f, tgt + 8 * (size_t)p, hp, dy, df);
     double s = 1.0 / n_pairs;
     for (int i = 0; i < 8; ++i) dy[i] *= s;
@@ -624,27 +691,33 @@ double orb_loss_grad(const double *params, const float *xyz, const int32_t *cnt,
       for (int o = 0; o < 8; ++o) t += params[offW[5] + o * 256 + i] * dy[o];
       dg2[i] = g2[i] > 0.0 ? t : 0.0;
     }
+    /* head layers 2 and 1 (matrix products in bf16 mode) */
+    orb_operand(dg2, 256, bf16, dg2r);
+    orb_operand(g1, 256, bf16, g1r);
     for (int o = 0; o < 256; ++o) {
       grad[offb[4] + o] += dg2[o];
-      for (int i = 0; i < 256; ++i) grad[offW[4] + o * 256 + i] += dg2[o] * g1[i];
+      for (int i = 0; i < 256; ++i) grad[offW[4] + o * 256 + i] += dg2r[o] * g1r[i];
     }
     for (int i = 0; i < 256; ++i) {
       double t = 0.0;
-      for (int o = 0; o < 256; ++o) t += params[offW[4] + o * 256 + i] * dg2[o];
+      for (int o = 0; o < 256; ++o) t += Pr[offW[4] + o * 256 + i] * dg2r[o];
       dg1[i] = g1[i] > 0.0 ? t : 0.0;
     }
+    orb_operand(dg1, 256, bf16, dg1r);
+    orb_operand(f, 512, bf16, fr);
     for (int o = 0; o < 256; ++o) {
       grad[offb[3] + o] += dg1[o];
-      for (int i = 0; i < 512; ++i) grad[offW[3] + o * 512 + i] += dg1[o] * f[i];
+      for (int i = 0; i < 512; ++i) grad[offW[3] + o * 512 + i] += dg1r[o] * fr[i];
     }
     for (int i = 0; i < 512; ++i) {
       double t = 0.0;
-      for (int o = 0; o < 256; ++o) t += params[offW[3] + o * 512 + i] * dg1[o];
+      for (int o = 0; o < 256; ++o) t += Pr[offW[3] + o * 512 + i] * dg1r[o];
       df[i] += t;
     }
-    orb_encode_backward(params, x, ca, df, grad);
-    orb_encode_backward(params, x + 3 * kmax, cb, df + 256, grad);
+    orb_encode_backward(params, Pr, bf16, x, ca, df, grad);
+    orb_encode_backward(params, Pr, bf16, x + 3 * kmax, cb, df + 256, grad);
   }
+  free(Pr);
   return total / n_pairs;
 }
 

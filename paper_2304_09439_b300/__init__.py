@@ -402,7 +402,8 @@ class Trainer:
     """Owns one ``locc_trainer`` (GPU training of a Detector's network)."""
 
     def __init__(self, det: "Detector", max_batch: int, lr=1e-3, beta1=0.9, beta2=0.999,
-                 eps=1e-8, w_pt=1.0, w_n=1.0, w_d=1.0, huber_beta=0.01, alpha=0.5, w_len=0.0):
+                 eps=1e-8, w_pt=1.0, w_n=1.0, w_d=1.0, huber_beta=0.01, alpha=0.5, w_len=0.0,
+                 precision: str = "fp32"):
         self._lib = abi.load()
         self.det = det
         self.max_batch = int(max_batch)
@@ -410,6 +411,15 @@ class Trainer:
         self._t = ctypes.c_void_p()
         abi.check(self._lib.locc_trainer_create(det._h, self.max_batch, ctypes.byref(cfg),
                                                 ctypes.byref(self._t)))
+        self.set_precision(precision)
+
+    def set_precision(self, precision: str) -> None:
+        """"fp32" (CUDA-core products) or "bf16" (tensor cores, bf16 operands,
+        float32 accumulation and state) for the following steps."""
+        if precision not in ("fp32", "bf16"):
+            raise ValueError(f"training precision must be 'fp32' or 'bf16', not {precision!r}")
+        abi.check(self._lib.locc_trainer_set_precision(self._t, abi.PRECISIONS[precision]))
+        self.precision = precision
 
     def close(self) -> None:
         if getattr(self, "_t", None) is not None and self._t.value:

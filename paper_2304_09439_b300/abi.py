@@ -34,7 +34,8 @@ EXPORTS = ["locc_create", "locc_set_precision", "locc_detect", "locc_detect_host
            "locc_voxel_set_precision",
            "locc_voxel_destroy", "locc_sim_step", "locc_sphere_contacts", "locc_set_crop_mode",
            "locc_gjk_create", "locc_gjk_detect", "locc_gjk_status", "locc_gjk_destroy",
-           "locc_selftest_wait_timeout", "locc_trainer_get_state", "locc_trainer_set_state"]
+           "locc_selftest_wait_timeout", "locc_trainer_get_state", "locc_trainer_set_state",
+           "locc_trainer_set_precision"]
 VOID_EXPORTS = ("locc_destroy", "locc_last_error", "locc_trainer_destroy", "locc_server_destroy",
                 "locc_voxel_destroy", "locc_gjk_destroy")
 
@@ -149,6 +150,7 @@ def load(build_if_needed: bool = True) -> ctypes.CDLL:
         lib.locc_trainer_set_params.argtypes = [P, P, P]
         lib.locc_trainer_commit.argtypes = [P]
         lib.locc_trainer_set_lr.argtypes = [P, ctypes.c_float]
+        lib.locc_trainer_set_precision.argtypes = [P, I]
         lib.locc_trainer_destroy.argtypes = [P]
         lib.locc_trainer_destroy.restype = None
         lib.locc_server_create.argtypes = [P, ctypes.POINTER(ServerConfig), ctypes.POINTER(P)]

@@ -128,4 +128,18 @@ int run_network_fp8(locc_handle* h, const float4* xyz, const PairRange& rg, cons
 int run_network_tc(locc_handle* h, const float4* xyz, const PairRange& rg, const PairInputs* in,
                    const float4* centre, float* out, float* y_raw, float* feat_out,
                    cudaStream_t stream, cudaEvent_t mid, int list_mode);
+// Tensor-core products of the BF16 trainer (train_tc.cu): same operand and
+// epilogue conventions as the trainer's float32 GEMM; err gets bit 2 when a
+// bounded wait runs out.
+cudaError_t prepare_train_tc_kernels();
+cudaError_t tg_gemm(bool ta, bool tb, int M, int N, int K, const float* A, int lda, const float* B,
+                    int ldb, float* C, int ldc, const float* bias, const float* mask, int ldm,
+                    bool relu, bool accumulate, int splits, int* err, cudaStream_t s);
+cudaError_t tg_layer3_pool(const float* W3, const float* b3, const float* H2, const float* X, int P,
+                           float* F, int32_t* amax, int* err, cudaStream_t s);
+cudaError_t tg_layer1_grad(const float* dH2, const float* W2, const float* X, const float* W1,
+                           const float* b1, int M, float* gW1, float* gB1, int* err, cudaStream_t s);
+cudaError_t sparse_layer3_backward(const float* dF, const float* F, const int32_t* amax,
+                                   const float* W3, const float* H2, int P, float* dH2, float* gW3,
+                                   float* gB3, float* gB2, int n_sm, cudaStream_t s);
 }  // namespace locc

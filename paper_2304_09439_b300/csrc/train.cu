@@ -15,8 +15,14 @@
 //   -> Z3 = H2 W3^T + b3 -> masked max-pool with argmax -> G1, G2, Y (head) ->
 //   loss and dL/dY -> head backward -> scatter of dL/dF to the argmax rows ->
 //   encoder backward -> Adam.
-// Matrix products use one tiled SIMT kernel (64 x 64 tiles, 4 x 4 per thread)
-// with optional transposes, bias, ReLU, ReLU-mask and split-K accumulation.
+// Two precisions (locc_trainer_set_precision):
+//   LOCC_FP32: every matrix product in one tiled SIMT kernel (64 x 64 tiles,
+//     4 x 4 per thread) with optional transposes, bias, ReLU, ReLU-mask and
+//     split-K accumulation; dZ3 formed densely from the argmax scatter.
+//   LOCC_BF16: the dense products on the tensor cores (train_tc.cu: bf16
+//     operands, float32 accumulation; layer 3 pooled in its epilogue, layer 1's
+//     gradient reduced in the epilogue of dH1), the sparse layer-3 backward
+//     on the CUDA cores without dZ3, the tiny products (N or K = 8) in SIMT.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -30,6 +36,8 @@ struct locc_trainer {
   int max_batch = 0;
   locc_train_config cfg{};
   long long step = 0;
+  int precision = LOCC_FP32;
+  int batch = 0;  // pairs of the current step
   float* params = nullptr;  // flat W [out][in], b [out] per layer
   float* grad = nullptr;
   float* m = nullptr;
@@ -240,11 +248,10 @@ __global__ void pool_kernel(const float* __restrict__ Z3, const float* __restric
   amax[i] = arg;
 }
 
-// Loss per pair and dL/dY (mean over the batch), plus the embedding
-// regulariser's gradient into dF.
+// Loss per pair (without the embedding regulariser, feat_reg_kernel) and
+// dL/dY, both as shares of the mean over the batch.
 __global__ void loss_kernel(const float* __restrict__ Y, const float* __restrict__ T,
-                            const float* __restrict__ F, float* __restrict__ dY,
-                            float* __restrict__ dF, float* __restrict__ loss, int P,
+                            float* __restrict__ dY, float* __restrict__ loss, int P,
                             locc_train_config cfg) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   float L = 0.f;
@@ -291,14 +298,6 @@ __global__ void loss_kernel(const float* __restrict__ Y, const float* __restrict
       L += cfg.w_d * (fabsf(e) - 0.5f * cfg.huber_beta);
       g[7] = cfg.w_d * (e > 0.f ? 1.f : -1.f);
     }
-    float sq = 0.f;
-    const float* f = F + 512 * (size_t)p;
-    float* df = dF + 512 * (size_t)p;
-    for (int i = 0; i < 512; ++i) {
-      sq += f[i] * f[i];
-      df[i] = cfg.alpha * 2.f * f[i] / 512.f * inv;
-    }
-    L += cfg.alpha * sq / 512.f;
     for (int i = 0; i < 8; ++i) dy[i] = g[i] * inv;
     L *= inv;
   }
@@ -311,6 +310,28 @@ __global__ void loss_kernel(const float* __restrict__ Y, const float* __restrict
     __syncthreads();
   }
   if (threadIdx.x == 0 && loss) atomicAdd(loss, red[0]);
+}
+
+// The embedding regulariser alpha mean(f^2) of every pair, one thread per
+// feature: its share of the mean loss and dL/dF = 2 alpha f / 512 / P.
+__global__ void feat_reg_kernel(const float* __restrict__ F, float* __restrict__ dF,
+                                float* __restrict__ loss, int P, float alpha) {
+  const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  const float inv = 1.f / P;
+  float sq = 0.f;
+  if (i < (size_t)P * 512) {
+    const float f = F[i];
+    dF[i] = alpha * 2.f * f / 512.f * inv;
+    sq = f * f;
+  }
+  __shared__ float red[256];
+  red[threadIdx.x] = sq;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if ((int)threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0 && loss) atomicAdd(loss, alpha * red[0] / 512.f * inv);
 }
 
 // dZ3 rows: dL/dF of channel c goes to the argmax slot of that channel (when
@@ -398,6 +419,111 @@ void trainer_free(locc_trainer* t) {
                   t->dH1, t->dH2, t->loss};
   for (void* p : ptrs) cudaFree(p);
 }
+
+// Forward, loss and backward of one batch in float32 SIMT (gradients into
+// t->grad, which the caller zeroed).
+int fp32_pass(locc_trainer* t, cudaStream_t s) {
+  const int P = t->batch, M = P * ROWS;
+  const float* prm = t->params;
+  auto W = [&](int l) { return prm + PARAM_OFF_W[l]; };
+  auto Bv = [&](int l) { return prm + PARAM_OFF_B[l]; };
+  float* g = t->grad;
+  auto gW = [&](int l) { return g + PARAM_OFF_W[l]; };
+  auto gB = [&](int l) { return g + PARAM_OFF_B[l]; };
+  layer1_kernel<<<(unsigned)(((size_t)M * 64 + 255) / 256), 256, 0, s>>>(t->X, W(0), Bv(0), t->H1, M);
+  TCU(cudaGetLastError());
+  TCU((gemm<false, true>(M, 128, 64, t->H1, 64, W(1), 64, t->H2, 128, Bv(1), nullptr, 0, true, false, 1, s)));
+  TCU((gemm<false, true>(M, 256, 128, t->H2, 128, W(2), 128, t->Z3, 256, Bv(2), nullptr, 0, false, false, 1, s)));
+  pool_kernel<<<(unsigned)(((size_t)P * 512 + 255) / 256), 256, 0, s>>>(t->Z3, t->X, t->F, t->amax, P);
+  TCU(cudaGetLastError());
+  TCU((gemm<false, true>(P, 256, 512, t->F, 512, W(3), 512, t->G1, 256, Bv(3), nullptr, 0, true, false, 1, s)));
+  TCU((gemm<false, true>(P, 256, 256, t->G1, 256, W(4), 256, t->G2, 256, Bv(4), nullptr, 0, true, false, 1, s)));
+  TCU((gemm<false, true>(P, 8, 256, t->G2, 256, W(5), 256, t->Y, 8, Bv(5), nullptr, 0, false, false, 1, s)));
+  loss_kernel<<<(P + 255) / 256, 256, 0, s>>>(t->Y, t->T, t->dY, t->loss, P, t->cfg);
+  feat_reg_kernel<<<(unsigned)(((size_t)P * 512 + 255) / 256), 256, 0, s>>>(t->F, t->dF, t->loss, P,
+                                                                           t->cfg.alpha);
+  TCU(cudaGetLastError());
+  // ---- head backward
+  const int split_p = std::max(1, P / 64);
+  TCU((gemm<true, false>(8, 256, P, t->dY, 8, t->G2, 256, gW(5), 256, nullptr, nullptr, 0, false, true, split_p, s)));
+  TCU((gemm<false, false>(P, 256, 8, t->dY, 8, W(5), 256, t->dG2, 256, nullptr, t->G2, 256, false, false, 1, s)));
+  TCU((gemm<true, false>(256, 256, P, t->dG2, 256, t->G1, 256, gW(4), 256, nullptr, nullptr, 0, false, true, split_p, s)));
+  TCU((gemm<false, false>(P, 256, 256, t->dG2, 256, W(4), 256, t->dG1, 256, nullptr, t->G1, 256, false, false, 1, s)));
+  TCU((gemm<true, false>(256, 512, P, t->dG1, 256, t->F, 512, gW(3), 512, nullptr, nullptr, 0, false, true, split_p, s)));
+  TCU((gemm<false, false>(P, 512, 256, t->dG1, 256, W(3), 512, t->dF, 512, nullptr, nullptr, 0, false, true, 1, s)));
+  {
+    dim3 gb(1, std::max(1, (P + 63) / 64));
+    colsum_kernel<<<gb, 256, 0, s>>>(t->dY, P, 8, gB(5), 64);
+    colsum_kernel<<<gb, 256, 0, s>>>(t->dG2, P, 256, gB(4), 64);
+    colsum_kernel<<<gb, 256, 0, s>>>(t->dG1, P, 256, gB(3), 64);
+    TCU(cudaGetLastError());
+  }
+  // ---- encoder backward (dZ3 reuses the Z3 buffer)
+  float* dZ3 = t->Z3;
+  TCU(cudaMemsetAsync(dZ3, 0, (size_t)M * 256 * 4, s));
+  scatter_kernel<<<(unsigned)(((size_t)P * 512 + 255) / 256), 256, 0, s>>>(t->dF, t->F, t->amax, dZ3, P);
+  TCU(cudaGetLastError());
+  const int split_m = std::max(1, M / 1024);
+  TCU((gemm<true, false>(256, 128, M, dZ3, 256, t->H2, 128, gW(2), 128, nullptr, nullptr, 0, false, true, split_m, s)));
+  TCU((gemm<false, false>(M, 128, 256, dZ3, 256, W(2), 128, t->dH2, 128, nullptr, t->H2, 128, false, false, 1, s)));
+  TCU((gemm<true, false>(128, 64, M, t->dH2, 128, t->H1, 64, gW(1), 64, nullptr, nullptr, 0, false, true, split_m, s)));
+  TCU((gemm<false, false>(M, 64, 128, t->dH2, 128, W(1), 64, t->dH1, 64, nullptr, t->H1, 64, false, false, 1, s)));
+  {
+    dim3 gb(1, std::max(1, (M + 255) / 256));
+    colsum_kernel<<<gb, 256, 0, s>>>(dZ3, M, 256, gB(2), 256);
+    colsum_kernel<<<gb, 256, 0, s>>>(t->dH2, M, 128, gB(1), 256);
+    colsum_kernel<<<gb, 256, 0, s>>>(t->dH1, M, 64, gB(0), 256);
+    dim3 gw(64, std::max(1, std::min(256, M / 256)));
+    dw1_kernel<<<gw, 256, 0, s>>>(t->dH1, t->X, M, gW(0));
+    TCU(cudaGetLastError());
+  }
+  return LOCC_OK;
+}
+
+// The same pass with the dense products on the tensor cores (bf16 operands,
+// float32 accumulation) and the sparse layer-3 backward.
+int bf16_pass(locc_trainer* t, cudaStream_t s) {
+  locc_handle* h = t->h;
+  int* err = h->d_err;
+  const int P = t->batch, M = P * ROWS;
+  const float* prm = t->params;
+  auto W = [&](int l) { return prm + PARAM_OFF_W[l]; };
+  auto Bv = [&](int l) { return prm + PARAM_OFF_B[l]; };
+  float* g = t->grad;
+  auto gW = [&](int l) { return g + PARAM_OFF_W[l]; };
+  auto gB = [&](int l) { return g + PARAM_OFF_B[l]; };
+  layer1_kernel<<<(unsigned)(((size_t)M * 64 + 255) / 256), 256, 0, s>>>(t->X, W(0), Bv(0), t->H1, M);
+  TCU(cudaGetLastError());
+  TCU(tg_gemm(false, true, M, 128, 64, t->H1, 64, W(1), 64, t->H2, 128, Bv(1), nullptr, 0, true, false, 1, err, s));
+  TCU(tg_layer3_pool(W(2), Bv(2), t->H2, t->X, P, t->F, t->amax, err, s));
+  TCU(tg_gemm(false, true, P, 256, 512, t->F, 512, W(3), 512, t->G1, 256, Bv(3), nullptr, 0, true, false, 1, err, s));
+  TCU(tg_gemm(false, true, P, 256, 256, t->G1, 256, W(4), 256, t->G2, 256, Bv(4), nullptr, 0, true, false, 1, err, s));
+  TCU((gemm<false, true>(P, 8, 256, t->G2, 256, W(5), 256, t->Y, 8, Bv(5), nullptr, 0, false, false, 1, s)));
+  loss_kernel<<<(P + 255) / 256, 256, 0, s>>>(t->Y, t->T, t->dY, t->loss, P, t->cfg);
+  feat_reg_kernel<<<(unsigned)(((size_t)P * 512 + 255) / 256), 256, 0, s>>>(t->F, t->dF, t->loss, P,
+                                                                           t->cfg.alpha);
+  TCU(cudaGetLastError());
+  // ---- head backward
+  const int split_p = std::max(1, std::min(64, P / 64));
+  TCU((gemm<true, false>(8, 256, P, t->dY, 8, t->G2, 256, gW(5), 256, nullptr, nullptr, 0, false, true, std::max(1, P / 64), s)));
+  TCU((gemm<false, false>(P, 256, 8, t->dY, 8, W(5), 256, t->dG2, 256, nullptr, t->G2, 256, false, false, 1, s)));
+  TCU(tg_gemm(true, false, 256, 256, P, t->dG2, 256, t->G1, 256, gW(4), 256, nullptr, nullptr, 0, false, true, split_p, err, s));
+  TCU(tg_gemm(false, false, P, 256, 256, t->dG2, 256, W(4), 256, t->dG1, 256, nullptr, t->G1, 256, false, false, 1, err, s));
+  TCU(tg_gemm(true, false, 256, 512, P, t->dG1, 256, t->F, 512, gW(3), 512, nullptr, nullptr, 0, false, true, split_p, err, s));
+  TCU(tg_gemm(false, false, P, 512, 256, t->dG1, 256, W(3), 512, t->dF, 512, nullptr, nullptr, 0, false, true, 1, err, s));
+  {
+    dim3 gb(1, std::max(1, (P + 63) / 64));
+    colsum_kernel<<<gb, 256, 0, s>>>(t->dY, P, 8, gB(5), 64);
+    colsum_kernel<<<gb, 256, 0, s>>>(t->dG2, P, 256, gB(4), 64);
+    colsum_kernel<<<gb, 256, 0, s>>>(t->dG1, P, 256, gB(3), 64);
+    TCU(cudaGetLastError());
+  }
+  // ---- encoder backward: layer 3 sparse (no dZ3), layers 2 and 1 on the tensor cores
+  TCU(sparse_layer3_backward(t->dF, t->F, t->amax, W(2), t->H2, P, t->dH2, gW(2), gB(2), gB(1), h->n_sm, s));
+  TCU(tg_gemm(true, false, 128, 64, M, t->dH2, 128, t->H1, 64, gW(1), 64, nullptr, nullptr, 0, false, true, 2 * h->n_sm, err, s));
+  TCU(tg_layer1_grad(t->dH2, W(1), t->X, W(0), Bv(0), M, gW(0), gB(0), err, s));
+  return LOCC_OK;
+}
 }  // namespace
 
 extern "C" {
@@ -407,6 +533,10 @@ int locc_trainer_create(locc_handle* h, int32_t max_batch, const locc_train_conf
   if (!out) return tfail(LOCC_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
   if (!h || !cfg || max_batch < 1) return tfail(LOCC_ERR_INVALID_ARG, "bad trainer arguments");
+  if (prepare_train_tc_kernels() != cudaSuccess) {
+    cudaGetLastError();
+    return tfail(LOCC_ERR_CUDA, "cannot configure the training kernels");
+  }
   locc_trainer* t = new (std::nothrow) locc_trainer();
   if (!t) return tfail(LOCC_ERR_OOM, "host allocation failed");
   t->h = h;
@@ -462,13 +592,9 @@ int locc_train_step(locc_trainer* t, const float* poses, const int32_t* obj_shap
   if (!poses || !obj_shape || !pairs || !targets) return tfail(LOCC_ERR_INVALID_ARG, "NULL array");
   locc_handle* h = t->h;
   cudaStream_t s = (cudaStream_t)stream;
-  const int P = n_pairs, M = P * ROWS;
-  const float* prm = t->params;
-  auto W = [&](int l) { return prm + PARAM_OFF_W[l]; };
-  auto Bv = [&](int l) { return prm + PARAM_OFF_B[l]; };
+  const int P = n_pairs;
   float* g = t->grad;
-  auto gW = [&](int l) { return g + PARAM_OFF_W[l]; };
-  auto gB = [&](int l) { return g + PARAM_OFF_B[l]; };
+  t->batch = P;
   PairInputs in{poses, obj_shape, pairs, n_obj, n_pairs};
   TCU(launch_crop(dev_library(h), in, whole_range(n_pairs, nullptr), h->radius, t->xyz, nullptr,
                   t->cnt, t->centre, h->d_err, t->defer, h->n_sm, 0, s, h->crop_mode));
@@ -476,52 +602,8 @@ int locc_train_step(locc_trainer* t, const float* poses, const int32_t* obj_shap
   TCU(cudaMemsetAsync(g, 0, (size_t)LOCC_N_PARAMS * 4, s));
   prep_kernel<<<P, ROWS, 0, s>>>(t->xyz, t->centre, poses, pairs, n_obj, targets, rot, t->X, t->T, P);
   TCU(cudaGetLastError());
-  // ---- forward
-  layer1_kernel<<<(unsigned)(((size_t)M * 64 + 255) / 256), 256, 0, s>>>(t->X, W(0), Bv(0), t->H1, M);
-  TCU(cudaGetLastError());
-  TCU((gemm<false, true>(M, 128, 64, t->H1, 64, W(1), 64, t->H2, 128, Bv(1), nullptr, 0, true, false, 1, s)));
-  TCU((gemm<false, true>(M, 256, 128, t->H2, 128, W(2), 128, t->Z3, 256, Bv(2), nullptr, 0, false, false, 1, s)));
-  pool_kernel<<<(unsigned)(((size_t)P * 512 + 255) / 256), 256, 0, s>>>(t->Z3, t->X, t->F, t->amax, P);
-  TCU(cudaGetLastError());
-  TCU((gemm<false, true>(P, 256, 512, t->F, 512, W(3), 512, t->G1, 256, Bv(3), nullptr, 0, true, false, 1, s)));
-  TCU((gemm<false, true>(P, 256, 256, t->G1, 256, W(4), 256, t->G2, 256, Bv(4), nullptr, 0, true, false, 1, s)));
-  TCU((gemm<false, true>(P, 8, 256, t->G2, 256, W(5), 256, t->Y, 8, Bv(5), nullptr, 0, false, false, 1, s)));
-  loss_kernel<<<(P + 255) / 256, 256, 0, s>>>(t->Y, t->T, t->F, t->dY, t->dF, t->loss, P, t->cfg);
-  TCU(cudaGetLastError());
-  // ---- head backward
-  const int split_p = std::max(1, P / 64);
-  TCU((gemm<true, false>(8, 256, P, t->dY, 8, t->G2, 256, gW(5), 256, nullptr, nullptr, 0, false, true, split_p, s)));
-  TCU((gemm<false, false>(P, 256, 8, t->dY, 8, W(5), 256, t->dG2, 256, nullptr, t->G2, 256, false, false, 1, s)));
-  TCU((gemm<true, false>(256, 256, P, t->dG2, 256, t->G1, 256, gW(4), 256, nullptr, nullptr, 0, false, true, split_p, s)));
-  TCU((gemm<false, false>(P, 256, 256, t->dG2, 256, W(4), 256, t->dG1, 256, nullptr, t->G1, 256, false, false, 1, s)));
-  TCU((gemm<true, false>(256, 512, P, t->dG1, 256, t->F, 512, gW(3), 512, nullptr, nullptr, 0, false, true, split_p, s)));
-  TCU((gemm<false, false>(P, 512, 256, t->dG1, 256, W(3), 512, t->dF, 512, nullptr, nullptr, 0, false, true, 1, s)));
-  {
-    dim3 gb(1, std::max(1, (P + 63) / 64));
-    colsum_kernel<<<gb, 256, 0, s>>>(t->dY, P, 8, gB(5), 64);
-    colsum_kernel<<<gb, 256, 0, s>>>(t->dG2, P, 256, gB(4), 64);
-    colsum_kernel<<<gb, 256, 0, s>>>(t->dG1, P, 256, gB(3), 64);
-    TCU(cudaGetLastError());
-  }
-  // ---- encoder backward (dZ3 reuses the Z3 buffer)
-  float* dZ3 = t->Z3;
-  TCU(cudaMemsetAsync(dZ3, 0, (size_t)M * 256 * 4, s));
-  scatter_kernel<<<(unsigned)(((size_t)P * 512 + 255) / 256), 256, 0, s>>>(t->dF, t->F, t->amax, dZ3, P);
-  TCU(cudaGetLastError());
-  const int split_m = std::max(1, M / 1024);
-  TCU((gemm<true, false>(256, 128, M, dZ3, 256, t->H2, 128, gW(2), 128, nullptr, nullptr, 0, false, true, split_m, s)));
-  TCU((gemm<false, false>(M, 128, 256, dZ3, 256, W(2), 128, t->dH2, 128, nullptr, t->H2, 128, false, false, 1, s)));
-  TCU((gemm<true, false>(128, 64, M, t->dH2, 128, t->H1, 64, gW(1), 64, nullptr, nullptr, 0, false, true, split_m, s)));
-  TCU((gemm<false, false>(M, 64, 128, t->dH2, 128, W(1), 64, t->dH1, 64, nullptr, t->H1, 64, false, false, 1, s)));
-  {
-    dim3 gb(1, std::max(1, (M + 255) / 256));
-    colsum_kernel<<<gb, 256, 0, s>>>(dZ3, M, 256, gB(2), 256);
-    colsum_kernel<<<gb, 256, 0, s>>>(t->dH2, M, 128, gB(1), 256);
-    colsum_kernel<<<gb, 256, 0, s>>>(t->dH1, M, 64, gB(0), 256);
-    dim3 gw(64, std::max(1, std::min(256, M / 256)));
-    dw1_kernel<<<gw, 256, 0, s>>>(t->dH1, t->X, M, gW(0));
-    TCU(cudaGetLastError());
-  }
+  const int st = t->precision == LOCC_BF16 ? bf16_pass(t, s) : fp32_pass(t, s);
+  if (st != LOCC_OK) return st;
   if (update) {
     t->step += 1;
     const float c1 = 1.f - powf(t->cfg.beta1, (float)t->step);
@@ -591,6 +673,14 @@ int locc_trainer_set_lr(locc_trainer* t, float lr) {
   if (!t) return tfail(LOCC_ERR_INVALID_ARG, "trainer is NULL");
   if (!(lr >= 0.f) || !std::isfinite(lr)) return tfail(LOCC_ERR_INVALID_ARG, "lr must be finite and >= 0");
   t->cfg.lr = lr;
+  return LOCC_OK;
+}
+
+int locc_trainer_set_precision(locc_trainer* t, int32_t precision) {
+  if (!t) return tfail(LOCC_ERR_INVALID_ARG, "trainer is NULL");
+  if (precision != LOCC_FP32 && precision != LOCC_BF16)
+    return tfail(LOCC_ERR_INVALID_ARG, "training precision must be LOCC_FP32 or LOCC_BF16");
+  t->precision = precision;
   return LOCC_OK;
 }
 

@@ -13,7 +13,12 @@ whose own correctness the other oracle tests do not fix:
   regression terms) against numbers worked out by hand on networks whose
   outputs are their biases;
 * the selection's tie rule (equal squared distances go to the lower sample
-  index) on samples placed at exactly equal float32 distances.
+  index) on samples placed at exactly equal float32 distances;
+* the bf16 operand mode of the loss and gradient (the arithmetic of a bf16
+  tensor-core trainer): its rounding against PyTorch's CPU bfloat16
+  conversion, and the loss and gradient against PyTorch CPU autograd through
+  the same network whose matrix products round their operands (forward and
+  backward, straight through) at the places the oracle's header lists.
 
 None of the expected values comes from the oracle itself or from the CUDA
 path."""
@@ -370,3 +375,103 @@ def test_selection_tie_at_the_boundary_of_the_ball():
     assert r["cnt"][0, 0] == KMAX and r["cnt"][0, 1] == 0
     np.testing.assert_array_equal(r["idx"][0, 0], slots[:64])
     assert np.all(r["idx"][0, 1] == -1)
+
+
+# ------------------------------------------------------------- bf16 operands
+
+def test_bf16_rounding_matches_torch():
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(3)
+    v = (rng.standard_normal(20000) * np.exp(rng.uniform(-30, 30, 20000))).astype(np.float32)
+    # exact ties and neighbours of ties: 1 + (2j + 1) 2^-8 at binade scales
+    j = np.arange(0, 128)
+    ties = np.concatenate([(1 + (2 * j + 1) * 2.0 ** -8) * s_ for s_ in (1.0, -2.0 ** 5, 2.0 ** -9)])
+    ties = ties.astype(np.float32)
+    nxt = np.nextafter(ties, np.float32(np.inf))
+    prv = np.nextafter(ties, np.float32(-np.inf))
+    v = np.concatenate([v, ties, nxt, prv, np.float32([0.0, -0.0, 1.0, -1.0, 3.0e38])])
+    want = torch.from_numpy(v).to(torch.bfloat16).to(torch.float64).numpy()
+    np.testing.assert_array_equal(oracle.round_bf16(v), want)
+    # float64 inputs are rounded to float32 first, as a float32 producer holds them
+    w = rng.standard_normal(1000)
+    want = torch.from_numpy(w.astype(np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
+    np.testing.assert_array_equal(oracle.round_bf16(w), want)
+
+
+def _st_net_loss(torch, flat, xyz, cnt, lab, alpha):
+    """Mean of BCE(y0, lab) + alpha mean(f^2) through the crop network in
+    float64 autograd, with straight-through bf16 operands (torch's rounding)
+    in encoder layers 2 and 3 and head layers 1 and 2; layer 3's backward
+    unrounded."""
+    def r(x):
+        return x.float().to(torch.bfloat16).double()
+
+    class RoundedLinear(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, x, W, b, round_back):
+            ctx.save_for_backward(x, W)
+            ctx.round_back = round_back
+            return r(x) @ r(W).T + b
+
+        @staticmethod
+        def backward(ctx, gy):
+            x, W = ctx.saved_tensors
+            if ctx.round_back:
+                return r(gy) @ r(W), r(gy).T @ r(x), gy.sum(0), None
+            return gy @ W, gy.T @ x, gy.sum(0), None
+
+    offs = np.cumsum([0] + [i * o + o for i, o in oracle.LAYER_DIMS])
+    prm = torch.tensor(flat, dtype=torch.float64, requires_grad=True)
+    Ws, bs = [], []
+    for l, (fi, fo) in enumerate(oracle.LAYER_DIMS):
+        Ws.append(prm[offs[l]:offs[l] + fi * fo].view(fo, fi))
+        bs.append(prm[offs[l] + fi * fo:offs[l + 1]])
+    P = cnt.shape[0]
+    feats = []
+    for p in range(P):
+        f = []
+        for o in range(2):
+            n = int(cnt[p, o])
+            if n == 0:
+                f.append(torch.zeros(256, dtype=torch.float64))
+                continue
+            x = torch.tensor(xyz[p, o, :n].astype(np.float64))
+            h1 = torch.relu(x @ Ws[0].T + bs[0])
+            h2 = torch.relu(RoundedLinear.apply(h1, Ws[1], bs[1], True))
+            h3 = torch.relu(RoundedLinear.apply(h2, Ws[2], bs[2], False))
+            f.append(h3.max(dim=0).values)
+        feats.append(torch.cat(f))
+    F = torch.stack(feats)
+    g1 = torch.relu(RoundedLinear.apply(F, Ws[3], bs[3], True))
+    g2 = torch.relu(RoundedLinear.apply(g1, Ws[4], bs[4], True))
+    y = g2 @ Ws[5].T + bs[5]
+    bce = torch.nn.functional.binary_cross_entropy_with_logits(
+        y[:, 0], torch.tensor(lab, dtype=torch.float64), reduction="none")
+    L = (bce + alpha * (F * F).mean(dim=1)).mean()
+    L.backward()
+    return float(L.detach()), prm.grad.numpy()
+
+
+def test_bf16_operand_mode_matches_straight_through_autograd():
+    torch = pytest.importorskip("torch")
+    import synth
+    rng = np.random.default_rng(8)
+    P = 4
+    cnt = np.array([[64, 17], [5, 0], [33, 64], [1, 40]], np.int32)
+    xyz = np.zeros((P, 2, KMAX, 3), np.float32)
+    for p in range(P):
+        for o in range(2):
+            xyz[p, o, :cnt[p, o]] = rng.uniform(-0.25, 0.25, (cnt[p, o], 3))
+    flat = oracle.flatten_params(synth.xavier_weights(9, bias_scale=0.1)).astype(np.float64)
+    lab = np.array([1.0, 0.0, 1.0, 0.0])
+    tgt = np.zeros((P, 8))
+    tgt[:, 0] = lab
+    hp = (0.0, 0.0, 0.0, 0.01, 0.5, 0.0)  # BCE and the embedding term only
+    L_b, g_b = oracle.loss_grad(flat, xyz, cnt, tgt, hp, operands="bf16")
+    L_e, g_e = oracle.loss_grad(flat, xyz, cnt, tgt, hp, operands="exact")
+    L_t, g_t = _st_net_loss(torch, flat, xyz, cnt, lab, hp[4])
+    assert abs(L_b - L_t) <= 1e-12 * abs(L_t)
+    assert np.linalg.norm(g_b - g_t) <= 1e-10 * np.linalg.norm(g_t)
+    # the rounding is really applied (the two modes differ at bf16 scale)
+    d = np.linalg.norm(g_b - g_e) / np.linalg.norm(g_e)
+    assert 1e-5 < d < 5e-2, d
