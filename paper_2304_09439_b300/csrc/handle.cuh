@@ -135,6 +135,10 @@ cudaError_t prepare_train_tc_kernels();
 cudaError_t tg_gemm(bool ta, bool tb, int M, int N, int K, const float* A, int lda, const float* B,
                     int ldb, float* C, int ldc, const float* bias, const float* mask, int ldm,
                     bool relu, bool accumulate, int splits, int* err, cudaStream_t s);
+cudaError_t tg_layer2_forward(const float* X, const float* W1, const float* b1, const float* W2,
+                              const float* b2, int M, float* H2, int* err, cudaStream_t s);
+cudaError_t tg_layer2_wgrad(const float* dH2, const float* X, const float* W1, const float* b1, int M,
+                            float* gW2, int splits, int* err, cudaStream_t s);
 cudaError_t tg_layer3_pool(const float* W3, const float* b3, const float* H2, const float* X, int P,
                            float* F, int32_t* amax, int* err, cudaStream_t s);
 cudaError_t tg_layer1_grad(const float* dH2, const float* W2, const float* X, const float* W1,

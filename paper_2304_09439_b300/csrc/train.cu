@@ -20,7 +20,8 @@
 //     4 x 4 per thread) with optional transposes, bias, ReLU, ReLU-mask and
 //     split-K accumulation; dZ3 formed densely from the argmax scatter.
 //   LOCC_BF16: the dense products on the tensor cores (train_tc.cu: bf16
-//     operands, float32 accumulation; layer 3 pooled in its epilogue, layer 1's
+//     operands, float32 accumulation; H1 recomputed from the crop rows by its
+//     consumers instead of stored, layer 3 pooled in its epilogue, layer 1's
 //     gradient reduced in the epilogue of dH1), the sparse layer-3 backward
 //     on the CUDA cores without dZ3, the tiny products (N or K = 8) in SIMT.
 #include <algorithm>
@@ -492,9 +493,7 @@ int bf16_pass(locc_trainer* t, cudaStream_t s) {
   float* g = t->grad;
   auto gW = [&](int l) { return g + PARAM_OFF_W[l]; };
   auto gB = [&](int l) { return g + PARAM_OFF_B[l]; };
-  layer1_kernel<<<(unsigned)(((size_t)M * 64 + 255) / 256), 256, 0, s>>>(t->X, W(0), Bv(0), t->H1, M);
-  TCU(cudaGetLastError());
-  TCU(tg_gemm(false, true, M, 128, 64, t->H1, 64, W(1), 64, t->H2, 128, Bv(1), nullptr, 0, true, false, 1, err, s));
+  TCU(tg_layer2_forward(t->X, W(0), Bv(0), W(1), Bv(1), M, t->H2, err, s));
   TCU(tg_layer3_pool(W(2), Bv(2), t->H2, t->X, P, t->F, t->amax, err, s));
   TCU(tg_gemm(false, true, P, 256, 512, t->F, 512, W(3), 512, t->G1, 256, Bv(3), nullptr, 0, true, false, 1, err, s));
   TCU(tg_gemm(false, true, P, 256, 256, t->G1, 256, W(4), 256, t->G2, 256, Bv(4), nullptr, 0, true, false, 1, err, s));
@@ -520,7 +519,7 @@ int bf16_pass(locc_trainer* t, cudaStream_t s) {
   }
   // ---- encoder backward: layer 3 sparse (no dZ3), layers 2 and 1 on the tensor cores
   TCU(sparse_layer3_backward(t->dF, t->F, t->amax, W(2), t->H2, P, t->dH2, gW(2), gB(2), gB(1), h->n_sm, s));
-  TCU(tg_gemm(true, false, 128, 64, M, t->dH2, 128, t->H1, 64, gW(1), 64, nullptr, nullptr, 0, false, true, 2 * h->n_sm, err, s));
+  TCU(tg_layer2_wgrad(t->dH2, t->X, W(0), Bv(0), M, gW(1), 2 * h->n_sm, err, s));
   TCU(tg_layer1_grad(t->dH2, W(1), t->X, W(0), Bv(0), M, gW(0), gB(0), err, s));
   return LOCC_OK;
 }

@@ -20,6 +20,8 @@
 //          (ties to the lower slot), Z3 never stored;
 //   L1GRAD dH1 = dH2 W2 masked by the recomputed layer-1 ReLU, reduced in the
 //          CTA into dL/dW1 = dH1^T X and dL/db1 = sum dH1 (dH1 never stored).
+//   H1 (layer 1's output) is never stored either: the A operand of layer 2 and
+//   the B operand of dL/dW2 recompute it from the crop rows while staging.
 //
 // Layer 3's backward is sparse (Sec. III-A max-pooling: dL/dZ3 is non-zero
 // only at each channel's argmax row, at most 256 of 64 x 256 entries per
@@ -44,6 +46,7 @@ constexpr long long TG_WAIT = 2000000000LL;  // ~1 s at 2 GHz
 constexpr int TG_BM = 128, TG_BK = 32, TG_NS = 3;
 constexpr int TG_A_BYTES = TG_BM * TG_BK * 2;  // 8 KB per stage
 enum { TG_STORE = 0, TG_POOL = 1, TG_L1GRAD = 2 };
+enum { TG_MEM = 0, TG_A_H1 = 1, TG_B_H1 = 2 };  // operand recomputed from X
 
 __host__ __device__ constexpr int tg_stage_bytes(int bn) { return TG_A_BYTES + bn * TG_BK * 2; }
 // Dynamic shared memory: the stages, also reused by the epilogues (STORE:
@@ -123,6 +126,71 @@ __device__ __forceinline__ void tile_load(float (&v)[R / 32][8], const float* __
   }
 }
 
+// Layer 1 of the encoder recomputed while staging (H1 is never stored):
+// relu(W1 x + b1) with the float32 operation order of the forward pass
+// (b1, then W1[c] x, y, z by fused multiply-adds), so that every consumer
+// sees the same H1 bits.  w = {W1[c][0..2], b1[c]} per channel c, in shared
+// memory; X rows are float4 (x, y, z, valid).
+__device__ __forceinline__ float layer1_value(const float4* w, int c, float4 x) {
+  const float4 q = w[c];
+  float h = q.w;
+  h = fmaf(q.x, x.x, h);
+  h = fmaf(q.y, x.y, h);
+  h = fmaf(q.z, x.z, h);
+  return fmaxf(h, 0.f);
+}
+
+// RC = false: rows are crop rows, K = the 64 layer-1 channels (the A operand
+// of layer 2); RC = true: rows are channels, K = crop rows (the B operand of
+// dL/dW2 = dH2^T H1).  The load keeps the raw crop rows in registers (one per
+// item for RC = false, eight for RC = true) and the layer-1 arithmetic runs
+// when the tile is stored, so that the loads stay in flight meanwhile.
+template <int R, bool RC>
+struct H1Regs {
+  float4 x[R / 32][RC ? 8 : 1];
+};
+
+template <int R, bool RC>
+__device__ __forceinline__ void tile_load_h1(H1Regs<R, RC>& v, const float4* __restrict__ X, int r0,
+                                             int rlim, int k0, int klim) {
+#pragma unroll
+  for (int u = 0; u < R / 32; ++u) {
+    int r, kg;
+    tile_item<R, RC>(u, &r, &kg);
+    const int gr = r0 + r, gk = k0 + kg * 8;
+    if (RC) {
+#pragma unroll
+      for (int j = 0; j < 8; ++j)
+        v.x[u][j] = (gr < rlim && gk + j < klim) ? __ldg(X + gk + j) : make_float4(0.f, 0.f, 0.f, 0.f);
+    } else {
+      v.x[u][0] = gr < rlim ? __ldg(X + gr) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+  }
+}
+
+template <int R, bool RC>
+__device__ __forceinline__ void tile_store_h1(unsigned char* dst, const H1Regs<R, RC>& v,
+                                              const float4* w, int r0, int rlim, int k0, int klim) {
+#pragma unroll
+  for (int u = 0; u < R / 32; ++u) {
+    int r, kg;
+    tile_item<R, RC>(u, &r, &kg);
+    const int gr = r0 + r, gk = k0 + kg * 8;
+    float h[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const bool e = gr < rlim && gk + j < klim;
+      h[j] = e ? (RC ? layer1_value(w, gr, v.x[u][j]) : layer1_value(w, gk + j, v.x[u][0])) : 0.f;
+    }
+    uint4 q;
+    q.x = pack_bf16(h[0], h[1]);
+    q.y = pack_bf16(h[2], h[3]);
+    q.z = pack_bf16(h[4], h[5]);
+    q.w = pack_bf16(h[6], h[7]);
+    *reinterpret_cast<uint4*>(dst + kmajor_off(r, kg * 8, TG_BK)) = q;
+  }
+}
+
 // Registers -> bf16 K-major no-swizzle tile (lbo 128, sbo 32 * 16).
 template <int R, bool RC>
 __device__ __forceinline__ void tile_store(unsigned char* dst, const float (&v)[R / 32][8]) {
@@ -139,12 +207,13 @@ __device__ __forceinline__ void tile_store(unsigned char* dst, const float (&v)[
   }
 }
 
-template <bool TA, bool TB, int BN, int EPI>
-__global__ void __launch_bounds__(128, BN == 128 ? 4 : 5) tg_kernel(TgArgs g) {
+template <bool TA, bool TB, int BN, int EPI, int XS>
+__global__ void __launch_bounds__(128, (BN == 128 || XS == TG_B_H1) ? 4 : 5) tg_kernel(TgArgs g) {
   static_assert(BN == 64 || BN == 128, "tile width");
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ __align__(8) uint64_t bars[TG_NS];
   __shared__ uint32_t tslot;
+  __shared__ float4 s_w1[XS != TG_MEM ? 64 : 1];  // {W1[c][0..2], b1[c]}
   constexpr int ST = tg_stage_bytes(BN);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int n0 = blockIdx.x * BN, m0 = blockIdx.y * TG_BM;
@@ -154,6 +223,8 @@ __global__ void __launch_bounds__(128, BN == 128 ? 4 : 5) tg_kernel(TgArgs g) {
     for (int s = 0; s < TG_NS; ++s) mbar_init(smem_u32(&bars[s]), 1);
     fence_mbar_init();
   }
+  if (XS != TG_MEM && tid < 64)
+    s_w1[tid] = make_float4(g.W1[3 * tid], g.W1[3 * tid + 1], g.W1[3 * tid + 2], g.b1[tid]);
   if (warp == 0) {
     tmem_alloc(smem_u32(&tslot), BN);
     tmem_relinquish();
@@ -164,11 +235,17 @@ __global__ void __launch_bounds__(128, BN == 128 ? 4 : 5) tg_kernel(TgArgs g) {
   const uint32_t tbase = tslot;
   constexpr uint32_t idesc = idesc_bf16(TG_BM, BN);
   bool ok = true;
-  float ra[TG_BM / 32][8], rb[BN / 32][8];
-  if (nk > 0) {
-    tile_load<TG_BM, TA>(ra, g.A, g.lda, m0, g.M, kb, ke, g.vec_a);
-    tile_load<BN, !TB>(rb, g.B, g.ldb, n0, g.N, kb, ke, g.vec_b);
-  }
+  float ra[XS == TG_A_H1 ? 1 : TG_BM / 32][8], rb[XS == TG_B_H1 ? 1 : BN / 32][8];
+  H1Regs<XS == TG_A_H1 ? TG_BM : 32, false> xa;
+  H1Regs<XS == TG_B_H1 ? BN : 32, true> xb;
+  const float4* X4 = reinterpret_cast<const float4*>(g.X);
+  auto load_tiles = [&](int k0) {
+    if constexpr (XS == TG_A_H1) tile_load_h1<TG_BM, false>(xa, X4, m0, g.M, k0, ke);
+    else tile_load<TG_BM, TA>(ra, g.A, g.lda, m0, g.M, k0, ke, g.vec_a);
+    if constexpr (XS == TG_B_H1) tile_load_h1<BN, true>(xb, X4, n0, g.N, k0, ke);
+    else tile_load<BN, !TB>(rb, g.B, g.ldb, n0, g.N, k0, ke, g.vec_b);
+  };
+  if (nk > 0) load_tiles(kb);
   for (int kt = 0; kt < nk; ++kt) {
     const int s = kt % TG_NS;
     unsigned char* sA = smem + s * ST;
@@ -176,8 +253,11 @@ __global__ void __launch_bounds__(128, BN == 128 ? 4 : 5) tg_kernel(TgArgs g) {
     // the MMAs that read this stage TG_NS steps ago must be done
     if (kt >= TG_NS) ok = mbar_wait(smem_u32(&bars[s]), ((kt / TG_NS) - 1) & 1, TG_WAIT);
     if (ok) {
-      tile_store<TG_BM, TA>(sA, ra);
-      tile_store<BN, !TB>(sB, rb);
+      const int k0 = kb + kt * TG_BK;
+      if constexpr (XS == TG_A_H1) tile_store_h1<TG_BM, false>(sA, xa, s_w1, m0, g.M, k0, ke);
+      else tile_store<TG_BM, TA>(sA, ra);
+      if constexpr (XS == TG_B_H1) tile_store_h1<BN, true>(sB, xb, s_w1, n0, g.N, k0, ke);
+      else tile_store<BN, !TB>(sB, rb);
     }
     fence_async_smem();
     ok = __syncthreads_and(ok);
@@ -193,11 +273,7 @@ __global__ void __launch_bounds__(128, BN == 128 ? 4 : 5) tg_kernel(TgArgs g) {
       }
       __syncwarp();
     }
-    if (kt + 1 < nk) {  // next tile's loads overlap this tile's MMAs
-      const int k1 = kb + (kt + 1) * TG_BK;
-      tile_load<TG_BM, TA>(ra, g.A, g.lda, m0, g.M, k1, ke, g.vec_a);
-      tile_load<BN, !TB>(rb, g.B, g.ldb, n0, g.N, k1, ke, g.vec_b);
-    }
+    if (kt + 1 < nk) load_tiles(kb + (kt + 1) * TG_BK);  // overlaps this tile's MMAs
   }
   if (ok && nk > 0) ok = mbar_wait(smem_u32(&bars[(nk - 1) % TG_NS]), ((nk - 1) / TG_NS) & 1, TG_WAIT);
   ok = __syncthreads_and(ok);
@@ -442,7 +518,7 @@ __global__ void __launch_bounds__(128) sparse_gw3_kernel(const float* __restrict
   if (j < GW3_CB) atomicAdd(gB3 + c0 + j, bs);
 }
 
-template <bool TA, bool TB, int BN, int EPI>
+template <bool TA, bool TB, int BN, int EPI, int XS = TG_MEM>
 cudaError_t tg_launch(TgArgs g, int splits, cudaStream_t s) {
   if (g.M <= 0 || g.N <= 0 || g.K <= 0) return cudaSuccess;
   splits = std::max(1, std::min(splits, (g.K + TG_BK - 1) / TG_BK));
@@ -454,7 +530,7 @@ cudaError_t tg_launch(TgArgs g, int splits, cudaStream_t s) {
   g.vec_a = (!TA && g.lda % 4 == 0 && al16(g.A)) ? 1 : 0;
   g.vec_b = (TB && g.ldb % 4 == 0 && al16(g.B)) ? 1 : 0;
   dim3 grid((g.N + BN - 1) / BN, (g.M + TG_BM - 1) / TG_BM, splits);
-  tg_kernel<TA, TB, BN, EPI><<<grid, 128, tg_smem_bytes(BN), s>>>(g);
+  tg_kernel<TA, TB, BN, EPI, XS><<<grid, 128, tg_smem_bytes(BN), s>>>(g);
   return cudaGetLastError();
 }
 
@@ -491,6 +567,24 @@ cudaError_t tg_gemm(bool ta, bool tb, int M, int N, int K, const float* A, int l
   return cudaErrorInvalidValue;
 }
 
+cudaError_t tg_layer2_forward(const float* X, const float* W1, const float* b1, const float* W2,
+                              const float* b2, int M, float* H2, int* err, cudaStream_t s) {
+  TgArgs g = tg_args(M, 128, 64, nullptr, 0, W2, 64, err);
+  g.X = X, g.W1 = W1, g.b1 = b1;
+  g.C = H2, g.ldc = 128, g.bias = b2, g.relu = 1;
+  if (!tg_store_aligned(g)) return cudaErrorInvalidValue;
+  return tg_launch<false, true, 128, TG_STORE, TG_A_H1>(g, 1, s);
+}
+
+cudaError_t tg_layer2_wgrad(const float* dH2, const float* X, const float* W1, const float* b1, int M,
+                            float* gW2, int splits, int* err, cudaStream_t s) {
+  TgArgs g = tg_args(128, 64, M, dH2, 128, nullptr, 0, err);
+  g.X = X, g.W1 = W1, g.b1 = b1;
+  g.C = gW2, g.ldc = 64, g.accumulate = 1;
+  if (!tg_store_aligned(g)) return cudaErrorInvalidValue;
+  return tg_launch<true, false, 64, TG_STORE, TG_B_H1>(g, splits, s);
+}
+
 cudaError_t tg_layer3_pool(const float* W3, const float* b3, const float* H2, const float* X, int P,
                            float* F, int32_t* amax, int* err, cudaStream_t s) {
   TgArgs g = tg_args(FEAT, P * ROWS, 128, W3, 128, H2, 128, err);
@@ -525,12 +619,14 @@ cudaError_t prepare_train_tc_kernels() {
   auto set = [&](const void* f, int bytes) {
     if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   };
-  set((const void*)tg_kernel<false, true, 128, TG_STORE>, tg_smem_bytes(128));
-  set((const void*)tg_kernel<true, false, 64, TG_STORE>, tg_smem_bytes(64));
-  set((const void*)tg_kernel<true, false, 128, TG_STORE>, tg_smem_bytes(128));
-  set((const void*)tg_kernel<false, false, 128, TG_STORE>, tg_smem_bytes(128));
-  set((const void*)tg_kernel<false, true, 128, TG_POOL>, tg_smem_bytes(128));
-  set((const void*)tg_kernel<false, false, 64, TG_L1GRAD>, tg_smem_bytes(64));
+  set((const void*)tg_kernel<false, true, 128, TG_STORE, TG_MEM>, tg_smem_bytes(128));
+  set((const void*)tg_kernel<true, false, 64, TG_STORE, TG_MEM>, tg_smem_bytes(64));
+  set((const void*)tg_kernel<true, false, 128, TG_STORE, TG_MEM>, tg_smem_bytes(128));
+  set((const void*)tg_kernel<false, false, 128, TG_STORE, TG_MEM>, tg_smem_bytes(128));
+  set((const void*)tg_kernel<false, true, 128, TG_POOL, TG_MEM>, tg_smem_bytes(128));
+  set((const void*)tg_kernel<false, false, 64, TG_L1GRAD, TG_MEM>, tg_smem_bytes(64));
+  set((const void*)tg_kernel<false, true, 128, TG_STORE, TG_A_H1>, tg_smem_bytes(128));
+  set((const void*)tg_kernel<true, false, 64, TG_STORE, TG_B_H1>, tg_smem_bytes(64));
   set((const void*)sparse_dh2_kernel, DH2_SMEM);
   return e;
 }
