@@ -275,6 +275,22 @@ def test_step_matches_broadphase_then_detect(scene64):
         assert hn == n
         np.testing.assert_array_equal(hp, pairs)
         np.testing.assert_array_equal(ho, ref_dev)
+        # page-locked buffers (copied directly, no staging); rows beyond the
+        # count untouched
+        def pin(a):
+            return torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+        h_out = torch.full((400_000, 8), -7.0, dtype=torch.float32).pin_memory().numpy()
+        h_pairs = torch.zeros((400_000, 2), dtype=torch.int32).pin_memory().numpy()
+        hp, ho, hn = det.step_host(pin(poses), pin(osh), pin(env), 400_000, pairs_out=h_pairs,
+                                   out=h_out)
+        assert hn == n
+        np.testing.assert_array_equal(hp, pairs)
+        np.testing.assert_array_equal(ho, ref_dev)
+        assert np.all(h_out[n:] == -7.0)
+        h_out[:] = 0.0
+        hp, ho, hn = det.step_host(poses, osh, env, 400_000, out=h_out)  # mixed pageable / pinned
+        np.testing.assert_array_equal(hp, pairs)
+        np.testing.assert_array_equal(ho, ref_dev)
         # a step with fewer pair slots than candidates detects only the first ones
         pr2, n2, out2 = det.step(tp, ts, te, 777)
         assert int(n2.item()) == n
