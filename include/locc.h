@@ -199,6 +199,41 @@ int locc_step_host(locc_handle *h, const float *poses, const int32_t *obj_shape,
                    int32_t *pairs_out, int32_t *n_pairs_out, int32_t max_pairs,
                    float *out, void *stream);
 
+/* ------------------------------------------------------- pipelined stepping
+ * Host-buffer steps with up to `depth` steps in flight (1..LOCC_STEPPER_MAX_
+ * DEPTH): each step's inputs are copied in, and its results copied out, on
+ * copy streams of their own while the neighbouring steps run on the device.
+ * The steps run one after another (they share the handle's scratch), so the
+ * handle must not be used by other calls while a stepper has steps in flight.
+ *
+ * locc_stepper_create: reserves the handle for max_pairs / max_env
+ *   (locc_reserve) and allocates depth slots of device staging (inputs for
+ *   max_obj objects and max_env environments, max_pairs pairs and outputs).
+ *   Errors: LOCC_ERR_INVALID_ARG (a size < 1, depth out of range), LOCC_ERR_OOM.
+ * locc_stepper_submit: enqueues one step (as locc_step) and returns at once
+ *   with a ticket.  poses [n_obj][7], obj_shape [n_obj], env_offsets
+ *   [n_env + 1], pairs_out [max_pairs][2] and out [max_pairs][8] are
+ *   page-locked HOST arrays that must stay valid, and the inputs unchanged,
+ *   until locc_stepper_wait returns for the ticket.  The pair list and the
+ *   outputs are copied back at the stepper's full max_pairs capacity: the
+ *   first min(count, max_pairs) rows are the step's, rows beyond are
+ *   unspecified.  LOCC_ERR_BUSY when depth steps are in flight (wait for one
+ *   first); LOCC_ERR_INVALID_ARG for pageable arrays or sizes beyond the
+ *   stepper's.  Index errors of the step are reported by locc_status.
+ * locc_stepper_wait: blocks until the ticket's step and its copies are done
+ *   and writes its pair count to *n_pairs_out (host); tickets may be waited
+ *   for in any order, each once (else LOCC_ERR_INVALID_ARG).
+ * locc_stepper_destroy: waits for everything in flight, then frees. */
+#define LOCC_STEPPER_MAX_DEPTH 4
+typedef struct locc_stepper locc_stepper;
+int locc_stepper_create(locc_handle *h, int32_t max_pairs, int32_t max_env, int32_t max_obj,
+                        int32_t depth, locc_stepper **out);
+int locc_stepper_submit(locc_stepper *t, const float *poses, const int32_t *obj_shape,
+                        int32_t n_obj, const int32_t *env_offsets, int32_t n_env,
+                        int32_t *pairs_out, int32_t *n_pairs_out, float *out, int64_t *ticket);
+int locc_stepper_wait(locc_stepper *t, int64_t ticket);
+void locc_stepper_destroy(locc_stepper *t);
+
 /* Pre-allocate scratch for up to max_pairs pairs and max_envs environments
  * per call (blocking).  Later calls within these sizes allocate nothing. */
 int locc_reserve(locc_handle *h, int32_t max_pairs, int32_t max_envs);

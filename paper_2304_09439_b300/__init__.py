@@ -19,7 +19,7 @@ from .abi import LoccError, LOCC_FP32, LOCC_BF16, LOCC_FP8, PRECISIONS
 KMAX = 64
 OUT_DIM = 8
 
-__all__ = ["Detector", "VoxelDetector", "GJK", "Trainer", "Server", "LoccError", "LOCC_FP32", "LOCC_BF16", "LOCC_FP8", "weights",
+__all__ = ["Detector", "VoxelDetector", "GJK", "Trainer", "Server", "Stepper", "LoccError", "LOCC_FP32", "LOCC_BF16", "LOCC_FP8", "weights",
            "abi", "KMAX", "OUT_DIM"]
 
 
@@ -274,6 +274,70 @@ class Detector:
                                            abi.ptr(n), M, abi.ptr(out), abi.stream_ptr(stream)))
         m = min(int(n[0]), M)
         return pairs_out[:m], out[:m], int(n[0])
+
+
+class Stepper:
+    """Owns one ``locc_stepper`` on a Detector: host-buffer steps with up to
+    ``depth`` in flight, their copies overlapping the neighbouring steps.
+
+    ``submit`` takes page-locked numpy arrays (e.g. from
+    ``torch.empty(..., pin_memory=True).numpy()``) and returns a ticket; the
+    arrays must stay alive and the inputs unchanged until ``wait`` returns
+    for it.  ``wait`` returns (pairs [n, 2], out [n, 8], n) as views of the
+    caller's output arrays."""
+
+    def __init__(self, det: "Detector", max_pairs: int, max_env: int, max_obj: int,
+                 depth: int = 2):
+        self._lib = abi.load()
+        self.det = det
+        self.max_pairs = int(max_pairs)
+        self._t = ctypes.c_void_p()
+        abi.check(self._lib.locc_stepper_create(det._h, self.max_pairs, int(max_env),
+                                                int(max_obj), int(depth), ctypes.byref(self._t)))
+        self._pending = {}
+
+    def close(self) -> None:
+        if getattr(self, "_t", None) is not None and self._t.value:
+            self._lib.locc_stepper_destroy(self._t)
+            self._t = None
+            self._pending = {}
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit(self, poses, obj_shape, env_offsets, pairs_out, out) -> int:
+        import numpy as np
+        for name, a, dt in (("poses", poses, np.float32), ("obj_shape", obj_shape, np.int32),
+                            ("env_offsets", env_offsets, np.int32),
+                            ("pairs_out", pairs_out, np.int32), ("out", out, np.float32)):
+            if a.dtype != dt or not a.flags["C_CONTIGUOUS"]:
+                raise ValueError(f"{name} must be a C-contiguous {np.dtype(dt).name} array")
+        if pairs_out.size < 2 * self.max_pairs or out.size < OUT_DIM * self.max_pairs:
+            raise ValueError("pairs_out / out must hold max_pairs rows")
+        n = np.zeros(1, np.int32)
+        t = ctypes.c_int64(-1)
+        abi.check(self._lib.locc_stepper_submit(self._t, abi.ptr(poses), abi.ptr(obj_shape),
+                                                poses.shape[0], abi.ptr(env_offsets),
+                                                env_offsets.shape[0] - 1, abi.ptr(pairs_out),
+                                                abi.ptr(n), abi.ptr(out), ctypes.byref(t)))
+        # keep the arrays alive until the wait
+        self._pending[int(t.value)] = (poses, obj_shape, env_offsets, pairs_out, out, n)
+        return int(t.value)
+
+    def wait(self, ticket: int):
+        abi.check(self._lib.locc_stepper_wait(self._t, int(ticket)))
+        _, _, _, pairs_out, out, n = self._pending.pop(int(ticket))
+        m = min(int(n[0]), self.max_pairs)
+        return pairs_out.reshape(-1, 2)[:m], out.reshape(-1, OUT_DIM)[:m], int(n[0])
 
 
 class VoxelDetector:

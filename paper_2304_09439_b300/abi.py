@@ -35,9 +35,10 @@ EXPORTS = ["locc_create", "locc_set_precision", "locc_detect", "locc_detect_host
            "locc_voxel_destroy", "locc_sim_step", "locc_sphere_contacts", "locc_set_crop_mode",
            "locc_gjk_create", "locc_gjk_detect", "locc_gjk_status", "locc_gjk_destroy",
            "locc_selftest_wait_timeout", "locc_trainer_get_state", "locc_trainer_set_state",
-           "locc_trainer_set_precision"]
+           "locc_trainer_set_precision", "locc_stepper_create", "locc_stepper_submit",
+           "locc_stepper_wait", "locc_stepper_destroy"]
 VOID_EXPORTS = ("locc_destroy", "locc_last_error", "locc_trainer_destroy", "locc_server_destroy",
-                "locc_voxel_destroy", "locc_gjk_destroy")
+                "locc_voxel_destroy", "locc_gjk_destroy", "locc_stepper_destroy")
 
 
 def _header_define(name: str) -> int:
@@ -151,6 +152,12 @@ def load(build_if_needed: bool = True) -> ctypes.CDLL:
         lib.locc_trainer_commit.argtypes = [P]
         lib.locc_trainer_set_lr.argtypes = [P, ctypes.c_float]
         lib.locc_trainer_set_precision.argtypes = [P, I]
+        lib.locc_stepper_create.argtypes = [P, I, I, I, I, ctypes.POINTER(P)]
+        lib.locc_stepper_submit.argtypes = [P, P, P, I, P, I, P, P, P,
+                                            ctypes.POINTER(ctypes.c_int64)]
+        lib.locc_stepper_wait.argtypes = [P, ctypes.c_int64]
+        lib.locc_stepper_destroy.argtypes = [P]
+        lib.locc_stepper_destroy.restype = None
         lib.locc_trainer_destroy.argtypes = [P]
         lib.locc_trainer_destroy.restype = None
         lib.locc_server_create.argtypes = [P, ctypes.POINTER(ServerConfig), ctypes.POINTER(P)]
