@@ -180,6 +180,9 @@ def main():
                     help="write a training checkpoint (parameters, Adam state, step, sampler "
                          "state, best-so-far) here at every validation and at the end")
     ap.add_argument("--resume", default=None, help="continue from a checkpoint of this run")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16"],
+                    help="trainer arithmetic: float32 CUDA cores, or the dense products on "
+                         "the tensor cores with bf16 operands (float32 accumulation and state)")
     ap.add_argument("--crop-mode", default="local", choices=["local", "global"],
                     help="local crops (the method) or global crops (the ablation without "
                          "locality)")
@@ -201,14 +204,14 @@ def main():
     tests = [(p,) + load_dataset(p) for p in args.test]
     det = Detector(lib.points, lib.aabb, synth.xavier_weights(args.seed), RADIUS, "fp32")
     det.set_crop_mode(args.crop_mode)
-    tr = Trainer(det, args.batch, lr=args.lr, w_len=args.w_len)
+    tr = Trainer(det, args.batch, lr=args.lr, w_len=args.w_len, precision=args.precision)
     cache = {"train_lib": lib_name, "crop_mode": args.crop_mode, "blob": lambda: weights.pack(
         weights.from_flat(tr.params().cpu().numpy()))}
 
     report = {"train": args.data, "n_train": int(len(train["pairs"])),
               "n_val": int(len(val["pairs"])), "batch": args.batch, "steps": args.steps,
               "lr": args.lr, "lr_final": args.lr_final, "schedule": "cosine",
-              "crop_mode": args.crop_mode, "evals": [],
+              "crop_mode": args.crop_mode, "precision": args.precision, "evals": [],
               "val": []}
 
     def run_eval(step):
