@@ -557,13 +557,25 @@ cudaError_t tg_gemm(bool ta, bool tb, int M, int N, int K, const float* A, int l
   g.C = C, g.ldc = ldc, g.bias = bias, g.mask = mask, g.ldm = ldm;
   g.relu = relu ? 1 : 0, g.accumulate = accumulate ? 1 : 0;
   if (!tg_store_aligned(g)) return cudaErrorInvalidValue;
-  const bool narrow = N <= 64;
-  if (!ta && tb) return tg_launch<false, true, 128, TG_STORE>(g, splits, s);
+  // tiles of 64 columns where 128-column tiles would leave most SMs idle (the
+  // head's products on small batches: 16-32 tiles with long K loops)
+  int n_sm = 0, dev = 0;
+  cudaGetDevice(&dev);
+  if (cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) n_sm = 148;
+  const long long tiles128 = (long long)((N + 127) / 128) * ((M + TG_BM - 1) / TG_BM) * std::max(splits, 1);
+  const bool narrow = N <= 64 || tiles128 < n_sm;
+  if (!ta && tb) {
+    if (narrow) return tg_launch<false, true, 64, TG_STORE>(g, splits, s);
+    return tg_launch<false, true, 128, TG_STORE>(g, splits, s);
+  }
   if (ta && !tb) {
     if (narrow) return tg_launch<true, false, 64, TG_STORE>(g, splits, s);
     return tg_launch<true, false, 128, TG_STORE>(g, splits, s);
   }
-  if (!ta && !tb) return tg_launch<false, false, 128, TG_STORE>(g, splits, s);
+  if (!ta && !tb) {
+    if (narrow) return tg_launch<false, false, 64, TG_STORE>(g, splits, s);
+    return tg_launch<false, false, 128, TG_STORE>(g, splits, s);
+  }
   return cudaErrorInvalidValue;
 }
 
@@ -620,6 +632,8 @@ cudaError_t prepare_train_tc_kernels() {
     if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   };
   set((const void*)tg_kernel<false, true, 128, TG_STORE, TG_MEM>, tg_smem_bytes(128));
+  set((const void*)tg_kernel<false, true, 64, TG_STORE, TG_MEM>, tg_smem_bytes(64));
+  set((const void*)tg_kernel<false, false, 64, TG_STORE, TG_MEM>, tg_smem_bytes(64));
   set((const void*)tg_kernel<true, false, 64, TG_STORE, TG_MEM>, tg_smem_bytes(64));
   set((const void*)tg_kernel<true, false, 128, TG_STORE, TG_MEM>, tg_smem_bytes(128));
   set((const void*)tg_kernel<false, false, 128, TG_STORE, TG_MEM>, tg_smem_bytes(128));
