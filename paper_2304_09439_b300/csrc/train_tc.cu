@@ -9,11 +9,14 @@
 //   Four warps load float32 tiles of 128 x 32 (A) and BN x 32 (B) from global
 //   memory into registers (the next tile while the current one is multiplied),
 //   round them to bf16 and store them in the K-major no-swizzle layout of the
-//   MMA operands (four stages); one elected lane issues two K = 16 MMAs
+//   MMA operands (three stages); one elected lane issues two K = 16 MMAs
 //   per stage and commits them to the stage's mbarrier, which the loaders wait
-//   on (bounded) before refilling the stage.  Split-K runs over gridDim.z.
-//   Epilogues (one TMEM lane = one row of C per thread):
+//   on (bounded) before refilling the stage.  Split-K runs over gridDim.z;
+//   BN = 64 where 128-column tiles would leave SMs idle.
+//   Epilogues (TMEM lane = tile row):
 //   STORE  + bias, ReLU-mask (mask > 0), ReLU, accumulate, atomic split-K;
+//          rows staged through shared memory so that each warp reads and
+//          writes C and the mask in whole 128-byte segments;
 //   POOL   layer 3 of the encoder computed transposed (M = 256 channels,
 //          N = the 128 crop rows of one pair, A = W3, B = H2): relu(z + b3)
 //          max-pooled over each object's valid rows with the argmax slot
