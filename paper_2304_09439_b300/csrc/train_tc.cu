@@ -53,7 +53,7 @@ enum { TG_MEM = 0, TG_A_H1 = 1, TG_B_H1 = 2 };  // operand recomputed from X
 
 __host__ __device__ constexpr int tg_stage_bytes(int bn) { return TG_A_BYTES + bn * TG_BK * 2; }
 // Dynamic shared memory: the stages, also reused by the epilogues (STORE:
-// 128 x 36 floats; L1GRAD: 128 x 65 floats + crop rows + W1, b1).  Padded so
+// 128 x 36 floats; L1GRAD: 128 x 65 floats + crop rows).  Padded so
 // that at most four CTAs of BN = 128 (five of BN = 64, by registers) share an
 // SM: their TMEM columns (BN each) then always fit the SM's 512.
 __host__ __device__ constexpr int tg_smem_bytes(int bn) { return bn == 128 ? 54 * 1024 : 40 * 1024; }
@@ -216,7 +216,8 @@ __global__ void __launch_bounds__(128, (BN == 128 || XS == TG_B_H1) ? 4 : 5) tg_
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ __align__(8) uint64_t bars[TG_NS];
   __shared__ uint32_t tslot;
-  __shared__ float4 s_w1[XS != TG_MEM ? 64 : 1];  // {W1[c][0..2], b1[c]}
+  constexpr bool W1S = XS != TG_MEM || EPI == TG_L1GRAD;
+  __shared__ float4 s_w1[W1S ? 64 : 1];  // {W1[c][0..2], b1[c]}
   constexpr int ST = tg_stage_bytes(BN);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int n0 = blockIdx.x * BN, m0 = blockIdx.y * TG_BM;
@@ -226,8 +227,12 @@ __global__ void __launch_bounds__(128, (BN == 128 || XS == TG_B_H1) ? 4 : 5) tg_
     for (int s = 0; s < TG_NS; ++s) mbar_init(smem_u32(&bars[s]), 1);
     fence_mbar_init();
   }
-  if (XS != TG_MEM && tid < 64)
+  if (W1S && tid < 64)
     s_w1[tid] = make_float4(g.W1[3 * tid], g.W1[3 * tid + 1], g.W1[3 * tid + 2], g.b1[tid]);
+  // L1GRAD: this thread's crop row, loaded before the K loop
+  float4 x_row = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (EPI == TG_L1GRAD && (int)blockIdx.y * TG_BM + tid < g.M)
+    x_row = __ldg(reinterpret_cast<const float4*>(g.X) + (size_t)blockIdx.y * TG_BM + tid);
   if (warp == 0) {
     tmem_alloc(smem_u32(&tslot), BN);
     tmem_relinquish();
@@ -374,11 +379,8 @@ __global__ void __launch_bounds__(128, (BN == 128 || XS == TG_B_H1) ? 4 : 5) tg_
     } else {  // TG_L1GRAD, BN = 64: thread = crop row
       float* s_g = reinterpret_cast<float*>(smem);         // [128][65]
       float4* s_x = reinterpret_cast<float4*>(smem + 128 * 65 * 4);
-      float* s_w = reinterpret_cast<float*>(smem + 128 * 65 * 4 + 128 * 16);  // W1 [64][3], b1 [64]
-      for (int i = tid; i < 64 * 3; i += 128) s_w[i] = g.W1[i];
-      if (tid < 64) s_w[192 + tid] = g.b1[tid];
       const int m = m0 + tid;
-      const float4 x = m < g.M ? reinterpret_cast<const float4*>(g.X)[m] : make_float4(0.f, 0.f, 0.f, 0.f);
+      const float4 x = x_row;
       s_x[tid] = x;
       __syncthreads();
       float v[64];
@@ -386,10 +388,11 @@ __global__ void __launch_bounds__(128, (BN == 128 || XS == TG_B_H1) ? 4 : 5) tg_
 #pragma unroll
       for (int i = 0; i < 64; ++i) {
         // the forward's layer 1, same operation order: the same ReLU decision
-        float h = s_w[192 + i];
-        h = fmaf(s_w[3 * i], x.x, h);
-        h = fmaf(s_w[3 * i + 1], x.y, h);
-        h = fmaf(s_w[3 * i + 2], x.z, h);
+        const float4 q = s_w1[i];
+        float h = q.w;
+        h = fmaf(q.x, x.x, h);
+        h = fmaf(q.y, x.y, h);
+        h = fmaf(q.z, x.z, h);
         s_g[tid * 65 + i] = (m < g.M && h > 0.f) ? v[i] : 0.f;
       }
       __syncthreads();
