@@ -114,3 +114,25 @@ def test_stepper_refusals(scenes):
         det.status()
         # the handle still steps on its own afterwards
         assert _reference(det, [scs[0]], dev)[0][2] == ref[2]
+
+
+def test_stepper_empty_scenes(scenes):
+    # no environment at all, and environments of one object each (no pair):
+    # count 0 and nothing else changes; a normal scene afterwards still matches
+    from paper_2304_09439_b300 import Detector, Stepper
+    dev = _dev()
+    lib, scs = scenes
+    layers = synth.xavier_weights(2, bias_scale=0.05)
+    p, s, e = scs[1]
+    single = (p[:5].copy(), s[:5].copy(), np.arange(6, dtype=np.int32))
+    with Detector(lib.points, lib.aabb, layers, R, "bf16") as det:
+        ref = _reference(det, [scs[1]], dev)[0]
+        with Stepper(det, MAX_PAIRS, len(e) - 1, len(p), 2) as st:
+            buf = (_pin(np.zeros((MAX_PAIRS, 2), np.int32)), _pin(np.zeros((MAX_PAIRS, 8), np.float32)))
+            none = (_pin(np.zeros((0, 7), np.float32)), _pin(np.zeros(0, np.int32)),
+                    _pin(np.zeros(1, np.int32)))
+            for inp in (none, tuple(_pin(a) for a in single)):
+                pairs, out, n = st.wait(st.submit(*inp, *buf))
+                assert n == 0 and len(pairs) == 0 and len(out) == 0
+            _check(st.wait(st.submit(*(_pin(a) for a in (p, s, e)), *buf)), ref)
+        det.status()
