@@ -153,7 +153,8 @@ BF16_OPS_TOL = 5e-3
 BF16_EXACT_TOL = 0.15
 
 
-@pytest.mark.parametrize("n,augment", [(48, False), (48, True), (200, True)])
+@pytest.mark.parametrize("n,augment", [(48, False), (48, True), (200, True), (5, False),
+                                       (129, True)])
 def test_bf16_gradient_matches_oracle(n, augment):
     from paper_2304_09439_b300 import Detector, Trainer
     dev = _dev()
