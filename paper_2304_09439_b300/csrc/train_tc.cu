@@ -422,44 +422,43 @@ __global__ void __launch_bounds__(128, (BN == 128 || XS == TG_B_H1) ? 4 : 5) tg_
   }
 }
 
-// dH2 of one pair (blockIdx.x), thread = (object o, column j): the column's
+// dH2 of one object (blockIdx.x = 2 p + o), thread = column j: the column's
 // 64 row sums accumulate in shared memory over the object's 256 channels
 // (each adds dF[c] W3[c, j] to its argmax row; a channel without gradient
-// adds 0 to row 0), then are masked by H2 > 0.
-constexpr int DH2_SMEM = 2 * KMAX * 128 * 4;
-__global__ void __launch_bounds__(256) sparse_dh2_kernel(const float* __restrict__ dF,
+// adds 0 to row 0), then are masked by H2 > 0.  One object per CTA (34 KB of
+// shared memory) lets about six CTAs share an SM, which hides the latency of
+// the W3 loads and of the read-modify-write chain.
+__global__ void __launch_bounds__(128) sparse_dh2_kernel(const float* __restrict__ dF,
                                                          const float* __restrict__ F,
                                                          const int32_t* __restrict__ amax,
                                                          const float* __restrict__ W3,
                                                          const float* __restrict__ H2,
                                                          float* __restrict__ dH2,
-                                                         float* __restrict__ gB2, int P) {
-  extern __shared__ float s_acc[];  // [2][KMAX][128]
-  __shared__ int s_k[512];
-  __shared__ float s_g[512];
-  float(*acc)[KMAX][128] = reinterpret_cast<float(*)[KMAX][128]>(s_acc);
-  const int p = blockIdx.x, tid = threadIdx.x, o = tid >> 7, j = tid & 127;
-  if (p >= P) return;
+                                                         float* __restrict__ gB2, int n_obj) {
+  __shared__ float acc[KMAX][128];
+  __shared__ int s_k[FEAT];
+  __shared__ float s_g[FEAT];
+  const int ob = blockIdx.x, j = threadIdx.x;
+  if (ob >= n_obj) return;
+  const int p = ob >> 1, o = ob & 1;
   const size_t row0 = (size_t)p * ROWS + o * KMAX;
-  for (int i = tid; i < 512; i += 256) {
-    const size_t f = (size_t)p * 512 + i;
+  for (int c = j; c < FEAT; c += 128) {
+    const size_t f = (size_t)p * 512 + o * FEAT + c;
     const int k = amax[f];
     const bool on = k >= 0 && F[f] > 0.f;
-    s_k[i] = on ? k : 0;
-    s_g[i] = on ? dF[f] : 0.f;
+    s_k[c] = on ? k : 0;
+    s_g[c] = on ? dF[f] : 0.f;
   }
-  for (int k = 0; k < KMAX; ++k) acc[o][k][j] = 0.f;
+  for (int k = 0; k < KMAX; ++k) acc[k][j] = 0.f;
   __syncthreads();
-  const int* sk = s_k + o * FEAT;
-  const float* sg = s_g + o * FEAT;
 #pragma unroll 16
   for (int c = 0; c < FEAT; ++c)
-    acc[o][sk[c]][j] = fmaf(sg[c], __ldg(W3 + (size_t)c * 128 + j), acc[o][sk[c]][j]);
+    acc[s_k[c]][j] = fmaf(s_g[c], __ldg(W3 + (size_t)c * 128 + j), acc[s_k[c]][j]);
   float col = 0.f;
 #pragma unroll 16
   for (int k = 0; k < KMAX; ++k) {
     const size_t e = (row0 + k) * 128 + j;
-    const float v = H2[e] > 0.f ? acc[o][k][j] : 0.f;
+    const float v = H2[e] > 0.f ? acc[k][j] : 0.f;
     dH2[e] = v;
     col += v;
   }
@@ -621,7 +620,7 @@ cudaError_t sparse_layer3_backward(const float* dF, const float* F, const int32_
                                    const float* W3, const float* H2, int P, float* dH2, float* gW3,
                                    float* gB3, float* gB2, int n_sm, cudaStream_t s) {
   if (P <= 0) return cudaSuccess;
-  sparse_dh2_kernel<<<P, 256, DH2_SMEM, s>>>(dF, F, amax, W3, H2, dH2, gB2, P);
+  sparse_dh2_kernel<<<2 * P, 128, 0, s>>>(dF, F, amax, W3, H2, dH2, gB2, 2 * P);
   const int n_obj = 2 * P;
   // about 8 x n_sm CTAs over 16 channel blocks; whole 16-object chunks
   const int want = std::max(1, (8 * n_sm) / (FEAT / GW3_CB));
@@ -647,7 +646,6 @@ cudaError_t prepare_train_tc_kernels() {
   set((const void*)tg_kernel<false, false, 64, TG_L1GRAD, TG_MEM>, tg_smem_bytes(64));
   set((const void*)tg_kernel<false, true, 128, TG_STORE, TG_A_H1>, tg_smem_bytes(128));
   set((const void*)tg_kernel<true, false, 64, TG_STORE, TG_B_H1>, tg_smem_bytes(64));
-  set((const void*)sparse_dh2_kernel, DH2_SMEM);
   return e;
 }
 
