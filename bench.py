@@ -566,6 +566,8 @@ def main():
                     help="requests admitted at once (sharing the launches)")
     ap.add_argument("--no-voxel", action="store_true", help="skip the voxel-latent variant leg")
     ap.add_argument("--no-train", action="store_true", help="skip the training-throughput leg")
+    ap.add_argument("--e2e-depth", type=int, default=2,
+                    help="steps in flight in the end-to-end leg (pipelined stepper, 1-4)")
     ap.add_argument("--train-only", action="store_true",
                     help="run only the training leg and print its JSON (profiler captures)")
     ap.add_argument("--train-batches", default="1024,8192",
@@ -721,7 +723,7 @@ def main():
         pr, out, n = det.step_host(poses, osh, env, MAX_PAIRS, pairs_out=h_pairs, out=h_out)
         sync_t += time.perf_counter() - t0
         sync_pairs += n
-    depth = 2
+    depth = args.e2e_depth
     bufs = [(_pinned_like(np.zeros((MAX_PAIRS, 2), np.int32)),
              _pinned_like(np.zeros((MAX_PAIRS, 8), np.float32))) for _ in range(depth)]
     max_obj = max(len(sc[0]) for sc in scenes)
@@ -845,7 +847,7 @@ def main():
                                                     if args.precision == "bf16" else None)},
             "e2e": {"value": e2e_pairs_all / e2e_max, "unit": "pairs/s",
                     "h2d_bytes_per_step": h2d // args.steps, "d2h_bytes_per_step": d2h // args.steps,
-                    "api": "locc_stepper (page-locked host arrays, 2 steps in flight)",
+                    "api": f"locc_stepper (page-locked host arrays, {args.e2e_depth} steps in flight)",
                     "sync_call": {"api": "locc_step_host", "value": sync_pairs / sync_t,
                                   "unit": "pairs/s"}},
             "gpu_launches": launches_per_step * args.steps,
