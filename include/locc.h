@@ -332,7 +332,10 @@ typedef struct {
 } locc_train_config;
 
 /* Trainer for the handle's network; parameters start from the handle's
- * current weights.  max_batch: largest n_pairs of a step.  Blocking. */
+ * current weights.  max_batch: largest n_pairs of a step.  Blocking.  The
+ * first LOCC_FP32 step also allocates that pass's own activation buffers
+ * (about 192 KB per pair of max_batch) and waits for the allocation; a
+ * trainer that only runs LOCC_BF16 steps never holds them. */
 int locc_trainer_create(locc_handle *h, int32_t max_batch,
                         const locc_train_config *cfg, locc_trainer **out);
 

@@ -424,6 +424,20 @@ void trainer_free(locc_trainer* t) {
 // Forward, loss and backward of one batch in float32 SIMT (gradients into
 // t->grad, which the caller zeroed).
 int fp32_pass(locc_trainer* t, cudaStream_t s) {
+  if (!t->Z3) {
+    // H1, Z3 (dZ3) and dH1 only exist for this pass: allocated at its first
+    // step, for max_batch pairs (the BF16 pass keeps none of them)
+    const size_t Mx = (size_t)t->max_batch * ROWS;
+    if (cudaMalloc(&t->H1, Mx * 64 * 4) != cudaSuccess || cudaMalloc(&t->Z3, Mx * 256 * 4) != cudaSuccess ||
+        cudaMalloc(&t->dH1, Mx * 64 * 4) != cudaSuccess) {
+      cudaGetLastError();
+      cudaFree(t->H1);
+      cudaFree(t->Z3);
+      cudaFree(t->dH1);
+      t->H1 = t->Z3 = t->dH1 = nullptr;
+      return tfail(LOCC_ERR_OOM, "cannot allocate the float32 training buffers");
+    }
+  }
   const int P = t->batch, M = P * ROWS;
   const float* prm = t->params;
   auto W = [&](int l) { return prm + PARAM_OFF_W[l]; };
@@ -547,14 +561,14 @@ int locc_trainer_create(locc_handle* h, int32_t max_batch, const locc_train_conf
             cudaMalloc(&t->xyz, M * 16) == cudaSuccess && cudaMalloc(&t->cnt, P * 8) == cudaSuccess &&
             cudaMalloc(&t->defer, (2 + 2 * P) * sizeof(int)) == cudaSuccess &&
             cudaMalloc(&t->centre, P * 16) == cudaSuccess && cudaMalloc(&t->X, M * 16) == cudaSuccess &&
-            cudaMalloc(&t->T, P * 32) == cudaSuccess && cudaMalloc(&t->H1, M * 64 * 4) == cudaSuccess &&
+            cudaMalloc(&t->T, P * 32) == cudaSuccess &&
             cudaMalloc(&t->H2, M * 128 * 4) == cudaSuccess &&
-            cudaMalloc(&t->Z3, M * 256 * 4) == cudaSuccess && cudaMalloc(&t->F, P * 512 * 4) == cudaSuccess &&
+            cudaMalloc(&t->F, P * 512 * 4) == cudaSuccess &&
             cudaMalloc(&t->amax, P * 512 * 4) == cudaSuccess && cudaMalloc(&t->G1, P * 256 * 4) == cudaSuccess &&
             cudaMalloc(&t->G2, P * 256 * 4) == cudaSuccess && cudaMalloc(&t->Y, P * 32) == cudaSuccess &&
             cudaMalloc(&t->dY, P * 32) == cudaSuccess && cudaMalloc(&t->dG1, P * 256 * 4) == cudaSuccess &&
             cudaMalloc(&t->dG2, P * 256 * 4) == cudaSuccess && cudaMalloc(&t->dF, P * 512 * 4) == cudaSuccess &&
-            cudaMalloc(&t->dH1, M * 64 * 4) == cudaSuccess && cudaMalloc(&t->dH2, M * 128 * 4) == cudaSuccess &&
+            cudaMalloc(&t->dH2, M * 128 * 4) == cudaSuccess &&
             cudaMalloc(&t->loss, 4) == cudaSuccess;
   if (ok) {
     // parameters start from the handle's float32 weights (W^T layout there)
