@@ -253,16 +253,34 @@ def main():
         first, best, hist = load_checkpoint(args.resume, tr, rng, report, dev)
     else:
         run_eval(0)
+    # batches go to the device from page-locked buffers without blocking, so
+    # the host draws batch k + 1 while the GPU runs step k; each of the
+    # NBUF buffers is reused only once its copy has run (same draws, in the
+    # same order, as a blocking copy)
+    NBUF = 3
+    h_objs = [torch.empty(2 * B, dtype=torch.int64).pin_memory() for _ in range(NBUF)]
+    h_idx = [torch.empty(B, dtype=torch.int64).pin_memory() for _ in range(NBUF)]
+    h_rot = [torch.empty((B, 9), dtype=torch.float32).pin_memory() for _ in range(NBUF)]
+    copied = [None] * NBUF
+    pairs = torch.arange(2 * B, dtype=torch.int32, device=dev).view(B, 2)
     t0 = time.time()
     for step in range(first, args.steps + 1):
         tr.set_lr(tr_lr(args, step))
+        k = step % NBUF
+        if copied[k] is not None:
+            copied[k].synchronize()
         idx = rng.integers(0, P, B)
-        objs = np.stack([2 * idx, 2 * idx + 1], 1).ravel()
-        bp = d_poses[torch.from_numpy(objs).to(dev)]
-        bs = d_shape[torch.from_numpy(objs).to(dev)]
-        pairs = torch.arange(2 * B, dtype=torch.int32, device=dev).view(B, 2)
-        bt = d_tgt[torch.from_numpy(idx).to(dev)]
-        rot = torch.from_numpy(random_rotations(B, rng)).to(dev)
+        h_idx[k].numpy()[:] = idx
+        h_objs[k].numpy()[:] = np.stack([2 * idx, 2 * idx + 1], 1).ravel()
+        h_rot[k].numpy()[:] = random_rotations(B, rng)
+        d_objs = h_objs[k].to(dev, non_blocking=True)
+        d_idx = h_idx[k].to(dev, non_blocking=True)
+        rot = h_rot[k].to(dev, non_blocking=True)
+        copied[k] = torch.cuda.Event()
+        copied[k].record()
+        bp = d_poses[d_objs]
+        bs = d_shape[d_objs]
+        bt = d_tgt[d_idx]
         tr.step(bp.contiguous(), bs.contiguous(), pairs, bt.contiguous(), rot, True, loss)
         if step % 200 == 0:
             hist.append((step, float(loss.item())))
